@@ -1,0 +1,402 @@
+"""Benchmark: even-odd CG solve to a 1e-10 true residual on a 32^3x64 lattice.
+
+One step is one full solve of M x = b, M = m^2 - D_eo D_oe, m = 0.02, on
+synthetic eps = 0.3 SU(3) fat links with their three-link products (every
+row of the hot path: two Dslash per iteration, the fused M epilogue and dot
+products, the fused vector updates, the device-side stopping test and the
+final true residual).  Inputs are resident in HBM when the timed region
+starts; they are larger than L2 (the links alone are 2.4 GB), so no flush is
+needed between steps.
+
+value  = algorithmic GB/s sustained over the solve
+         (iterations * bytes per iteration / solve time),
+plus the Dslash kernel's own GB/s (algorithmic bytes per launch / launch time
+from CUDA events on the lattice stream) in "roofline", the solve time in
+"cg", the end-to-end rate through the C ABI with host buffers in "e2e", and
+the CPU oracle on a bounded sample in "cpu_baseline".
+
+--impl reference runs the CPU oracle (the reference arm of this project) on
+the host cores instead.  N > 1 (torchrun) runs one independent solve per rank
+per step (different sources; no data-path collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+DIMS = (32, 32, 32, 64)
+MASS = 0.02
+TOL = 1e-10
+EPS = 0.3
+SEED_LINKS = 1001
+SEED_SOURCE = 1101
+METRIC = "Dslash GB/s (% HBM peak) & CG time-to-1e-10 residual, mixed/learned vs FP64"
+DSLASH_SOURCES = ["common.cuh", "fields.cuh", "dslash.cuh", "kernels_dslash.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="df64", choices=["df64", "f64"])
+    ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,32")
+    ap.add_argument("--dslash-launches", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dslash_source_hash() -> str:
+    h = hashlib.sha256()
+    for n in DSLASH_SOURCES:
+        with open(os.path.join(ROOT, "paper_1411_2087_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec: str, dims):
+    """DRAM bytes per Dslash launch from the committed ncu summary, if it was
+    taken on the current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and ":" in line:
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    key = f"bytes_per_site_{prec}"
+    if rec.get("source_hash") != dslash_source_hash() or key not in rec:
+        return None
+    return float(rec[key]) * (int(np.prod(dims)) // 2)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.tmp is None:
+            return None
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(dims, device, rank):
+    import torch
+    from paper_1411_2087_gb300 import synth
+    U = synth.su3_field(dims, EPS, SEED_LINKS, device=device)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, SEED_SOURCE + rank)
+    return U, b
+
+
+def cg_bytes_per_iter_site(prec):
+    from paper_1411_2087_gb300 import metrics
+    return metrics.cg_bytes_per_iteration_per_site(8)
+
+
+def run_native(args):
+    import torch
+    from paper_1411_2087_gb300 import metrics, stag
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        pg = dist
+    dims = tuple(int(v) for v in args.dims.split(",")) if args.dims else DIMS
+    Vh = int(np.prod(dims)) // 2
+    prec = args.prec
+
+    U, b_host = make_inputs(dims, dev, rank)
+    torch.cuda.synchronize()
+    # all library work goes to this stream; CUDA events are recorded on it
+    stream = torch.cuda.Stream(dev)
+    lat = stag.Lattice(dims, device=local, stream=stream.cuda_stream)
+    lat.upload_gauge(U, None, precisions=(prec,))
+    del U
+    torch.cuda.empty_cache()
+    b_pinned = b_host.pin_memory()
+    x_pinned = torch.empty_like(b_pinned).pin_memory()
+    fb = lat.field(stag.EVEN, prec, b_pinned)
+    fx = lat.field(stag.EVEN, prec)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    # warm-up (also builds the solve graph)
+    for _ in range(args.warmup):
+        info = lat.cg(fx, fb, MASS, TOL, 20000)
+    assert info["return"] == stag.OK, info
+
+    # ---- timed: device-resident solves
+    iters = []
+    solve_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            info = lat.cg(fx, fb, MASS, TOL, 20000)
+            iters.append(info["iters"])
+            solve_ms.append(info["seconds"] * 1e3)
+            assert info["return"] == stag.OK, info
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        # ---- Dslash launches alone, CUDA events on the lattice stream
+        fo = lat.field(stag.ODD, prec)
+        fo2 = lat.field(stag.EVEN, prec)
+        for _ in range(10):
+            lat.dslash(fo, fb)
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for k in range(args.dslash_launches):
+            if k % 2 == 0:
+                lat.dslash(fo, fb)
+            else:
+                lat.dslash(fo2, fo)
+        d1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    total_ms = e0.elapsed_time(e1)
+    dslash_ms = d0.elapsed_time(d1) / args.dslash_launches
+
+    # ---- end to end through the C ABI with host buffers
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        fb.import_(b_pinned)              # host -> device
+        info = lat.cg(fx, fb, MASS, TOL, 20000)
+        fx.export(x_pinned)               # device -> host
+        e2e_iters += info["iters"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+
+    # ---- aggregate over ranks (max time, sum of work)
+    bpi = cg_bytes_per_iter_site(prec) * Vh
+    work_bytes = sum(iters) * bpi
+    e2e_bytes = e2e_iters * bpi
+    vals = torch.tensor([total_ms, e2e_s, work_bytes, e2e_bytes, dslash_ms], dtype=torch.float64)
+    if pg is not None:
+        mx = vals.clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        sm = vals.clone()
+        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
+        total_ms, e2e_s, dslash_ms = mx[0].item(), mx[1].item(), mx[4].item()
+        work_bytes, e2e_bytes = sm[2].item(), sm[3].item()
+    value = work_bytes / (total_ms * 1e-3) / 1e9
+    e2e_value = e2e_bytes / e2e_s / 1e9
+
+    peak, peak_kind = measured_peak()
+    alg_dslash = metrics.dslash_bytes_per_site(8) * Vh
+    achieved = alg_dslash / (dslash_ms * 1e-3) / 1e9
+    launches_per_solve = [4 * k + 3 for k in iters]
+    gpu_launches = sum(launches_per_solve) + args.dslash_launches
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(dims, rank)
+
+    lat.close()
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "df64" if prec == "df64" else "f64",
+        "data": "synthetic (seeded SU(3) links eps=0.3, three-link products, Gaussian source)",
+        "config": {
+            "workload": f"even-odd CG to 1e-10 true residual, {'x'.join(map(str, dims))} lattice, m={MASS}",
+            "lattice": list(dims), "mass": MASS, "tol": TOL, "eps": EPS,
+            "prec": prec, "global_batch": world, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (links 2.4 GB), no flush",
+            "step": "one CG solve (init, iterations, true residual)",
+        },
+        "cg": {"iters": iters[0], "seconds_per_solve": round(statistics.median(solve_ms) * 1e-3, 4),
+               "true_rel_resid": info["true_rel_resid"], "gflops": round(info["gflops"], 1)},
+        "dslash": {"gbs": round(achieved, 1), "pct_hbm": round(100 * achieved / peak, 1),
+                   "gflops": round(1146 * Vh / (dslash_ms * 1e-3) / 1e9, 1),
+                   "us_per_launch": round(dslash_ms * 1e3, 2)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": ncu_traffic(prec, dims),
+                     "kernel": f"dslash_kernel<{prec}, EPI_NONE, 128>",
+                     "peak_source": peak_kind},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
+                "h2d_bytes_per_step": Vh * 48, "d2h_bytes_per_step": Vh * 48},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    return line
+
+
+class OracleWorkload:
+    """The bench workload on the host, for the CPU oracle."""
+
+    def __init__(self, dims, rank):
+        import oracle
+        from paper_1411_2087_gb300 import synth
+        self.oracle = oracle
+        self.dims = dims
+        self.U = synth.su3_field(dims, EPS, SEED_LINKS).numpy()
+        self.N = oracle.long_links(dims, self.U)
+        Vh = int(np.prod(dims)) // 2
+        self.b = synth.gaussian_colour_field(Vh, SEED_SOURCE + rank).numpy()
+
+    def run(self, n_iter):
+        """Time `n_iter` CG iterations (plus the final true-residual check)."""
+        t0 = time.perf_counter()
+        x, info = self.oracle.cg(self.dims, self.U, self.N, MASS, self.b, tol=TOL, max_iter=n_iter)
+        return info["iters"], time.perf_counter() - t0, self.oracle.num_threads()
+
+
+def cpu_baseline(dims, rank, n_iter=10):
+    Vh = int(np.prod(dims)) // 2
+    it, dt, cores = OracleWorkload(dims, rank).run(n_iter)
+    gbs = it * cg_bytes_per_iter_site("f64") * Vh / dt / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{it} CG iterations of the FP64 oracle on the same {'x'.join(map(str, dims))} "
+                      f"workload ({dt:.1f} s incl. the final true-residual check), "
+                      f"rate = iterations * bytes/iteration / time"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    dims = tuple(int(v) for v in args.dims.split(",")) if args.dims else DIMS
+    Vh = int(np.prod(dims)) // 2
+    wl = OracleWorkload(dims, 0)
+    for _ in range(args.warmup):
+        wl.run(1)
+    times, its = [], []
+    cores = 1
+    for _ in range(args.steps):
+        it, dt, cores = wl.run(3)
+        times.append(dt)
+        its.append(it)
+    bpi = cg_bytes_per_iter_site("f64") * Vh
+    value = sum(its) * bpi / sum(times) / 1e9
+    return {
+        "impl": "reference",
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / len(times), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SU(3) links eps=0.3, three-link products, Gaussian source)",
+        "config": {"workload": f"even-odd CG to 1e-10 true residual, {'x'.join(map(str, dims))} "
+                               f"lattice, m={MASS}", "lattice": list(dims), "mass": MASS,
+                   "tol": TOL, "eps": EPS, "prec": "f64"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": "each step: 3 CG iterations of the FP64 CPU oracle on the "
+                                   "same workload (plus its final true-residual check)"},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_native(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

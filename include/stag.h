@@ -1,0 +1,180 @@
+/*
+ * stag.h — C ABI of the GB300 improved-staggered (Naik) Dslash and even-odd
+ * conjugate-gradient library.
+ *
+ * The operation is the one Li & Gottlieb benchmark ("Staggered Dslash
+ * Performance on Intel Xeon Phi Architecture", Lattice 2014, Sec. 3): for every
+ * site of one checkerboard, 16 SU(3) matrix x colour-vector products over the
+ * 8 forward/backward directions, with the one-link (fat) and three-link (Naik,
+ * long) matrices, summed into one colour vector; and the CG solver that calls
+ * it twice per iteration.  Written out:
+ *
+ *   (D psi)(x) = sum_mu eta_mu(x) { c1 [ b U_mu(x) psi(x+mu)  - b U_mu(x-mu)^+ psi(x-mu)  ]
+ *                                 + c3 [ b N_mu(x) psi(x+3mu) - b N_mu(x-3mu)^+ psi(x-3mu) ] }
+ *
+ *   eta_mu(x) = (-1)^(x_0+...+x_{mu-1})   Kogut-Susskind phases (Sec. 4: "absorbed
+ *                                          into the gauge fields")
+ *   b = bc_mu^w, w = number of times the hop wraps around direction mu
+ *   M = m^2 - D_eo D_oe on the even checkerboard (no factor 1/2 in D; MILC's
+ *       4m^2 - D D convention is this one with m_MILC = m/2).
+ *
+ * Conventions shared by every call:
+ *   - dims[4] = {Lx, Ly, Lz, Lt}; every extent even and >= 2; V = product,
+ *     Vh = V/2 sites per parity.  Site i = x + Lx*(y + Ly*(z + Lz*t));
+ *     parity (x+y+z+t) & 1 (0 = even).
+ *   - A gauge field in canonical layout is complex128 [4][V][3][3] (direction,
+ *     site, row, column; (re, im) interleaved doubles).
+ *   - A colour field on one parity in canonical layout is complex128 [Vh][3],
+ *     site i of that parity at position i/2 ("checkerboard order").
+ *   - Host pointers (STAG_PTR_HOST) are ordinary host memory (pinned memory
+ *     makes copies faster); device pointers (STAG_PTR_DEVICE) must be device
+ *     memory of the lattice's device.  The caller keeps ownership of every
+ *     buffer it passes; the library copies what it needs before returning
+ *     (or, for asynchronous calls on device pointers, before the work it
+ *     enqueued completes).
+ *   - Every function returns STAG_OK (0) or a negative STAG_ERR_* code; no
+ *     exception crosses the ABI.  stag_last_error_message() gives a
+ *     human-readable reason for the last failure on the calling thread.
+ *   - Work is enqueued on the lattice's CUDA stream.  Dslash calls are
+ *     asynchronous; field import/export and the solvers return after their
+ *     work is complete.  One lattice must not be used by two host threads at
+ *     the same time.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    STAG_OK = 0,
+    STAG_ERR_ARG = -1,           /* null pointer, bad dims, size or enum value          */
+    STAG_ERR_STATE = -2,         /* no gauge field uploaded, parity/precision mismatch  */
+    STAG_ERR_CUDA = -3,          /* a CUDA call failed (message has the CUDA error)     */
+    STAG_ERR_NOT_CONVERGED = -4, /* solver hit max_iter; x holds the last iterate       */
+    STAG_ERR_BREAKDOWN = -5,     /* <p, M p> not positive or not finite                 */
+    STAG_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up                  */
+    STAG_ERR_NOMEM = -7          /* device or host allocation failed                    */
+};
+
+/* ---- precisions ---------------------------------------------------------
+ * STAG_F64   IEEE double storage and double arithmetic.
+ * STAG_DF64  "double-float": each real stored as a pair of floats (hi, lo)
+ *            with hi + lo the value (about 48 significant bits, float
+ *            exponent range); arithmetic in error-free float operations.
+ *            GB300's FP64 pipe is far narrower than its FP32 pipes, and this
+ *            form keeps FP64-level accuracy at FP32 throughput.
+ * STAG_F32   float storage and arithmetic.
+ * STAG_F16   half storage of links and vectors (vectors with one float norm
+ *            per site), float arithmetic.
+ */
+enum { STAG_F64 = 0, STAG_F32 = 1, STAG_F16 = 2, STAG_DF64 = 3 };
+#define STAG_PREC_BIT(p) (1u << (p))
+
+enum { STAG_EVEN = 0, STAG_ODD = 1 };
+enum { STAG_PTR_HOST = 0, STAG_PTR_DEVICE = 1 };
+
+typedef struct stag_lattice_s *stag_lattice;
+typedef struct stag_field_s *stag_field;
+
+/* ---- lattice ------------------------------------------------------------ */
+
+/* Create a lattice on CUDA device `device`.
+ * dims: {Lx, Ly, Lz, Lt}, each even and >= 2, V <= 2^31 - 2.
+ * bc:   boundary sign per direction, each +1 (periodic) or -1 (antiperiodic);
+ *       NULL means {+1, +1, +1, -1}.
+ * cuda_stream: a cudaStream_t of that device to enqueue all work on, or NULL
+ *       for a stream owned by the lattice.
+ * Errors: STAG_ERR_ARG (argument checks run before any CUDA call),
+ *         STAG_ERR_CUDA, STAG_ERR_NOMEM. */
+int stag_lattice_create(stag_lattice *out, const int dims[4], const double bc[4],
+                        int device, void *cuda_stream);
+
+/* Free every device buffer the lattice owns.  Fields created on the lattice
+ * must be destroyed first (STAG_ERR_STATE otherwise). NULL is accepted. */
+int stag_lattice_destroy(stag_lattice lat);
+
+/* Sizes: V, Vh.  Pure host queries. */
+int stag_lattice_volume(const stag_lattice lat, long long *V, long long *Vh);
+
+/* ---- gauge field ---------------------------------------------------------
+ * Upload the fat (one-link) field and the long (three-link, Naik) field,
+ * both canonical complex128 [4][V][3][3], with Naik coefficients c1 (one-link)
+ * and c3 (three-link), e.g. 9/8 and -1/24.  lng == NULL builds the long links
+ * on the GPU as the three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+ * of the raw fat links (Sec. 4 "three-link products").
+ * The library folds c1, c3, the Kogut-Susskind phases and the boundary signs
+ * into its own copies and re-lays them out per parity (structure of arrays).
+ * prec_mask: OR of STAG_PREC_BIT(p) for each precision to build a copy for
+ *            (0 means F64 | DF64).  A later upload replaces all copies.
+ * Blocks until the copies are built. */
+int stag_gauge_upload(stag_lattice lat, const double *fat, const double *lng,
+                      double c1, double c3, int ptr_kind, unsigned prec_mask);
+
+/* Compute the three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+ * (Sec. 4 "three-link products") of the raw fat links `fat` on the GPU and
+ * write them to `lng`, both canonical complex128 [4][V][3][3] (periodic
+ * indexing, no coefficient, phase or boundary sign).  FP64 arithmetic.
+ * Blocks until `lng` is written.  Does not change the uploaded gauge field. */
+int stag_long_links_build(stag_lattice lat, const double *fat, double *lng, int ptr_kind);
+
+/* ---- colour fields (one parity, internal layout, owned by the library) -- */
+int stag_field_create(stag_lattice lat, int parity, int prec, stag_field *out);
+int stag_field_destroy(stag_field f);
+/* Import/export canonical complex128 [Vh][3]; blocks until complete. */
+int stag_field_import(stag_field f, const double *src, int ptr_kind);
+int stag_field_export(const stag_field f, double *dst, int ptr_kind);
+/* Set a field to zero (asynchronous). */
+int stag_field_zero(stag_field f);
+/* Device address and size in bytes of the field's internal storage (for
+ * zero-copy views; layout is internal). */
+int stag_field_storage(const stag_field f, void **dev_ptr, unsigned long long *bytes);
+
+/* ---- Dslash --------------------------------------------------------------
+ * out = D_eo in  (out even, in odd)    stag_dslash_eo
+ * out = D_oe in  (out odd,  in even)   stag_dslash_oe
+ * Both fields must have the same precision, and a gauge copy of that
+ * precision must have been uploaded.  Asynchronous on the lattice stream. */
+int stag_dslash_eo(stag_lattice lat, stag_field out_even, const stag_field in_odd);
+int stag_dslash_oe(stag_lattice lat, stag_field out_odd, const stag_field in_even);
+
+/* out = M in = m^2 in - D_eo D_oe in, both even.  Asynchronous. */
+int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_field in_even,
+                 double mass);
+
+/* ---- solvers ------------------------------------------------------------- */
+typedef struct {
+    int iters;             /* CG iterations performed                          */
+    int status;            /* STAG_OK, STAG_ERR_NOT_CONVERGED or _BREAKDOWN    */
+    double true_rel_resid; /* |b - M x| / |b| recomputed at exit in the        */
+                           /* solve's outer precision (FP64 or DF64)           */
+    double iter_rel_resid; /* sqrt(|r|^2 / |b|^2) of the recursive residual     */
+    double seconds;        /* wall time of the solve on the device             */
+    double gflops;         /* model flops / seconds                            */
+    double gbs;            /* model bytes / seconds                            */
+    int restarts;          /* reliable updates (mixed precision) or 0          */
+    int reserved;
+} stag_solve_info;
+
+/* Solve M x = b by conjugate gradient from x0 = 0 (Hestenes-Stiefel),
+ * stopping when |r| <= rel_tol |b| or after max_iter iterations.  x and b are
+ * even fields of the same precision (F64 or DF64), mass > 0.  The iteration
+ * runs as one CUDA graph with a device-side loop condition; the host waits
+ * once, at the end.  Returns STAG_OK, STAG_ERR_NOT_CONVERGED (x holds the last
+ * iterate) or STAG_ERR_BREAKDOWN; info (may be NULL) is filled in all cases. */
+int stag_cg_solve(stag_lattice lat, stag_field x_even, const stag_field b_even,
+                  double mass, double rel_tol, int max_iter, stag_solve_info *info);
+
+/* ---- errors -------------------------------------------------------------- */
+const char *stag_strerror(int status);
+const char *stag_last_error_message(void);
+
+/* Library version, e.g. "0.1.0". */
+const char *stag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAG_H */

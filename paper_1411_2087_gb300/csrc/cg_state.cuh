@@ -1,0 +1,52 @@
+// Device-resident scalars of one CG solve.  The kernels of the iteration read
+// and write them directly, so the host is not involved until the solve ends.
+#pragma once
+#include "common.cuh"
+
+namespace stag {
+
+// A scalar kept both as a double and as its double-float split, so that
+// kernels of every precision can read it without FP64 conversions.
+struct dpair {
+    double d;
+    float hi, lo;
+};
+
+STAG_HD dpair make_dpair(double v) {
+    dpair p;
+    p.d = v;
+    p.hi = (float)v;
+    p.lo = (float)(v - (double)p.hi);
+    return p;
+}
+
+template <class R> STAG_D R scalar_as(const dpair &p);
+template <> STAG_D double scalar_as<double>(const dpair &p) { return p.d; }
+template <> STAG_D float scalar_as<float>(const dpair &p) { return p.hi; }
+template <> STAG_D df scalar_as<df>(const dpair &p) { return df_make(p.hi, p.lo); }
+
+enum CgStatus { CG_RUNNING = 0, CG_CONVERGED = 1, CG_MAXITER = 2, CG_BREAKDOWN = 3 };
+
+struct CgScalars {
+    // inputs, set by the host before each solve
+    dpair m2;        // mass^2
+    double tol2;     // rel_tol^2
+    int max_iter;
+    int pad0;
+    // state
+    double bb;       // |b|^2
+    double rr;       // |r_k|^2
+    double rr_stop;  // tol^2 |b|^2
+    double pAp;      // <p, M p>
+    double true_rr;  // |b - M x|^2 at exit
+    dpair alpha, beta;
+    int iter;
+    int status;      // CgStatus
+    unsigned ticket; // grid-reduction ticket, zero between kernels
+    unsigned pad1;
+    cudaGraphConditionalHandle cond;  // loop condition of the solve graph
+    int has_cond;
+    int pad2;
+};
+
+}  // namespace stag

@@ -1,0 +1,38 @@
+// Host-side launchers of the libstag kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include "cg_state.cuh"
+#include "common.cuh"
+
+namespace stag {
+
+struct DslashArgs;
+
+// Dslash with epilogue `epi` (Epi enum) in precision `prec`; block = 0 picks
+// the default block size.
+cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, int block, cudaStream_t s);
+int dslash_default_block(int prec);
+int dslash_grid(const Geom &g, int block);
+
+// CG vector kernels (grid = ceil(Vh / CG_BLOCK))
+constexpr int CG_BLOCK = 256;
+cudaError_t launch_cg_init(int prec, const Geom &g, void *x, void *r, void *p, const void *b,
+                           double *partial, CgScalars *sc, cudaStream_t s);
+cudaError_t launch_cg_update(int prec, const Geom &g, void *x, void *r, const void *p,
+                             const void *Ap, double *partial, CgScalars *sc, cudaStream_t s);
+cudaError_t launch_cg_p_update(int prec, const Geom &g, const void *r, void *p,
+                               const CgScalars *sc, cudaStream_t s);
+
+// canonical complex128 [Vh][3] (device) <-> internal field layout
+cudaError_t launch_import(int prec, const Geom &g, const double *canon, void *field, cudaStream_t s);
+cudaError_t launch_export(int prec, const Geom &g, const void *field, double *canon, cudaStream_t s);
+
+// fold c1/c3, Kogut-Susskind phases and boundary signs into the canonical
+// fat/long links (device, complex128 [4][V][3][3]) and lay them out per parity
+cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], double c1, double c3,
+                              const double *fat, const double *lng, void *links, cudaStream_t s);
+
+// three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu), canonical layout
+cudaError_t launch_long_links(const Geom &g, const double *fat, double *lng, cudaStream_t s);
+
+}  // namespace stag

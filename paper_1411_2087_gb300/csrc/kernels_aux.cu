@@ -1,0 +1,345 @@
+// CG vector kernels, field import/export, link folding and the three-link
+// products.
+#include "dslash.cuh"
+#include "kernels.h"
+
+namespace stag {
+
+// --------------------------------------------------------------------------
+// CG vector kernels.  Each reads the device scalars written by the previous
+// kernel; the last block of a reducing kernel updates them and, inside the
+// solve graph, sets the loop condition.
+// --------------------------------------------------------------------------
+
+STAG_D void set_loop_condition(CgScalars *sc) {
+    if (sc->has_cond)
+        cudaGraphSetConditional(sc->cond, sc->status == CG_RUNNING ? 1u : 0u);
+}
+
+// x = 0, r = b, p = b, |b|^2
+template <int P, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+cg_init_kernel(Geom g, typename Fmt<P>::Elem *x, typename Fmt<P>::Elem *r,
+               typename Fmt<P>::Elem *p, const typename Fmt<P>::Elem *b, double *partial,
+               CgScalars *sc) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    __shared__ double smem[32];
+    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    double dot = 0.0;
+    if (c < g.Vh) {
+        cplx<R> bv[3], z[3];
+        load_vec<P>(b, g.stride, c, bv);
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            z[k] = czero<R>();
+        store_vec<P>(x, g.stride, c, z);
+        store_vec<P>(r, g.stride, c, bv);
+        store_vec<P>(p, g.stride, c, bv);
+        dot = re_dot3<R>(bv, bv);
+    }
+    double total;
+    if (grid_sum<BLOCK>(dot, partial, &sc->ticket, smem, total) && threadIdx.x == 0) {
+        sc->bb = total;
+        sc->rr = total;
+        sc->rr_stop = sc->tol2 * total;
+        sc->iter = 0;
+        sc->alpha = make_dpair(0.0);
+        sc->beta = make_dpair(0.0);
+        if (!(total < INFINITY))
+            sc->status = CG_BREAKDOWN;
+        else if (total <= sc->rr_stop)
+            sc->status = CG_CONVERGED;
+        else if (sc->max_iter <= 0)
+            sc->status = CG_MAXITER;
+        else
+            sc->status = CG_RUNNING;
+        set_loop_condition(sc);
+    }
+}
+
+// x += alpha p, r -= alpha Ap, |r|^2 -> beta, convergence
+template <int P, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+cg_update_kernel(Geom g, typename Fmt<P>::Elem *x, typename Fmt<P>::Elem *r,
+                 const typename Fmt<P>::Elem *p, const typename Fmt<P>::Elem *Ap,
+                 double *partial, CgScalars *sc) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    __shared__ double smem[32];
+    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    const bool run = sc->status == CG_RUNNING;
+    double dot = 0.0;
+    if (run && c < g.Vh) {
+        const R alpha = scalar_as<R>(sc->alpha);
+        const R malpha = -alpha;
+        cplx<R> xv[3], rv[3], pv[3], av[3];
+        load_vec<P>(x, g.stride, c, xv);
+        load_vec<P>(r, g.stride, c, rv);
+        load_vec<P>(p, g.stride, c, pv);
+        load_vec<P>(Ap, g.stride, c, av);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            mac(xv[k].re, alpha, pv[k].re);
+            mac(xv[k].im, alpha, pv[k].im);
+            mac(rv[k].re, malpha, av[k].re);
+            mac(rv[k].im, malpha, av[k].im);
+            xv[k].re = rnorm<R>(xv[k].re);
+            xv[k].im = rnorm<R>(xv[k].im);
+            rv[k].re = rnorm<R>(rv[k].re);
+            rv[k].im = rnorm<R>(rv[k].im);
+        }
+        store_vec<P>(x, g.stride, c, xv);
+        store_vec<P>(r, g.stride, c, rv);
+        dot = re_dot3<R>(rv, rv);
+    }
+    double total;
+    if (grid_sum<BLOCK>(dot, partial, &sc->ticket, smem, total) && threadIdx.x == 0) {
+        if (sc->status == CG_RUNNING) {
+            const double beta = total / sc->rr;
+            sc->beta = make_dpair(beta);
+            sc->rr = total;
+            sc->iter += 1;
+            if (!(total < INFINITY))
+                sc->status = CG_BREAKDOWN;
+            else if (total <= sc->rr_stop)
+                sc->status = CG_CONVERGED;
+            else if (sc->iter >= sc->max_iter)
+                sc->status = CG_MAXITER;
+        } else {
+            sc->beta = make_dpair(0.0);
+        }
+        set_loop_condition(sc);
+    }
+}
+
+// p = r + beta p
+template <int P, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+cg_p_kernel(Geom g, const typename Fmt<P>::Elem *r, typename Fmt<P>::Elem *p, const CgScalars *sc) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    if (c >= g.Vh)
+        return;
+    const R beta = scalar_as<R>(sc->beta);
+    cplx<R> rv[3], pv[3];
+    load_vec<P>(r, g.stride, c, rv);
+    load_vec<P>(p, g.stride, c, pv);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        mac(rv[k].re, beta, pv[k].re);
+        mac(rv[k].im, beta, pv[k].im);
+        rv[k].re = rnorm<R>(rv[k].re);
+        rv[k].im = rnorm<R>(rv[k].im);
+    }
+    store_vec<P>(p, g.stride, c, rv);
+}
+
+static int cg_grid(const Geom &g) { return (g.Vh + CG_BLOCK - 1) / CG_BLOCK; }
+
+#define STAG_PREC_SWITCH(prec, ...)                                   \
+    switch (prec) {                                                   \
+    case P_F64: { constexpr int P = P_F64; __VA_ARGS__; } break;      \
+    case P_DF64: { constexpr int P = P_DF64; __VA_ARGS__; } break;    \
+    case P_F32: { constexpr int P = P_F32; __VA_ARGS__; } break;      \
+    default: return cudaErrorInvalidValue;                            \
+    }
+
+cudaError_t launch_cg_init(int prec, const Geom &g, void *x, void *r, void *p, const void *b,
+                           double *partial, CgScalars *sc, cudaStream_t s) {
+    STAG_PREC_SWITCH(prec, {
+        using E = typename Fmt<P>::Elem;
+        cg_init_kernel<P, CG_BLOCK><<<cg_grid(g), CG_BLOCK, 0, s>>>(g, (E *)x, (E *)r, (E *)p,
+                                                                    (const E *)b, partial, sc);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(int prec, const Geom &g, void *x, void *r, const void *p,
+                             const void *Ap, double *partial, CgScalars *sc, cudaStream_t s) {
+    STAG_PREC_SWITCH(prec, {
+        using E = typename Fmt<P>::Elem;
+        cg_update_kernel<P, CG_BLOCK><<<cg_grid(g), CG_BLOCK, 0, s>>>(
+            g, (E *)x, (E *)r, (const E *)p, (const E *)Ap, partial, sc);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p_update(int prec, const Geom &g, const void *r, void *p,
+                               const CgScalars *sc, cudaStream_t s) {
+    STAG_PREC_SWITCH(prec, {
+        using E = typename Fmt<P>::Elem;
+        cg_p_kernel<P, CG_BLOCK><<<cg_grid(g), CG_BLOCK, 0, s>>>(g, (const E *)r, (E *)p, sc);
+    });
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// import / export between canonical complex128 [Vh][3] and the SoA layout
+// --------------------------------------------------------------------------
+template <int P>
+__global__ void import_kernel(Geom g, const double *__restrict__ canon, typename Fmt<P>::Elem *f) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.Vh)
+        return;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double re = canon[(3 * (size_t)c + a) * 2];
+        const double im = canon[(3 * (size_t)c + a) * 2 + 1];
+        f[a * g.stride + c] = Fmt<P>::from_double(re, im);
+    }
+}
+
+template <int P>
+__global__ void export_kernel(Geom g, const typename Fmt<P>::Elem *f, double *__restrict__ canon) {
+    using R = typename Fmt<P>::R;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.Vh)
+        return;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cplx<R> v = Fmt<P>::unpack(f[a * g.stride + c]);
+        canon[(3 * (size_t)c + a) * 2] = to_double<R>(v.re);
+        canon[(3 * (size_t)c + a) * 2 + 1] = to_double<R>(v.im);
+    }
+}
+
+cudaError_t launch_import(int prec, const Geom &g, const double *canon, void *field, cudaStream_t s) {
+    const int grid = (g.Vh + 255) / 256;
+    STAG_PREC_SWITCH(prec, {
+        import_kernel<P><<<grid, 256, 0, s>>>(g, canon, (typename Fmt<P>::Elem *)field);
+    });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(int prec, const Geom &g, const void *field, double *canon, cudaStream_t s) {
+    const int grid = (g.Vh + 255) / 256;
+    STAG_PREC_SWITCH(prec, {
+        export_kernel<P><<<grid, 256, 0, s>>>(g, (const typename Fmt<P>::Elem *)field, canon);
+    });
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// link folding: G[par][kind][j][cb] = coef * L[mu][i][j], kind = mu (+4 long)
+//   coef = c * eta_mu(x) * bc_mu^w,  w = floor((x_mu + s) / L_mu), s = 1 or 3
+// so that the stencil applies  + G(x) psi(x+s mu)  and  - G(x-s mu)^+ psi(x-s mu).
+// --------------------------------------------------------------------------
+struct FoldArgs {
+    Geom g;
+    double bc[4];
+    double c1, c3;
+};
+
+STAG_D void full_coords(const Geom &g, long long i, int x[4]) {
+    x[0] = (int)(i % g.L[0]);
+    i /= g.L[0];
+    x[1] = (int)(i % g.L[1]);
+    i /= g.L[1];
+    x[2] = (int)(i % g.L[2]);
+    x[3] = (int)(i / g.L[2]);
+}
+
+template <int P>
+__global__ void fold_kernel(FoldArgs fa, const double *__restrict__ fat, const double *__restrict__ lng,
+                            typename Fmt<P>::Elem *G) {
+    const Geom &g = fa.g;
+    const long long V = 2LL * g.Vh;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 8 * V)
+        return;
+    const int kind = (int)(t / V);
+    const long long i = t % V;
+    const int mu = kind & 3;
+    const bool three = kind >= 4;
+    int x[4];
+    full_coords(g, i, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const int cb = (int)(i >> 1);
+    int eta_sum = 0;
+    for (int nu = 0; nu < mu; nu++)
+        eta_sum += x[nu];
+    const int s = three ? 3 : 1;
+    const int wraps = (x[mu] + s) / g.L[mu];
+    double coef = three ? fa.c3 : fa.c1;
+    if (eta_sum & 1)
+        coef = -coef;
+    if ((wraps & 1) && fa.bc[mu] < 0)
+        coef = -coef;
+    const double *src = (three ? lng : fat) + ((size_t)mu * V + i) * 18;
+    typename Fmt<P>::Elem *dst = G + ((size_t)par * 8 + kind) * 9 * g.stride + cb;
+    for (int j = 0; j < 9; j++)
+        dst[(size_t)j * g.stride] = Fmt<P>::from_double(coef * src[2 * j], coef * src[2 * j + 1]);
+}
+
+cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], double c1, double c3,
+                              const double *fat, const double *lng, void *links, cudaStream_t s) {
+    FoldArgs fa;
+    fa.g = g;
+    for (int k = 0; k < 4; k++)
+        fa.bc[k] = bc[k];
+    fa.c1 = c1;
+    fa.c3 = c3;
+    const long long n = 16LL * g.Vh;
+    const int grid = (int)((n + 255) / 256);
+    STAG_PREC_SWITCH(prec, {
+        fold_kernel<P><<<grid, 256, 0, s>>>(fa, fat, lng, (typename Fmt<P>::Elem *)links);
+    });
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// three-link products (FP64): N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu)
+// --------------------------------------------------------------------------
+STAG_D void mat_mul_c(double2 C[9], const double2 A[9], const double2 B[9]) {
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) {
+            double re = 0.0, im = 0.0;
+            for (int k = 0; k < 3; k++) {
+                const double2 x = A[3 * a + k], y = B[3 * k + b];
+                re = fma(x.x, y.x, re);
+                re = fma(-x.y, y.y, re);
+                im = fma(x.x, y.y, im);
+                im = fma(x.y, y.x, im);
+            }
+            C[3 * a + b] = make_double2(re, im);
+        }
+}
+
+__global__ void long_links_kernel(Geom g, const double2 *__restrict__ U, double2 *__restrict__ N) {
+    const long long V = 2LL * g.Vh;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V)
+        return;
+    const int mu = (int)(t / V);
+    const long long i = t % V;
+    int x[4];
+    full_coords(g, i, x);
+    long long step = 1;
+    for (int nu = 0; nu < mu; nu++)
+        step *= g.L[nu];
+    const int L = g.L[mu];
+    const long long i1 = i + ((x[mu] + 1) % L - x[mu]) * step;
+    const long long i2 = i + ((x[mu] + 2) % L - x[mu]) * step;
+    double2 A[9], B[9], T[9];
+    for (int j = 0; j < 9; j++) {
+        A[j] = U[((size_t)mu * V + i) * 9 + j];
+        B[j] = U[((size_t)mu * V + i1) * 9 + j];
+    }
+    mat_mul_c(T, A, B);
+    for (int j = 0; j < 9; j++)
+        B[j] = U[((size_t)mu * V + i2) * 9 + j];
+    mat_mul_c(A, T, B);
+    for (int j = 0; j < 9; j++)
+        N[((size_t)mu * V + i) * 9 + j] = A[j];
+}
+
+cudaError_t launch_long_links(const Geom &g, const double *fat, double *lng, cudaStream_t s) {
+    const long long n = 8LL * g.Vh;
+    const int grid = (int)((n + 127) / 128);
+    long_links_kernel<<<grid, 128, 0, s>>>(g, (const double2 *)fat, (double2 *)lng);
+    return cudaGetLastError();
+}
+
+}  // namespace stag

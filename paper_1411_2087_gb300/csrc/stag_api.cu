@@ -1,0 +1,833 @@
+// libstag C ABI: handles, argument checking, memory, uploads and the CG
+// solve graph.  Declarations and documentation are in include/stag.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/stag.h"
+#include "dslash.cuh"
+#include "kernels.h"
+
+using namespace stag;
+
+// --------------------------------------------------------------------------
+// errors
+// --------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,  \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                         \
+    } while (0)
+
+#define STAG_TRY(call)           \
+    do {                         \
+        int s_ = (call);         \
+        if (s_ != STAG_OK)       \
+            return s_;           \
+    } while (0)
+
+// make `dev` current for the scope of one API call, then restore
+struct DeviceGuard {
+    int prev = -1;
+    int err = 0;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess)
+            prev = -1;
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
+            err = 1;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+            cudaSetDevice(prev);
+    }
+};
+
+#define DEVICE_SCOPE(dev)                                                        \
+    DeviceGuard guard_(dev);                                                     \
+    if (guard_.err)                                                              \
+        return fail(STAG_ERR_CUDA, "cannot make CUDA device %d current", (dev));
+
+static bool prec_valid(int p) { return p == STAG_F64 || p == STAG_DF64 || p == STAG_F32; }
+static const char *prec_name(int p) {
+    switch (p) {
+    case STAG_F64: return "F64";
+    case STAG_DF64: return "DF64";
+    case STAG_F32: return "F32";
+    case STAG_F16: return "F16";
+    default: return "?";
+    }
+}
+
+// --------------------------------------------------------------------------
+// handles
+// --------------------------------------------------------------------------
+struct CgWork {
+    int prec = -1;
+    void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *bw = nullptr, *xw = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+};
+
+struct stag_lattice_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int dims[4];
+    double bc[4];
+    long long V = 0, Vh = 0;
+    Geom geom;
+    void *links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision [2][8][9][stride]
+    bool has_gauge = false;
+    double c1 = 0, c3 = 0;
+    int live_fields = 0;
+    // reduction scratch and scalars
+    double *partial = nullptr;
+    CgScalars *sc = nullptr;
+    CgScalars *sc_host = nullptr;  // pinned mirror
+    CgWork cg[4];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double *staging = nullptr;  // canonical [Vh][3] complex128 for host import/export
+};
+
+struct stag_field_s {
+    stag_lattice lat = nullptr;
+    int parity = 0;
+    int prec = 0;
+    void *data = nullptr;
+    size_t bytes = 0;
+};
+
+static size_t field_bytes(const stag_lattice lat, int prec) {
+    return 3ull * lat->geom.stride * prec_elem_bytes(prec);
+}
+static size_t link_bytes(const stag_lattice lat, int prec) {
+    return 2ull * 8 * 9 * lat->geom.stride * prec_elem_bytes(prec);
+}
+static const void *links_of(const stag_lattice lat, int prec, int parity) {
+    const char *base = (const char *)lat->links[prec];
+    return base + (size_t)parity * 8 * 9 * lat->geom.stride * prec_elem_bytes(prec);
+}
+
+// --------------------------------------------------------------------------
+// lattice
+// --------------------------------------------------------------------------
+extern "C" int stag_lattice_create(stag_lattice *out, const int dims[4], const double bc[4],
+                                   int device, void *cuda_stream) {
+    if (!out)
+        return fail(STAG_ERR_ARG, "stag_lattice_create: out is NULL");
+    *out = nullptr;
+    if (!dims)
+        return fail(STAG_ERR_ARG, "stag_lattice_create: dims is NULL");
+    long long V = 1;
+    for (int k = 0; k < 4; k++) {
+        if (dims[k] < 2 || dims[k] % 2)
+            return fail(STAG_ERR_ARG, "stag_lattice_create: dims[%d] = %d must be even and >= 2", k,
+                        dims[k]);
+        V *= dims[k];
+        if (V > (1LL << 31) - 2)
+            return fail(STAG_ERR_ARG, "stag_lattice_create: volume too large");
+    }
+    double bcv[4] = {1.0, 1.0, 1.0, -1.0};
+    if (bc) {
+        for (int k = 0; k < 4; k++) {
+            if (bc[k] != 1.0 && bc[k] != -1.0)
+                return fail(STAG_ERR_ARG, "stag_lattice_create: bc[%d] = %g must be +1 or -1", k, bc[k]);
+            bcv[k] = bc[k];
+        }
+    }
+    if (device < 0)
+        return fail(STAG_ERR_ARG, "stag_lattice_create: device %d < 0", device);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(STAG_ERR_CUDA, "stag_lattice_create: no CUDA device available");
+    }
+    if (device >= ndev)
+        return fail(STAG_ERR_ARG, "stag_lattice_create: device %d >= device count %d", device, ndev);
+    // 72 component planes of one parity must be addressable with 32-bit offsets
+    const long long Vh = V / 2;
+    const long long stride = (Vh + 255) / 256 * 256;
+    if (72 * stride >= (1LL << 31))
+        return fail(STAG_ERR_ARG, "stag_lattice_create: volume too large for 32-bit link offsets");
+
+    DEVICE_SCOPE(device);
+    stag_lattice lat = new (std::nothrow) stag_lattice_s();
+    if (!lat)
+        return fail(STAG_ERR_NOMEM, "stag_lattice_create: host allocation failed");
+    lat->device = device;
+    for (int k = 0; k < 4; k++) {
+        lat->dims[k] = dims[k];
+        lat->bc[k] = bcv[k];
+    }
+    lat->V = V;
+    lat->Vh = Vh;
+    Geom &g = lat->geom;
+    for (int k = 0; k < 4; k++)
+        g.L[k] = dims[k];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (int)Vh;
+    g.stride = (int)stride;
+    g.plane[0] = 0;
+    g.plane[1] = dims[0] / 2;
+    g.plane[2] = dims[0] * dims[1] / 2;
+    g.plane[3] = dims[0] * dims[1] * dims[2] / 2;
+
+    auto cleanup = [&](int code) {
+        stag_lattice_destroy(lat);
+        return code;
+    };
+    cudaError_t e;
+    if (cuda_stream) {
+        lat->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&lat->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess)
+            return cleanup(fail(STAG_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+        lat->own_stream = true;
+    }
+    const int nblk = (int)((Vh + 63) / 64) + 1;
+    if ((e = cudaMalloc(&lat->partial, sizeof(double) * nblk)) != cudaSuccess ||
+        (e = cudaMalloc(&lat->sc, sizeof(CgScalars))) != cudaSuccess ||
+        (e = cudaMemset(lat->sc, 0, sizeof(CgScalars))) != cudaSuccess ||
+        (e = cudaMallocHost(&lat->sc_host, sizeof(CgScalars))) != cudaSuccess ||
+        (e = cudaEventCreate(&lat->ev0)) != cudaSuccess ||
+        (e = cudaEventCreate(&lat->ev1)) != cudaSuccess)
+        return cleanup(fail(STAG_ERR_NOMEM, "stag_lattice_create: %s", cudaGetErrorString(e)));
+    memset(lat->sc_host, 0, sizeof(CgScalars));
+    *out = lat;
+    return STAG_OK;
+}
+
+static void free_cg(CgWork &w) {
+    if (w.exec)
+        cudaGraphExecDestroy(w.exec);
+    if (w.graph)
+        cudaGraphDestroy(w.graph);
+    void *bufs[] = {w.r, w.p, w.Ap, w.t, w.bw, w.xw};
+    for (void *b : bufs)
+        if (b)
+            cudaFree(b);
+    w = CgWork();
+}
+
+extern "C" int stag_lattice_destroy(stag_lattice lat) {
+    if (!lat)
+        return STAG_OK;
+    if (lat->live_fields > 0)
+        return fail(STAG_ERR_STATE, "stag_lattice_destroy: %d fields still alive", lat->live_fields);
+    DEVICE_SCOPE(lat->device);
+    if (lat->stream)
+        cudaStreamSynchronize(lat->stream);
+    for (int p = 0; p < 4; p++) {
+        free_cg(lat->cg[p]);
+        if (lat->links[p])
+            cudaFree(lat->links[p]);
+    }
+    if (lat->partial)
+        cudaFree(lat->partial);
+    if (lat->staging)
+        cudaFree(lat->staging);
+    if (lat->sc)
+        cudaFree(lat->sc);
+    if (lat->sc_host)
+        cudaFreeHost(lat->sc_host);
+    if (lat->ev0)
+        cudaEventDestroy(lat->ev0);
+    if (lat->ev1)
+        cudaEventDestroy(lat->ev1);
+    if (lat->own_stream && lat->stream)
+        cudaStreamDestroy(lat->stream);
+    delete lat;
+    return STAG_OK;
+}
+
+extern "C" int stag_lattice_volume(const stag_lattice lat, long long *V, long long *Vh) {
+    if (!lat)
+        return fail(STAG_ERR_ARG, "stag_lattice_volume: lattice is NULL");
+    if (V)
+        *V = lat->V;
+    if (Vh)
+        *Vh = lat->Vh;
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// gauge upload
+// --------------------------------------------------------------------------
+
+// device copy of a canonical gauge field: returns a device pointer, allocating
+// a temporary when the source is on the host
+static int gauge_to_device(stag_lattice lat, const double *src, int ptr_kind, double **dev,
+                           bool *owned) {
+    const size_t bytes = 4ull * lat->V * 18 * sizeof(double);
+    if (ptr_kind == STAG_PTR_DEVICE) {
+        *dev = (double *)src;
+        *owned = false;
+        return STAG_OK;
+    }
+    CUDA_TRY(cudaMalloc(dev, bytes));
+    *owned = true;
+    cudaError_t e = cudaMemcpyAsync(*dev, src, bytes, cudaMemcpyHostToDevice, lat->stream);
+    if (e != cudaSuccess) {
+        cudaFree(*dev);
+        *dev = nullptr;
+        return fail(STAG_ERR_CUDA, "gauge copy to device: %s", cudaGetErrorString(e));
+    }
+    return STAG_OK;
+}
+
+extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const double *lng, double c1,
+                                 double c3, int ptr_kind, unsigned prec_mask) {
+    if (!lat || !fat)
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: lattice or fat links NULL");
+    if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: bad ptr_kind %d", ptr_kind);
+    if (!std::isfinite(c1) || !std::isfinite(c3))
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: coefficients must be finite");
+    if (prec_mask == 0)
+        prec_mask = STAG_PREC_BIT(STAG_F64) | STAG_PREC_BIT(STAG_DF64);
+    for (int p = 0; p < 32; p++)
+        if ((prec_mask >> p) & 1u)
+            if (!prec_valid(p))
+                return fail(STAG_ERR_ARG, "stag_gauge_upload: precision %d (%s) not available", p,
+                            prec_name(p));
+    DEVICE_SCOPE(lat->device);
+    double *fat_d = nullptr, *lng_d = nullptr;
+    bool fat_owned = false, lng_owned = false;
+    int st = gauge_to_device(lat, fat, ptr_kind, &fat_d, &fat_owned);
+    if (st != STAG_OK)
+        return st;
+    auto release = [&]() {
+        cudaStreamSynchronize(lat->stream);
+        if (fat_owned)
+            cudaFree(fat_d);
+        if (lng_owned)
+            cudaFree(lng_d);
+    };
+    if (lng) {
+        st = gauge_to_device(lat, lng, ptr_kind, &lng_d, &lng_owned);
+    } else {
+        cudaError_t e = cudaMalloc(&lng_d, 4ull * lat->V * 18 * sizeof(double));
+        if (e == cudaSuccess) {
+            lng_owned = true;
+            e = launch_long_links(lat->geom, fat_d, lng_d, lat->stream);
+        }
+        if (e != cudaSuccess)
+            st = fail(STAG_ERR_CUDA, "long-link build: %s", cudaGetErrorString(e));
+    }
+    if (st != STAG_OK) {
+        release();
+        return st;
+    }
+    // drop old copies and solver graphs
+    cudaStreamSynchronize(lat->stream);
+    for (int p = 0; p < 4; p++) {
+        free_cg(lat->cg[p]);
+        if (lat->links[p]) {
+            cudaFree(lat->links[p]);
+            lat->links[p] = nullptr;
+        }
+    }
+    lat->has_gauge = false;
+    for (int p = 0; p < 4; p++) {
+        if (!((prec_mask >> p) & 1u))
+            continue;
+        cudaError_t e = cudaMalloc(&lat->links[p], link_bytes(lat, p));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(lat->links[p], 0, link_bytes(lat, p), lat->stream);
+        if (e == cudaSuccess)
+            e = launch_fold_links(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links[p], lat->stream);
+        if (e != cudaSuccess) {
+            release();
+            return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,
+                        "gauge fold (%s): %s", prec_name(p), cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(lat->stream);
+    release();
+    if (e != cudaSuccess)
+        return fail(STAG_ERR_CUDA, "stag_gauge_upload: %s", cudaGetErrorString(e));
+    lat->has_gauge = true;
+    lat->c1 = c1;
+    lat->c3 = c3;
+    return STAG_OK;
+}
+
+extern "C" int stag_long_links_build(stag_lattice lat, const double *fat, double *lng, int ptr_kind) {
+    if (!lat || !fat || !lng)
+        return fail(STAG_ERR_ARG, "stag_long_links_build: NULL argument");
+    if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
+        return fail(STAG_ERR_ARG, "stag_long_links_build: bad ptr_kind %d", ptr_kind);
+    DEVICE_SCOPE(lat->device);
+    const size_t bytes = 4ull * lat->V * 18 * sizeof(double);
+    double *fat_d = nullptr;
+    bool owned = false;
+    STAG_TRY(gauge_to_device(lat, fat, ptr_kind, &fat_d, &owned));
+    double *out_d = (double *)lng;
+    cudaError_t e = cudaSuccess;
+    if (ptr_kind == STAG_PTR_HOST)
+        e = cudaMalloc(&out_d, bytes);
+    if (e == cudaSuccess)
+        e = launch_long_links(lat->geom, fat_d, out_d, lat->stream);
+    if (e == cudaSuccess && ptr_kind == STAG_PTR_HOST)
+        e = cudaMemcpyAsync(lng, out_d, bytes, cudaMemcpyDeviceToHost, lat->stream);
+    cudaError_t e2 = cudaStreamSynchronize(lat->stream);
+    if (owned)
+        cudaFree(fat_d);
+    if (ptr_kind == STAG_PTR_HOST && out_d)
+        cudaFree(out_d);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e != cudaSuccess)
+        return fail(STAG_ERR_CUDA, "stag_long_links_build: %s", cudaGetErrorString(e));
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// fields
+// --------------------------------------------------------------------------
+extern "C" int stag_field_create(stag_lattice lat, int parity, int prec, stag_field *out) {
+    if (!out)
+        return fail(STAG_ERR_ARG, "stag_field_create: out is NULL");
+    *out = nullptr;
+    if (!lat)
+        return fail(STAG_ERR_ARG, "stag_field_create: lattice is NULL");
+    if (parity != STAG_EVEN && parity != STAG_ODD)
+        return fail(STAG_ERR_ARG, "stag_field_create: bad parity %d", parity);
+    if (!prec_valid(prec))
+        return fail(STAG_ERR_ARG, "stag_field_create: precision %d (%s) not available", prec,
+                    prec_name(prec));
+    DEVICE_SCOPE(lat->device);
+    stag_field f = new (std::nothrow) stag_field_s();
+    if (!f)
+        return fail(STAG_ERR_NOMEM, "stag_field_create: host allocation failed");
+    f->lat = lat;
+    f->parity = parity;
+    f->prec = prec;
+    f->bytes = field_bytes(lat, prec);
+    cudaError_t e = cudaMalloc(&f->data, f->bytes);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(f->data, 0, f->bytes, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess) {
+        if (f->data)
+            cudaFree(f->data);
+        delete f;
+        return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,
+                    "stag_field_create: %s", cudaGetErrorString(e));
+    }
+    lat->live_fields++;
+    *out = f;
+    return STAG_OK;
+}
+
+extern "C" int stag_field_destroy(stag_field f) {
+    if (!f)
+        return STAG_OK;
+    DEVICE_SCOPE(f->lat->device);
+    cudaStreamSynchronize(f->lat->stream);
+    cudaFree(f->data);
+    f->lat->live_fields--;
+    delete f;
+    return STAG_OK;
+}
+
+static int field_io(stag_field f, const double *src, double *dst, int ptr_kind) {
+    stag_lattice lat = f->lat;
+    DEVICE_SCOPE(lat->device);
+    const size_t bytes = (size_t)lat->Vh * 6 * sizeof(double);
+    double *canon = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (ptr_kind == STAG_PTR_DEVICE) {
+        canon = src ? (double *)src : dst;
+    } else {
+        if (!lat->staging)
+            e = cudaMalloc(&lat->staging, bytes);
+        canon = lat->staging;
+        if (e == cudaSuccess && src)
+            e = cudaMemcpyAsync(canon, src, bytes, cudaMemcpyHostToDevice, lat->stream);
+    }
+    if (e == cudaSuccess)
+        e = src ? launch_import(f->prec, lat->geom, canon, f->data, lat->stream)
+                : launch_export(f->prec, lat->geom, f->data, canon, lat->stream);
+    if (e == cudaSuccess && dst && ptr_kind == STAG_PTR_HOST)
+        e = cudaMemcpyAsync(dst, canon, bytes, cudaMemcpyDeviceToHost, lat->stream);
+    cudaError_t e2 = cudaStreamSynchronize(lat->stream);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,
+                    "field %s: %s", src ? "import" : "export", cudaGetErrorString(e));
+    return STAG_OK;
+}
+
+extern "C" int stag_field_import(stag_field f, const double *src, int ptr_kind) {
+    if (!f || !src)
+        return fail(STAG_ERR_ARG, "stag_field_import: NULL argument");
+    if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
+        return fail(STAG_ERR_ARG, "stag_field_import: bad ptr_kind %d", ptr_kind);
+    return field_io(f, src, nullptr, ptr_kind);
+}
+
+extern "C" int stag_field_export(const stag_field f, double *dst, int ptr_kind) {
+    if (!f || !dst)
+        return fail(STAG_ERR_ARG, "stag_field_export: NULL argument");
+    if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
+        return fail(STAG_ERR_ARG, "stag_field_export: bad ptr_kind %d", ptr_kind);
+    return field_io((stag_field)f, nullptr, dst, ptr_kind);
+}
+
+extern "C" int stag_field_zero(stag_field f) {
+    if (!f)
+        return fail(STAG_ERR_ARG, "stag_field_zero: NULL field");
+    DEVICE_SCOPE(f->lat->device);
+    CUDA_TRY(cudaMemsetAsync(f->data, 0, f->bytes, f->lat->stream));
+    return STAG_OK;
+}
+
+extern "C" int stag_field_storage(const stag_field f, void **dev_ptr, unsigned long long *bytes) {
+    if (!f)
+        return fail(STAG_ERR_ARG, "stag_field_storage: NULL field");
+    if (dev_ptr)
+        *dev_ptr = f->data;
+    if (bytes)
+        *bytes = f->bytes;
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// Dslash and M
+// --------------------------------------------------------------------------
+static int check_pair(stag_lattice lat, const stag_field out, const stag_field in, int out_par,
+                      const char *who) {
+    if (!lat || !out || !in)
+        return fail(STAG_ERR_ARG, "%s: NULL argument", who);
+    if (out->lat != lat || in->lat != lat)
+        return fail(STAG_ERR_ARG, "%s: field belongs to another lattice", who);
+    if (out->parity != out_par || in->parity != 1 - out_par)
+        return fail(STAG_ERR_STATE, "%s: parity mismatch (out %d, in %d)", who, out->parity,
+                    in->parity);
+    if (out->prec != in->prec)
+        return fail(STAG_ERR_STATE, "%s: precision mismatch (%s vs %s)", who, prec_name(out->prec),
+                    prec_name(in->prec));
+    if (out == in)
+        return fail(STAG_ERR_ARG, "%s: out and in must differ", who);
+    if (!lat->has_gauge || !lat->links[out->prec])
+        return fail(STAG_ERR_STATE, "%s: no %s gauge copy uploaded", who, prec_name(out->prec));
+    return STAG_OK;
+}
+
+static DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, const void *in, void *out) {
+    DslashArgs a;
+    memset(&a, 0, sizeof a);
+    a.g = lat->geom;
+    a.out_par = out_par;
+    a.links_out = links_of(lat, prec, out_par);
+    a.links_in = links_of(lat, prec, 1 - out_par);
+    a.in = in;
+    a.out = out;
+    a.partial = lat->partial;
+    a.sc = lat->sc;
+    return a;
+}
+
+static int dslash_impl(stag_lattice lat, stag_field out, const stag_field in, int out_par,
+                       const char *who) {
+    STAG_TRY(check_pair(lat, out, in, out_par, who));
+    DEVICE_SCOPE(lat->device);
+    DslashArgs a = dslash_args(lat, out->prec, out_par, in->data, out->data);
+    CUDA_TRY(launch_dslash(out->prec, EPI_NONE, a, 0, lat->stream));
+    return STAG_OK;
+}
+
+extern "C" int stag_dslash_eo(stag_lattice lat, stag_field out_even, const stag_field in_odd) {
+    return dslash_impl(lat, out_even, in_odd, STAG_EVEN, "stag_dslash_eo");
+}
+
+extern "C" int stag_dslash_oe(stag_lattice lat, stag_field out_odd, const stag_field in_even) {
+    return dslash_impl(lat, out_odd, in_even, STAG_ODD, "stag_dslash_oe");
+}
+
+// odd temporary of the CG workspace of one precision
+static int ensure_cg_work(stag_lattice lat, int prec) {
+    CgWork &w = lat->cg[prec];
+    if (w.r)
+        return STAG_OK;
+    w.prec = prec;
+    const size_t b = field_bytes(lat, prec);
+    void **bufs[] = {&w.r, &w.p, &w.Ap, &w.t, &w.bw, &w.xw};
+    for (void **pp : bufs) {
+        cudaError_t e = cudaMalloc(pp, b);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(*pp, 0, b, lat->stream);
+        if (e != cudaSuccess) {
+            free_cg(w);
+            return fail(STAG_ERR_NOMEM, "CG workspace (%s): %s", prec_name(prec), cudaGetErrorString(e));
+        }
+    }
+    return STAG_OK;
+}
+
+static int upload_scalars(stag_lattice lat, double mass, double tol, int max_iter, bool has_cond,
+                          cudaGraphConditionalHandle cond) {
+    // pageable source: the copy has read it when cudaMemcpyAsync returns
+    CgScalars h;
+    memset(&h, 0, sizeof h);
+    h.m2 = make_dpair(mass * mass);
+    h.tol2 = tol * tol;
+    h.max_iter = max_iter;
+    h.has_cond = has_cond ? 1 : 0;
+    h.cond = cond;
+    CUDA_TRY(cudaMemcpyAsync(lat->sc, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
+    return STAG_OK;
+}
+
+extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_field in_even,
+                            double mass) {
+    if (!lat || !out_even || !in_even)
+        return fail(STAG_ERR_ARG, "stag_apply_M: NULL argument");
+    if (out_even->parity != STAG_EVEN || in_even->parity != STAG_EVEN)
+        return fail(STAG_ERR_STATE, "stag_apply_M: fields must be even");
+    if (out_even->prec != in_even->prec)
+        return fail(STAG_ERR_STATE, "stag_apply_M: precision mismatch");
+    if (out_even == in_even)
+        return fail(STAG_ERR_ARG, "stag_apply_M: out and in must differ");
+    if (!std::isfinite(mass))
+        return fail(STAG_ERR_ARG, "stag_apply_M: mass must be finite");
+    const int prec = in_even->prec;
+    if (!lat->has_gauge || !lat->links[prec])
+        return fail(STAG_ERR_STATE, "stag_apply_M: no %s gauge copy uploaded", prec_name(prec));
+    DEVICE_SCOPE(lat->device);
+    STAG_TRY(ensure_cg_work(lat, prec));
+    CgWork &w = lat->cg[prec];
+    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, in_even->data, w.t);
+    CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, 0, lat->stream));
+    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, out_even->data);
+    a2.p = in_even->data;
+    a2.m2 = make_dpair(mass * mass);
+    a2.m2_in_args = 1;
+    CUDA_TRY(launch_dslash(prec, EPI_M, a2, 0, lat->stream));
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// CG solve graph:
+//   init (x=0, r=p=b, |b|^2)
+//   while (running) { t = D_oe p; Ap = m^2 p - D_eo t, alpha;
+//                     x += alpha p, r -= alpha Ap, beta; p = r + beta p }
+//   true residual |b - M x|^2
+// --------------------------------------------------------------------------
+static cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s) {
+    const int prec = w.prec;
+    cudaError_t e;
+    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
+    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+        return e;
+    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
+    a2.p = w.p;
+    if ((e = launch_dslash(prec, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_cg_update(prec, lat->geom, w.xw, w.r, w.p, w.Ap, lat->partial, lat->sc, s)) !=
+        cudaSuccess)
+        return e;
+    return launch_cg_p_update(prec, lat->geom, w.r, w.p, lat->sc, s);
+}
+
+static cudaError_t enqueue_true_residual(stag_lattice lat, CgWork &w, cudaStream_t s) {
+    const int prec = w.prec;
+    cudaError_t e;
+    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.xw, w.t);
+    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+        return e;
+    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, nullptr);
+    a2.p = w.xw;
+    a2.b = w.bw;
+    return launch_dslash(prec, EPI_RESID, a2, 0, s);
+}
+
+static int build_cg_graph(stag_lattice lat, CgWork &w) {
+    cudaStream_t s = lat->stream;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+    }
+    auto bail = [&](const char *what, cudaError_t err) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+            if (junk && junk != graph)
+                cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "CG graph (%s): %s", what, cudaGetErrorString(err));
+    };
+    // init, then the loop node, then the true residual, captured into `graph`
+    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin capture", e);
+    if ((e = launch_cg_init(w.prec, lat->geom, w.xw, w.r, w.p, w.bw, lat->partial, lat->sc, s)) !=
+        cudaSuccess)
+        return bail("init", e);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return bail("capture info", e);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+        return bail("add loop node", e);
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return bail("update deps", e);
+    if ((e = enqueue_true_residual(lat, w, s)) != cudaSuccess)
+        return bail("true residual", e);
+    cudaGraph_t captured = nullptr;
+    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
+        return bail("end capture", e);
+    // loop body
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin body capture", e);
+    if ((e = enqueue_cg_body(lat, w, s)) != cudaSuccess)
+        return bail("body", e);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
+        return bail("end body capture", e);
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        return bail("instantiate", e);
+    w.graph = graph;
+    w.exec = exec;
+    w.cond = cond;
+    return STAG_OK;
+}
+
+static void fill_info(stag_lattice lat, int prec, const CgScalars &h, float ms,
+                      stag_solve_info *info) {
+    if (!info)
+        return;
+    memset(info, 0, sizeof *info);
+    info->iters = h.iter;
+    info->status = h.status == CG_CONVERGED ? STAG_OK
+                   : h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
+                                              : STAG_ERR_NOT_CONVERGED;
+    info->true_rel_resid = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+    info->iter_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    info->seconds = ms * 1e-3;
+    const double rb = prec == STAG_F32 ? 4.0 : 8.0;
+    // per iteration and even site: two Dslash (1146 flops, 300 reals each)
+    // plus the vector passes (p read again, x/r/p/Ap update, p update)
+    const double flops = (2.0 * 1146 + 72) * (double)lat->Vh * h.iter;
+    const double bytes = (2.0 * 300 + 60) * rb * (double)lat->Vh * h.iter;
+    if (ms > 0) {
+        info->gflops = flops / (ms * 1e-3) / 1e9;
+        info->gbs = bytes / (ms * 1e-3) / 1e9;
+    }
+}
+
+extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b, double mass,
+                             double rel_tol, int max_iter, stag_solve_info *info) {
+    if (info)
+        memset(info, 0, sizeof *info);
+    if (!lat || !x || !b)
+        return fail(STAG_ERR_ARG, "stag_cg_solve: NULL argument");
+    if (x->lat != lat || b->lat != lat)
+        return fail(STAG_ERR_ARG, "stag_cg_solve: field belongs to another lattice");
+    if (x->parity != STAG_EVEN || b->parity != STAG_EVEN)
+        return fail(STAG_ERR_STATE, "stag_cg_solve: x and b must be even fields");
+    if (x->prec != b->prec)
+        return fail(STAG_ERR_STATE, "stag_cg_solve: precision mismatch");
+    if (x == b)
+        return fail(STAG_ERR_ARG, "stag_cg_solve: x and b must differ");
+    if (x->prec != STAG_F64 && x->prec != STAG_DF64)
+        return fail(STAG_ERR_STATE, "stag_cg_solve: fields must be F64 or DF64 (got %s)",
+                    prec_name(x->prec));
+    if (!(mass > 0) || !std::isfinite(mass))
+        return fail(STAG_ERR_ARG, "stag_cg_solve: mass must be positive and finite");
+    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
+        return fail(STAG_ERR_ARG, "stag_cg_solve: rel_tol must be >= 0");
+    if (max_iter < 0)
+        return fail(STAG_ERR_ARG, "stag_cg_solve: max_iter must be >= 0");
+    const int prec = x->prec;
+    if (!lat->has_gauge || !lat->links[prec])
+        return fail(STAG_ERR_STATE, "stag_cg_solve: no %s gauge copy uploaded", prec_name(prec));
+    DEVICE_SCOPE(lat->device);
+    STAG_TRY(ensure_cg_work(lat, prec));
+    CgWork &w = lat->cg[prec];
+    if (!w.exec)
+        STAG_TRY(build_cg_graph(lat, w));
+    cudaStream_t s = lat->stream;
+    CUDA_TRY(cudaMemcpyAsync(w.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+    STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, w.cond));
+    CUDA_TRY(cudaEventRecord(lat->ev0, s));
+    CUDA_TRY(cudaGraphLaunch(w.exec, s));
+    CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    CUDA_TRY(cudaMemcpyAsync(x->data, w.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+    stag_solve_info local;
+    fill_info(lat, prec, *lat->sc_host, ms, &local);
+    if (info)
+        *info = local;
+    if (local.status != STAG_OK)
+        return fail(local.status, "stag_cg_solve: %s after %d iterations (|r|/|b| = %.3e)",
+                    local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
+                    local.iter_rel_resid);
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+extern "C" const char *stag_strerror(int status) {
+    switch (status) {
+    case STAG_OK: return "ok";
+    case STAG_ERR_ARG: return "invalid argument";
+    case STAG_ERR_STATE: return "invalid state";
+    case STAG_ERR_CUDA: return "CUDA error";
+    case STAG_ERR_NOT_CONVERGED: return "not converged";
+    case STAG_ERR_BREAKDOWN: return "solver breakdown";
+    case STAG_ERR_TIMEOUT: return "device wait timed out";
+    case STAG_ERR_NOMEM: return "out of memory";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *stag_last_error_message(void) { return g_last_error.c_str(); }
+
+extern "C" const char *stag_version(void) { return "0.1.0"; }

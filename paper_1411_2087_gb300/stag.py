@@ -1,0 +1,306 @@
+"""Thin Python binding of libstag (include/stag.h) over ctypes.
+
+Argument marshalling only: every step of the Dslash and the solvers runs in
+the CUDA library.  If ``libstag.so`` has not been built the first call raises
+``LibraryNotBuilt``; there is no fallback.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA), complex128
+in the canonical layouts of ``include/stag.h``:
+
+* gauge field ``[4][V][3][3]``
+* one-parity colour field ``[Vh][3]`` in checkerboard order
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libstag.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_STATE = -2
+ERR_CUDA = -3
+ERR_NOT_CONVERGED = -4
+ERR_BREAKDOWN = -5
+ERR_TIMEOUT = -6
+ERR_NOMEM = -7
+
+F64, F32, F16, DF64 = 0, 1, 2, 3
+PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
+EVEN, ODD = 0, 1
+PTR_HOST, PTR_DEVICE = 0, 1
+
+C1_NAIK = 9.0 / 8.0
+C3_NAIK = -1.0 / 24.0
+BC_DEFAULT = (1.0, 1.0, 1.0, -1.0)
+
+# every symbol include/stag.h declares (checked by the CPU tests)
+EXPORTED = [
+    "stag_lattice_create", "stag_lattice_destroy", "stag_lattice_volume",
+    "stag_gauge_upload", "stag_long_links_build",
+    "stag_field_create", "stag_field_destroy", "stag_field_import", "stag_field_export",
+    "stag_field_zero", "stag_field_storage",
+    "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
+    "stag_cg_solve",
+    "stag_strerror", "stag_last_error_message", "stag_version",
+]
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class StagError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double), ("iter_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("gflops", ctypes.c_double),
+                ("gbs", ctypes.c_double), ("restarts", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libstag.so (built by ``paper_1411_2087_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise LibraryNotBuilt(
+                f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "stag_lattice_create": ([PP, P, P, I, P], I),
+            "stag_lattice_destroy": ([P], I),
+            "stag_lattice_volume": ([P, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(ctypes.c_longlong)], I),
+            "stag_gauge_upload": ([P, P, P, D, D, I, ctypes.c_uint], I),
+            "stag_long_links_build": ([P, P, P, I], I),
+            "stag_field_create": ([P, I, I, PP], I),
+            "stag_field_destroy": ([P], I),
+            "stag_field_import": ([P, P, I], I),
+            "stag_field_export": ([P, P, I], I),
+            "stag_field_zero": ([P], I),
+            "stag_field_storage": ([P, PP, ctypes.POINTER(ctypes.c_ulonglong)], I),
+            "stag_dslash_eo": ([P, P, P], I),
+            "stag_dslash_oe": ([P, P, P], I),
+            "stag_apply_M": ([P, P, P, D], I),
+            "stag_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_strerror": ([I], ctypes.c_char_p),
+            "stag_last_error_message": ([], ctypes.c_char_p),
+            "stag_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(status: int, allow=()) -> int:
+    if status != OK and status not in allow:
+        msg = lib().stag_last_error_message().decode(errors="replace")
+        raise StagError(status, msg or lib().stag_strerror(status).decode())
+    return status
+
+
+# --------------------------------------------------------------------------
+# buffer marshalling
+# --------------------------------------------------------------------------
+
+def _is_torch(a) -> bool:
+    try:
+        import torch
+        return isinstance(a, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+def _as_buffer(a, shape, writable=False):
+    """(pointer, ptr_kind, keepalive) for a complex128 array of `shape`."""
+    if _is_torch(a):
+        import torch
+        if a.dtype != torch.complex128 or tuple(a.shape) != tuple(shape):
+            raise ValueError(f"expected complex128 tensor of shape {tuple(shape)}, "
+                             f"got {a.dtype} {tuple(a.shape)}")
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        kind = PTR_DEVICE if a.is_cuda else PTR_HOST
+        return ctypes.c_void_p(a.data_ptr()), kind, a
+    arr = np.asarray(a)
+    if arr.dtype != np.complex128 or arr.shape != tuple(shape):
+        raise ValueError(f"expected complex128 array of shape {tuple(shape)}, "
+                         f"got {arr.dtype} {arr.shape}")
+    if not arr.flags.c_contiguous or (writable and not arr.flags.writeable):
+        raise ValueError("array must be C-contiguous" + (" and writable" if writable else ""))
+    return arr.ctypes.data_as(ctypes.c_void_p), PTR_HOST, arr
+
+
+# --------------------------------------------------------------------------
+# objects
+# --------------------------------------------------------------------------
+
+class Field:
+    """One-parity colour field in the library's internal layout."""
+
+    def __init__(self, lattice: "Lattice", parity: int, prec="df64"):
+        self.lattice = lattice
+        self.parity = int(parity)
+        self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        h = ctypes.c_void_p()
+        _check(lib().stag_field_create(lattice.handle, self.parity, self.prec, ctypes.byref(h)))
+        self.handle = h
+        lattice._fields.add(self)
+
+    @property
+    def shape(self):
+        return (self.lattice.Vh, 3)
+
+    def import_(self, src) -> "Field":
+        p, kind, keep = _as_buffer(src, self.shape)
+        _check(lib().stag_field_import(self.handle, p, kind))
+        return self
+
+    def export(self, out=None):
+        """Canonical complex128 [Vh][3]; a new numpy array unless `out` is given."""
+        if out is None:
+            out = np.empty(self.shape, dtype=np.complex128)
+        p, kind, keep = _as_buffer(out, self.shape, writable=True)
+        _check(lib().stag_field_export(self.handle, p, kind))
+        return out
+
+    def zero(self):
+        _check(lib().stag_field_zero(self.handle))
+
+    def storage(self):
+        ptr = ctypes.c_void_p()
+        n = ctypes.c_ulonglong()
+        _check(lib().stag_field_storage(self.handle, ctypes.byref(ptr), ctypes.byref(n)))
+        return ptr.value, n.value
+
+    def destroy(self):
+        if self.handle:
+            _check(lib().stag_field_destroy(self.handle))
+            self.handle = None
+            self.lattice._fields.discard(self)
+
+
+class Lattice:
+    """A lattice on one CUDA device (see stag_lattice_create)."""
+
+    def __init__(self, dims, bc=BC_DEFAULT, device: int = 0, stream: Optional[int] = None):
+        self.dims = tuple(int(d) for d in dims)
+        d = (ctypes.c_int * 4)(*self.dims)
+        b = (ctypes.c_double * 4)(*[float(v) for v in bc]) if bc is not None else None
+        h = ctypes.c_void_p()
+        _check(lib().stag_lattice_create(ctypes.byref(h), d, b, int(device),
+                                         ctypes.c_void_p(stream) if stream else None))
+        self.handle = h
+        self._fields = set()
+        V = ctypes.c_longlong()
+        Vh = ctypes.c_longlong()
+        _check(lib().stag_lattice_volume(h, ctypes.byref(V), ctypes.byref(Vh)))
+        self.V, self.Vh = V.value, Vh.value
+
+    # gauge -----------------------------------------------------------------
+    def upload_gauge(self, fat, lng=None, c1=C1_NAIK, c3=C3_NAIK, precisions=("f64", "df64")):
+        shape = (4, self.V, 3, 3)
+        pf, kind, keep_f = _as_buffer(fat, shape)
+        if lng is not None:
+            pl, kind_l, keep_l = _as_buffer(lng, shape)
+            if kind_l != kind:
+                raise ValueError("fat and long links must both be on the host or both on the device")
+        else:
+            pl = None
+        mask = 0
+        for p in precisions:
+            mask |= 1 << (PREC[p] if isinstance(p, str) else int(p))
+        _check(lib().stag_gauge_upload(self.handle, pf, pl, float(c1), float(c3), kind, mask))
+
+    def long_links(self, fat, out=None):
+        """Three-link products of `fat` computed on the GPU (canonical layout)."""
+        shape = (4, self.V, 3, 3)
+        pf, kind, keep_f = _as_buffer(fat, shape)
+        if out is None:
+            if kind == PTR_DEVICE:
+                import torch
+                out = torch.empty(shape, dtype=torch.complex128, device=fat.device)
+            else:
+                out = np.empty(shape, dtype=np.complex128)
+        po, kind_o, keep_o = _as_buffer(out, shape, writable=True)
+        if kind_o != kind:
+            raise ValueError("fat and output must both be on the host or both on the device")
+        _check(lib().stag_long_links_build(self.handle, pf, po, kind))
+        return out
+
+    # fields ----------------------------------------------------------------
+    def field(self, parity: int, prec="df64", data=None) -> Field:
+        f = Field(self, parity, prec)
+        if data is not None:
+            f.import_(data)
+        return f
+
+    # operators -------------------------------------------------------------
+    def dslash(self, out: Field, inp: Field):
+        if out.parity == EVEN:
+            _check(lib().stag_dslash_eo(self.handle, out.handle, inp.handle))
+        else:
+            _check(lib().stag_dslash_oe(self.handle, out.handle, inp.handle))
+
+    def apply_M(self, out: Field, inp: Field, mass: float):
+        _check(lib().stag_apply_M(self.handle, out.handle, inp.handle, float(mass)))
+
+    def cg(self, x: Field, b: Field, mass: float, tol: float = 1e-10, max_iter: int = 20000,
+           raise_on_failure: bool = False) -> dict:
+        info = SolveInfo()
+        st = lib().stag_cg_solve(self.handle, x.handle, b.handle, float(mass), float(tol),
+                                 int(max_iter), ctypes.byref(info))
+        if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def close(self):
+        for f in list(self._fields):
+            f.destroy()
+        if self.handle:
+            _check(lib().stag_lattice_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            if getattr(self, "handle", None) and _lib is not None:
+                self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return lib().stag_version().decode()

@@ -1,0 +1,117 @@
+"""GPU even-odd CG against the CPU oracle through the C ABI.
+
+Criteria (CG iterates cannot agree bit for bit when reductions sum in a
+different order): the GPU solution's true residual, recomputed by the oracle,
+meets the tolerance; the iteration counts agree within max(3, 1%); solving
+both sides to 1e-13 gives solutions that agree to 1e-12 times the condition
+number estimate; edge cases return the documented status.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2087_gb300 import stag, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def fields(dims, eps, seed):
+    U = synth.su3_field(dims, eps, seed).numpy()
+    return U, oracle.long_links(dims, U)
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+@pytest.mark.parametrize("dims,mass", [((8, 8, 8, 8), 0.1), ((6, 4, 6, 10), 0.05),
+                                       ((4, 4, 4, 4), 0.2)])
+def test_cg_matches_oracle(dims, mass, prec):
+    U, N = fields(dims, 0.3, 1000)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 1100).numpy()
+    x_o, info_o = oracle.cg(dims, U, N, mass, b, tol=1e-10)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(prec,))
+        fb = lat.field(stag.EVEN, prec, b)
+        fx = lat.field(stag.EVEN, prec)
+        info = lat.cg(fx, fb, mass, 1e-10, 5000)
+        x = fx.export()
+    assert info["return"] == stag.OK, info
+    res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
+    assert res <= 1e-10 * 1.05, res
+    assert abs(info["true_rel_resid"] - res) <= 1e-3 * res + 1e-15
+    assert abs(info["iters"] - info_o["iters"]) <= max(3, 0.01 * info_o["iters"]), (info, info_o)
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_cg_tight_solution_agrees(prec):
+    dims, mass = (4, 4, 4, 8), 0.1
+    U, N = fields(dims, 0.3, 77)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 78).numpy()
+    x_o, info_o = oracle.cg(dims, U, N, mass, b, tol=1e-13)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(prec,))
+        fb = lat.field(stag.EVEN, prec, b)
+        fx = lat.field(stag.EVEN, prec)
+        info = lat.cg(fx, fb, mass, 1e-13, 5000)
+        x = fx.export()
+    assert info["return"] == stag.OK, info
+    # kappa <= (m^2 + 16 (7/6)^2 * max|U|-ish) / m^2; free-field bound is 2180 at m = 0.1
+    kappa = (mass ** 2 + 4 * 4 * (7 / 6) ** 2) / mass ** 2
+    assert np.abs(x - x_o).max() / np.abs(x_o).max() <= 1e-12 * kappa
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_cg_edge_cases(prec):
+    dims = (4, 4, 4, 4)
+    U, N = fields(dims, 0.3, 5)
+    Vh = int(np.prod(dims)) // 2
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(prec,))
+        fx = lat.field(stag.EVEN, prec)
+        # zero source: x = 0, no iterations
+        fz = lat.field(stag.EVEN, prec, np.zeros((Vh, 3), complex))
+        info = lat.cg(fx, fz, 0.1, 1e-10, 100)
+        assert info["return"] == stag.OK and info["iters"] == 0
+        assert not np.any(fx.export())
+        # max_iter reached
+        b = synth.gaussian_colour_field(Vh, 6).numpy()
+        fb = lat.field(stag.EVEN, prec, b)
+        info = lat.cg(fx, fb, 0.01, 1e-14, 3)
+        assert info["return"] == stag.ERR_NOT_CONVERGED and info["iters"] == 3
+        # the returned x is the 3rd iterate: compare with the oracle's
+        x_o, info_o = oracle.cg(dims, U, N, 0.01, b, tol=1e-14, max_iter=3)
+        assert np.abs(fx.export() - x_o).max() <= 1e-12 * np.abs(x_o).max()
+        # max_iter = 0
+        info = lat.cg(fx, fb, 0.01, 1e-10, 0)
+        assert info["return"] == stag.ERR_NOT_CONVERGED and info["iters"] == 0
+        # bad mass
+        with pytest.raises(stag.StagError):
+            lat.cg(fx, fb, -1.0, 1e-10, 10, raise_on_failure=True)
+        # a NaN in the source is reported as a breakdown, not a hang
+        bn = b.copy()
+        bn[3, 1] = np.nan
+        fn = lat.field(stag.EVEN, prec, bn)
+        info = lat.cg(fx, fn, 0.1, 1e-10, 100)
+        assert info["return"] == stag.ERR_BREAKDOWN
+        # a later good solve on the same lattice still works
+        info = lat.cg(fx, fb, 0.1, 1e-10, 1000)
+        assert info["return"] == stag.OK
+
+
+def test_cg_repeated_solves_reuse_graph():
+    dims = (8, 8, 8, 8)
+    U, N = fields(dims, 0.3, 1000)
+    Vh = int(np.prod(dims)) // 2
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("df64",))
+        fx = lat.field(stag.EVEN, "df64")
+        iters = []
+        for seed, mass in ((1, 0.1), (2, 0.2), (1, 0.1)):
+            b = synth.gaussian_colour_field(Vh, seed).numpy()
+            fb = lat.field(stag.EVEN, "df64", b)
+            info = lat.cg(fx, fb, mass, 1e-10, 5000)
+            assert info["return"] == stag.OK
+            res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, fx.export())) / np.linalg.norm(b)
+            assert res <= 1.05e-10
+            iters.append(info["iters"])
+        assert iters[0] == iters[2]  # deterministic reductions
