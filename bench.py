@@ -343,7 +343,7 @@ class OracleWorkload:
         return info["iters"], time.perf_counter() - t0, self.oracle.num_threads()
 
 
-def cpu_baseline(dims, rank, n_iter=10):
+def cpu_baseline(dims, rank, n_iter=150):
     Vh = int(np.prod(dims)) // 2
     it, dt, cores = OracleWorkload(dims, rank).run(n_iter)
     gbs = it * cg_bytes_per_iter_site("f64") * Vh / dt / 1e9
