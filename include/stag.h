@@ -167,6 +167,35 @@ typedef struct {
 int stag_cg_solve(stag_lattice lat, stag_field x_even, const stag_field b_even,
                   double mass, double rel_tol, int max_iter, stag_solve_info *info);
 
+/* ---- allocation-free M ---------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code invoked while its caller captures
+ * a CUDA graph, services that hand out fixed device buffers up front, or
+ * programs whose own allocator owns all device memory.  Creating a lattice
+ * allocates, so such callers cannot use stag_apply_M.
+ *
+ * out_even = m^2 in_even - D_eo D_oe in_even, computed on the caller's
+ * buffers in the canonical layouts (no lattice handle, no upload):
+ *   fat, lng   complex128 [4][V][3][3] raw links (c1, c3, phases and
+ *              boundary signs are applied by the kernel)
+ *   in_even    complex128 [Vh][3], out_even complex128 [Vh][3] (distinct)
+ * All four must be device memory of the current CUDA device; dims and bc as
+ * for stag_lattice_create (bc NULL = {+1,+1,+1,-1}).  FP64 arithmetic.
+ *
+ * Limit: Vh = V/2 <= 65536 (e.g. 16^4, 16^3 x 32); larger lattices return
+ * STAG_ERR_ARG.  The odd intermediate D_oe in_even lives in a 3 MiB array
+ * compiled into the library (held on every GPU that loads it until the
+ * process exits); every call overwrites all of the part it reads, so nothing
+ * needs clearing between calls, but two calls that overlap on the GPU (on
+ * different streams or devices sharing a context) race on that array.
+ * The first call on a device looks up the array's device address (set-up
+ * done once per device, with that device current); make that first call
+ * before any stream capture.  Calls no allocating CUDA routine.  Asynchronous
+ * on `cuda_stream` (NULL = legacy default stream). */
+int stag_apply_M_noalloc(const int dims[4], const double bc[4], double c1, double c3,
+                         const double *fat, const double *lng, double mass,
+                         const double *in_even, double *out_even, void *cuda_stream);
+
 /* ---- errors -------------------------------------------------------------- */
 const char *stag_strerror(int status);
 const char *stag_last_error_message(void);

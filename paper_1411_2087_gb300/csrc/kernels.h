@@ -35,4 +35,8 @@ cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], doubl
 // three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu), canonical layout
 cudaError_t launch_long_links(const Geom &g, const double *fat, double *lng, cudaStream_t s);
 
+// record the calling thread's last error message (read back by
+// stag_last_error_message) and return `code`
+int set_error(int code, const char *fmt, ...);
+
 }  // namespace stag

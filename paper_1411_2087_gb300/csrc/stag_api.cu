@@ -31,6 +31,18 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+namespace stag {
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+}  // namespace stag
+
 #define CUDA_TRY(call)                                                                     \
     do {                                                                                   \
         cudaError_t e_ = (call);                                                           \

@@ -47,7 +47,7 @@ EXPORTED = [
     "stag_field_create", "stag_field_destroy", "stag_field_import", "stag_field_export",
     "stag_field_zero", "stag_field_storage",
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
-    "stag_cg_solve",
+    "stag_cg_solve", "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -105,6 +105,7 @@ def lib():
             "stag_dslash_oe": ([P, P, P], I),
             "stag_apply_M": ([P, P, P, D], I),
             "stag_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_apply_M_noalloc": ([P, P, D, D, P, P, D, P, P, P], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
             "stag_version": ([], ctypes.c_char_p),
@@ -300,6 +301,24 @@ class Lattice:
                 self.close()
         except Exception:
             pass
+
+
+def apply_M_noalloc(dims, fat, lng, mass, in_even, out_even, bc=BC_DEFAULT, c1=C1_NAIK,
+                    c3=C3_NAIK, stream=None):
+    """stag_apply_M_noalloc on CUDA tensors the caller owns (see stag.h)."""
+    V = int(np.prod(dims))
+    for t, shape in ((fat, (4, V, 3, 3)), (lng, (4, V, 3, 3)), (in_even, (V // 2, 3)),
+                     (out_even, (V // 2, 3))):
+        p, kind, keep = _as_buffer(t, shape)
+        if kind != PTR_DEVICE:
+            raise ValueError("stag_apply_M_noalloc needs device tensors")
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    b = (ctypes.c_double * 4)(*[float(v) for v in bc]) if bc is not None else None
+    _check(lib().stag_apply_M_noalloc(d, b, float(c1), float(c3), ctypes.c_void_p(fat.data_ptr()),
+                                      ctypes.c_void_p(lng.data_ptr()), float(mass),
+                                      ctypes.c_void_p(in_even.data_ptr()),
+                                      ctypes.c_void_p(out_even.data_ptr()),
+                                      ctypes.c_void_p(stream) if stream else None))
 
 
 def version() -> str:
