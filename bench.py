@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,32")
     ap.add_argument("--dslash-launches", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
+                    help="host: the same CG kernels launched one by one (per-kernel profiling)")
     return ap.parse_args()
 
 
@@ -190,6 +192,7 @@ def run_native(args):
     stream = torch.cuda.Stream(dev)
     lat = stag.Lattice(dims, device=local, stream=stream.cuda_stream)
     lat.upload_gauge(U, None, precisions=(prec,))
+    lat.set_cg_launch(args.cg_launch)
     del U
     torch.cuda.empty_cache()
     b_pinned = b_host.pin_memory()
@@ -214,6 +217,7 @@ def run_native(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             info = lat.cg(fx, fb, MASS, TOL, 20000)
@@ -239,6 +243,7 @@ def run_native(args):
                 lat.dslash(fo2, fo)
         d1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     clocks = clk.summary()
     total_ms = e0.elapsed_time(e1)
     dslash_ms = d0.elapsed_time(d1) / args.dslash_launches
@@ -303,6 +308,7 @@ def run_native(args):
             "prec": prec, "global_batch": world, "parallelism": f"replicas{world}",
             "l2": "inputs larger than L2 (links 2.4 GB), no flush",
             "step": "one CG solve (init, iterations, true residual)",
+            "cg_launch": args.cg_launch,
         },
         "cg": {"iters": iters[0], "seconds_per_solve": round(statistics.median(solve_ms) * 1e-3, 4),
                "true_rel_resid": info["true_rel_resid"], "gflops": round(info["gflops"], 1)},

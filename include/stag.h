@@ -99,6 +99,18 @@ int stag_lattice_destroy(stag_lattice lat);
 /* Sizes: V, Vh.  Pure host queries. */
 int stag_lattice_volume(const stag_lattice lat, long long *V, long long *Vh);
 
+/* How stag_cg_solve drives its iterations.
+ * STAG_CG_LAUNCH_GRAPH (default): one CUDA graph per solve whose loop is a
+ *   conditional WHILE node; the last kernel of each iteration sets the loop
+ *   condition on the device, so the host waits once per solve.
+ * STAG_CG_LAUNCH_HOST: the same kernels launched individually; the host
+ *   reads the solver status every `chunk` iterations (1..4096) and kernels
+ *   of iterations past convergence return at once.  For drivers or tools
+ *   that cannot run or inspect conditional graph nodes (e.g. per-kernel
+ *   profiling).  Results are identical in both modes. */
+enum { STAG_CG_LAUNCH_GRAPH = 0, STAG_CG_LAUNCH_HOST = 1 };
+int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk);
+
 /* ---- gauge field ---------------------------------------------------------
  * Upload the fat (one-link) field and the long (three-link, Naik) field,
  * both canonical complex128 [4][V][3][3], with Naik coefficients c1 (one-link)

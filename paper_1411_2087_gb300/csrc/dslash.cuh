@@ -37,6 +37,7 @@ struct DslashArgs {
     CgScalars *sc;          // device scalars (m2, rr, alpha, ...)
     dpair m2;               // EPI_M: m^2 when m2_in_args, else read from sc
     int m2_in_args;
+    int skip_if_done;       // return at once when sc->status is no longer CG_RUNNING
 };
 
 template <int P>
@@ -120,6 +121,9 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     using R = typename F::R;
     using E = typename F::Elem;
     __shared__ double smem[32];
+    // the status is uniform over the grid: either every block returns here or none
+    if (a.skip_if_done && a.sc->status != CG_RUNNING)
+        return;
     const int c = blockIdx.x * BLOCK + threadIdx.x;
     const int S = a.g.stride;
     double dot = 0.0;

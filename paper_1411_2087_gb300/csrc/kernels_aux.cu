@@ -120,7 +120,8 @@ cg_p_kernel(Geom g, const typename Fmt<P>::Elem *r, typename Fmt<P>::Elem *p, co
     using F = Fmt<P>;
     using R = typename F::R;
     const int c = blockIdx.x * BLOCK + threadIdx.x;
-    if (c >= g.Vh)
+    // after convergence or breakdown p is no longer used
+    if (c >= g.Vh || sc->status != CG_RUNNING)
         return;
     const R beta = scalar_as<R>(sc->beta);
     cplx<R> rv[3], pv[3];

@@ -121,7 +121,9 @@ struct stag_lattice_s {
     CgScalars *sc_host = nullptr;  // pinned mirror
     CgWork cg[4];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double *staging = nullptr;  // canonical [Vh][3] complex128 for host import/export
+    double *staging = nullptr;
+    int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
+    int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
 };
 
 struct stag_field_s {
@@ -283,6 +285,19 @@ extern "C" int stag_lattice_volume(const stag_lattice lat, long long *V, long lo
         *V = lat->V;
     if (Vh)
         *Vh = lat->Vh;
+    return STAG_OK;
+}
+
+extern "C" int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk) {
+    if (!lat)
+        return fail(STAG_ERR_ARG, "stag_lattice_set_cg_launch: lattice is NULL");
+    if (mode != STAG_CG_LAUNCH_GRAPH && mode != STAG_CG_LAUNCH_HOST)
+        return fail(STAG_ERR_ARG, "stag_lattice_set_cg_launch: bad mode %d", mode);
+    if (mode == STAG_CG_LAUNCH_HOST && (chunk < 1 || chunk > 4096))
+        return fail(STAG_ERR_ARG, "stag_lattice_set_cg_launch: chunk must be in [1, 4096]");
+    lat->cg_launch = mode;
+    if (mode == STAG_CG_LAUNCH_HOST)
+        lat->cg_chunk = chunk;
     return STAG_OK;
 }
 
@@ -653,14 +668,16 @@ extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_fi
 //                     x += alpha p, r -= alpha Ap, beta; p = r + beta p }
 //   true residual |b - M x|^2
 // --------------------------------------------------------------------------
-static cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s) {
+static cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done) {
     const int prec = w.prec;
     cudaError_t e;
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
+    a1.skip_if_done = skip_if_done;
     if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
         return e;
     DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
     a2.p = w.p;
+    a2.skip_if_done = skip_if_done;
     if ((e = launch_dslash(prec, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
         return e;
     if ((e = launch_cg_update(prec, lat->geom, w.xw, w.r, w.p, w.Ap, lat->partial, lat->sc, s)) !=
@@ -735,7 +752,7 @@ static int build_cg_graph(stag_lattice lat, CgWork &w) {
     if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return bail("begin body capture", e);
-    if ((e = enqueue_cg_body(lat, w, s)) != cudaSuccess)
+    if ((e = enqueue_cg_body(lat, w, s, false)) != cudaSuccess)
         return bail("body", e);
     cudaGraph_t body_out = nullptr;
     if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
@@ -801,14 +818,36 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
     DEVICE_SCOPE(lat->device);
     STAG_TRY(ensure_cg_work(lat, prec));
     CgWork &w = lat->cg[prec];
-    if (!w.exec)
-        STAG_TRY(build_cg_graph(lat, w));
     cudaStream_t s = lat->stream;
     CUDA_TRY(cudaMemcpyAsync(w.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
-    STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, w.cond));
-    CUDA_TRY(cudaEventRecord(lat->ev0, s));
-    CUDA_TRY(cudaGraphLaunch(w.exec, s));
-    CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
+        if (!w.exec)
+            STAG_TRY(build_cg_graph(lat, w));
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, w.cond));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(cudaGraphLaunch(w.exec, s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    } else {
+        // the same kernels launched one by one; the host reads the status
+        // every cg_chunk iterations, and kernels of iterations past the end
+        // return at once
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(launch_cg_init(prec, lat->geom, w.xw, w.r, w.p, w.bw, lat->partial, lat->sc, s));
+        const int chunk = lat->cg_chunk;
+        const long long max_chunks = (long long)max_iter / chunk + 2;
+        for (long long k = 0; k < max_chunks; k++) {
+            CUDA_TRY(cudaMemcpyAsync(&lat->sc_host->status, &lat->sc->status, sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (lat->sc_host->status != CG_RUNNING)
+                break;
+            for (int j = 0; j < chunk; j++)
+                CUDA_TRY(enqueue_cg_body(lat, w, s, true));
+        }
+        CUDA_TRY(enqueue_true_residual(lat, w, s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    }
     CUDA_TRY(cudaMemcpyAsync(x->data, w.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));

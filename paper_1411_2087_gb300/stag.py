@@ -34,6 +34,7 @@ ERR_NOMEM = -7
 F64, F32, F16, DF64 = 0, 1, 2, 3
 PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
 EVEN, ODD = 0, 1
+CG_LAUNCH_GRAPH, CG_LAUNCH_HOST = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 
 C1_NAIK = 9.0 / 8.0
@@ -43,6 +44,7 @@ BC_DEFAULT = (1.0, 1.0, 1.0, -1.0)
 # every symbol include/stag.h declares (checked by the CPU tests)
 EXPORTED = [
     "stag_lattice_create", "stag_lattice_destroy", "stag_lattice_volume",
+    "stag_lattice_set_cg_launch",
     "stag_gauge_upload", "stag_long_links_build",
     "stag_field_create", "stag_field_destroy", "stag_field_import", "stag_field_export",
     "stag_field_zero", "stag_field_storage",
@@ -93,6 +95,7 @@ def lib():
             "stag_lattice_destroy": ([P], I),
             "stag_lattice_volume": ([P, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(ctypes.c_longlong)], I),
+            "stag_lattice_set_cg_launch": ([P, I, I], I),
             "stag_gauge_upload": ([P, P, P, D, D, I, ctypes.c_uint], I),
             "stag_long_links_build": ([P, P, P, I], I),
             "stag_field_create": ([P, I, I, PP], I),
@@ -222,6 +225,11 @@ class Lattice:
         Vh = ctypes.c_longlong()
         _check(lib().stag_lattice_volume(h, ctypes.byref(V), ctypes.byref(Vh)))
         self.V, self.Vh = V.value, Vh.value
+
+    def set_cg_launch(self, mode: str = "graph", chunk: int = 32):
+        """'graph' (device-side loop, default) or 'host' (individual launches)."""
+        m = {"graph": CG_LAUNCH_GRAPH, "host": CG_LAUNCH_HOST}[mode]
+        _check(lib().stag_lattice_set_cg_launch(self.handle, m, int(chunk)))
 
     # gauge -----------------------------------------------------------------
     def upload_gauge(self, fat, lng=None, c1=C1_NAIK, c3=C3_NAIK, precisions=("f64", "df64")):

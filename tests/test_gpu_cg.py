@@ -115,3 +115,29 @@ def test_cg_repeated_solves_reuse_graph():
             assert res <= 1.05e-10
             iters.append(info["iters"])
         assert iters[0] == iters[2]  # deterministic reductions
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_host_launch_mode_is_identical(prec):
+    """The host-driven launch mode runs the same kernels in the same order:
+    bit-identical solution and iteration count."""
+    dims = (6, 4, 6, 10)
+    U, N = fields(dims, 0.3, 1000)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 31).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(prec,))
+        fb = lat.field(stag.EVEN, prec, b)
+        fx = lat.field(stag.EVEN, prec)
+        info_g = lat.cg(fx, fb, 0.05, 1e-10, 5000)
+        xg = fx.export()
+        for chunk in (1, 7, 64):
+            lat.set_cg_launch("host", chunk)
+            info_h = lat.cg(fx, fb, 0.05, 1e-10, 5000)
+            assert info_h["return"] == stag.OK
+            assert info_h["iters"] == info_g["iters"]
+            assert np.array_equal(fx.export(), xg)
+        info_h = lat.cg(fx, fb, 0.01, 1e-14, 5)
+        assert info_h["return"] == stag.ERR_NOT_CONVERGED and info_h["iters"] == 5
+        with pytest.raises(stag.StagError):
+            lat.set_cg_launch("host", 0)
