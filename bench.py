@@ -43,7 +43,7 @@ EPS = 0.3
 SEED_LINKS = 1001
 SEED_SOURCE = 1101
 METRIC = "Dslash GB/s (% HBM peak) & CG time-to-1e-10 residual, mixed/learned vs FP64"
-DSLASH_SOURCES = ["common.cuh", "fields.cuh", "dslash.cuh", "kernels_dslash.cu"]
+DSLASH_SOURCES = ["common.cuh", "fields.cuh", "dslash.cuh", "dslash_launch.cuh"]
 
 
 def parse():
@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--dims", default=None, help="override lattice, e.g. 16,16,16,32")
     ap.add_argument("--dslash-launches", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision comparison on the 48^3x96 workload")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
                     help="host: the same CG kernels launched one by one (per-kernel profiling)")
     return ap.parse_args()
@@ -282,11 +284,17 @@ def run_native(args):
     launches_per_solve = [4 * k + 3 for k in iters]
     gpu_launches = sum(launches_per_solve) + args.dslash_launches
 
+    lat.close()
+    torch.cuda.empty_cache()
+
+    mixed = None
+    if not args.no_mixed:
+        mixed = mixed_comparison(local, rank, args.cg_launch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(dims, rank)
 
-    lat.close()
     if rank != 0:
         return None
     line = {
@@ -325,8 +333,56 @@ def run_native(args):
         "gpu_launches": gpu_launches,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "mixed_vs_fp64": mixed,
     }
     return line
+
+
+MIXED_DIMS = (48, 48, 48, 96)
+MIXED_MASS = 0.01
+MIXED_EPS = 0.35
+MIXED_DELTA = 0.1
+
+
+def mixed_comparison(local, rank, cg_launch):
+    """Time to a 1e-10 true residual on the 48^3x96, m = 0.01, eps = 0.35
+    workload: double-float CG against mixed precision (FP32 and 16-bit inner
+    iterations with double-float reliable updates, delta = 0.1).  One warm-up
+    and one timed solve each; the true residual of every returned x is
+    recomputed in double-float."""
+    import torch
+    from paper_1411_2087_gb300 import stag, synth
+    dev = torch.device("cuda", local)
+    U = synth.su3_field(MIXED_DIMS, MIXED_EPS, 1002, device=dev)
+    Vh = int(np.prod(MIXED_DIMS)) // 2
+    b = synth.gaussian_colour_field(Vh, 1102 + rank)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": f"{'x'.join(map(str, MIXED_DIMS))}, m={MIXED_MASS}, eps={MIXED_EPS}, tol=1e-10"}
+    with stag.Lattice(MIXED_DIMS, device=local, stream=stream.cuda_stream) as lat:
+        lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
+        lat.set_cg_launch(cg_launch)
+        del U
+        torch.cuda.empty_cache()
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        fr = lat.field(stag.EVEN, "df64")
+        runs = (("fp64_df64", lambda: lat.cg(fx, fb, MIXED_MASS, 1e-10, 20000)),
+                ("mixed_f32", lambda: lat.cg_mixed(fx, fb, MIXED_MASS, 1e-10, 20000, "f32", MIXED_DELTA)),
+                ("mixed_f16", lambda: lat.cg_mixed(fx, fb, MIXED_MASS, 1e-10, 20000, "f16", MIXED_DELTA)))
+        for name, fn in runs:
+            fn()
+            info = fn()
+            lat.apply_M(fr, fx, MIXED_MASS)
+            r = fr.export() - b.numpy()
+            res = float(np.linalg.norm(r) / np.linalg.norm(b.numpy()))
+            out[name] = {"seconds": round(info["seconds"], 4), "iters": info["iters"],
+                         "reliable_updates": info["restarts"], "true_rel_resid": res,
+                         "ok": info["return"] == stag.OK and res <= 1.05e-10}
+        base = out["fp64_df64"]["seconds"]
+        for name in ("mixed_f32", "mixed_f16"):
+            out[name]["speedup_vs_fp64"] = round(base / out[name]["seconds"], 3)
+    return out
 
 
 class OracleWorkload:

@@ -67,8 +67,10 @@ enum {
  *            GB300's FP64 pipe is far narrower than its FP32 pipes, and this
  *            form keeps FP64-level accuracy at FP32 throughput.
  * STAG_F32   float storage and arithmetic.
- * STAG_F16   half storage of links and vectors (vectors with one float norm
- *            per site), float arithmetic.
+ * STAG_F16   16-bit storage ("half" in the lattice-QCD sense): signed
+ *            fixed point, links with one scale per field (the largest folded
+ *            entry), colour vectors with one float norm per site; float
+ *            arithmetic.  1/32767 of the scale per entry.
  */
 enum { STAG_F64 = 0, STAG_F32 = 1, STAG_F16 = 2, STAG_DF64 = 3 };
 #define STAG_PREC_BIT(p) (1u << (p))
@@ -178,6 +180,23 @@ typedef struct {
  * iterate) or STAG_ERR_BREAKDOWN; info (may be NULL) is filled in all cases. */
 int stag_cg_solve(stag_lattice lat, stag_field x_even, const stag_field b_even,
                   double mass, double rel_tol, int max_iter, stag_solve_info *info);
+
+/* Mixed-precision CG with reliable updates (Sleijpen & van der Vorst;
+ * Clark et al. for lattice QCD): the iteration runs in `inner_prec`
+ * (STAG_F32, or STAG_F16 = 16-bit fixed-point storage with float arithmetic),
+ * and whenever the iterated residual has dropped below `delta` times its
+ * largest value since the last update (e.g. delta = 0.1), or claims
+ * convergence, the accumulated correction is added to x and the true
+ * residual b - M x is recomputed in the precision of x and b (F64 or DF64).
+ * Convergence (|b - M x| <= rel_tol |b|) is only declared on such a
+ * recomputed residual, so info->true_rel_resid is the residual of the
+ * returned x.  Needs gauge copies of both precisions.  info->iters counts
+ * inner iterations, info->restarts the reliable updates.  Dot products and
+ * the scalars of the iteration are accumulated in FP64.  Same return values
+ * as stag_cg_solve. */
+int stag_cg_solve_mixed(stag_lattice lat, stag_field x_even, const stag_field b_even,
+                        double mass, double rel_tol, int max_iter, int inner_prec,
+                        double delta, stag_solve_info *info);
 
 /* ---- allocation-free M ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -47,6 +47,11 @@ struct CgScalars {
     cudaGraphConditionalHandle cond;  // loop condition of the solve graph
     int has_cond;
     int pad2;
+    // mixed precision with reliable updates
+    double delta;    // update when |r_sloppy| < delta * rmax
+    double rmax;     // largest |r_sloppy| since the last update
+    int reliable;    // this iteration ends with a reliable update
+    int restarts;    // reliable updates so far
 };
 
 }  // namespace stag

@@ -21,7 +21,8 @@ enum Epi {
     EPI_NONE = 0,   // out = D in
     EPI_M = 1,      // out = m^2 p - D in                (M p with in = D_oe p)
     EPI_M_PAP = 2,  // as EPI_M, plus <p, out> -> alpha = rr / <p, M p>
-    EPI_RESID = 3   // r = b - (m^2 p - D in), |r|^2 -> true residual (r not stored)
+    EPI_RESID = 3,  // r = b - (m^2 p - D in), |r|^2 -> true residual (r not stored)
+    EPI_RESID_STORE = 4  // as EPI_RESID, and r stored to out
 };
 
 struct DslashArgs {
@@ -38,23 +39,9 @@ struct DslashArgs {
     dpair m2;               // EPI_M: m^2 when m2_in_args, else read from sc
     int m2_in_args;
     int skip_if_done;       // return at once when sc->status is no longer CG_RUNNING
+    const int *gate;        // if set, return at once unless *gate != 0 (uniform flag)
+    float link_scale[2];    // 16-bit links: value = q * scale (one-link, three-link)
 };
-
-template <int P>
-STAG_D void load_vec(const typename Fmt<P>::Elem *__restrict__ v, int stride, int c,
-                     cplx<typename Fmt<P>::R> w[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-        w[a] = Fmt<P>::unpack(ld_keep(v + a * stride + c));
-}
-
-template <int P>
-STAG_D void store_vec(typename Fmt<P>::Elem *__restrict__ v, int stride, int c,
-                      const cplx<typename Fmt<P>::R> w[3]) {
-#pragma unroll
-    for (int a = 0; a < 3; a++)
-        __stcs(v + a * stride + c, Fmt<P>::pack(w[a]));
-}
 
 // acc += D psi at checkerboard site c of parity par
 template <int P>
@@ -62,7 +49,7 @@ STAG_D void dslash_site(const Geom &g, int par, int c,
                         const typename Fmt<P>::Elem *__restrict__ Gout,
                         const typename Fmt<P>::Elem *__restrict__ Gin,
                         const typename Fmt<P>::Elem *__restrict__ in,
-                        cplx<typename Fmt<P>::R> acc[3]) {
+                        const float link_scale[2], cplx<typename Fmt<P>::R> acc[3]) {
     using F = Fmt<P>;
     using R = typename F::R;
     const int S = g.stride;
@@ -74,6 +61,7 @@ STAG_D void dslash_site(const Geom &g, int par, int c,
         for (int h = 0; h < 2; h++) {
             const int s = h ? 3 : 1;
             const int kind = 4 * h + mu;
+            const float ls = link_scale[h];
             // forward: + L(x) psi(x + s mu)
             {
                 const int j = cb_hop(g, c, x, mu, +s);
@@ -84,7 +72,7 @@ STAG_D void dslash_site(const Geom &g, int par, int c,
                 for (int a = 0; a < 3; a++)
 #pragma unroll
                     for (int b = 0; b < 3; b++)
-                        cmac(acc[a], F::unpack(ld_stream(Lp + (3 * a + b) * S)), v[b]);
+                        cmac(acc[a], F::unpack_link(ld_stream(Lp + (3 * a + b) * S), ls), v[b]);
             }
             // backward: - L(x - s mu)^+ psi(x - s mu)
             {
@@ -99,7 +87,7 @@ STAG_D void dslash_site(const Geom &g, int par, int c,
                 for (int a = 0; a < 3; a++)
 #pragma unroll
                     for (int b = 0; b < 3; b++)
-                        cmac_conj(acc[a], F::unpack(ld_stream(Lp + (3 * b + a) * S)), v[b]);
+                        cmac_conj(acc[a], F::unpack_link(ld_stream(Lp + (3 * b + a) * S), ls), v[b]);
             }
         }
     }
@@ -124,13 +112,15 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     // the status is uniform over the grid: either every block returns here or none
     if (a.skip_if_done && a.sc->status != CG_RUNNING)
         return;
+    if (a.gate && *a.gate == 0)
+        return;
     const int c = blockIdx.x * BLOCK + threadIdx.x;
     const int S = a.g.stride;
     double dot = 0.0;
     if (c < a.g.Vh) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
         dslash_site<P>(a.g, a.out_par, c, (const E *)a.links_out, (const E *)a.links_in,
-                       (const E *)a.in, acc);
+                       (const E *)a.in, a.link_scale, acc);
         if (EPI == EPI_NONE) {
 #pragma unroll
             for (int k = 0; k < 3; k++) {
@@ -150,7 +140,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
                 o[k].re = rnorm<R>(o[k].re);
                 o[k].im = rnorm<R>(o[k].im);
             }
-            if (EPI == EPI_RESID) {
+            if (EPI == EPI_RESID || EPI == EPI_RESID_STORE) {
                 cplx<R> bb[3];
                 load_vec<P>((const E *)a.b, S, c, bb);
 #pragma unroll
@@ -159,6 +149,8 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
                     o[k].im = rsub(bb[k].im, o[k].im);
                 }
                 dot = re_dot3<R>(o, o);
+                if (EPI == EPI_RESID_STORE)
+                    store_vec<P>((E *)a.out, S, c, o);
             } else {
                 store_vec<P>((E *)a.out, S, c, o);
                 if (EPI == EPI_M_PAP)
@@ -166,7 +158,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
             }
         }
     }
-    if (EPI == EPI_M_PAP || EPI == EPI_RESID) {
+    if (EPI == EPI_M_PAP || EPI == EPI_RESID || EPI == EPI_RESID_STORE) {
         double total;
         if (grid_sum<BLOCK>(dot, a.partial, &a.sc->ticket, smem, total) && threadIdx.x == 0) {
             CgScalars *sc = a.sc;

@@ -1,0 +1,6 @@
+// Dslash kernels instantiated for precision P_F64.
+#include "dslash_launch.cuh"
+
+namespace stag {
+template cudaError_t launch_dslash_p<P_F64>(int, const DslashArgs &, int, cudaStream_t);
+}  // namespace stag

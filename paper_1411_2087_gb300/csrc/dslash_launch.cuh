@@ -1,0 +1,33 @@
+// Launcher template of the Dslash kernels; each precision is instantiated in
+// its own translation unit (dslash_<prec>.cu) so that they compile in parallel.
+#pragma once
+#include "dslash.cuh"
+#include "kernels.h"
+
+namespace stag {
+
+template <int P, int BLOCK>
+static cudaError_t launch_p_b(int epi, const DslashArgs &a, cudaStream_t s) {
+    const int grid = dslash_grid(a.g, BLOCK);
+    if (grid == 0)
+        return cudaSuccess;
+    switch (epi) {
+    case EPI_NONE: dslash_kernel<P, EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_M: dslash_kernel<P, EPI_M, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int P> cudaError_t launch_dslash_p(int epi, const DslashArgs &a, int block, cudaStream_t s) {
+    switch (block) {
+    case 128: return launch_p_b<P, 128>(epi, a, s);
+    case 256: return launch_p_b<P, 256>(epi, a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace stag

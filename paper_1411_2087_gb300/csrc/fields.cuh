@@ -3,10 +3,11 @@
 //
 // Layout (structure of arrays, one checkerboard):
 //   colour vector   Elem v[3][stride]           component a of site c at a*stride + c
+//                   (16-bit: followed by float norm[stride], one per site)
 //   links           Elem G[2][8][9][stride]     [site parity][kind][row*3+col][cb site]
 //                   kind 0..3 = folded one-link U~_mu, 4..7 = folded three-link N~_mu
 // One Elem holds one complex number: a warp loading component j of 32
-// consecutive sites touches one contiguous 512-byte (16-byte Elem) segment.
+// consecutive sites touches one contiguous segment.
 #pragma once
 #include "common.cuh"
 
@@ -16,12 +17,8 @@ enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_DF64 = 3 };
 
 // cache hints: links stream through once (evict-first); colour vectors are
 // gathered 16 times per launch and should stay in L1/L2.
-STAG_D double2 ld_stream(const double2 *p) { return __ldcs(p); }
-STAG_D float4 ld_stream(const float4 *p) { return __ldcs(p); }
-STAG_D float2 ld_stream(const float2 *p) { return __ldcs(p); }
-STAG_D double2 ld_keep(const double2 *p) { return __ldg(p); }
-STAG_D float4 ld_keep(const float4 *p) { return __ldg(p); }
-STAG_D float2 ld_keep(const float2 *p) { return __ldg(p); }
+template <class T> STAG_D T ld_stream(const T *p) { return __ldcs(p); }
+template <class T> STAG_D T ld_keep(const T *p) { return __ldg(p); }
 
 template <int P> struct Fmt;
 
@@ -30,7 +27,9 @@ template <> struct Fmt<P_F64> {
     using R = double;
     STAG_D static cplx<R> unpack(double2 e) { return cplx<R>{e.x, e.y}; }
     STAG_D static double2 pack(const cplx<R> &c) { return make_double2(c.re, c.im); }
-    STAG_HD static double2 from_double(double re, double im) { return make_double2(re, im); }
+    STAG_D static cplx<R> make(double re, double im) { return cplx<R>{re, im}; }
+    STAG_D static cplx<R> unpack_link(double2 e, float) { return unpack(e); }
+    STAG_D static double2 pack_link(double re, double im, float) { return make_double2(re, im); }
 };
 
 template <> struct Fmt<P_DF64> {
@@ -38,10 +37,11 @@ template <> struct Fmt<P_DF64> {
     using R = df;
     STAG_D static cplx<R> unpack(float4 e) { return cplx<R>{df_make(e.x, e.y), df_make(e.z, e.w)}; }
     STAG_D static float4 pack(const cplx<R> &c) { return make_float4(c.re.hi, c.re.lo, c.im.hi, c.im.lo); }
-    STAG_HD static float4 from_double(double re, double im) {
-        df r = df_from_double(re), i = df_from_double(im);
-        return make_float4(r.hi, r.lo, i.hi, i.lo);
+    STAG_D static cplx<R> make(double re, double im) {
+        return cplx<R>{df_from_double(re), df_from_double(im)};
     }
+    STAG_D static cplx<R> unpack_link(float4 e, float) { return unpack(e); }
+    STAG_D static float4 pack_link(double re, double im, float) { return pack(make(re, im)); }
 };
 
 template <> struct Fmt<P_F32> {
@@ -49,18 +49,95 @@ template <> struct Fmt<P_F32> {
     using R = float;
     STAG_D static cplx<R> unpack(float2 e) { return cplx<R>{e.x, e.y}; }
     STAG_D static float2 pack(const cplx<R> &c) { return make_float2(c.re, c.im); }
-    STAG_HD static float2 from_double(double re, double im) { return make_float2((float)re, (float)im); }
+    STAG_D static cplx<R> make(double re, double im) { return cplx<R>{(float)re, (float)im}; }
+    STAG_D static cplx<R> unpack_link(float2 e, float) { return unpack(e); }
+    STAG_D static float2 pack_link(double re, double im, float) { return make_float2((float)re, (float)im); }
 };
 
-template <int P> STAG_HD size_t elem_bytes() { return sizeof(typename Fmt<P>::Elem); }
+// 16-bit storage: signed fixed point q = round(v / scale * 32767), float
+// arithmetic.  Links use one scale per field (the largest |entry| of the
+// folded one-link or three-link field); colour vectors one per site (the
+// largest |component| at that site), stored in a float plane after the three
+// component planes.
+constexpr float kQ16 = 32767.f;
 
-inline size_t prec_elem_bytes(int p) {
+STAG_D short q16(float v) { return (short)__float2int_rn(fminf(fmaxf(v, -kQ16), kQ16)); }
+
+template <> struct Fmt<P_F16> {
+    using Elem = short2;
+    using R = float;
+    STAG_D static cplx<R> make(double re, double im) { return cplx<R>{(float)re, (float)im}; }
+    // scale = field max / 32767
+    STAG_D static cplx<R> unpack_link(short2 e, float scale) {
+        return cplx<R>{(float)e.x * scale, (float)e.y * scale};
+    }
+    // inv_scale = 32767 / field max
+    STAG_D static short2 pack_link(double re, double im, float inv_scale) {
+        return make_short2(q16((float)re * inv_scale), q16((float)im * inv_scale));
+    }
+};
+
+// bytes of one colour-vector field / one complex link entry
+inline size_t prec_vec_bytes(int p, size_t stride) {
+    switch (p) {
+    case P_F64: return 3 * stride * sizeof(double2);
+    case P_DF64: return 3 * stride * sizeof(float4);
+    case P_F32: return 3 * stride * sizeof(float2);
+    case P_F16: return 3 * stride * sizeof(short2) + stride * sizeof(float);
+    default: return 0;
+    }
+}
+inline size_t prec_link_elem_bytes(int p) {
     switch (p) {
     case P_F64: return sizeof(double2);
     case P_DF64: return sizeof(float4);
     case P_F32: return sizeof(float2);
+    case P_F16: return sizeof(short2);
     default: return 0;
     }
+}
+
+// --------------------------------------------------------------------------
+// colour-vector loads and stores (one site, three components)
+// --------------------------------------------------------------------------
+template <int P>
+STAG_D void load_vec(const typename Fmt<P>::Elem *__restrict__ v, int stride, int c,
+                     cplx<typename Fmt<P>::R> w[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        w[a] = Fmt<P>::unpack(ld_keep(v + a * stride + c));
+}
+
+template <>
+STAG_D void load_vec<P_F16>(const short2 *__restrict__ v, int stride, int c, cplx<float> w[3]) {
+    const float *norm = (const float *)(v + 3 * stride);
+    const float s = ld_keep(norm + c) * (1.f / kQ16);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const short2 q = ld_keep(v + a * stride + c);
+        w[a] = cplx<float>{(float)q.x * s, (float)q.y * s};
+    }
+}
+
+template <int P>
+STAG_D void store_vec(typename Fmt<P>::Elem *__restrict__ v, int stride, int c,
+                      const cplx<typename Fmt<P>::R> w[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        __stcs(v + a * stride + c, Fmt<P>::pack(w[a]));
+}
+
+template <>
+STAG_D void store_vec<P_F16>(short2 *__restrict__ v, int stride, int c, const cplx<float> w[3]) {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        m = fmaxf(m, fmaxf(fabsf(w[a].re), fabsf(w[a].im)));
+    const float inv = m > 0.f ? kQ16 / m : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        __stcs(v + a * stride + c, make_short2(q16(w[a].re * inv), q16(w[a].im * inv)));
+    __stcs((float *)(v + 3 * stride) + c, m);
 }
 
 // to/from canonical complex128 for export and the double-valued epilogues
@@ -68,5 +145,19 @@ template <class R> STAG_D double to_double(R a);
 template <> STAG_D double to_double<double>(double a) { return a; }
 template <> STAG_D double to_double<float>(float a) { return (double)a; }
 template <> STAG_D double to_double<df>(df a) { return df_to_double(a); }
+
+// convert between arithmetic types (used when one kernel reads two precisions)
+template <class RO, class RI> STAG_D RO rconv(RI a);
+template <> STAG_D double rconv<double, double>(double a) { return a; }
+template <> STAG_D double rconv<double, float>(float a) { return (double)a; }
+template <> STAG_D float rconv<float, double>(double a) { return (float)a; }
+template <> STAG_D float rconv<float, float>(float a) { return a; }
+template <> STAG_D df rconv<df, df>(df a) { return a; }
+template <> STAG_D df rconv<df, float>(float a) { return df_make(a, 0.f); }
+template <> STAG_D float rconv<float, df>(df a) { return a.hi + a.lo; }
+
+template <class RO, class RI> STAG_D cplx<RO> cconv(const cplx<RI> &a) {
+    return cplx<RO>{rconv<RO, RI>(a.re), rconv<RO, RI>(a.im)};
+}
 
 }  // namespace stag

@@ -29,11 +29,28 @@ cudaError_t launch_export(int prec, const Geom &g, const void *field, double *ca
 
 // fold c1/c3, Kogut-Susskind phases and boundary signs into the canonical
 // fat/long links (device, complex128 [4][V][3][3]) and lay them out per parity
+// (inv_scale: 16-bit links only, 32767 / largest |entry| of the folded
+// one-link and three-link fields; ignored otherwise)
 cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], double c1, double c3,
-                              const double *fat, const double *lng, void *links, cudaStream_t s);
+                              const double *fat, const double *lng, void *links,
+                              const float inv_scale[2], cudaStream_t s);
+
+// largest |re| / |im| over n doubles, as float bits in *out (device)
+cudaError_t launch_absmax(const double *a, long long n, unsigned *out, cudaStream_t s);
 
 // three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu), canonical layout
 cudaError_t launch_long_links(const Geom &g, const double *fat, double *lng, cudaStream_t s);
+
+// mixed-precision CG with reliable updates: hi = F64 or DF64 (x, r, b),
+// lo = F32 or F16 (p, Ap, r_sloppy), x_sloppy always F32
+cudaError_t launch_mixed_init(int hi, int lo, const Geom &g, void *x, void *r, const void *b, float *xs,
+                              void *rs, void *p, double *partial, CgScalars *sc, cudaStream_t s);
+cudaError_t launch_mixed_update(int lo, const Geom &g, float *xs, void *rs, const void *p, const void *Ap,
+                                double *partial, CgScalars *sc, cudaStream_t s);
+cudaError_t launch_mixed_accum(int hi, const Geom &g, void *x, float *xs, const CgScalars *sc,
+                               cudaStream_t s);
+cudaError_t launch_mixed_restart(int hi, int lo, const Geom &g, const void *r, void *rs, CgScalars *sc,
+                                 cudaStream_t s);
 
 // record the calling thread's last error message (read back by
 // stag_last_error_message) and return `code`

@@ -144,6 +144,7 @@ static int cg_grid(const Geom &g) { return (g.Vh + CG_BLOCK - 1) / CG_BLOCK; }
     case P_F64: { constexpr int P = P_F64; __VA_ARGS__; } break;      \
     case P_DF64: { constexpr int P = P_DF64; __VA_ARGS__; } break;    \
     case P_F32: { constexpr int P = P_F32; __VA_ARGS__; } break;      \
+    case P_F16: { constexpr int P = P_F16; __VA_ARGS__; } break;      \
     default: return cudaErrorInvalidValue;                            \
     }
 
@@ -181,15 +182,15 @@ cudaError_t launch_cg_p_update(int prec, const Geom &g, const void *r, void *p,
 // --------------------------------------------------------------------------
 template <int P>
 __global__ void import_kernel(Geom g, const double *__restrict__ canon, typename Fmt<P>::Elem *f) {
+    using R = typename Fmt<P>::R;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.Vh)
         return;
+    cplx<R> w[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const double re = canon[(3 * (size_t)c + a) * 2];
-        const double im = canon[(3 * (size_t)c + a) * 2 + 1];
-        f[a * g.stride + c] = Fmt<P>::from_double(re, im);
-    }
+    for (int a = 0; a < 3; a++)
+        w[a] = Fmt<P>::make(canon[(3 * (size_t)c + a) * 2], canon[(3 * (size_t)c + a) * 2 + 1]);
+    store_vec<P>(f, g.stride, c, w);
 }
 
 template <int P>
@@ -198,11 +199,12 @@ __global__ void export_kernel(Geom g, const typename Fmt<P>::Elem *f, double *__
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.Vh)
         return;
+    cplx<R> w[3];
+    load_vec<P>(f, g.stride, c, w);
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        cplx<R> v = Fmt<P>::unpack(f[a * g.stride + c]);
-        canon[(3 * (size_t)c + a) * 2] = to_double<R>(v.re);
-        canon[(3 * (size_t)c + a) * 2 + 1] = to_double<R>(v.im);
+        canon[(3 * (size_t)c + a) * 2] = to_double<R>(w[a].re);
+        canon[(3 * (size_t)c + a) * 2 + 1] = to_double<R>(w[a].im);
     }
 }
 
@@ -231,6 +233,7 @@ struct FoldArgs {
     Geom g;
     double bc[4];
     double c1, c3;
+    float inv_scale[2];  // 16-bit links: 32767 / field max (one-link, three-link)
 };
 
 STAG_D void full_coords(const Geom &g, long long i, int x[4]) {
@@ -271,13 +274,17 @@ __global__ void fold_kernel(FoldArgs fa, const double *__restrict__ fat, const d
     const double *src = (three ? lng : fat) + ((size_t)mu * V + i) * 18;
     typename Fmt<P>::Elem *dst = G + ((size_t)par * 8 + kind) * 9 * g.stride + cb;
     for (int j = 0; j < 9; j++)
-        dst[(size_t)j * g.stride] = Fmt<P>::from_double(coef * src[2 * j], coef * src[2 * j + 1]);
+        dst[(size_t)j * g.stride] =
+            Fmt<P>::pack_link(coef * src[2 * j], coef * src[2 * j + 1], fa.inv_scale[three ? 1 : 0]);
 }
 
 cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], double c1, double c3,
-                              const double *fat, const double *lng, void *links, cudaStream_t s) {
+                              const double *fat, const double *lng, void *links,
+                              const float inv_scale[2], cudaStream_t s) {
     FoldArgs fa;
     fa.g = g;
+    fa.inv_scale[0] = inv_scale ? inv_scale[0] : 0.f;
+    fa.inv_scale[1] = inv_scale ? inv_scale[1] : 0.f;
     for (int k = 0; k < 4; k++)
         fa.bc[k] = bc[k];
     fa.c1 = c1;
@@ -287,6 +294,30 @@ cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], doubl
     STAG_PREC_SWITCH(prec, {
         fold_kernel<P><<<grid, 256, 0, s>>>(fa, fat, lng, (typename Fmt<P>::Elem *)links);
     });
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// largest |re| or |im| of a canonical link field (for the 16-bit scales);
+// non-negative floats order like their bit patterns, so atomicMax on the
+// bits finds the maximum
+// --------------------------------------------------------------------------
+__global__ void absmax_kernel(const double *__restrict__ a, long long n, unsigned *out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, (float)fabs(a[i]));
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_absmax(const double *a, long long n, unsigned *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    absmax_kernel<<<1024, 256, 0, s>>>(a, n, out);
     return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -81,7 +82,9 @@ struct DeviceGuard {
     if (guard_.err)                                                              \
         return fail(STAG_ERR_CUDA, "cannot make CUDA device %d current", (dev));
 
-static bool prec_valid(int p) { return p == STAG_F64 || p == STAG_DF64 || p == STAG_F32; }
+static bool prec_valid(int p) {
+    return p == STAG_F64 || p == STAG_DF64 || p == STAG_F32 || p == STAG_F16;
+}
 static const char *prec_name(int p) {
     switch (p) {
     case STAG_F64: return "F64";
@@ -122,6 +125,14 @@ struct stag_lattice_s {
     CgWork cg[4];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double *staging = nullptr;
+    float link_scale[2] = {0.f, 0.f};      // 16-bit links: field max / 32767 (one-link, three-link)
+    float *xs = nullptr;                   // F32 correction x_sloppy of the mixed solver
+    unsigned *absmax = nullptr;            // scratch for the 16-bit link scales
+    struct MixedGraph {
+        cudaGraphExec_t exec = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphConditionalHandle cond = 0;
+    } mixed[4][4];
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
     int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
 };
@@ -135,14 +146,14 @@ struct stag_field_s {
 };
 
 static size_t field_bytes(const stag_lattice lat, int prec) {
-    return 3ull * lat->geom.stride * prec_elem_bytes(prec);
+    return prec_vec_bytes(prec, (size_t)lat->geom.stride);
 }
 static size_t link_bytes(const stag_lattice lat, int prec) {
-    return 2ull * 8 * 9 * lat->geom.stride * prec_elem_bytes(prec);
+    return 2ull * 8 * 9 * lat->geom.stride * prec_link_elem_bytes(prec);
 }
 static const void *links_of(const stag_lattice lat, int prec, int parity) {
     const char *base = (const char *)lat->links[prec];
-    return base + (size_t)parity * 8 * 9 * lat->geom.stride * prec_elem_bytes(prec);
+    return base + (size_t)parity * 8 * 9 * lat->geom.stride * prec_link_elem_bytes(prec);
 }
 
 // --------------------------------------------------------------------------
@@ -264,6 +275,17 @@ extern "C" int stag_lattice_destroy(stag_lattice lat) {
         cudaFree(lat->partial);
     if (lat->staging)
         cudaFree(lat->staging);
+    if (lat->xs)
+        cudaFree(lat->xs);
+    if (lat->absmax)
+        cudaFree(lat->absmax);
+    for (int h = 0; h < 4; h++)
+        for (int l = 0; l < 4; l++) {
+            if (lat->mixed[h][l].exec)
+                cudaGraphExecDestroy(lat->mixed[h][l].exec);
+            if (lat->mixed[h][l].graph)
+                cudaGraphDestroy(lat->mixed[h][l].graph);
+        }
     if (lat->sc)
         cudaFree(lat->sc);
     if (lat->sc_host)
@@ -299,6 +321,18 @@ extern "C" int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk)
     if (mode == STAG_CG_LAUNCH_HOST)
         lat->cg_chunk = chunk;
     return STAG_OK;
+}
+
+static void drop_mixed_graphs(stag_lattice lat) {
+    for (int h = 0; h < 4; h++)
+        for (int l = 0; l < 4; l++) {
+            auto &m = lat->mixed[h][l];
+            if (m.exec)
+                cudaGraphExecDestroy(m.exec);
+            if (m.graph)
+                cudaGraphDestroy(m.graph);
+            m = stag_lattice_s::MixedGraph();
+        }
 }
 
 // --------------------------------------------------------------------------
@@ -378,7 +412,35 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
             lat->links[p] = nullptr;
         }
     }
+    drop_mixed_graphs(lat);
     lat->has_gauge = false;
+    float inv_scale[2] = {0.f, 0.f};
+    if ((prec_mask >> STAG_F16) & 1u) {
+        // 16-bit links: one scale per field, the largest |entry| after folding
+        cudaError_t e = lat->absmax ? cudaSuccess : cudaMalloc(&lat->absmax, 2 * sizeof(unsigned));
+        const long long n = 4LL * lat->V * 18;
+        if (e == cudaSuccess)
+            e = launch_absmax(fat_d, n, lat->absmax, lat->stream);
+        if (e == cudaSuccess)
+            e = launch_absmax(lng_d, n, lat->absmax + 1, lat->stream);
+        unsigned bits[2] = {0u, 0u};
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bits, lat->absmax, sizeof bits, cudaMemcpyDeviceToHost, lat->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(lat->stream);
+        if (e != cudaSuccess) {
+            release();
+            return fail(STAG_ERR_CUDA, "16-bit link scales: %s", cudaGetErrorString(e));
+        }
+        const double cf[2] = {std::fabs(c1), std::fabs(c3)};
+        for (int h = 0; h < 2; h++) {
+            float m;
+            memcpy(&m, &bits[h], sizeof m);
+            const double mx = (double)m * cf[h];
+            lat->link_scale[h] = mx > 0 ? (float)(mx / 32767.0) : 0.f;
+            inv_scale[h] = mx > 0 ? (float)(32767.0 / mx) : 0.f;
+        }
+    }
     for (int p = 0; p < 4; p++) {
         if (!((prec_mask >> p) & 1u))
             continue;
@@ -386,7 +448,8 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         if (e == cudaSuccess)
             e = cudaMemsetAsync(lat->links[p], 0, link_bytes(lat, p), lat->stream);
         if (e == cudaSuccess)
-            e = launch_fold_links(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links[p], lat->stream);
+            e = launch_fold_links(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links[p], inv_scale,
+                                  lat->stream);
         if (e != cudaSuccess) {
             release();
             return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,
@@ -579,6 +642,10 @@ static DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, const voi
     a.out = out;
     a.partial = lat->partial;
     a.sc = lat->sc;
+    if (prec == STAG_F16) {
+        a.link_scale[0] = lat->link_scale[0];
+        a.link_scale[1] = lat->link_scale[1];
+    }
     return a;
 }
 
@@ -620,7 +687,7 @@ static int ensure_cg_work(stag_lattice lat, int prec) {
 }
 
 static int upload_scalars(stag_lattice lat, double mass, double tol, int max_iter, bool has_cond,
-                          cudaGraphConditionalHandle cond) {
+                          cudaGraphConditionalHandle cond, double delta = 0.0) {
     // pageable source: the copy has read it when cudaMemcpyAsync returns
     CgScalars h;
     memset(&h, 0, sizeof h);
@@ -629,6 +696,7 @@ static int upload_scalars(stag_lattice lat, double mass, double tol, int max_ite
     h.max_iter = max_iter;
     h.has_cond = has_cond ? 1 : 0;
     h.cond = cond;
+    h.delta = delta;
     CUDA_TRY(cudaMemcpyAsync(lat->sc, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
     return STAG_OK;
 }
@@ -861,6 +929,218 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
         return fail(local.status, "stag_cg_solve: %s after %d iterations (|r|/|b| = %.3e)",
                     local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
                     local.iter_rel_resid);
+    return STAG_OK;
+}
+
+
+// --------------------------------------------------------------------------
+// mixed-precision CG with reliable updates (kernels_mixed.cu has the method)
+// --------------------------------------------------------------------------
+static const int *reliable_flag(stag_lattice lat) {
+    return (const int *)((const char *)lat->sc + offsetof(CgScalars, reliable));
+}
+
+static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool host_mode) {
+    CgWork &H = lat->cg[hi];
+    CgWork &L = lat->cg[lo];
+    cudaStream_t s = lat->stream;
+    const Geom &g = lat->geom;
+    cudaError_t e;
+    // low precision: t_s = D_oe p; Ap = m^2 p - D_eo t_s, alpha
+    DslashArgs a1 = dslash_args(lat, lo, STAG_ODD, L.p, L.t);
+    a1.skip_if_done = host_mode;
+    if ((e = launch_dslash(lo, EPI_NONE, a1, 0, s)) != cudaSuccess)
+        return e;
+    DslashArgs a2 = dslash_args(lat, lo, STAG_EVEN, L.t, L.Ap);
+    a2.p = L.p;
+    a2.skip_if_done = host_mode;
+    if ((e = launch_dslash(lo, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_mixed_update(lo, g, lat->xs, L.r, L.p, L.Ap, lat->partial, lat->sc, s)) != cudaSuccess)
+        return e;
+    // reliable update (every kernel returns at once unless it is due)
+    if ((e = launch_mixed_accum(hi, g, H.xw, lat->xs, lat->sc, s)) != cudaSuccess)
+        return e;
+    DslashArgs a3 = dslash_args(lat, hi, STAG_ODD, H.xw, H.t);
+    a3.gate = reliable_flag(lat);
+    if ((e = launch_dslash(hi, EPI_NONE, a3, 0, s)) != cudaSuccess)
+        return e;
+    DslashArgs a4 = dslash_args(lat, hi, STAG_EVEN, H.t, H.r);
+    a4.p = H.xw;
+    a4.b = H.bw;
+    a4.gate = reliable_flag(lat);
+    if ((e = launch_dslash(hi, EPI_RESID_STORE, a4, 0, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_mixed_restart(hi, lo, g, H.r, L.r, lat->sc, s)) != cudaSuccess)
+        return e;
+    return launch_cg_p_update(lo, g, L.r, L.p, lat->sc, s);
+}
+
+static cudaError_t enqueue_mixed_init(stag_lattice lat, int hi, int lo) {
+    CgWork &H = lat->cg[hi];
+    CgWork &L = lat->cg[lo];
+    return launch_mixed_init(hi, lo, lat->geom, H.xw, H.r, H.bw, lat->xs, L.r, L.p, lat->partial,
+                             lat->sc, lat->stream);
+}
+
+static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
+    auto &mg = lat->mixed[hi][lo];
+    cudaStream_t s = lat->stream;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
+    }
+    auto bail = [&](const char *what, cudaError_t err) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+        }
+        cudaGetLastError();
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "mixed CG graph (%s): %s", what, cudaGetErrorString(err));
+    };
+    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin capture", e);
+    if ((e = enqueue_mixed_init(lat, hi, lo)) != cudaSuccess)
+        return bail("init", e);
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return bail("capture info", e);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+        return bail("add loop node", e);
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return bail("update deps", e);
+    cudaGraph_t captured = nullptr;
+    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
+        return bail("end capture", e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin body capture", e);
+    if ((e = enqueue_mixed_body(lat, hi, lo, false)) != cudaSuccess)
+        return bail("body", e);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
+        return bail("end body capture", e);
+    cudaGraphExec_t exec = nullptr;
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        return bail("instantiate", e);
+    mg.graph = graph;
+    mg.exec = exec;
+    mg.cond = cond;
+    return STAG_OK;
+}
+
+extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_field b, double mass,
+                                   double rel_tol, int max_iter, int inner_prec, double delta,
+                                   stag_solve_info *info) {
+    if (info)
+        memset(info, 0, sizeof *info);
+    if (!lat || !x || !b)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: NULL argument");
+    if (x->lat != lat || b->lat != lat)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: field belongs to another lattice");
+    if (x->parity != STAG_EVEN || b->parity != STAG_EVEN)
+        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: x and b must be even fields");
+    if (x->prec != b->prec || (x->prec != STAG_F64 && x->prec != STAG_DF64))
+        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: x and b must both be F64 or both DF64");
+    if (x == b)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: x and b must differ");
+    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: inner precision must be F32 or F16");
+    if (!(mass > 0) || !std::isfinite(mass))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: mass must be positive and finite");
+    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: rel_tol must be >= 0");
+    if (max_iter < 0)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: max_iter must be >= 0");
+    if (!(delta > 0 && delta < 1))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: delta must be in (0, 1)");
+    const int hi = x->prec, lo = inner_prec;
+    if (!lat->has_gauge || !lat->links[hi] || !lat->links[lo])
+        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: needs %s and %s gauge copies", prec_name(hi),
+                    prec_name(lo));
+    DEVICE_SCOPE(lat->device);
+    STAG_TRY(ensure_cg_work(lat, hi));
+    STAG_TRY(ensure_cg_work(lat, lo));
+    if (!lat->xs) {
+        CUDA_TRY(cudaMalloc(&lat->xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
+        CUDA_TRY(cudaMemsetAsync(lat->xs, 0, prec_vec_bytes(STAG_F32, lat->geom.stride), lat->stream));
+    }
+    CgWork &H = lat->cg[hi];
+    cudaStream_t s = lat->stream;
+    CUDA_TRY(cudaMemcpyAsync(H.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
+        auto &mg = lat->mixed[hi][lo];
+        if (!mg.exec)
+            STAG_TRY(build_mixed_graph(lat, hi, lo));
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(cudaGraphLaunch(mg.exec, s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    } else {
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0, delta));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(enqueue_mixed_init(lat, hi, lo));
+        const int chunk = lat->cg_chunk;
+        const long long max_chunks = (long long)max_iter / chunk + 2;
+        for (long long k = 0; k < max_chunks; k++) {
+            CUDA_TRY(cudaMemcpyAsync(&lat->sc_host->status, &lat->sc->status, sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (lat->sc_host->status != CG_RUNNING)
+                break;
+            for (int j = 0; j < chunk; j++)
+                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true));
+        }
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(x->data, H.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+    const CgScalars &h = *lat->sc_host;
+    stag_solve_info local;
+    memset(&local, 0, sizeof local);
+    local.iters = h.iter;
+    local.restarts = h.restarts;
+    local.status = h.status == CG_CONVERGED ? STAG_OK
+                   : h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
+                                              : STAG_ERR_NOT_CONVERGED;
+    local.true_rel_resid = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+    local.iter_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    local.seconds = ms * 1e-3;
+    // model: low-precision iterations plus one high-precision M per update
+    const double lo_real = lo == STAG_F16 ? 2.0 : 4.0;
+    const double Vh = (double)lat->Vh;
+    const double bytes = h.iter * ((2.0 * 300 + 60) * lo_real + (lo == STAG_F16 ? 2 * 2 * 4 : 0) + 48) * Vh +
+                         h.restarts * (2.0 * 2400 + 4 * 48) * Vh;
+    const double flops = h.iter * (2.0 * 1146 + 72) * Vh + h.restarts * (2.0 * 1146 + 24) * Vh;
+    if (ms > 0) {
+        local.gflops = flops / (ms * 1e-3) / 1e9;
+        local.gbs = bytes / (ms * 1e-3) / 1e9;
+    }
+    if (info)
+        *info = local;
+    if (local.status != STAG_OK)
+        return fail(local.status, "stag_cg_solve_mixed: %s after %d iterations (true |r|/|b| = %.3e)",
+                    local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
+                    local.true_rel_resid);
     return STAG_OK;
 }
 

@@ -49,7 +49,7 @@ EXPORTED = [
     "stag_field_create", "stag_field_destroy", "stag_field_import", "stag_field_export",
     "stag_field_zero", "stag_field_storage",
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
-    "stag_cg_solve", "stag_apply_M_noalloc",
+    "stag_cg_solve", "stag_cg_solve_mixed", "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -109,6 +109,7 @@ def lib():
             "stag_apply_M": ([P, P, P, D], I),
             "stag_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_apply_M_noalloc": ([P, P, D, D, P, P, D, P, P, P], I),
+            "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
             "stag_version": ([], ctypes.c_char_p),
@@ -284,6 +285,18 @@ class Lattice:
         info = SolveInfo()
         st = lib().stag_cg_solve(self.handle, x.handle, b.handle, float(mass), float(tol),
                                  int(max_iter), ctypes.byref(info))
+        if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def cg_mixed(self, x: Field, b: Field, mass: float, tol: float = 1e-10, max_iter: int = 20000,
+                 inner="f32", delta: float = 0.1, raise_on_failure: bool = False) -> dict:
+        info = SolveInfo()
+        ip = PREC[inner] if isinstance(inner, str) else int(inner)
+        st = lib().stag_cg_solve_mixed(self.handle, x.handle, b.handle, float(mass), float(tol),
+                                       int(max_iter), ip, float(delta), ctypes.byref(info))
         if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(st)
         d = info.as_dict()

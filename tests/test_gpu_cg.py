@@ -141,3 +141,64 @@ def test_host_launch_mode_is_identical(prec):
         assert info_h["return"] == stag.ERR_NOT_CONVERGED and info_h["iters"] == 5
         with pytest.raises(stag.StagError):
             lat.set_cg_launch("host", 0)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision with reliable updates
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("outer,inner", [("df64", "f32"), ("df64", "f16"), ("f64", "f32"),
+                                         ("f64", "f16")])
+@pytest.mark.parametrize("dims,mass", [((8, 8, 8, 8), 0.1), ((6, 4, 6, 10), 0.02)])
+def test_mixed_cg_reaches_true_residual(dims, mass, outer, inner):
+    U, N = fields(dims, 0.35, 1002)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 1102).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(outer, inner))
+        fb = lat.field(stag.EVEN, outer, b)
+        fx = lat.field(stag.EVEN, outer)
+        info = lat.cg_mixed(fx, fb, mass, 1e-10, 20000, inner=inner, delta=0.1)
+        x = fx.export()
+    assert info["return"] == stag.OK, info
+    res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
+    assert res <= 1e-10 * 1.05, (res, info)
+    # the reported residual is the recomputed one of the returned x
+    assert abs(info["true_rel_resid"] - res) <= 1e-2 * res
+    assert info["restarts"] >= 1
+
+
+def test_mixed_host_mode_identical_and_edges():
+    dims = (6, 4, 6, 10)
+    U, N = fields(dims, 0.35, 7)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 8).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("df64", "f16"))
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        ig = lat.cg_mixed(fx, fb, 0.05, 1e-10, 5000, inner="f16")
+        xg = fx.export()
+        lat.set_cg_launch("host", 5)
+        ih = lat.cg_mixed(fx, fb, 0.05, 1e-10, 5000, inner="f16")
+        assert ih["iters"] == ig["iters"] and ih["restarts"] == ig["restarts"]
+        assert np.array_equal(fx.export(), xg)
+        lat.set_cg_launch("graph")
+        # zero source
+        fz = lat.field(stag.EVEN, "df64", np.zeros((Vh, 3), complex))
+        iz = lat.cg_mixed(fx, fz, 0.05, 1e-10, 100, inner="f16")
+        assert iz["return"] == stag.OK and iz["iters"] == 0 and not np.any(fx.export())
+        # iteration limit: x is the last reliably updated iterate, its true
+        # residual is the reported one
+        il = lat.cg_mixed(fx, fb, 0.01, 1e-14, 7, inner="f16")
+        assert il["return"] == stag.ERR_NOT_CONVERGED and il["iters"] == 7
+        r = np.linalg.norm(b - oracle.apply_M(dims, U, N, 0.01, fx.export())) / np.linalg.norm(b)
+        assert abs(r - il["true_rel_resid"]) <= 1e-6 * r
+        # argument errors
+        with pytest.raises(stag.StagError):
+            lat.cg_mixed(fx, fb, 0.05, 1e-10, 100, inner="f16", delta=1.5, raise_on_failure=True)
+        with pytest.raises(stag.StagError):
+            lat.cg_mixed(fx, fb, 0.05, 1e-10, 100, inner="df64", raise_on_failure=True)
+        f32x = lat.field(stag.EVEN, "f32")
+        with pytest.raises(stag.StagError):  # no F32 gauge copy uploaded
+            lat.cg_mixed(fx, fb, 0.05, 1e-10, 100, inner="f32", raise_on_failure=True)

@@ -2,8 +2,10 @@
 element, through the C ABI.
 
 Tolerance: max|gpu - oracle| / max|oracle| <= 1e-12 for FP64 and the
-double-float form (the FP64 target); FP32 results are held to 2e-6 and their
-error against FP64 is stated in the assertion message.
+double-float form (the FP64 target).  Reduced precisions are held to bounds
+derived from their storage: FP32 (24-bit significand, 16 products summed)
+to 2e-6, 16-bit fixed point (1/32767 of the link-field and per-site vector
+scales) to 3e-4; the assertion message states the error against FP64.
 """
 import numpy as np
 import pytest
@@ -13,7 +15,7 @@ from paper_1411_2087_gb300 import stag, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "f16": 3e-4}
 
 # 2^4 and 4^4 alias the +-1/+-3 hops; (6,4,6,10) has Vh = 720: several
 # blocks and a ragged tail; 8^4 has all 16 neighbours distinct.
@@ -33,12 +35,12 @@ def setup(request):
     psi_e = synth.gaussian_colour_field(Vh, 1100).numpy()
     psi_o = synth.gaussian_colour_field(Vh, 1101).numpy()
     lat = stag.Lattice(dims)
-    lat.upload_gauge(U, N, precisions=("f64", "df64", "f32"))
+    lat.upload_gauge(U, N, precisions=("f64", "df64", "f32", "f16"))
     yield dims, U, N, psi_e, psi_o, lat
     lat.close()
 
 
-@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 def test_dslash_both_parities(setup, prec):
     dims, U, N, psi_e, psi_o, lat = setup
     fe = lat.field(stag.EVEN, prec, psi_e)
@@ -72,6 +74,13 @@ def test_import_export_roundtrip(setup):
     f = lat.field(stag.EVEN, "f64", psi_e)
     assert np.array_equal(f.export(), psi_e)
     f.destroy()
+    h = lat.field(stag.EVEN, "f16", psi_e)
+    # per-site norm, 1/32767 quantum, rounding to nearest: half a quantum
+    site_max = np.maximum(np.abs(psi_e.real), np.abs(psi_e.imag)).max(axis=1)
+    d = h.export() - psi_e
+    bound = site_max[:, None] * (0.5 / 32767) * 1.001 + 1e-12
+    assert np.all(np.abs(d.real) <= bound) and np.all(np.abs(d.imag) <= bound)
+    h.destroy()
     g = lat.field(stag.EVEN, "df64", psi_e)
     # double-float keeps about 48 bits
     assert np.abs(g.export() - psi_e).max() <= 2.0 ** -47 * np.abs(psi_e).max()
