@@ -198,6 +198,33 @@ int stag_cg_solve_mixed(stag_lattice lat, stag_field x_even, const stag_field b_
                         double mass, double rel_tol, int max_iter, int inner_prec,
                         double delta, stag_solve_info *info);
 
+/* Multi-shift CG (Jegerlehner's shifted Krylov method; the paper's Sec. 3
+ * benchmarks MILC's HISQ multishift solver with 9 or 11 shifts): solves
+ * (M + shifts[s]) xs[s] = b for s = 0..n-1 (1 <= n <= 32, shifts >= 0, any
+ * order) with one Dslash pair per iteration, all systems sharing the Krylov
+ * space of the smallest shift.  A shifted system stops updating once its
+ * residual zeta_s |r| meets rel_tol |b|; the solve ends when all have.
+ * xs[s] and b: distinct even fields of one precision (F64, DF64 or F32) with
+ * a gauge copy of that precision.  infos (may be NULL) receives n entries:
+ * per shift the iterations until it met the tolerance and the recomputed
+ * true residual |b - (M + shifts[s]) xs[s]| / |b|; infos[0] also carries the
+ * model GB/s and GFLOP/s of the whole solve. */
+int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                       const stag_field b, double mass, double rel_tol, int max_iter,
+                       stag_solve_info *infos);
+
+/* Multi-shift CG in FP32 to max(rel_tol, 1e-5), then every shift refined to
+ * rel_tol by stag_cg_solve_mixed-style reliable-update CG (inner_prec F32 or
+ * F16, delta) on its own residual, the correction added in the precision of
+ * xs and b (F64 or DF64).  Needs gauge copies of that precision, F32 and
+ * inner_prec.  infos[s]: iters = multi-shift iterations, restarts =
+ * refinement iterations, iter_rel_resid = residual after the FP32 phase,
+ * true_rel_resid = final recomputed residual, seconds = wall time of the
+ * whole call. */
+int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                             const stag_field b, double mass, double rel_tol, int max_iter,
+                             int inner_prec, double delta, stag_solve_info *infos);
+
 /* ---- allocation-free M ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: code invoked while its caller captures

@@ -52,6 +52,29 @@ struct CgScalars {
     double rmax;     // largest |r_sloppy| since the last update
     int reliable;    // this iteration ends with a reliable update
     int restarts;    // reliable updates so far
+    // multi-shift CG: the base CG's previous alpha and beta
+    double alpha_prev, beta_prev;
+};
+
+// multi-shift CG
+constexpr int MS_MAX = 32;
+
+struct ShiftState {
+    double zeta_prev, zeta;        // zeta_{k-1}, zeta_k
+    dpair zeta_next;               // zeta_{k+1}, read by the direction update
+    dpair alpha_s, beta_s;         // alpha^s_k, beta^s_k
+    int active;                    // still iterating
+    int iters;                     // iterations until this shift met the tolerance
+};
+
+struct MsArgs {
+    int n;                         // number of shifts
+    int base;                      // index of the smallest shift
+    double delta[MS_MAX];          // sigma_s - sigma_base >= 0
+    void *x[MS_MAX];               // solutions
+    void *p[MS_MAX];               // search directions
+    const void *b;                 // right-hand side
+    void *r;                       // residual of the base system
 };
 
 }  // namespace stag

@@ -52,6 +52,17 @@ cudaError_t launch_mixed_accum(int hi, const Geom &g, void *x, float *xs, const 
 cudaError_t launch_mixed_restart(int hi, int lo, const Geom &g, const void *r, void *rs, CgScalars *sc,
                                  cudaStream_t s);
 
+// multi-shift CG (kernels_multishift.cu) and vector helpers
+cudaError_t launch_ms_init(int prec, const Geom &g, const MsArgs &a, double *partial, CgScalars *sc,
+                           ShiftState *st, cudaStream_t s);
+cudaError_t launch_ms_update(int prec, const Geom &g, const MsArgs &a, const void *Ap, double *partial,
+                             CgScalars *sc, ShiftState *st, cudaStream_t s);
+cudaError_t launch_ms_p(int prec, const Geom &g, const MsArgs &a, const CgScalars *sc,
+                        const ShiftState *st, cudaStream_t s);
+cudaError_t launch_axpy1(int prec, const Geom &g, const void *x, void *y, cudaStream_t s);
+cudaError_t launch_convert(int prec_out, int prec_in, const Geom &g, const void *in, void *out,
+                           cudaStream_t s);
+
 // record the calling thread's last error message (read back by
 // stag_last_error_message) and return `code`
 int set_error(int code, const char *fmt, ...);

@@ -2,6 +2,7 @@
 // solve graph.  Declarations and documentation are in include/stag.h.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -133,6 +134,16 @@ struct stag_lattice_s {
         cudaGraph_t graph = nullptr;
         cudaGraphConditionalHandle cond = 0;
     } mixed[4][4];
+    // multi-shift CG
+    ShiftState *ms_state = nullptr;        // device, MS_MAX entries
+    ShiftState *ms_state_host = nullptr;   // pinned mirror
+    double *ms_true = nullptr;             // device, |b - (M + sigma_s) x_s|^2 per shift
+    double *ms_true_host = nullptr;        // pinned mirror
+    void *ms_p[4][MS_MAX] = {};            // search directions per precision
+    void *ms_xlo[MS_MAX] = {};             // FP32 solutions of the sloppy multi-shift phase
+    void *ms_blo = nullptr;                // FP32 right-hand side of that phase
+    void *ms_rhi[4] = {};                  // residual of one shift (high precision)
+    void *ms_ehi[4] = {};                  // correction of one shift (high precision)
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
     int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
 };
@@ -277,6 +288,28 @@ extern "C" int stag_lattice_destroy(stag_lattice lat) {
         cudaFree(lat->staging);
     if (lat->xs)
         cudaFree(lat->xs);
+    if (lat->ms_state)
+        cudaFree(lat->ms_state);
+    if (lat->ms_state_host)
+        cudaFreeHost(lat->ms_state_host);
+    if (lat->ms_true)
+        cudaFree(lat->ms_true);
+    if (lat->ms_true_host)
+        cudaFreeHost(lat->ms_true_host);
+    for (int q = 0; q < 4; q++) {
+        for (int k = 0; k < MS_MAX; k++)
+            if (lat->ms_p[q][k])
+                cudaFree(lat->ms_p[q][k]);
+        if (lat->ms_rhi[q])
+            cudaFree(lat->ms_rhi[q]);
+        if (lat->ms_ehi[q])
+            cudaFree(lat->ms_ehi[q]);
+    }
+    for (int k = 0; k < MS_MAX; k++)
+        if (lat->ms_xlo[k])
+            cudaFree(lat->ms_xlo[k]);
+    if (lat->ms_blo)
+        cudaFree(lat->ms_blo);
     if (lat->absmax)
         cudaFree(lat->absmax);
     for (int h = 0; h < 4; h++)
@@ -1045,6 +1078,80 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
     return STAG_OK;
 }
 
+// the mixed solver on raw buffers of precision hi (x_data, b_data: bytes each);
+// arguments already checked
+static int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *b_data,
+                           size_t bytes, double mass, double rel_tol, int max_iter, double delta,
+                           stag_solve_info *info) {
+    STAG_TRY(ensure_cg_work(lat, hi));
+    STAG_TRY(ensure_cg_work(lat, lo));
+    if (!lat->xs) {
+        CUDA_TRY(cudaMalloc(&lat->xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
+        CUDA_TRY(cudaMemsetAsync(lat->xs, 0, prec_vec_bytes(STAG_F32, lat->geom.stride), lat->stream));
+    }
+    CgWork &H = lat->cg[hi];
+    cudaStream_t s = lat->stream;
+    CUDA_TRY(cudaMemcpyAsync(H.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
+    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
+        auto &mg = lat->mixed[hi][lo];
+        if (!mg.exec)
+            STAG_TRY(build_mixed_graph(lat, hi, lo));
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(cudaGraphLaunch(mg.exec, s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    } else {
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0, delta));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        CUDA_TRY(enqueue_mixed_init(lat, hi, lo));
+        const int chunk = lat->cg_chunk;
+        const long long max_chunks = (long long)max_iter / chunk + 2;
+        for (long long k = 0; k < max_chunks; k++) {
+            CUDA_TRY(cudaMemcpyAsync(&lat->sc_host->status, &lat->sc->status, sizeof(int),
+                                     cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (lat->sc_host->status != CG_RUNNING)
+                break;
+            for (int j = 0; j < chunk; j++)
+                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true));
+        }
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(x_data, H.xw, bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+    const CgScalars &h = *lat->sc_host;
+    stag_solve_info local;
+    memset(&local, 0, sizeof local);
+    local.iters = h.iter;
+    local.restarts = h.restarts;
+    local.status = h.status == CG_CONVERGED ? STAG_OK
+                   : h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
+                                              : STAG_ERR_NOT_CONVERGED;
+    local.true_rel_resid = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
+    local.iter_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    local.seconds = ms * 1e-3;
+    // model: low-precision iterations plus one high-precision M per update
+    const double lo_real = lo == STAG_F16 ? 2.0 : 4.0;
+    const double Vh = (double)lat->Vh;
+    const double model_bytes = h.iter * ((2.0 * 300 + 60) * lo_real + (lo == STAG_F16 ? 2 * 2 * 4 : 0) + 48) * Vh +
+                         h.restarts * (2.0 * 2400 + 4 * 48) * Vh;
+    const double flops = h.iter * (2.0 * 1146 + 72) * Vh + h.restarts * (2.0 * 1146 + 24) * Vh;
+    if (ms > 0) {
+        local.gflops = flops / (ms * 1e-3) / 1e9;
+        local.gbs = model_bytes / (ms * 1e-3) / 1e9;
+    }
+    if (info)
+        *info = local;
+    if (local.status != STAG_OK)
+        return fail(local.status, "stag_cg_solve_mixed: %s after %d iterations (true |r|/|b| = %.3e)",
+                    local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
+                    local.true_rel_resid);
+    return STAG_OK;
+}
+
 extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_field b, double mass,
                                    double rel_tol, int max_iter, int inner_prec, double delta,
                                    stag_solve_info *info) {
@@ -1075,27 +1182,156 @@ extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_fi
         return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: needs %s and %s gauge copies", prec_name(hi),
                     prec_name(lo));
     DEVICE_SCOPE(lat->device);
-    STAG_TRY(ensure_cg_work(lat, hi));
-    STAG_TRY(ensure_cg_work(lat, lo));
-    if (!lat->xs) {
-        CUDA_TRY(cudaMalloc(&lat->xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
-        CUDA_TRY(cudaMemsetAsync(lat->xs, 0, prec_vec_bytes(STAG_F32, lat->geom.stride), lat->stream));
+    return mixed_solve_raw(lat, hi, lo, x->data, b->data, b->bytes, mass, rel_tol, max_iter, delta, info);
+}
+
+
+// --------------------------------------------------------------------------
+// multi-shift CG (kernels_multishift.cu has the recurrences)
+// --------------------------------------------------------------------------
+static int alloc_vec(stag_lattice lat, int prec, void **p) {
+    if (*p)
+        return STAG_OK;
+    const size_t b = field_bytes(lat, prec);
+    cudaError_t e = cudaMalloc(p, b);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(*p, 0, b, lat->stream);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(STAG_ERR_NOMEM, "vector allocation (%s): %s", prec_name(prec), cudaGetErrorString(e));
     }
-    CgWork &H = lat->cg[hi];
+    return STAG_OK;
+}
+
+static int ensure_ms_state(stag_lattice lat) {
+    if (lat->ms_state)
+        return STAG_OK;
+    CUDA_TRY(cudaMalloc(&lat->ms_state, sizeof(ShiftState) * MS_MAX));
+    CUDA_TRY(cudaMallocHost(&lat->ms_state_host, sizeof(ShiftState) * MS_MAX));
+    CUDA_TRY(cudaMalloc(&lat->ms_true, sizeof(double) * MS_MAX));
+    CUDA_TRY(cudaMallocHost(&lat->ms_true_host, sizeof(double) * MS_MAX));
+    return STAG_OK;
+}
+
+static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, bool host_mode) {
+    CgWork &w = lat->cg[prec];
     cudaStream_t s = lat->stream;
-    CUDA_TRY(cudaMemcpyAsync(H.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
+    cudaError_t e;
+    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, a.p[a.base], w.t);
+    a1.skip_if_done = host_mode;
+    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+        return e;
+    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
+    a2.p = a.p[a.base];
+    a2.skip_if_done = host_mode;
+    if ((e = launch_dslash(prec, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_ms_update(prec, lat->geom, a, w.Ap, lat->partial, lat->sc, lat->ms_state, s)) !=
+        cudaSuccess)
+        return e;
+    return launch_ms_p(prec, lat->geom, a, lat->sc, lat->ms_state, s);
+}
+
+// one graph: init, WHILE(body); built per call (the solution buffers are
+// the caller's) and destroyed after it
+static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass_base, double tol,
+                        int max_iter) {
+    cudaStream_t s = lat->stream;
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
+    auto bail = [&](const char *what, cudaError_t err) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+        }
+        cudaGetLastError();
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "multi-shift graph (%s): %s", what, cudaGetErrorString(err));
+    };
+    if (e != cudaSuccess)
+        return bail("conditional handle", e);
+    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin capture", e);
+    if ((e = launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s)) != cudaSuccess)
+        return bail("init", e);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return bail("capture info", e);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+        return bail("add loop node", e);
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return bail("update deps", e);
+    cudaGraph_t captured = nullptr;
+    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
+        return bail("end capture", e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin body capture", e);
+    if ((e = enqueue_ms_body(lat, prec, a, false)) != cudaSuccess)
+        return bail("body", e);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
+        return bail("end body capture", e);
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        return bail("instantiate", e);
+    STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, true, cond));
+    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess)
+        return bail("launch", e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return bail("run", e);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return STAG_OK;
+}
+
+// multi-shift CG on raw buffers of precision prec; infos[s] per shift
+static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const double *shifts, int n,
+                        const void *b_data, size_t bytes, double mass, double tol, int max_iter,
+                        stag_solve_info *infos, double *seconds) {
+    STAG_TRY(ensure_cg_work(lat, prec));
+    STAG_TRY(ensure_ms_state(lat));
+    for (int k = 0; k < n; k++)
+        STAG_TRY(alloc_vec(lat, prec, &lat->ms_p[prec][k]));
+    CgWork &w = lat->cg[prec];
+    cudaStream_t s = lat->stream;
+    MsArgs a;
+    memset(&a, 0, sizeof a);
+    a.n = n;
+    a.base = 0;
+    for (int k = 1; k < n; k++)
+        if (shifts[k] < shifts[a.base])
+            a.base = k;
+    for (int k = 0; k < n; k++) {
+        a.delta[k] = shifts[k] - shifts[a.base];
+        a.x[k] = x_data[k];
+        a.p[k] = lat->ms_p[prec][k];
+    }
+    a.b = w.bw;
+    a.r = w.r;
+    const double mass_base = std::sqrt(mass * mass + shifts[a.base]);
+    CUDA_TRY(cudaMemcpyAsync(w.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaEventRecord(lat->ev0, s));
     if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
-        auto &mg = lat->mixed[hi][lo];
-        if (!mg.exec)
-            STAG_TRY(build_mixed_graph(lat, hi, lo));
-        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(cudaGraphLaunch(mg.exec, s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+        STAG_TRY(run_ms_graph(lat, prec, a, mass_base, tol, max_iter));
     } else {
-        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0, delta));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(enqueue_mixed_init(lat, hi, lo));
+        STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, false, 0));
+        CUDA_TRY(launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s));
         const int chunk = lat->cg_chunk;
         const long long max_chunks = (long long)max_iter / chunk + 2;
         for (long long k = 0; k < max_chunks; k++) {
@@ -1105,42 +1341,204 @@ extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_fi
             if (lat->sc_host->status != CG_RUNNING)
                 break;
             for (int j = 0; j < chunk; j++)
-                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true));
+                CUDA_TRY(enqueue_ms_body(lat, prec, a, true));
         }
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
     }
-    CUDA_TRY(cudaMemcpyAsync(x->data, H.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    // true residual of every shift, |b - (M + sigma_s) x_s|^2
+    for (int k = 0; k < n; k++) {
+        DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, x_data[k], w.t);
+        CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, 0, s));
+        DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, nullptr);
+        a2.p = x_data[k];
+        a2.b = w.bw;
+        a2.m2 = make_dpair(mass * mass + shifts[k]);
+        a2.m2_in_args = 1;
+        CUDA_TRY(launch_dslash(prec, EPI_RESID, a2, 0, s));
+        CUDA_TRY(cudaMemcpyAsync(lat->ms_true + k, (const char *)lat->sc + offsetof(CgScalars, true_rr),
+                                 sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->ms_state_host, lat->ms_state, sizeof(ShiftState) * n,
+                             cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->ms_true_host, lat->ms_true, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+    if (seconds)
+        *seconds = ms * 1e-3;
     const CgScalars &h = *lat->sc_host;
-    stag_solve_info local;
-    memset(&local, 0, sizeof local);
-    local.iters = h.iter;
-    local.restarts = h.restarts;
-    local.status = h.status == CG_CONVERGED ? STAG_OK
-                   : h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
-                                              : STAG_ERR_NOT_CONVERGED;
-    local.true_rel_resid = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
-    local.iter_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-    local.seconds = ms * 1e-3;
-    // model: low-precision iterations plus one high-precision M per update
-    const double lo_real = lo == STAG_F16 ? 2.0 : 4.0;
-    const double Vh = (double)lat->Vh;
-    const double bytes = h.iter * ((2.0 * 300 + 60) * lo_real + (lo == STAG_F16 ? 2 * 2 * 4 : 0) + 48) * Vh +
-                         h.restarts * (2.0 * 2400 + 4 * 48) * Vh;
-    const double flops = h.iter * (2.0 * 1146 + 72) * Vh + h.restarts * (2.0 * 1146 + 24) * Vh;
-    if (ms > 0) {
-        local.gflops = flops / (ms * 1e-3) / 1e9;
-        local.gbs = bytes / (ms * 1e-3) / 1e9;
+    int worst = STAG_OK;
+    for (int k = 0; k < n; k++) {
+        const ShiftState &st = lat->ms_state_host[k];
+        stag_solve_info &inf = infos[k];
+        memset(&inf, 0, sizeof inf);
+        inf.iters = h.bb > 0 && st.iters == 0 && h.status != CG_CONVERGED ? h.iter : st.iters;
+        inf.status = h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
+                     : (st.active == 0 ? STAG_OK : STAG_ERR_NOT_CONVERGED);
+        inf.true_rel_resid = h.bb > 0 ? std::sqrt(lat->ms_true_host[k] / h.bb) : 0.0;
+        inf.iter_rel_resid = h.bb > 0 ? std::sqrt(st.zeta * st.zeta * h.rr / h.bb) : 0.0;
+        inf.seconds = ms * 1e-3;
+        if (inf.status != STAG_OK && worst == STAG_OK)
+            worst = inf.status;
     }
-    if (info)
-        *info = local;
-    if (local.status != STAG_OK)
-        return fail(local.status, "stag_cg_solve_mixed: %s after %d iterations (true |r|/|b| = %.3e)",
-                    local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
-                    local.true_rel_resid);
+    // model rates on the first entry: base CG plus the per-shift vector passes
+    const double rb = prec == STAG_F32 ? 4.0 : 8.0;
+    const double Vh = (double)lat->Vh;
+    const double bytes_it = ((2.0 * 300 + 60) * rb + n * 4 * 6 * rb) * Vh;
+    const double flops_it = (2.0 * 1146 + 72 + n * 24.0) * Vh;
+    if (ms > 0) {
+        infos[0].gbs = bytes_it * h.iter / (ms * 1e-3) / 1e9;
+        infos[0].gflops = flops_it * h.iter / (ms * 1e-3) / 1e9;
+    }
+    return worst;
+}
+
+static int check_ms_args(stag_lattice lat, stag_field *xs, const double *shifts, int n, const stag_field b,
+                         double mass, double rel_tol, int max_iter, const char *who) {
+    if (!lat || !xs || !shifts || !b)
+        return fail(STAG_ERR_ARG, "%s: NULL argument", who);
+    if (n < 1 || n > MS_MAX)
+        return fail(STAG_ERR_ARG, "%s: number of shifts %d not in [1, %d]", who, n, MS_MAX);
+    if (b->lat != lat || b->parity != STAG_EVEN)
+        return fail(STAG_ERR_ARG, "%s: b must be an even field of this lattice", who);
+    for (int k = 0; k < n; k++) {
+        if (!xs[k] || xs[k]->lat != lat || xs[k]->parity != STAG_EVEN || xs[k]->prec != b->prec)
+            return fail(STAG_ERR_ARG, "%s: xs[%d] must be an even field of b's precision", who, k);
+        if (xs[k] == b)
+            return fail(STAG_ERR_ARG, "%s: xs[%d] aliases b", who, k);
+        for (int j = 0; j < k; j++)
+            if (xs[j] == xs[k])
+                return fail(STAG_ERR_ARG, "%s: xs[%d] and xs[%d] are the same field", who, j, k);
+        if (!(shifts[k] >= 0) || !std::isfinite(shifts[k]))
+            return fail(STAG_ERR_ARG, "%s: shift %d must be finite and >= 0", who, k);
+    }
+    if (!(mass > 0) || !std::isfinite(mass))
+        return fail(STAG_ERR_ARG, "%s: mass must be positive and finite", who);
+    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
+        return fail(STAG_ERR_ARG, "%s: rel_tol must be >= 0", who);
+    if (max_iter < 0)
+        return fail(STAG_ERR_ARG, "%s: max_iter must be >= 0", who);
+    return STAG_OK;
+}
+
+extern "C" int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                                  const stag_field b, double mass, double rel_tol, int max_iter,
+                                  stag_solve_info *infos) {
+    STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift"));
+    const int prec = b->prec;
+    if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
+        return fail(STAG_ERR_STATE, "stag_cg_multishift: fields must be F64, DF64 or F32");
+    if (!lat->has_gauge || !lat->links[prec])
+        return fail(STAG_ERR_STATE, "stag_cg_multishift: no %s gauge copy uploaded", prec_name(prec));
+    DEVICE_SCOPE(lat->device);
+    void *xd[MS_MAX];
+    for (int k = 0; k < n; k++)
+        xd[k] = xs[k]->data;
+    stag_solve_info local[MS_MAX];
+    const int st = ms_solve_raw(lat, prec, xd, shifts, n, b->data, b->bytes, mass, rel_tol, max_iter,
+                                local, nullptr);
+    if (infos)
+        memcpy(infos, local, sizeof(stag_solve_info) * n);
+    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED && st != STAG_ERR_BREAKDOWN)
+        return st;
+    if (st != STAG_OK)
+        return fail(st, "stag_cg_multishift: %s", st == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged");
+    return STAG_OK;
+}
+
+// |b - (M + m_k^2 - m^2) x|^2 into the host, r stored to r_out (precision hi)
+static int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, double mk, void *r_out,
+                            double *rr) {
+    CgWork &H = lat->cg[hi];
+    cudaStream_t s = lat->stream;
+    DslashArgs a1 = dslash_args(lat, hi, STAG_ODD, x, H.t);
+    CUDA_TRY(launch_dslash(hi, EPI_NONE, a1, 0, s));
+    DslashArgs a2 = dslash_args(lat, hi, STAG_EVEN, H.t, r_out);
+    a2.p = x;
+    a2.b = b;
+    a2.m2 = make_dpair(mk * mk);
+    a2.m2_in_args = 1;
+    CUDA_TRY(launch_dslash(hi, r_out ? EPI_RESID_STORE : EPI_RESID, a2, 0, s));
+    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *rr = lat->sc_host->true_rr;
+    return STAG_OK;
+}
+
+extern "C" int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                                        const stag_field b, double mass, double rel_tol, int max_iter,
+                                        int inner_prec, double delta, stag_solve_info *infos) {
+    STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift_mixed"));
+    const int hi = b->prec;
+    if (hi != STAG_F64 && hi != STAG_DF64)
+        return fail(STAG_ERR_STATE, "stag_cg_multishift_mixed: fields must be F64 or DF64");
+    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
+        return fail(STAG_ERR_ARG, "stag_cg_multishift_mixed: inner precision must be F32 or F16");
+    if (!(delta > 0 && delta < 1))
+        return fail(STAG_ERR_ARG, "stag_cg_multishift_mixed: delta must be in (0, 1)");
+    if (!lat->has_gauge || !lat->links[hi] || !lat->links[STAG_F32] || !lat->links[inner_prec])
+        return fail(STAG_ERR_STATE, "stag_cg_multishift_mixed: needs %s, F32 and %s gauge copies",
+                    prec_name(hi), prec_name(inner_prec));
+    DEVICE_SCOPE(lat->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = lat->stream;
+    const Geom &g = lat->geom;
+    STAG_TRY(ensure_cg_work(lat, hi));
+    STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_blo));
+    for (int k = 0; k < n; k++)
+        STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_xlo[k]));
+    STAG_TRY(alloc_vec(lat, hi, &lat->ms_rhi[hi]));
+    STAG_TRY(alloc_vec(lat, hi, &lat->ms_ehi[hi]));
+    // |b|^2 in the high precision: the residual of x = 0
+    CUDA_TRY(cudaMemsetAsync(lat->ms_ehi[hi], 0, field_bytes(lat, hi), s));
+    double bb = 0;
+    STAG_TRY(shifted_residual(lat, hi, lat->ms_ehi[hi], b->data, mass, nullptr, &bb));
+    // phase 1: all shifts at once in FP32, to max(rel_tol, 1e-5)
+    CUDA_TRY(launch_convert(STAG_F32, hi, g, b->data, lat->ms_blo, s));
+    const double sloppy_tol = rel_tol > 1e-5 ? rel_tol : 1e-5;
+    stag_solve_info lo_info[MS_MAX];
+    int st = ms_solve_raw(lat, STAG_F32, lat->ms_xlo, shifts, n, lat->ms_blo, field_bytes(lat, STAG_F32),
+                          mass, sloppy_tol, max_iter, lo_info, nullptr);
+    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED)
+        return st;
+    // phase 2: per shift, x_k = x_lo, then the mixed solver on its residual
+    int worst = STAG_OK;
+    stag_solve_info out[MS_MAX];
+    for (int k = 0; k < n; k++) {
+        memset(&out[k], 0, sizeof out[k]);
+        CUDA_TRY(launch_convert(hi, STAG_F32, g, lat->ms_xlo[k], xs[k]->data, s));
+        const double mk = std::sqrt(mass * mass + shifts[k]);
+        double rr0 = 0;
+        STAG_TRY(shifted_residual(lat, hi, xs[k]->data, b->data, mk, lat->ms_rhi[hi], &rr0));
+        const double rel0 = bb > 0 ? std::sqrt(rr0 / bb) : 0.0;
+        stag_solve_info ri;
+        memset(&ri, 0, sizeof ri);
+        if (rel0 > rel_tol) {
+            const int rs = mixed_solve_raw(lat, hi, inner_prec, lat->ms_ehi[hi], lat->ms_rhi[hi],
+                                           field_bytes(lat, hi), mk, rel_tol / rel0, max_iter, delta, &ri);
+            if (rs != STAG_OK && rs != STAG_ERR_NOT_CONVERGED && rs != STAG_ERR_BREAKDOWN)
+                return rs;
+            CUDA_TRY(launch_axpy1(hi, g, lat->ms_ehi[hi], xs[k]->data, s));
+        }
+        double rr1 = 0;
+        STAG_TRY(shifted_residual(lat, hi, xs[k]->data, b->data, mk, nullptr, &rr1));
+        out[k].iters = lo_info[k].iters;
+        out[k].restarts = ri.iters;  // refinement iterations (inner precision)
+        out[k].true_rel_resid = bb > 0 ? std::sqrt(rr1 / bb) : 0.0;
+        out[k].iter_rel_resid = rel0;
+        out[k].status = out[k].true_rel_resid <= rel_tol * 1.05 || bb == 0 ? STAG_OK
+                        : ri.status != STAG_OK ? ri.status : STAG_ERR_NOT_CONVERGED;
+        if (out[k].status != STAG_OK && worst == STAG_OK)
+            worst = out[k].status;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < n; k++)
+        out[k].seconds = secs;
+    if (infos)
+        memcpy(infos, out, sizeof(stag_solve_info) * n);
+    if (worst != STAG_OK)
+        return fail(worst, "stag_cg_multishift_mixed: a shift did not reach the tolerance");
     return STAG_OK;
 }
 

@@ -49,7 +49,8 @@ EXPORTED = [
     "stag_field_create", "stag_field_destroy", "stag_field_import", "stag_field_export",
     "stag_field_zero", "stag_field_storage",
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
-    "stag_cg_solve", "stag_cg_solve_mixed", "stag_apply_M_noalloc",
+    "stag_cg_solve", "stag_cg_solve_mixed", "stag_cg_multishift", "stag_cg_multishift_mixed",
+    "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -110,6 +111,8 @@ def lib():
             "stag_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_apply_M_noalloc": ([P, P, D, D, P, P, D, P, P, P], I),
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
+            "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
             "stag_version": ([], ctypes.c_char_p),
@@ -302,6 +305,27 @@ class Lattice:
         d = info.as_dict()
         d["return"] = st
         return d
+
+    def cg_multishift(self, xs, b: Field, shifts, mass: float, tol: float = 1e-10,
+                      max_iter: int = 20000, mixed: Optional[str] = None, delta: float = 0.1):
+        """Multi-shift CG; `mixed` = 'f32' or 'f16' refines FP32 multi-shift
+        solutions with reliable-update CG.  Returns (status, [info per shift])."""
+        n = len(shifts)
+        if len(xs) != n:
+            raise ValueError("one solution field per shift")
+        hx = (ctypes.c_void_p * n)(*[x.handle.value for x in xs])
+        sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+        infos = (SolveInfo * n)()
+        if mixed is None:
+            st = lib().stag_cg_multishift(self.handle, hx, sh, n, b.handle, float(mass), float(tol),
+                                          int(max_iter), infos)
+        else:
+            st = lib().stag_cg_multishift_mixed(self.handle, hx, sh, n, b.handle, float(mass),
+                                                float(tol), int(max_iter), PREC[mixed], float(delta),
+                                                infos)
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        return st, [i.as_dict() for i in infos]
 
     def close(self):
         for f in list(self._fields):
