@@ -225,6 +225,43 @@ int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shi
                              const stag_field b, double mass, double rel_tol, int max_iter,
                              int inner_prec, double delta, stag_solve_info *infos);
 
+/* Batched CG: n systems M_i x_i = b_i (1 <= n <= 64), possibly on several
+ * lattices of different sizes on one device, iterate in lock step inside
+ * one CUDA graph launch.  Systems on the same lattice (which must be
+ * consecutive in the arrays) share every link load: the multi-right-hand-side
+ * Dslash streams each link matrix once per site and applies it to up to 8
+ * (FP32) or 4 (F64/DF64) vectors.  Each system has its own mass, scalars and
+ * stopping test; the loop ends when none is running.  All fields have one
+ * precision (F64, DF64 or F32) with gauge copies of it on every lattice.
+ * Work runs on lats[0]'s stream (the others' streams are synchronized
+ * first).  infos (may be NULL): one entry per system; infos[0].gbs/gflops
+ * are the rates of the whole batch counted as if every system had been
+ * solved alone. */
+int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                          const double *masses, double rel_tol, int max_iter,
+                          stag_solve_info *infos);
+
+/* Batched CG in FP32 to max(rel_tol, 1e-5) for all systems in one graph,
+ * then every system refined to rel_tol by reliable-update CG (inner_prec F32
+ * or F16, delta) on its own residual, in the precision of xs and bs (F64 or
+ * DF64).  Every lattice needs gauge copies of that precision, F32 and
+ * inner_prec.  infos[i]: iters = batched FP32 iterations, restarts =
+ * refinement iterations, iter_rel_resid = residual after the FP32 phase,
+ * true_rel_resid = final recomputed residual, seconds = wall time of the
+ * call. */
+int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                                const double *masses, double rel_tol, int max_iter, int inner_prec,
+                                double delta, stag_solve_info *infos);
+
+/* Autotuner: time the candidate block sizes (128, 256 threads) of the Dslash
+ * kernel and of the batched multi-right-hand-side Dslash in precision `prec`
+ * on this lattice (10 launches each after 2 warm-ups, CUDA events on the
+ * lattice stream) and keep the fastest for every later call on this lattice.
+ * dslash_us[2] and batch_us[2] (may be NULL) receive the measured
+ * microseconds per launch for 128 and 256.  Needs a gauge copy of `prec`;
+ * overwrites the lattice's internal work vectors. */
+int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us);
+
 /* ---- allocation-free M ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: code invoked while its caller captures

@@ -63,6 +63,11 @@ cudaError_t launch_axpy1(int prec, const Geom &g, const void *x, void *y, cudaSt
 cudaError_t launch_convert(int prec_out, int prec_in, const Geom &g, const void *in, void *out,
                            cudaStream_t s);
 
+// batched CG (batched.cuh, kernels_batched.cu): `what` is a BatchKernel
+struct BatchArgs;
+cudaError_t launch_batch(int prec, int what, const BatchArgs &a, int block, cudaStream_t s);
+int batch_max_k(int prec);
+
 // record the calling thread's last error message (read back by
 // stag_last_error_message) and return `code`
 int set_error(int code, const char *fmt, ...);

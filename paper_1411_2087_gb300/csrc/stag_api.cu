@@ -11,8 +11,10 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/stag.h"
+#include "batched.cuh"
 #include "dslash.cuh"
 #include "kernels.h"
 
@@ -144,6 +146,12 @@ struct stag_lattice_s {
     void *ms_blo = nullptr;                // FP32 right-hand side of that phase
     void *ms_rhi[4] = {};                  // residual of one shift (high precision)
     void *ms_ehi[4] = {};                  // correction of one shift (high precision)
+    // batched CG: per-system work vectors (r, p, Ap, t) by precision and slot
+    void *bwork[4][BATCH_MAX_G * BATCH_KMAX][4] = {};
+    void *bxlo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 solutions of the sloppy batched phase
+    void *bblo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 right-hand sides of that phase
+    int batch_block[4] = {128, 128, 128, 128};  // block size of the batched kernels (autotuned)
+    int dslash_block[4] = {0, 0, 0, 0};         // block size of the Dslash kernels (0 = default)
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
     int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
 };
@@ -308,6 +316,17 @@ extern "C" int stag_lattice_destroy(stag_lattice lat) {
     for (int k = 0; k < MS_MAX; k++)
         if (lat->ms_xlo[k])
             cudaFree(lat->ms_xlo[k]);
+    for (int q = 0; q < 4; q++)
+        for (int k = 0; k < BATCH_MAX_G * BATCH_KMAX; k++)
+            for (int v = 0; v < 4; v++)
+                if (lat->bwork[q][k][v])
+                    cudaFree(lat->bwork[q][k][v]);
+    for (int k = 0; k < BATCH_MAX_G * BATCH_KMAX; k++) {
+        if (lat->bxlo[k])
+            cudaFree(lat->bxlo[k]);
+        if (lat->bblo[k])
+            cudaFree(lat->bblo[k]);
+    }
     if (lat->ms_blo)
         cudaFree(lat->ms_blo);
     if (lat->absmax)
@@ -753,12 +772,12 @@ extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_fi
     STAG_TRY(ensure_cg_work(lat, prec));
     CgWork &w = lat->cg[prec];
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, in_even->data, w.t);
-    CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, 0, lat->stream));
+    CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], lat->stream));
     DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, out_even->data);
     a2.p = in_even->data;
     a2.m2 = make_dpair(mass * mass);
     a2.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(prec, EPI_M, a2, 0, lat->stream));
+    CUDA_TRY(launch_dslash(prec, EPI_M, a2, lat->dslash_block[prec], lat->stream));
     return STAG_OK;
 }
 
@@ -774,12 +793,12 @@ static cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, 
     cudaError_t e;
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
     a1.skip_if_done = skip_if_done;
-    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
     DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
     a2.p = w.p;
     a2.skip_if_done = skip_if_done;
-    if ((e = launch_dslash(prec, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(prec, EPI_M_PAP, a2, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
     if ((e = launch_cg_update(prec, lat->geom, w.xw, w.r, w.p, w.Ap, lat->partial, lat->sc, s)) !=
         cudaSuccess)
@@ -791,12 +810,12 @@ static cudaError_t enqueue_true_residual(stag_lattice lat, CgWork &w, cudaStream
     const int prec = w.prec;
     cudaError_t e;
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.xw, w.t);
-    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
     DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, nullptr);
     a2.p = w.xw;
     a2.b = w.bw;
-    return launch_dslash(prec, EPI_RESID, a2, 0, s);
+    return launch_dslash(prec, EPI_RESID, a2, lat->dslash_block[prec], s);
 }
 
 static int build_cg_graph(stag_lattice lat, CgWork &w) {
@@ -982,12 +1001,12 @@ static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool hos
     // low precision: t_s = D_oe p; Ap = m^2 p - D_eo t_s, alpha
     DslashArgs a1 = dslash_args(lat, lo, STAG_ODD, L.p, L.t);
     a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_NONE, a1, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(lo, EPI_NONE, a1, lat->dslash_block[lo], s)) != cudaSuccess)
         return e;
     DslashArgs a2 = dslash_args(lat, lo, STAG_EVEN, L.t, L.Ap);
     a2.p = L.p;
     a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(lo, EPI_M_PAP, a2, lat->dslash_block[lo], s)) != cudaSuccess)
         return e;
     if ((e = launch_mixed_update(lo, g, lat->xs, L.r, L.p, L.Ap, lat->partial, lat->sc, s)) != cudaSuccess)
         return e;
@@ -996,13 +1015,13 @@ static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool hos
         return e;
     DslashArgs a3 = dslash_args(lat, hi, STAG_ODD, H.xw, H.t);
     a3.gate = reliable_flag(lat);
-    if ((e = launch_dslash(hi, EPI_NONE, a3, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(hi, EPI_NONE, a3, lat->dslash_block[hi], s)) != cudaSuccess)
         return e;
     DslashArgs a4 = dslash_args(lat, hi, STAG_EVEN, H.t, H.r);
     a4.p = H.xw;
     a4.b = H.bw;
     a4.gate = reliable_flag(lat);
-    if ((e = launch_dslash(hi, EPI_RESID_STORE, a4, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(hi, EPI_RESID_STORE, a4, lat->dslash_block[hi], s)) != cudaSuccess)
         return e;
     if ((e = launch_mixed_restart(hi, lo, g, H.r, L.r, lat->sc, s)) != cudaSuccess)
         return e;
@@ -1219,12 +1238,12 @@ static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, 
     cudaError_t e;
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, a.p[a.base], w.t);
     a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_NONE, a1, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
     DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
     a2.p = a.p[a.base];
     a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_M_PAP, a2, 0, s)) != cudaSuccess)
+    if ((e = launch_dslash(prec, EPI_M_PAP, a2, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
     if ((e = launch_ms_update(prec, lat->geom, a, w.Ap, lat->partial, lat->sc, lat->ms_state, s)) !=
         cudaSuccess)
@@ -1348,13 +1367,13 @@ static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const d
     // true residual of every shift, |b - (M + sigma_s) x_s|^2
     for (int k = 0; k < n; k++) {
         DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, x_data[k], w.t);
-        CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, 0, s));
+        CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s));
         DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, nullptr);
         a2.p = x_data[k];
         a2.b = w.bw;
         a2.m2 = make_dpair(mass * mass + shifts[k]);
         a2.m2_in_args = 1;
-        CUDA_TRY(launch_dslash(prec, EPI_RESID, a2, 0, s));
+        CUDA_TRY(launch_dslash(prec, EPI_RESID, a2, lat->dslash_block[prec], s));
         CUDA_TRY(cudaMemcpyAsync(lat->ms_true + k, (const char *)lat->sc + offsetof(CgScalars, true_rr),
                                  sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
@@ -1453,7 +1472,7 @@ static int shifted_residual(stag_lattice lat, int hi, const void *x, const void 
     CgWork &H = lat->cg[hi];
     cudaStream_t s = lat->stream;
     DslashArgs a1 = dslash_args(lat, hi, STAG_ODD, x, H.t);
-    CUDA_TRY(launch_dslash(hi, EPI_NONE, a1, 0, s));
+    CUDA_TRY(launch_dslash(hi, EPI_NONE, a1, lat->dslash_block[hi], s));
     DslashArgs a2 = dslash_args(lat, hi, STAG_EVEN, H.t, r_out);
     a2.p = x;
     a2.b = b;
@@ -1539,6 +1558,495 @@ extern "C" int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const 
         memcpy(infos, out, sizeof(stag_solve_info) * n);
     if (worst != STAG_OK)
         return fail(worst, "stag_cg_multishift_mixed: a shift did not reach the tolerance");
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// batched CG over many (lattice, right-hand side) systems, one graph
+// --------------------------------------------------------------------------
+struct BatchPlan {
+    BatchArgs a;
+    int nsys = 0;
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    int block = 128;
+    // device buffers owned by one call
+    CgScalars *sys = nullptr;
+    unsigned *tickets = nullptr;
+    BatchCtl *ctl = nullptr;
+    double *partial = nullptr;
+    void release() {
+        if (sys) cudaFree(sys);
+        if (tickets) cudaFree(tickets);
+        if (ctl) cudaFree(ctl);
+        if (partial) cudaFree(partial);
+        sys = nullptr;
+        tickets = nullptr;
+        ctl = nullptr;
+        partial = nullptr;
+    }
+};
+
+// group systems by lattice (consecutive, at most batch_max_k per group) and
+// allocate work vectors and reduction buffers; x/b are raw buffers
+static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, const void *const *b,
+                      int prec) {
+    const int K = batch_max_k(prec);
+    memset(&P.a, 0, sizeof P.a);
+    P.nsys = n;
+    P.prec = prec;
+    P.stream = lats[0]->stream;
+    P.block = lats[0]->batch_block[prec];
+    int slot_of_lat[BATCH_MAX_G * BATCH_KMAX];
+    int G = 0, blocks = 0;
+    size_t partial_total = 0;
+    for (int i = 0; i < n; i++) {
+        // slot = index of this system among the earlier systems of its lattice
+        int slot = 0;
+        for (int j = 0; j < i; j++)
+            if (lats[j] == lats[i])
+                slot++;
+        slot_of_lat[i] = slot;
+        const bool new_group = G == 0 || lats[i] != lats[i - 1] || P.a.grp[G - 1].K == K;
+        if (new_group) {
+            if (G == BATCH_MAX_G)
+                return fail(STAG_ERR_ARG, "stag_cg_solve_batched: more than %d groups (at most %d "
+                            "systems of one lattice per group; keep systems of a lattice together)",
+                            BATCH_MAX_G, K);
+            BatchGroup &gr = P.a.grp[G];
+            gr.g = lats[i]->geom;
+            gr.K = 0;
+            gr.block0 = blocks;
+            gr.nblocks = (gr.g.Vh + P.block - 1) / P.block;
+            gr.sys0 = i;
+            gr.links[0] = links_of(lats[i], prec, 0);
+            gr.links[1] = links_of(lats[i], prec, 1);
+            gr.link_scale[0] = gr.link_scale[1] = 0.f;
+            blocks += gr.nblocks;
+            partial_total += (size_t)gr.nblocks * BATCH_KMAX;
+            G++;
+        }
+        BatchGroup &gr = P.a.grp[G - 1];
+        const int k = gr.K++;
+        stag_lattice L = lats[i];
+        for (int v = 0; v < 4; v++)
+            STAG_TRY(alloc_vec(L, prec, &L->bwork[prec][slot_of_lat[i]][v]));
+        gr.x[k] = x[i];
+        gr.b[k] = b[i];
+        gr.r[k] = L->bwork[prec][slot_of_lat[i]][0];
+        gr.p[k] = L->bwork[prec][slot_of_lat[i]][1];
+        gr.Ap[k] = L->bwork[prec][slot_of_lat[i]][2];
+        gr.t[k] = L->bwork[prec][slot_of_lat[i]][3];
+    }
+    P.a.G = G;
+    P.a.nblocks = blocks;
+    cudaError_t e;
+    if ((e = cudaMalloc(&P.sys, sizeof(CgScalars) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&P.tickets, sizeof(unsigned) * G)) != cudaSuccess ||
+        (e = cudaMalloc(&P.ctl, sizeof(BatchCtl))) != cudaSuccess ||
+        (e = cudaMalloc(&P.partial, sizeof(double) * partial_total)) != cudaSuccess) {
+        P.release();
+        return fail(STAG_ERR_NOMEM, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
+    }
+    // every system starts as CG_RUNNING (0) until the init kernel decides
+    if ((e = cudaMemsetAsync(P.sys, 0, sizeof(CgScalars) * n, P.stream)) != cudaSuccess) {
+        P.release();
+        return fail(STAG_ERR_CUDA, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
+    }
+    size_t off = 0;
+    for (int gi = 0; gi < G; gi++) {
+        P.a.grp[gi].partial = P.partial + off;
+        off += (size_t)P.a.grp[gi].nblocks * BATCH_KMAX;
+    }
+    P.a.sys = P.sys;
+    P.a.tickets = P.tickets;
+    P.a.ctl = P.ctl;
+    return STAG_OK;
+}
+
+static cudaError_t enqueue_batch_body(const BatchPlan &P) {
+    cudaError_t e;
+    const int w[4] = {BATCH_DSLASH_OE, BATCH_M_PAP, BATCH_UPDATE, BATCH_P};
+    for (int k = 0; k < 4; k++)
+        if ((e = launch_batch(P.prec, w[k], P.a, P.block, P.stream)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
+}
+
+// run the batched CG to completion: init, WHILE(body), true residuals
+static int run_batch(BatchPlan &P, const double *masses, double tol, int max_iter, float *ms_out) {
+    cudaStream_t s = P.stream;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
+    auto bail = [&](const char *what, cudaError_t err) {
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(s, &junk);
+        }
+        cudaGetLastError();
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return fail(STAG_ERR_CUDA, "batched CG graph (%s): %s", what, cudaGetErrorString(err));
+    };
+    if (e != cudaSuccess)
+        return bail("conditional handle", e);
+    // scalars: per system m^2, tol^2, max_iter; control block
+    {
+        std::vector<CgScalars> h(P.nsys);
+        memset(h.data(), 0, sizeof(CgScalars) * P.nsys);
+        for (int i = 0; i < P.nsys; i++) {
+            h[i].m2 = make_dpair(masses[i] * masses[i]);
+            h[i].tol2 = tol * tol;
+            h[i].max_iter = max_iter;
+        }
+        BatchCtl c;
+        memset(&c, 0, sizeof c);
+        c.cond = cond;
+        c.has_cond = 1;
+        if ((e = cudaMemcpyAsync(P.sys, h.data(), sizeof(CgScalars) * P.nsys, cudaMemcpyHostToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(P.ctl, &c, sizeof c, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.tickets, 0, sizeof(unsigned) * P.a.G, s)) != cudaSuccess)
+            return bail("scalars", e);
+    }
+    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin capture", e);
+    if ((e = launch_batch(P.prec, BATCH_INIT, P.a, P.block, s)) != cudaSuccess)
+        return bail("init", e);
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return bail("capture info", e);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop;
+    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
+        return bail("add loop node", e);
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
+        return bail("update deps", e);
+    if ((e = launch_batch(P.prec, BATCH_DSLASH_X, P.a, P.block, s)) != cudaSuccess ||
+        (e = launch_batch(P.prec, BATCH_RESID, P.a, P.block, s)) != cudaSuccess)
+        return bail("true residual", e);
+    cudaGraph_t captured = nullptr;
+    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
+        return bail("end capture", e);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return bail("begin body capture", e);
+    if ((e = enqueue_batch_body(P)) != cudaSuccess)
+        return bail("body", e);
+    cudaGraph_t body_out = nullptr;
+    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
+        return bail("end body capture", e);
+    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        return bail("instantiate", e);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    e = cudaGraphLaunch(exec, s);
+    cudaEventRecord(e1, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return bail("run", e != cudaSuccess ? e : e2);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (ms_out)
+        *ms_out = ms;
+    return STAG_OK;
+}
+
+static int check_batch(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs, const double *masses,
+                       double rel_tol, int max_iter, const char *who) {
+    if (!lats || !xs || !bs || !masses)
+        return fail(STAG_ERR_ARG, "%s: NULL argument", who);
+    if (n < 1 || n > BATCH_MAX_G * BATCH_KMAX)
+        return fail(STAG_ERR_ARG, "%s: number of systems %d not in [1, %d]", who, n, BATCH_MAX_G * BATCH_KMAX);
+    for (int i = 0; i < n; i++) {
+        if (!lats[i] || !xs[i] || !bs[i])
+            return fail(STAG_ERR_ARG, "%s: NULL lattice or field for system %d", who, i);
+        if (lats[i]->device != lats[0]->device)
+            return fail(STAG_ERR_ARG, "%s: all lattices must be on one device", who);
+        if (xs[i]->lat != lats[i] || bs[i]->lat != lats[i] || xs[i]->parity != STAG_EVEN ||
+            bs[i]->parity != STAG_EVEN)
+            return fail(STAG_ERR_ARG, "%s: system %d needs even fields of its lattice", who, i);
+        if (xs[i]->prec != bs[0]->prec || bs[i]->prec != bs[0]->prec)
+            return fail(STAG_ERR_ARG, "%s: all fields must have one precision", who);
+        if (xs[i] == bs[i])
+            return fail(STAG_ERR_ARG, "%s: x and b of system %d alias", who, i);
+        for (int j = 0; j < i; j++)
+            if (xs[j] == xs[i])
+                return fail(STAG_ERR_ARG, "%s: systems %d and %d share a solution field", who, j, i);
+        if (!(masses[i] > 0) || !std::isfinite(masses[i]))
+            return fail(STAG_ERR_ARG, "%s: mass %d must be positive and finite", who, i);
+        // systems of one lattice must be consecutive
+        for (int j = 0; j + 1 < i; j++)
+            if (lats[j] == lats[i] && lats[j + 1] != lats[i])
+                return fail(STAG_ERR_ARG, "%s: systems of one lattice must be consecutive", who);
+    }
+    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
+        return fail(STAG_ERR_ARG, "%s: rel_tol must be >= 0", who);
+    if (max_iter < 0)
+        return fail(STAG_ERR_ARG, "%s: max_iter must be >= 0", who);
+    return STAG_OK;
+}
+
+static int batch_solve_raw(int n, stag_lattice *lats, void *const *x, const void *const *b, const double *masses,
+                           int prec, double rel_tol, int max_iter, stag_solve_info *infos) {
+    for (int i = 0; i < n; i++)
+        if (!lats[i]->has_gauge || !lats[i]->links[prec])
+            return fail(STAG_ERR_STATE, "stag_cg_solve_batched: lattice of system %d has no %s gauge copy",
+                        i, prec_name(prec));
+    // work of the other lattices' streams must be done before the batch
+    // runs on the first lattice's stream
+    for (int i = 1; i < n; i++)
+        if (lats[i]->stream != lats[0]->stream)
+            CUDA_TRY(cudaStreamSynchronize(lats[i]->stream));
+    BatchPlan P;
+    STAG_TRY(plan_batch(P, n, lats, x, b, prec));
+    float ms = 0.f;
+    int st = run_batch(P, masses, rel_tol, max_iter, &ms);
+    if (st != STAG_OK) {
+        P.release();
+        return st;
+    }
+    std::vector<CgScalars> h(n);
+    cudaError_t e = cudaMemcpy(h.data(), P.sys, sizeof(CgScalars) * n, cudaMemcpyDeviceToHost);
+    P.release();
+    if (e != cudaSuccess)
+        return fail(STAG_ERR_CUDA, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
+    int worst = STAG_OK;
+    double total_bytes = 0, total_flops = 0;
+    const double rb = prec == STAG_F32 ? 4.0 : 8.0;
+    for (int i = 0; i < n; i++) {
+        stag_solve_info &inf = infos[i];
+        memset(&inf, 0, sizeof inf);
+        inf.iters = h[i].iter;
+        inf.status = h[i].status == CG_CONVERGED ? STAG_OK
+                     : h[i].status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
+                                                   : STAG_ERR_NOT_CONVERGED;
+        inf.true_rel_resid = h[i].bb > 0 ? std::sqrt(h[i].true_rr / h[i].bb) : 0.0;
+        inf.iter_rel_resid = h[i].bb > 0 ? std::sqrt(h[i].rr / h[i].bb) : 0.0;
+        inf.seconds = ms * 1e-3;
+        if (inf.status != STAG_OK && worst == STAG_OK)
+            worst = inf.status;
+        total_bytes += (2.0 * 300 + 60) * rb * (double)lats[i]->Vh * h[i].iter;
+        total_flops += (2.0 * 1146 + 72) * (double)lats[i]->Vh * h[i].iter;
+    }
+    if (ms > 0) {
+        // per-system-equivalent rates of the whole batch (links counted once
+        // per system, as if solved alone)
+        infos[0].gbs = total_bytes / (ms * 1e-3) / 1e9;
+        infos[0].gflops = total_flops / (ms * 1e-3) / 1e9;
+    }
+    return worst;
+}
+
+extern "C" int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                                     const double *masses, double rel_tol, int max_iter,
+                                     stag_solve_info *infos) {
+    STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched"));
+    const int prec = bs[0]->prec;
+    if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
+        return fail(STAG_ERR_STATE, "stag_cg_solve_batched: fields must be F64, DF64 or F32");
+    DEVICE_SCOPE(lats[0]->device);
+    std::vector<void *> x(n);
+    std::vector<const void *> b(n);
+    for (int i = 0; i < n; i++) {
+        x[i] = xs[i]->data;
+        b[i] = bs[i]->data;
+    }
+    std::vector<stag_solve_info> loc(n);
+    const int st = batch_solve_raw(n, lats, x.data(), b.data(), masses, prec, rel_tol, max_iter, loc.data());
+    if (infos)
+        memcpy(infos, loc.data(), sizeof(stag_solve_info) * n);
+    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED && st != STAG_ERR_BREAKDOWN)
+        return st;
+    if (st != STAG_OK)
+        return fail(st, "stag_cg_solve_batched: a system %s", st == STAG_ERR_BREAKDOWN ? "broke down"
+                                                                                      : "did not converge");
+    return STAG_OK;
+}
+
+extern "C" int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                                           const double *masses, double rel_tol, int max_iter, int inner_prec,
+                                           double delta, stag_solve_info *infos) {
+    STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched_mixed"));
+    const int hi = bs[0]->prec;
+    if (hi != STAG_F64 && hi != STAG_DF64)
+        return fail(STAG_ERR_STATE, "stag_cg_solve_batched_mixed: fields must be F64 or DF64");
+    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_batched_mixed: inner precision must be F32 or F16");
+    if (!(delta > 0 && delta < 1))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_batched_mixed: delta must be in (0, 1)");
+    for (int i = 0; i < n; i++)
+        if (!lats[i]->has_gauge || !lats[i]->links[hi] || !lats[i]->links[STAG_F32] ||
+            !lats[i]->links[inner_prec])
+            return fail(STAG_ERR_STATE, "stag_cg_solve_batched_mixed: every lattice needs %s, F32 and %s "
+                        "gauge copies", prec_name(hi), prec_name(inner_prec));
+    DEVICE_SCOPE(lats[0]->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    // phase 1: every system in FP32 in one batched graph, to max(rel_tol, 1e-5)
+    std::vector<void *> xl(n);
+    std::vector<const void *> bl(n);
+    for (int i = 0; i < n; i++) {
+        int slot = 0;
+        for (int j = 0; j < i; j++)
+            slot += lats[j] == lats[i];
+        STAG_TRY(alloc_vec(lats[i], STAG_F32, &lats[i]->bxlo[slot]));
+        STAG_TRY(alloc_vec(lats[i], STAG_F32, &lats[i]->bblo[slot]));
+        CUDA_TRY(launch_convert(STAG_F32, hi, lats[i]->geom, bs[i]->data, lats[i]->bblo[slot], lats[i]->stream));
+        xl[i] = lats[i]->bxlo[slot];
+        bl[i] = lats[i]->bblo[slot];
+    }
+    const double sloppy = rel_tol > 1e-5 ? rel_tol : 1e-5;
+    std::vector<stag_solve_info> lo(n);
+    int st = batch_solve_raw(n, lats, xl.data(), bl.data(), masses, STAG_F32, sloppy, max_iter, lo.data());
+    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED)
+        return st;
+    // phase 2: per system, x = x_lo, then reliable-update CG on its residual
+    int worst = STAG_OK;
+    std::vector<stag_solve_info> out(n);
+    for (int i = 0; i < n; i++) {
+        stag_lattice L = lats[i];
+        const Geom &g = L->geom;
+        memset(&out[i], 0, sizeof out[i]);
+        STAG_TRY(ensure_cg_work(L, hi));
+        STAG_TRY(alloc_vec(L, hi, &L->ms_rhi[hi]));
+        STAG_TRY(alloc_vec(L, hi, &L->ms_ehi[hi]));
+        CUDA_TRY(launch_convert(hi, STAG_F32, g, xl[i], xs[i]->data, L->stream));
+        CUDA_TRY(cudaMemsetAsync(L->ms_ehi[hi], 0, field_bytes(L, hi), L->stream));
+        double bb = 0, rr0 = 0, rr1 = 0;
+        STAG_TRY(shifted_residual(L, hi, L->ms_ehi[hi], bs[i]->data, masses[i], nullptr, &bb));
+        STAG_TRY(shifted_residual(L, hi, xs[i]->data, bs[i]->data, masses[i], L->ms_rhi[hi], &rr0));
+        const double rel0 = bb > 0 ? std::sqrt(rr0 / bb) : 0.0;
+        stag_solve_info ri;
+        memset(&ri, 0, sizeof ri);
+        if (rel0 > rel_tol) {
+            const int rs = mixed_solve_raw(L, hi, inner_prec, L->ms_ehi[hi], L->ms_rhi[hi], field_bytes(L, hi),
+                                           masses[i], rel_tol / rel0, max_iter, delta, &ri);
+            if (rs != STAG_OK && rs != STAG_ERR_NOT_CONVERGED && rs != STAG_ERR_BREAKDOWN)
+                return rs;
+            CUDA_TRY(launch_axpy1(hi, g, L->ms_ehi[hi], xs[i]->data, L->stream));
+        }
+        STAG_TRY(shifted_residual(L, hi, xs[i]->data, bs[i]->data, masses[i], nullptr, &rr1));
+        out[i].iters = lo[i].iters;
+        out[i].restarts = ri.iters;
+        out[i].iter_rel_resid = rel0;
+        out[i].true_rel_resid = bb > 0 ? std::sqrt(rr1 / bb) : 0.0;
+        out[i].status = out[i].true_rel_resid <= rel_tol * 1.05 || bb == 0 ? STAG_OK
+                        : ri.status != STAG_OK ? ri.status : STAG_ERR_NOT_CONVERGED;
+        if (out[i].status != STAG_OK && worst == STAG_OK)
+            worst = out[i].status;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; i++)
+        out[i].seconds = secs;
+    if (infos)
+        memcpy(infos, out.data(), sizeof(stag_solve_info) * n);
+    if (worst != STAG_OK)
+        return fail(worst, "stag_cg_solve_batched_mixed: a system did not reach the tolerance");
+    return STAG_OK;
+}
+
+// --------------------------------------------------------------------------
+// autotuner: time the candidate block sizes, keep the fastest per lattice
+// and precision
+// --------------------------------------------------------------------------
+extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us) {
+    if (!lat)
+        return fail(STAG_ERR_ARG, "stag_lattice_autotune: lattice is NULL");
+    if (!prec_valid(prec))
+        return fail(STAG_ERR_ARG, "stag_lattice_autotune: bad precision %d", prec);
+    if (!lat->has_gauge || !lat->links[prec])
+        return fail(STAG_ERR_STATE, "stag_lattice_autotune: no %s gauge copy uploaded", prec_name(prec));
+    DEVICE_SCOPE(lat->device);
+    STAG_TRY(ensure_cg_work(lat, prec));
+    cudaStream_t s = lat->stream;
+    CgWork &w = lat->cg[prec];
+    const int cand[2] = {128, 256};
+    const int reps = 10;
+    double best = 1e300;
+    int best_b = 128;
+    for (int k = 0; k < 2; k++) {
+        DslashArgs a = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
+        for (int i = 0; i < 2; i++)
+            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        for (int i = 0; i < reps; i++)
+            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+        CUDA_TRY(cudaEventSynchronize(lat->ev1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+        const double us = 1e3 * ms / reps;
+        if (dslash_us)
+            dslash_us[k] = us;
+        if (us < best) {
+            best = us;
+            best_b = cand[k];
+        }
+    }
+    lat->dslash_block[prec] = best_b;
+    if (prec == STAG_F16)
+        return STAG_OK;  // no batched kernels in 16-bit storage
+    // batched kernels: one group with the largest K on this lattice
+    const int K = batch_max_k(prec);
+    std::vector<stag_lattice> lats(K, lat);
+    std::vector<void *> x(K);
+    std::vector<const void *> b(K);
+    for (int i = 0; i < K; i++) {
+        STAG_TRY(alloc_vec(lat, prec, &lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0]));
+        x[i] = lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0];
+        b[i] = w.p;
+    }
+    best = 1e300;
+    best_b = 128;
+    for (int k = 0; k < 2; k++) {
+        lat->batch_block[prec] = cand[k];
+        BatchPlan P;
+        STAG_TRY(plan_batch(P, K, lats.data(), x.data(), b.data(), prec));
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < 2 && e == cudaSuccess; i++)
+            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(lat->ev0, s);
+        for (int i = 0; i < reps && e == cudaSuccess; i++)
+            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(lat->ev1, s);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(lat->ev1);
+        float ms = 0.f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, lat->ev0, lat->ev1);
+        P.release();
+        if (e != cudaSuccess)
+            return fail(STAG_ERR_CUDA, "stag_lattice_autotune: %s", cudaGetErrorString(e));
+        const double us = 1e3 * ms / reps;
+        if (batch_us)
+            batch_us[k] = us;
+        if (us < best) {
+            best = us;
+            best_b = cand[k];
+        }
+    }
+    lat->batch_block[prec] = best_b;
     return STAG_OK;
 }
 

@@ -50,6 +50,7 @@ EXPORTED = [
     "stag_field_zero", "stag_field_storage",
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
     "stag_cg_solve", "stag_cg_solve_mixed", "stag_cg_multishift", "stag_cg_multishift_mixed",
+    "stag_cg_solve_batched", "stag_cg_solve_batched_mixed", "stag_lattice_autotune",
     "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
@@ -110,6 +111,9 @@ def lib():
             "stag_apply_M": ([P, P, P, D], I),
             "stag_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_apply_M_noalloc": ([P, P, D, D, P, P, D, P, P, P], I),
+            "stag_cg_solve_batched": ([I, P, P, P, P, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_cg_solve_batched_mixed": ([I, P, P, P, P, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
+            "stag_lattice_autotune": ([P, I, P, P], I),
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
@@ -327,6 +331,13 @@ class Lattice:
             _check(st)
         return st, [i.as_dict() for i in infos]
 
+    def autotune(self, prec="df64"):
+        """Pick the fastest block sizes for `prec`; returns the timings (us)."""
+        d = (ctypes.c_double * 2)()
+        b = (ctypes.c_double * 2)()
+        _check(lib().stag_lattice_autotune(self.handle, PREC[prec], d, b))
+        return {"dslash_us": {128: d[0], 256: d[1]}, "batch_us": {128: b[0], 256: b[1]}}
+
     def close(self):
         for f in list(self._fields):
             f.destroy()
@@ -364,6 +375,27 @@ def apply_M_noalloc(dims, fat, lng, mass, in_even, out_even, bc=BC_DEFAULT, c1=C
                                       ctypes.c_void_p(in_even.data_ptr()),
                                       ctypes.c_void_p(out_even.data_ptr()),
                                       ctypes.c_void_p(stream) if stream else None))
+
+
+def cg_batched(systems, tol: float = 1e-10, max_iter: int = 20000, mixed: Optional[str] = None,
+               delta: float = 0.1):
+    """Batched CG over [(lattice, x, b, mass), ...] (systems of one lattice
+    consecutive).  `mixed` = 'f32' or 'f16' runs the FP32 batch and refines.
+    Returns (status, [info per system])."""
+    n = len(systems)
+    lats = (ctypes.c_void_p * n)(*[s[0].handle.value for s in systems])
+    xs = (ctypes.c_void_p * n)(*[s[1].handle.value for s in systems])
+    bs = (ctypes.c_void_p * n)(*[s[2].handle.value for s in systems])
+    ms = (ctypes.c_double * n)(*[float(s[3]) for s in systems])
+    infos = (SolveInfo * n)()
+    if mixed is None:
+        st = lib().stag_cg_solve_batched(n, lats, xs, bs, ms, float(tol), int(max_iter), infos)
+    else:
+        st = lib().stag_cg_solve_batched_mixed(n, lats, xs, bs, ms, float(tol), int(max_iter),
+                                               PREC[mixed], float(delta), infos)
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+        _check(st)
+    return st, [i.as_dict() for i in infos]
 
 
 def version() -> str:
