@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_kernel(BatchArgs a, int ou
     __shared__ int act[K];
     const int gi = group_of(a, blockIdx.x);
     const BatchGroup &G = a.grp[gi];
-    load_active<K>(a, G, act, EPI != EPI_RESID);
+    // the true-residual passes (D of x, then the residual) cover every system
+    load_active<K>(a, G, act, EPI != EPI_RESID && !src_x);
     const int lblk = blockIdx.x - G.block0;
     const int c = lblk * BLOCK + threadIdx.x;
     const Geom &g = G.g;
