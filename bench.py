@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision comparison on the 48^3x96 workload")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched / multi-shift comparison (16 RHS on three lattices, 12 shifts)")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
                     help="host: the same CG kernels launched one by one (per-kernel profiling)")
     return ap.parse_args()
@@ -290,6 +292,9 @@ def run_native(args):
     mixed = None
     if not args.no_mixed:
         mixed = mixed_comparison(local, rank, args.cg_launch)
+    batched = None
+    if not args.no_batched:
+        batched = batched_comparison(local, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -334,8 +339,103 @@ def run_native(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
         "mixed_vs_fp64": mixed,
+        "batched_multishift": batched,
     }
     return line
+
+
+BATCH_LATTICES = (((16, 16, 16, 16), 6, 1003), ((24, 24, 24, 48), 5, 1004), ((32, 32, 32, 64), 5, 1005))
+BATCH_MASS = 0.02
+MS_DIMS = (24, 24, 24, 48)
+MS_SHIFTS = list(np.geomspace(1e-4, 0.5, 12))
+
+
+def batched_comparison(local, rank):
+    """16 Gaussian right-hand sides on 16^4, 24^3x48 and 32^3x64 (6 + 5 + 5,
+    m = 0.02, eps = 0.3) to a 1e-10 true residual: one after another with
+    double-float CG, in one batched double-float graph, and as one batched
+    FP32 graph refined per system with FP32- or 16-bit-inner reliable
+    updates.  Then 12 shifts 1e-4..0.5 (log-spaced) on 24^3x48: 12 separate
+    double-float solves against one double-float multi-shift solve and against
+    the FP32 multi-shift solve refined per shift.  One warm-up each; wall time
+    of the timed call."""
+    import torch
+    from paper_1411_2087_gb300 import stag, synth
+    dev = torch.device("cuda", local)
+    out = {"batched_workload": "16 RHS: 6 on 16^4, 5 on 24^3x48, 5 on 32^3x64; m=0.02, eps=0.3, tol=1e-10",
+           "multishift_workload": "12 shifts geomspace(1e-4, 0.5) on 24^3x48, m=0.02, eps=0.3, tol=1e-10"}
+    lats, systems = [], []
+    for dims, nrhs, seed in BATCH_LATTICES:
+        U = synth.su3_field(dims, 0.3, seed, device=dev)
+        lat = stag.Lattice(dims, device=local)
+        lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
+        del U
+        lat.autotune("df64")
+        lat.autotune("f32")
+        lats.append(lat)
+        Vh = int(np.prod(dims)) // 2
+        for k in range(nrhs):
+            b = synth.gaussian_colour_field(Vh, 3000 + 17 * seed + k + 100 * rank)
+            systems.append((lat, lat.field(stag.EVEN, "df64"), lat.field(stag.EVEN, "df64", b), BATCH_MASS))
+    torch.cuda.empty_cache()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    def one_by_one():
+        return [lat.cg(x, b, m, 1e-10, 20000) for lat, x, b, m in systems]
+
+    t_seq, infos = timed(one_by_one)
+    ok_seq = all(i["return"] == stag.OK for i in infos)
+    t_b, (st_b, infos_b) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000))
+    t_m32, (st_m32, infos_m32) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000, mixed="f32"))
+    t_m16, (st_m16, infos_m16) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000, mixed="f16"))
+
+    def worst(infs):
+        return max(i["true_rel_resid"] for i in infs)
+
+    out["sequential_df64_cg"] = {"seconds": round(t_seq, 4), "ok": ok_seq,
+                                 "iters": [i["iters"] for i in infos]}
+    out["batched_df64"] = {"seconds": round(t_b, 4), "ok": st_b == stag.OK,
+                           "max_true_rel_resid": worst(infos_b),
+                           "speedup_vs_sequential": round(t_seq / t_b, 3)}
+    out["batched_f32_refined_f32"] = {"seconds": round(t_m32, 4), "ok": st_m32 == stag.OK,
+                                      "max_true_rel_resid": worst(infos_m32),
+                                      "speedup_vs_sequential": round(t_seq / t_m32, 3)}
+    out["batched_f32_refined_f16"] = {"seconds": round(t_m16, 4), "ok": st_m16 == stag.OK,
+                                      "max_true_rel_resid": worst(infos_m16),
+                                      "speedup_vs_sequential": round(t_seq / t_m16, 3)}
+    # multi-shift on the 24^3x48 lattice of the batch
+    lat = lats[1]
+    b = systems[6][2]
+    xs = [lat.field(stag.EVEN, "df64") for _ in MS_SHIFTS]
+
+    def separate():
+        return [lat.cg(x, b, float(np.sqrt(BATCH_MASS ** 2 + s)), 1e-10, 20000)
+                for x, s in zip(xs, MS_SHIFTS)]
+
+    t_sep, inf_sep = timed(separate)
+    t_ms, (st_ms, inf_ms) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, 20000))
+    t_msm, (st_msm, inf_msm) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, 20000,
+                                                               mixed="f32"))
+    out["separate_df64_cg_12_shifts"] = {"seconds": round(t_sep, 4),
+                                         "ok": all(i["return"] == stag.OK for i in inf_sep),
+                                         "iters": [i["iters"] for i in inf_sep]}
+    out["multishift_df64"] = {"seconds": round(t_ms, 4), "ok": st_ms == stag.OK,
+                              "iters": max(i["iters"] for i in inf_ms),
+                              "max_true_rel_resid": worst(inf_ms),
+                              "speedup_vs_separate": round(t_sep / t_ms, 3)}
+    out["multishift_f32_refined"] = {"seconds": round(t_msm, 4), "ok": st_msm == stag.OK,
+                                     "max_true_rel_resid": worst(inf_msm),
+                                     "speedup_vs_separate": round(t_sep / t_msm, 3)}
+    for lat in lats:
+        lat.close()
+    return out
 
 
 MIXED_DIMS = (48, 48, 48, 96)
