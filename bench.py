@@ -367,6 +367,7 @@ def batched_comparison(local, rank):
     lats, systems = [], []
     for dims, nrhs, seed in BATCH_LATTICES:
         U = synth.su3_field(dims, 0.3, seed, device=dev)
+        torch.cuda.synchronize()
         lat = stag.Lattice(dims, device=local)
         lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
         del U
@@ -387,14 +388,16 @@ def batched_comparison(local, rank):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, r
 
+    maxit = 5000  # bounds the section's run time should a solve misbehave
+
     def one_by_one():
-        return [lat.cg(x, b, m, 1e-10, 20000) for lat, x, b, m in systems]
+        return [lat.cg(x, b, m, 1e-10, maxit) for lat, x, b, m in systems]
 
     t_seq, infos = timed(one_by_one)
     ok_seq = all(i["return"] == stag.OK for i in infos)
-    t_b, (st_b, infos_b) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000))
-    t_m32, (st_m32, infos_m32) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000, mixed="f32"))
-    t_m16, (st_m16, infos_m16) = timed(lambda: stag.cg_batched(systems, 1e-10, 20000, mixed="f16"))
+    t_b, (st_b, infos_b) = timed(lambda: stag.cg_batched(systems, 1e-10, maxit))
+    t_m32, (st_m32, infos_m32) = timed(lambda: stag.cg_batched(systems, 1e-10, maxit, mixed="f32"))
+    t_m16, (st_m16, infos_m16) = timed(lambda: stag.cg_batched(systems, 1e-10, maxit, mixed="f16"))
 
     def worst(infs):
         return max(i["true_rel_resid"] for i in infs)
@@ -416,12 +419,12 @@ def batched_comparison(local, rank):
     xs = [lat.field(stag.EVEN, "df64") for _ in MS_SHIFTS]
 
     def separate():
-        return [lat.cg(x, b, float(np.sqrt(BATCH_MASS ** 2 + s)), 1e-10, 20000)
+        return [lat.cg(x, b, float(np.sqrt(BATCH_MASS ** 2 + s)), 1e-10, maxit)
                 for x, s in zip(xs, MS_SHIFTS)]
 
     t_sep, inf_sep = timed(separate)
-    t_ms, (st_ms, inf_ms) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, 20000))
-    t_msm, (st_msm, inf_msm) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, 20000,
+    t_ms, (st_ms, inf_ms) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, maxit))
+    t_msm, (st_msm, inf_msm) = timed(lambda: lat.cg_multishift(xs, b, MS_SHIFTS, BATCH_MASS, 1e-10, maxit,
                                                                mixed="f32"))
     out["separate_df64_cg_12_shifts"] = {"seconds": round(t_sep, 4),
                                          "ok": all(i["return"] == stag.OK for i in inf_sep),

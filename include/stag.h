@@ -28,7 +28,11 @@
  *     site i of that parity at position i/2 ("checkerboard order").
  *   - Host pointers (STAG_PTR_HOST) are ordinary host memory (pinned memory
  *     makes copies faster); device pointers (STAG_PTR_DEVICE) must be device
- *     memory of the lattice's device.  The caller keeps ownership of every
+ *     memory of the lattice's device.  Gauge uploads and long-link builds
+ *     from device pointers synchronize the device first, so the source may
+ *     have been written on any stream; field imports from device pointers
+ *     read on the lattice stream, so the caller must have finished writing
+ *     the source (or written it on that stream).  The caller keeps ownership of every
  *     buffer it passes; the library copies what it needs before returning
  *     (or, for asynchronous calls on device pointers, before the work it
  *     enqueued completes).

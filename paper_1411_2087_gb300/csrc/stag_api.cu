@@ -428,6 +428,9 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
                 return fail(STAG_ERR_ARG, "stag_gauge_upload: precision %d (%s) not available", p,
                             prec_name(p));
     DEVICE_SCOPE(lat->device);
+    // device sources may have been written on any stream of the caller
+    if (ptr_kind == STAG_PTR_DEVICE)
+        CUDA_TRY(cudaDeviceSynchronize());
     double *fat_d = nullptr, *lng_d = nullptr;
     bool fat_owned = false, lng_owned = false;
     int st = gauge_to_device(lat, fat, ptr_kind, &fat_d, &fat_owned);
@@ -524,6 +527,8 @@ extern "C" int stag_long_links_build(stag_lattice lat, const double *fat, double
     if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
         return fail(STAG_ERR_ARG, "stag_long_links_build: bad ptr_kind %d", ptr_kind);
     DEVICE_SCOPE(lat->device);
+    if (ptr_kind == STAG_PTR_DEVICE)
+        CUDA_TRY(cudaDeviceSynchronize());
     const size_t bytes = 4ull * lat->V * 18 * sizeof(double);
     double *fat_d = nullptr;
     bool owned = false;
