@@ -168,3 +168,23 @@ def test_state_errors():
         with pytest.raises(stag.StagError) as ei:
             lat.dslash(fe, fe)  # parity mismatch
         assert ei.value.status == stag.ERR_STATE
+
+
+def test_upload_from_device_tensor_written_on_another_stream():
+    """Links generated by torch on its own stream and uploaded at once (no
+    synchronisation by the caller) must be read complete."""
+    import torch
+    dims = (16, 16, 8, 8)
+    dev = torch.device("cuda", 0)
+    Vh = int(np.prod(dims)) // 2
+    psi = synth.gaussian_colour_field(Vh, 44).numpy()
+    for _ in range(2):
+        U = synth.su3_field(dims, 0.3, 43, device=dev)  # queued on torch's stream
+        with stag.Lattice(dims) as lat:
+            lat.upload_gauge(U, None, precisions=("df64",))
+            fe = lat.field(stag.EVEN, "df64", psi)
+            fo = lat.field(stag.ODD, "df64")
+            lat.dslash(fo, fe)
+            Uh = U.cpu().numpy()
+            want = oracle.dslash_parity(dims, Uh, oracle.long_links(dims, Uh), 1, psi)
+            assert rel_err(fo.export(), want) <= 1e-12
