@@ -81,6 +81,8 @@ def _load():
         lib.orc_cg.argtypes = [P, P, D, D, P, P, D, P, P, D, I,
                                ctypes.POINTER(I), ctypes.POINTER(D), P]
         lib.orc_cg.restype = I
+        lib.orc_covconv.argtypes = [P, P, P, I, I, P, P, P]
+        lib.orc_covconv.restype = None
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = I
         lib.orc_set_num_threads.argtypes = [I]
@@ -224,3 +226,43 @@ def cb_to_full(dims, psi_cb, parity: int) -> np.ndarray:
     out = np.zeros((volume(dims), 3), dtype=np.complex128)
     out[idx] = np.asarray(psi_cb)[idx // 2]
     return out
+
+
+# --------------------------------------------------------------------------
+# learned preconditioner: gauge-covariant convolution net (oracle side)
+# --------------------------------------------------------------------------
+
+def covconv(dims, U, W, psi, bc=BC_DEFAULT) -> np.ndarray:
+    """One covariant convolution layer (see orc_covconv in stag_oracle.c).
+
+    W: complex [9][cout][cin]; psi: complex [cin][V][3] -> [cout][V][3]."""
+    d = _dims(dims)
+    V = volume(d)
+    U = _c(U, (4, V, 3, 3))
+    W = _c(W)
+    if W.ndim != 3 or W.shape[0] != 9:
+        raise ValueError("W must have shape [9][cout][cin]")
+    cout, cin = W.shape[1], W.shape[2]
+    psi = _c(psi, (cin, V, 3))
+    y = np.empty((cout, V, 3), dtype=np.complex128)
+    _load().orc_covconv(_ptr(d), _ptr(_bc(bc)), _ptr(U), cin, cout, _ptr(W), _ptr(psi), _ptr(y))
+    return y
+
+
+def net_apply(dims, U, weights, r_even, bc=BC_DEFAULT) -> np.ndarray:
+    """The preconditioner: r (even sites) zero-extended to the full lattice,
+    the layers applied in order (no nonlinearity), the result restricted to
+    the even sites.  weights: list of complex [9][cout][cin]."""
+    psi = cb_to_full(dims, r_even, 0)[None]
+    for W in weights:
+        psi = covconv(dims, U, W, psi, bc)
+    return full_to_cb(dims, psi[0], 0)
+
+
+def net_loss(dims, U, weights, rs, es, bc=BC_DEFAULT) -> float:
+    """sum over pairs of |N(r) - e|^2 / |e|^2."""
+    tot = 0.0
+    for r, e in zip(rs, es):
+        z = net_apply(dims, U, weights, r, bc)
+        tot += float(np.vdot(z - e, z - e).real / np.vdot(e, e).real)
+    return tot

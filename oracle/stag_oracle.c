@@ -341,6 +341,68 @@ int orc_cg(const int L[4], const double bc[4], double c1, double c3,
     return status;
 }
 
+/* ------------------------------------------------------------------ */
+/* gauge-covariant convolution (the learned preconditioner's layer)    */
+/* ------------------------------------------------------------------ */
+
+/*
+ * One layer on the full lattice, cin input and cout output channels of
+ * colour vectors, complex weights W[d][o][i] (d = 0: the site itself,
+ * d = 1 + 2 mu: the neighbour x + mu transported by U_mu(x), d = 2 + 2 mu:
+ * the neighbour x - mu transported by U_mu(x - mu)^+):
+ *
+ *   y_o(x) = sum_i [ W[0][o][i] psi_i(x)
+ *                    + sum_mu ( W[1+2mu][o][i] b(x,+1) U_mu(x) psi_i(x+mu)
+ *                             + W[2+2mu][o][i] b(x,-1) U_mu(x-mu)^+ psi_i(x-mu) ) ]
+ *
+ * with the raw links U (no phases, no coefficients) and the same boundary
+ * sign b = bc_mu^w of a wrapping hop as the Dslash.  Colour-blind complex
+ * weights and parallel transport make the layer gauge covariant.
+ * The paper has no learned preconditioner: this layer defines the one the
+ * library adds (a gauge-equivariant convolution in the sense of Lehner and
+ * Wettig's gauge-equivariant preconditioners for lattice QCD).
+ * psi: [cin][V][3], y: [cout][V][3].
+ */
+void orc_covconv(const int L[4], const double bc[4], const cplx *U, int cin, int cout,
+                 const cplx *W, const cplx *psi, cplx *y)
+{
+    const long V = volume_of(L);
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < V; i++) {
+        int x[4];
+        coords_of(L, i, x);
+        for (int o = 0; o < cout; o++) {
+            cplx acc[3] = {0, 0, 0};
+            for (int c = 0; c < cin; c++) {
+                const cplx *v = psi + ((long)c * V + i) * 3;
+                const cplx w0 = W[(0 * cout + o) * cin + c];
+                for (int a = 0; a < 3; a++)
+                    acc[a] += w0 * v[a];
+                for (int mu = 0; mu < 4; mu++) {
+                    double b;
+                    cplx t[3];
+                    /* forward neighbour */
+                    long j = hop(L, bc, x, mu, +1, &b);
+                    t[0] = t[1] = t[2] = 0;
+                    add_mat_vec(t, b, link_at(U, V, mu, i), psi + ((long)c * V + j) * 3);
+                    const cplx wf = W[((1 + 2 * mu) * cout + o) * cin + c];
+                    for (int a = 0; a < 3; a++)
+                        acc[a] += wf * t[a];
+                    /* backward neighbour */
+                    j = hop(L, bc, x, mu, -1, &b);
+                    t[0] = t[1] = t[2] = 0;
+                    add_adj_mat_vec(t, b, link_at(U, V, mu, j), psi + ((long)c * V + j) * 3);
+                    const cplx wb = W[((2 + 2 * mu) * cout + o) * cin + c];
+                    for (int a = 0; a < 3; a++)
+                        acc[a] += wb * t[a];
+                }
+            }
+            for (int a = 0; a < 3; a++)
+                y[((long)o * V + i) * 3 + a] = acc[a];
+        }
+    }
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -28,6 +28,14 @@ MUTATIONS = {
     "cg_beta_inverted": ("const double beta = rr_new / rr;", "const double beta = rr / rr_new;"),
     "cg_x_update": ("x[q] += alpha * p[q];", "x[q] += alpha * r[q];"),
     "mass_not_squared": ("out_even[k] = mass * mass * in_even[k]", "out_even[k] = mass * in_even[k]"),
+    "covconv_backward_link_site": (
+        "add_adj_mat_vec(t, b, link_at(U, V, mu, j), psi + ((long)c * V + j) * 3);",
+        "add_adj_mat_vec(t, b, link_at(U, V, mu, i), psi + ((long)c * V + j) * 3);"),
+    "covconv_backward_weight": ("const cplx wb = W[((2 + 2 * mu) * cout + o) * cin + c];",
+                                "const cplx wb = W[((1 + 2 * mu) * cout + o) * cin + c];"),
+    "covconv_forward_no_transport": (
+        "add_mat_vec(t, b, link_at(U, V, mu, i), psi + ((long)c * V + j) * 3);",
+        "add_adj_mat_vec(t, b, link_at(U, V, mu, i), psi + ((long)c * V + j) * 3);"),
 }
 
 
@@ -44,7 +52,8 @@ def _compile(src_text, out_dir, name):
 def _run_pins(so):
     env = dict(os.environ, STAG_ORACLE_SO=so, OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_net_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     return r.returncode
 

@@ -1,0 +1,160 @@
+"""Pins of the oracle's gauge-covariant convolution (the learned
+preconditioner's layer): identity weights, the free-field closed form of a
+plane wave, gauge covariance, the adjoint relation that defines the backward
+pass, and finite differences of the training loss against the gradient the
+adjoint relation gives."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2087_gb300 import synth
+
+BC = (1.0, 1.0, 1.0, -1.0)
+
+
+def rand_w(cout, cin, seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return scale * (rng.standard_normal((9, cout, cin)) + 1j * rng.standard_normal((9, cout, cin)))
+
+
+def adjoint_w(W):
+    """W^+[dbar][i][o] = conj(W[d][o][i]) with dbar the reversed hop."""
+    A = np.conj(np.transpose(W, (0, 2, 1))).copy()
+    out = A.copy()
+    for mu in range(4):
+        out[1 + 2 * mu] = A[2 + 2 * mu]
+        out[2 + 2 * mu] = A[1 + 2 * mu]
+    return out
+
+
+def colour(n, c, seed):
+    return np.stack([synth.gaussian_colour_field(n, seed + k).numpy() for k in range(c)])
+
+
+def coords(dims):
+    Lx, Ly, Lz, Lt = dims
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
+    return [a.reshape(-1) for a in (x, y, z, t)]
+
+
+def shift(field, dims, mu, s):
+    Lx, Ly, Lz, Lt = dims
+    f = field.reshape((Lt, Lz, Ly, Lx) + field.shape[1:])
+    return np.roll(f, -s, axis=3 - mu).reshape(field.shape)
+
+
+def test_identity_weights():
+    dims = (4, 2, 4, 2)
+    U = synth.su3_field(dims, 0.5, 1).numpy()
+    V = int(np.prod(dims))
+    psi = colour(V, 3, 10)
+    W = np.zeros((9, 3, 3), complex)
+    W[0] = np.eye(3)
+    assert np.array_equal(oracle.covconv(dims, U, W, psi), psi)
+
+
+@pytest.mark.parametrize("bc", [BC, (1.0, -1.0, 1.0, 1.0)])
+def test_free_field_plane_wave(bc):
+    dims = (4, 6, 2, 8)
+    V = int(np.prod(dims))
+    U = synth.unit_gauge_field(dims).numpy()
+    xs = coords(dims)
+    rng = np.random.default_rng(3)
+    p = [(2 * math.pi * rng.integers(L) + (math.pi if b < 0 else 0)) / L for L, b in zip(dims, bc)]
+    c = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    wave = np.exp(1j * sum(pm * xm for pm, xm in zip(p, xs)))[:, None] * c
+    W = rand_w(2, 1, 4)
+    y = oracle.covconv(dims, U, W, wave[None], bc)
+    for o in range(2):
+        factor = W[0, o, 0] + sum(W[1 + 2 * m, o, 0] * np.exp(1j * p[m]) +
+                                  W[2 + 2 * m, o, 0] * np.exp(-1j * p[m]) for m in range(4))
+        assert np.abs(y[o] - factor * wave).max() < 1e-13
+
+
+def test_gauge_covariance():
+    dims = (4, 4, 2, 6)
+    V = int(np.prod(dims))
+    U = synth.su3_field(dims, 0.6, 5).numpy()
+    g = synth.gauge_transform(dims, 6).numpy()
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[mu] = g @ U[mu] @ shift(g, dims, mu, 1).conj().transpose(0, 2, 1)
+    psi = colour(V, 2, 20)
+    W = rand_w(3, 2, 7)
+    gpsi = np.einsum("vab,cvb->cva", g, psi)
+    lhs = oracle.covconv(dims, Ug, W, gpsi)
+    rhs = np.einsum("vab,cvb->cva", g, oracle.covconv(dims, U, W, psi))
+    assert np.abs(lhs - rhs).max() < 1e-12
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 6, 4)])
+def test_adjoint_relation(dims):
+    V = int(np.prod(dims))
+    U = synth.su3_field(dims, 0.7, 8).numpy()
+    W = rand_w(3, 2, 9)
+    a = colour(V, 3, 30)
+    b = colour(V, 2, 40)
+    lhs = np.vdot(a.reshape(-1), oracle.covconv(dims, U, W, b).reshape(-1))
+    rhs = np.vdot(oracle.covconv(dims, U, adjoint_w(W), a).reshape(-1), b.reshape(-1))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def analytic_grad(dims, U, Ws, rs, es):
+    """dL/dW* from the adjoint relation: backward pass of the linear net."""
+    grads = [np.zeros_like(W) for W in Ws]
+    V = int(np.prod(dims))
+    for r, e in zip(rs, es):
+        acts = [oracle.cb_to_full(dims, r, 0)[None]]
+        for W in Ws:
+            acts.append(oracle.covconv(dims, U, W, acts[-1]))
+        z = oracle.full_to_cb(dims, acts[-1][0], 0)
+        g = oracle.cb_to_full(dims, (z - e) / np.vdot(e, e).real, 0)[None]
+        for li in range(len(Ws) - 1, -1, -1):
+            W = Ws[li]
+            a = acts[li]
+            cout, cin = W.shape[1], W.shape[2]
+            for d in range(9):
+                sel = np.zeros((9, 1, 1), complex)
+                sel[d] = 1
+                for i in range(cin):
+                    h = oracle.covconv(dims, U, sel, a[i:i + 1])[0]
+                    for o in range(cout):
+                        grads[li][d, o, i] += np.vdot(h.reshape(-1), g[o].reshape(-1))
+            g = oracle.covconv(dims, U, adjoint_w(W), g)
+    return grads
+
+
+def test_loss_gradient_finite_differences():
+    dims = (2, 2, 2, 4)
+    Vh = int(np.prod(dims)) // 2
+    U = synth.su3_field(dims, 0.5, 11).numpy()
+    Ws = [rand_w(2, 1, 12), rand_w(2, 2, 13), rand_w(1, 2, 14)]
+    rs = [synth.gaussian_colour_field(Vh, 50 + k).numpy() for k in range(2)]
+    es = [synth.gaussian_colour_field(Vh, 60 + k).numpy() for k in range(2)]
+    grads = analytic_grad(dims, U, Ws, rs, es)
+    h = 1e-6
+    for li, W in enumerate(Ws):
+        for idx in np.ndindex(W.shape):
+            for unit in (1.0, 1j):
+                Wp = [w.copy() for w in Ws]
+                Wm = [w.copy() for w in Ws]
+                Wp[li][idx] += unit * h
+                Wm[li][idx] -= unit * h
+                fd = (oracle.net_loss(dims, U, Wp, rs, es) - oracle.net_loss(dims, U, Wm, rs, es)) / (2 * h)
+                an = 2 * (grads[li][idx].real if unit == 1.0 else grads[li][idx].imag)
+                assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (li, idx, unit, fd, an)
+
+
+def test_net_ignores_odd_input_and_is_linear():
+    dims = (4, 4, 2, 2)
+    Vh = int(np.prod(dims)) // 2
+    U = synth.su3_field(dims, 0.4, 15).numpy()
+    Ws = [rand_w(4, 1, 16), rand_w(4, 4, 17), rand_w(1, 4, 18)]
+    r1 = synth.gaussian_colour_field(Vh, 70).numpy()
+    r2 = synth.gaussian_colour_field(Vh, 71).numpy()
+    z = oracle.net_apply(dims, U, Ws, 2.0 * r1 - 0.5j * r2)
+    z1 = oracle.net_apply(dims, U, Ws, r1)
+    z2 = oracle.net_apply(dims, U, Ws, r2)
+    assert np.abs(z - (2.0 * z1 - 0.5j * z2)).max() < 1e-12 * np.abs(z).max()
