@@ -1,41 +1,17 @@
-// libstag C ABI: handles, argument checking, memory, uploads and the CG
-// solve graph.  Declarations and documentation are in include/stag.h.
-#include <cuda_runtime.h>
-
-#include <chrono>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstddef>
-#include <cstring>
-#include <mutex>
-#include <new>
-#include <string>
-#include <vector>
-
-#include "../../include/stag.h"
-#include "batched.cuh"
-#include "dslash.cuh"
-#include "kernels.h"
-
-using namespace stag;
+// libstag C ABI: handles, argument checking, memory, uploads, Dslash and the
+// plain CG solve graph.  The other solvers are in solvers.cu, the learned
+// preconditioner in learned.cu; declarations and documentation in
+// include/stag.h.
+#include "api_internal.h"
 
 // --------------------------------------------------------------------------
 // errors
 // --------------------------------------------------------------------------
 static thread_local std::string g_last_error;
 
-static int fail(int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    g_last_error = buf;
-    return code;
-}
-
 namespace stag {
+void set_error_message(const char *msg) { g_last_error = msg; }
+
 int set_error(int code, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -46,134 +22,6 @@ int set_error(int code, const char *fmt, ...) {
     return code;
 }
 }  // namespace stag
-
-#define CUDA_TRY(call)                                                                     \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail(e_ == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,  \
-                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
-                        __LINE__);                                                         \
-    } while (0)
-
-#define STAG_TRY(call)           \
-    do {                         \
-        int s_ = (call);         \
-        if (s_ != STAG_OK)       \
-            return s_;           \
-    } while (0)
-
-// make `dev` current for the scope of one API call, then restore
-struct DeviceGuard {
-    int prev = -1;
-    int err = 0;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess)
-            prev = -1;
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess)
-            err = 1;
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
-            cudaSetDevice(prev);
-    }
-};
-
-#define DEVICE_SCOPE(dev)                                                        \
-    DeviceGuard guard_(dev);                                                     \
-    if (guard_.err)                                                              \
-        return fail(STAG_ERR_CUDA, "cannot make CUDA device %d current", (dev));
-
-static bool prec_valid(int p) {
-    return p == STAG_F64 || p == STAG_DF64 || p == STAG_F32 || p == STAG_F16;
-}
-static const char *prec_name(int p) {
-    switch (p) {
-    case STAG_F64: return "F64";
-    case STAG_DF64: return "DF64";
-    case STAG_F32: return "F32";
-    case STAG_F16: return "F16";
-    default: return "?";
-    }
-}
-
-// --------------------------------------------------------------------------
-// handles
-// --------------------------------------------------------------------------
-struct CgWork {
-    int prec = -1;
-    void *r = nullptr, *p = nullptr, *Ap = nullptr, *t = nullptr, *bw = nullptr, *xw = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphConditionalHandle cond = 0;
-};
-
-struct stag_lattice_s {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    int dims[4];
-    double bc[4];
-    long long V = 0, Vh = 0;
-    Geom geom;
-    void *links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision [2][8][9][stride]
-    bool has_gauge = false;
-    double c1 = 0, c3 = 0;
-    int live_fields = 0;
-    // reduction scratch and scalars
-    double *partial = nullptr;
-    CgScalars *sc = nullptr;
-    CgScalars *sc_host = nullptr;  // pinned mirror
-    CgWork cg[4];
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double *staging = nullptr;
-    float link_scale[2] = {0.f, 0.f};      // 16-bit links: field max / 32767 (one-link, three-link)
-    float *xs = nullptr;                   // F32 correction x_sloppy of the mixed solver
-    unsigned *absmax = nullptr;            // scratch for the 16-bit link scales
-    struct MixedGraph {
-        cudaGraphExec_t exec = nullptr;
-        cudaGraph_t graph = nullptr;
-        cudaGraphConditionalHandle cond = 0;
-    } mixed[4][4];
-    // multi-shift CG
-    ShiftState *ms_state = nullptr;        // device, MS_MAX entries
-    ShiftState *ms_state_host = nullptr;   // pinned mirror
-    double *ms_true = nullptr;             // device, |b - (M + sigma_s) x_s|^2 per shift
-    double *ms_true_host = nullptr;        // pinned mirror
-    void *ms_p[4][MS_MAX] = {};            // search directions per precision
-    void *ms_xlo[MS_MAX] = {};             // FP32 solutions of the sloppy multi-shift phase
-    void *ms_blo = nullptr;                // FP32 right-hand side of that phase
-    void *ms_rhi[4] = {};                  // residual of one shift (high precision)
-    void *ms_ehi[4] = {};                  // correction of one shift (high precision)
-    // batched CG: per-system work vectors (r, p, Ap, t) by precision and slot
-    void *bwork[4][BATCH_MAX_G * BATCH_KMAX][4] = {};
-    void *bxlo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 solutions of the sloppy batched phase
-    void *bblo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 right-hand sides of that phase
-    int batch_block[4] = {128, 128, 128, 128};  // block size of the batched kernels (autotuned)
-    int dslash_block[4] = {0, 0, 0, 0};         // block size of the Dslash kernels (0 = default)
-    int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
-    int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
-};
-
-struct stag_field_s {
-    stag_lattice lat = nullptr;
-    int parity = 0;
-    int prec = 0;
-    void *data = nullptr;
-    size_t bytes = 0;
-};
-
-static size_t field_bytes(const stag_lattice lat, int prec) {
-    return prec_vec_bytes(prec, (size_t)lat->geom.stride);
-}
-static size_t link_bytes(const stag_lattice lat, int prec) {
-    return 2ull * 8 * 9 * lat->geom.stride * prec_link_elem_bytes(prec);
-}
-static const void *links_of(const stag_lattice lat, int prec, int parity) {
-    const char *base = (const char *)lat->links[prec];
-    return base + (size_t)parity * 8 * 9 * lat->geom.stride * prec_link_elem_bytes(prec);
-}
 
 // --------------------------------------------------------------------------
 // lattice
@@ -263,18 +111,6 @@ extern "C" int stag_lattice_create(stag_lattice *out, const int dims[4], const d
     memset(lat->sc_host, 0, sizeof(CgScalars));
     *out = lat;
     return STAG_OK;
-}
-
-static void free_cg(CgWork &w) {
-    if (w.exec)
-        cudaGraphExecDestroy(w.exec);
-    if (w.graph)
-        cudaGraphDestroy(w.graph);
-    void *bufs[] = {w.r, w.p, w.Ap, w.t, w.bw, w.xw};
-    for (void *b : bufs)
-        if (b)
-            cudaFree(b);
-    w = CgWork();
 }
 
 extern "C" int stag_lattice_destroy(stag_lattice lat) {
@@ -373,18 +209,6 @@ extern "C" int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk)
     if (mode == STAG_CG_LAUNCH_HOST)
         lat->cg_chunk = chunk;
     return STAG_OK;
-}
-
-static void drop_mixed_graphs(stag_lattice lat) {
-    for (int h = 0; h < 4; h++)
-        for (int l = 0; l < 4; l++) {
-            auto &m = lat->mixed[h][l];
-            if (m.exec)
-                cudaGraphExecDestroy(m.exec);
-            if (m.graph)
-                cudaGraphDestroy(m.graph);
-            m = stag_lattice_s::MixedGraph();
-        }
 }
 
 // --------------------------------------------------------------------------
@@ -688,24 +512,6 @@ static int check_pair(stag_lattice lat, const stag_field out, const stag_field i
     return STAG_OK;
 }
 
-static DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, const void *in, void *out) {
-    DslashArgs a;
-    memset(&a, 0, sizeof a);
-    a.g = lat->geom;
-    a.out_par = out_par;
-    a.links_out = links_of(lat, prec, out_par);
-    a.links_in = links_of(lat, prec, 1 - out_par);
-    a.in = in;
-    a.out = out;
-    a.partial = lat->partial;
-    a.sc = lat->sc;
-    if (prec == STAG_F16) {
-        a.link_scale[0] = lat->link_scale[0];
-        a.link_scale[1] = lat->link_scale[1];
-    }
-    return a;
-}
-
 static int dslash_impl(stag_lattice lat, stag_field out, const stag_field in, int out_par,
                        const char *who) {
     STAG_TRY(check_pair(lat, out, in, out_par, who));
@@ -724,40 +530,6 @@ extern "C" int stag_dslash_oe(stag_lattice lat, stag_field out_odd, const stag_f
 }
 
 // odd temporary of the CG workspace of one precision
-static int ensure_cg_work(stag_lattice lat, int prec) {
-    CgWork &w = lat->cg[prec];
-    if (w.r)
-        return STAG_OK;
-    w.prec = prec;
-    const size_t b = field_bytes(lat, prec);
-    void **bufs[] = {&w.r, &w.p, &w.Ap, &w.t, &w.bw, &w.xw};
-    for (void **pp : bufs) {
-        cudaError_t e = cudaMalloc(pp, b);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(*pp, 0, b, lat->stream);
-        if (e != cudaSuccess) {
-            free_cg(w);
-            return fail(STAG_ERR_NOMEM, "CG workspace (%s): %s", prec_name(prec), cudaGetErrorString(e));
-        }
-    }
-    return STAG_OK;
-}
-
-static int upload_scalars(stag_lattice lat, double mass, double tol, int max_iter, bool has_cond,
-                          cudaGraphConditionalHandle cond, double delta = 0.0) {
-    // pageable source: the copy has read it when cudaMemcpyAsync returns
-    CgScalars h;
-    memset(&h, 0, sizeof h);
-    h.m2 = make_dpair(mass * mass);
-    h.tol2 = tol * tol;
-    h.max_iter = max_iter;
-    h.has_cond = has_cond ? 1 : 0;
-    h.cond = cond;
-    h.delta = delta;
-    CUDA_TRY(cudaMemcpyAsync(lat->sc, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
-    return STAG_OK;
-}
-
 extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_field in_even,
                             double mass) {
     if (!lat || !out_even || !in_even)
@@ -991,1071 +763,6 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
 
 
 // --------------------------------------------------------------------------
-// mixed-precision CG with reliable updates (kernels_mixed.cu has the method)
-// --------------------------------------------------------------------------
-static const int *reliable_flag(stag_lattice lat) {
-    return (const int *)((const char *)lat->sc + offsetof(CgScalars, reliable));
-}
-
-static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool host_mode) {
-    CgWork &H = lat->cg[hi];
-    CgWork &L = lat->cg[lo];
-    cudaStream_t s = lat->stream;
-    const Geom &g = lat->geom;
-    cudaError_t e;
-    // low precision: t_s = D_oe p; Ap = m^2 p - D_eo t_s, alpha
-    DslashArgs a1 = dslash_args(lat, lo, STAG_ODD, L.p, L.t);
-    a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_NONE, a1, lat->dslash_block[lo], s)) != cudaSuccess)
-        return e;
-    DslashArgs a2 = dslash_args(lat, lo, STAG_EVEN, L.t, L.Ap);
-    a2.p = L.p;
-    a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_M_PAP, a2, lat->dslash_block[lo], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_mixed_update(lo, g, lat->xs, L.r, L.p, L.Ap, lat->partial, lat->sc, s)) != cudaSuccess)
-        return e;
-    // reliable update (every kernel returns at once unless it is due)
-    if ((e = launch_mixed_accum(hi, g, H.xw, lat->xs, lat->sc, s)) != cudaSuccess)
-        return e;
-    DslashArgs a3 = dslash_args(lat, hi, STAG_ODD, H.xw, H.t);
-    a3.gate = reliable_flag(lat);
-    if ((e = launch_dslash(hi, EPI_NONE, a3, lat->dslash_block[hi], s)) != cudaSuccess)
-        return e;
-    DslashArgs a4 = dslash_args(lat, hi, STAG_EVEN, H.t, H.r);
-    a4.p = H.xw;
-    a4.b = H.bw;
-    a4.gate = reliable_flag(lat);
-    if ((e = launch_dslash(hi, EPI_RESID_STORE, a4, lat->dslash_block[hi], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_mixed_restart(hi, lo, g, H.r, L.r, lat->sc, s)) != cudaSuccess)
-        return e;
-    return launch_cg_p_update(lo, g, L.r, L.p, lat->sc, s);
-}
-
-static cudaError_t enqueue_mixed_init(stag_lattice lat, int hi, int lo) {
-    CgWork &H = lat->cg[hi];
-    CgWork &L = lat->cg[lo];
-    return launch_mixed_init(hi, lo, lat->geom, H.xw, H.r, H.bw, lat->xs, L.r, L.p, lat->partial,
-                             lat->sc, lat->stream);
-}
-
-static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
-    auto &mg = lat->mixed[hi][lo];
-    cudaStream_t s = lat->stream;
-    cudaGraph_t graph = nullptr;
-    CUDA_TRY(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle cond;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(graph);
-        return fail(STAG_ERR_CUDA, "cudaGraphConditionalHandleCreate: %s", cudaGetErrorString(e));
-    }
-    auto bail = [&](const char *what, cudaError_t err) {
-        cudaStreamCaptureStatus st;
-        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(s, &junk);
-        }
-        cudaGetLastError();
-        cudaGraphDestroy(graph);
-        return fail(STAG_ERR_CUDA, "mixed CG graph (%s): %s", what, cudaGetErrorString(err));
-    };
-    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin capture", e);
-    if ((e = enqueue_mixed_init(lat, hi, lo)) != cudaSuccess)
-        return bail("init", e);
-    cudaStreamCaptureStatus st;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
-        return bail("capture info", e);
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t loop;
-    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
-        return bail("add loop node", e);
-    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
-                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
-        return bail("update deps", e);
-    cudaGraph_t captured = nullptr;
-    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
-        return bail("end capture", e);
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin body capture", e);
-    if ((e = enqueue_mixed_body(lat, hi, lo, false)) != cudaSuccess)
-        return bail("body", e);
-    cudaGraph_t body_out = nullptr;
-    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
-        return bail("end body capture", e);
-    cudaGraphExec_t exec = nullptr;
-    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
-        return bail("instantiate", e);
-    mg.graph = graph;
-    mg.exec = exec;
-    mg.cond = cond;
-    return STAG_OK;
-}
-
-// the mixed solver on raw buffers of precision hi (x_data, b_data: bytes each);
-// arguments already checked
-static int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *b_data,
-                           size_t bytes, double mass, double rel_tol, int max_iter, double delta,
-                           stag_solve_info *info) {
-    STAG_TRY(ensure_cg_work(lat, hi));
-    STAG_TRY(ensure_cg_work(lat, lo));
-    if (!lat->xs) {
-        CUDA_TRY(cudaMalloc(&lat->xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
-        CUDA_TRY(cudaMemsetAsync(lat->xs, 0, prec_vec_bytes(STAG_F32, lat->geom.stride), lat->stream));
-    }
-    CgWork &H = lat->cg[hi];
-    cudaStream_t s = lat->stream;
-    CUDA_TRY(cudaMemcpyAsync(H.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
-    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
-        auto &mg = lat->mixed[hi][lo];
-        if (!mg.exec)
-            STAG_TRY(build_mixed_graph(lat, hi, lo));
-        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(cudaGraphLaunch(mg.exec, s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
-    } else {
-        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0, delta));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(enqueue_mixed_init(lat, hi, lo));
-        const int chunk = lat->cg_chunk;
-        const long long max_chunks = (long long)max_iter / chunk + 2;
-        for (long long k = 0; k < max_chunks; k++) {
-            CUDA_TRY(cudaMemcpyAsync(&lat->sc_host->status, &lat->sc->status, sizeof(int),
-                                     cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            if (lat->sc_host->status != CG_RUNNING)
-                break;
-            for (int j = 0; j < chunk; j++)
-                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true));
-        }
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
-    }
-    CUDA_TRY(cudaMemcpyAsync(x_data, H.xw, bytes, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
-    const CgScalars &h = *lat->sc_host;
-    stag_solve_info local;
-    memset(&local, 0, sizeof local);
-    local.iters = h.iter;
-    local.restarts = h.restarts;
-    local.status = h.status == CG_CONVERGED ? STAG_OK
-                   : h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
-                                              : STAG_ERR_NOT_CONVERGED;
-    local.true_rel_resid = h.bb > 0 ? std::sqrt(h.true_rr / h.bb) : 0.0;
-    local.iter_rel_resid = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-    local.seconds = ms * 1e-3;
-    // model: low-precision iterations plus one high-precision M per update
-    const double lo_real = lo == STAG_F16 ? 2.0 : 4.0;
-    const double Vh = (double)lat->Vh;
-    const double model_bytes = h.iter * ((2.0 * 300 + 60) * lo_real + (lo == STAG_F16 ? 2 * 2 * 4 : 0) + 48) * Vh +
-                         h.restarts * (2.0 * 2400 + 4 * 48) * Vh;
-    const double flops = h.iter * (2.0 * 1146 + 72) * Vh + h.restarts * (2.0 * 1146 + 24) * Vh;
-    if (ms > 0) {
-        local.gflops = flops / (ms * 1e-3) / 1e9;
-        local.gbs = model_bytes / (ms * 1e-3) / 1e9;
-    }
-    if (info)
-        *info = local;
-    if (local.status != STAG_OK)
-        return fail(local.status, "stag_cg_solve_mixed: %s after %d iterations (true |r|/|b| = %.3e)",
-                    local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
-                    local.true_rel_resid);
-    return STAG_OK;
-}
-
-extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_field b, double mass,
-                                   double rel_tol, int max_iter, int inner_prec, double delta,
-                                   stag_solve_info *info) {
-    if (info)
-        memset(info, 0, sizeof *info);
-    if (!lat || !x || !b)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: NULL argument");
-    if (x->lat != lat || b->lat != lat)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: field belongs to another lattice");
-    if (x->parity != STAG_EVEN || b->parity != STAG_EVEN)
-        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: x and b must be even fields");
-    if (x->prec != b->prec || (x->prec != STAG_F64 && x->prec != STAG_DF64))
-        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: x and b must both be F64 or both DF64");
-    if (x == b)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: x and b must differ");
-    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: inner precision must be F32 or F16");
-    if (!(mass > 0) || !std::isfinite(mass))
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: mass must be positive and finite");
-    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: rel_tol must be >= 0");
-    if (max_iter < 0)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: max_iter must be >= 0");
-    if (!(delta > 0 && delta < 1))
-        return fail(STAG_ERR_ARG, "stag_cg_solve_mixed: delta must be in (0, 1)");
-    const int hi = x->prec, lo = inner_prec;
-    if (!lat->has_gauge || !lat->links[hi] || !lat->links[lo])
-        return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: needs %s and %s gauge copies", prec_name(hi),
-                    prec_name(lo));
-    DEVICE_SCOPE(lat->device);
-    return mixed_solve_raw(lat, hi, lo, x->data, b->data, b->bytes, mass, rel_tol, max_iter, delta, info);
-}
-
-
-// --------------------------------------------------------------------------
-// multi-shift CG (kernels_multishift.cu has the recurrences)
-// --------------------------------------------------------------------------
-static int alloc_vec(stag_lattice lat, int prec, void **p) {
-    if (*p)
-        return STAG_OK;
-    const size_t b = field_bytes(lat, prec);
-    cudaError_t e = cudaMalloc(p, b);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(*p, 0, b, lat->stream);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return fail(STAG_ERR_NOMEM, "vector allocation (%s): %s", prec_name(prec), cudaGetErrorString(e));
-    }
-    return STAG_OK;
-}
-
-static int ensure_ms_state(stag_lattice lat) {
-    if (lat->ms_state)
-        return STAG_OK;
-    CUDA_TRY(cudaMalloc(&lat->ms_state, sizeof(ShiftState) * MS_MAX));
-    CUDA_TRY(cudaMallocHost(&lat->ms_state_host, sizeof(ShiftState) * MS_MAX));
-    CUDA_TRY(cudaMalloc(&lat->ms_true, sizeof(double) * MS_MAX));
-    CUDA_TRY(cudaMallocHost(&lat->ms_true_host, sizeof(double) * MS_MAX));
-    return STAG_OK;
-}
-
-static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, bool host_mode) {
-    CgWork &w = lat->cg[prec];
-    cudaStream_t s = lat->stream;
-    cudaError_t e;
-    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, a.p[a.base], w.t);
-    a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
-        return e;
-    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
-    a2.p = a.p[a.base];
-    a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_M_PAP, a2, lat->dslash_block[prec], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_ms_update(prec, lat->geom, a, w.Ap, lat->partial, lat->sc, lat->ms_state, s)) !=
-        cudaSuccess)
-        return e;
-    return launch_ms_p(prec, lat->geom, a, lat->sc, lat->ms_state, s);
-}
-
-// one graph: init, WHILE(body); built per call (the solution buffers are
-// the caller's) and destroyed after it
-static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass_base, double tol,
-                        int max_iter) {
-    cudaStream_t s = lat->stream;
-    cudaGraph_t graph = nullptr;
-    CUDA_TRY(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle cond;
-    cudaGraphExec_t exec = nullptr;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
-    auto bail = [&](const char *what, cudaError_t err) {
-        cudaStreamCaptureStatus st;
-        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(s, &junk);
-        }
-        cudaGetLastError();
-        if (exec)
-            cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        return fail(STAG_ERR_CUDA, "multi-shift graph (%s): %s", what, cudaGetErrorString(err));
-    };
-    if (e != cudaSuccess)
-        return bail("conditional handle", e);
-    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin capture", e);
-    if ((e = launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s)) != cudaSuccess)
-        return bail("init", e);
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
-        return bail("capture info", e);
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t loop;
-    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
-        return bail("add loop node", e);
-    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
-                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
-        return bail("update deps", e);
-    cudaGraph_t captured = nullptr;
-    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
-        return bail("end capture", e);
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin body capture", e);
-    if ((e = enqueue_ms_body(lat, prec, a, false)) != cudaSuccess)
-        return bail("body", e);
-    cudaGraph_t body_out = nullptr;
-    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
-        return bail("end body capture", e);
-    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
-        return bail("instantiate", e);
-    STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, true, cond));
-    if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess)
-        return bail("launch", e);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return bail("run", e);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    return STAG_OK;
-}
-
-// multi-shift CG on raw buffers of precision prec; infos[s] per shift
-static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const double *shifts, int n,
-                        const void *b_data, size_t bytes, double mass, double tol, int max_iter,
-                        stag_solve_info *infos, double *seconds) {
-    STAG_TRY(ensure_cg_work(lat, prec));
-    STAG_TRY(ensure_ms_state(lat));
-    for (int k = 0; k < n; k++)
-        STAG_TRY(alloc_vec(lat, prec, &lat->ms_p[prec][k]));
-    CgWork &w = lat->cg[prec];
-    cudaStream_t s = lat->stream;
-    MsArgs a;
-    memset(&a, 0, sizeof a);
-    a.n = n;
-    a.base = 0;
-    for (int k = 1; k < n; k++)
-        if (shifts[k] < shifts[a.base])
-            a.base = k;
-    for (int k = 0; k < n; k++) {
-        a.delta[k] = shifts[k] - shifts[a.base];
-        a.x[k] = x_data[k];
-        a.p[k] = lat->ms_p[prec][k];
-    }
-    a.b = w.bw;
-    a.r = w.r;
-    const double mass_base = std::sqrt(mass * mass + shifts[a.base]);
-    CUDA_TRY(cudaMemcpyAsync(w.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
-    CUDA_TRY(cudaEventRecord(lat->ev0, s));
-    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
-        STAG_TRY(run_ms_graph(lat, prec, a, mass_base, tol, max_iter));
-    } else {
-        STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, false, 0));
-        CUDA_TRY(launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s));
-        const int chunk = lat->cg_chunk;
-        const long long max_chunks = (long long)max_iter / chunk + 2;
-        for (long long k = 0; k < max_chunks; k++) {
-            CUDA_TRY(cudaMemcpyAsync(&lat->sc_host->status, &lat->sc->status, sizeof(int),
-                                     cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            if (lat->sc_host->status != CG_RUNNING)
-                break;
-            for (int j = 0; j < chunk; j++)
-                CUDA_TRY(enqueue_ms_body(lat, prec, a, true));
-        }
-    }
-    CUDA_TRY(cudaEventRecord(lat->ev1, s));
-    // true residual of every shift, |b - (M + sigma_s) x_s|^2
-    for (int k = 0; k < n; k++) {
-        DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, x_data[k], w.t);
-        CUDA_TRY(launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s));
-        DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, nullptr);
-        a2.p = x_data[k];
-        a2.b = w.bw;
-        a2.m2 = make_dpair(mass * mass + shifts[k]);
-        a2.m2_in_args = 1;
-        CUDA_TRY(launch_dslash(prec, EPI_RESID, a2, lat->dslash_block[prec], s));
-        CUDA_TRY(cudaMemcpyAsync(lat->ms_true + k, (const char *)lat->sc + offsetof(CgScalars, true_rr),
-                                 sizeof(double), cudaMemcpyDeviceToDevice, s));
-    }
-    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(lat->ms_state_host, lat->ms_state, sizeof(ShiftState) * n,
-                             cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(lat->ms_true_host, lat->ms_true, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
-    if (seconds)
-        *seconds = ms * 1e-3;
-    const CgScalars &h = *lat->sc_host;
-    int worst = STAG_OK;
-    for (int k = 0; k < n; k++) {
-        const ShiftState &st = lat->ms_state_host[k];
-        stag_solve_info &inf = infos[k];
-        memset(&inf, 0, sizeof inf);
-        inf.iters = h.bb > 0 && st.iters == 0 && h.status != CG_CONVERGED ? h.iter : st.iters;
-        inf.status = h.status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
-                     : (st.active == 0 ? STAG_OK : STAG_ERR_NOT_CONVERGED);
-        inf.true_rel_resid = h.bb > 0 ? std::sqrt(lat->ms_true_host[k] / h.bb) : 0.0;
-        inf.iter_rel_resid = h.bb > 0 ? std::sqrt(st.zeta * st.zeta * h.rr / h.bb) : 0.0;
-        inf.seconds = ms * 1e-3;
-        if (inf.status != STAG_OK && worst == STAG_OK)
-            worst = inf.status;
-    }
-    // model rates on the first entry: base CG plus the per-shift vector passes
-    const double rb = prec == STAG_F32 ? 4.0 : 8.0;
-    const double Vh = (double)lat->Vh;
-    const double bytes_it = ((2.0 * 300 + 60) * rb + n * 4 * 6 * rb) * Vh;
-    const double flops_it = (2.0 * 1146 + 72 + n * 24.0) * Vh;
-    if (ms > 0) {
-        infos[0].gbs = bytes_it * h.iter / (ms * 1e-3) / 1e9;
-        infos[0].gflops = flops_it * h.iter / (ms * 1e-3) / 1e9;
-    }
-    return worst;
-}
-
-static int check_ms_args(stag_lattice lat, stag_field *xs, const double *shifts, int n, const stag_field b,
-                         double mass, double rel_tol, int max_iter, const char *who) {
-    if (!lat || !xs || !shifts || !b)
-        return fail(STAG_ERR_ARG, "%s: NULL argument", who);
-    if (n < 1 || n > MS_MAX)
-        return fail(STAG_ERR_ARG, "%s: number of shifts %d not in [1, %d]", who, n, MS_MAX);
-    if (b->lat != lat || b->parity != STAG_EVEN)
-        return fail(STAG_ERR_ARG, "%s: b must be an even field of this lattice", who);
-    for (int k = 0; k < n; k++) {
-        if (!xs[k] || xs[k]->lat != lat || xs[k]->parity != STAG_EVEN || xs[k]->prec != b->prec)
-            return fail(STAG_ERR_ARG, "%s: xs[%d] must be an even field of b's precision", who, k);
-        if (xs[k] == b)
-            return fail(STAG_ERR_ARG, "%s: xs[%d] aliases b", who, k);
-        for (int j = 0; j < k; j++)
-            if (xs[j] == xs[k])
-                return fail(STAG_ERR_ARG, "%s: xs[%d] and xs[%d] are the same field", who, j, k);
-        if (!(shifts[k] >= 0) || !std::isfinite(shifts[k]))
-            return fail(STAG_ERR_ARG, "%s: shift %d must be finite and >= 0", who, k);
-    }
-    if (!(mass > 0) || !std::isfinite(mass))
-        return fail(STAG_ERR_ARG, "%s: mass must be positive and finite", who);
-    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
-        return fail(STAG_ERR_ARG, "%s: rel_tol must be >= 0", who);
-    if (max_iter < 0)
-        return fail(STAG_ERR_ARG, "%s: max_iter must be >= 0", who);
-    return STAG_OK;
-}
-
-extern "C" int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double *shifts, int n,
-                                  const stag_field b, double mass, double rel_tol, int max_iter,
-                                  stag_solve_info *infos) {
-    STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift"));
-    const int prec = b->prec;
-    if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
-        return fail(STAG_ERR_STATE, "stag_cg_multishift: fields must be F64, DF64 or F32");
-    if (!lat->has_gauge || !lat->links[prec])
-        return fail(STAG_ERR_STATE, "stag_cg_multishift: no %s gauge copy uploaded", prec_name(prec));
-    DEVICE_SCOPE(lat->device);
-    void *xd[MS_MAX];
-    for (int k = 0; k < n; k++)
-        xd[k] = xs[k]->data;
-    stag_solve_info local[MS_MAX];
-    const int st = ms_solve_raw(lat, prec, xd, shifts, n, b->data, b->bytes, mass, rel_tol, max_iter,
-                                local, nullptr);
-    if (infos)
-        memcpy(infos, local, sizeof(stag_solve_info) * n);
-    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED && st != STAG_ERR_BREAKDOWN)
-        return st;
-    if (st != STAG_OK)
-        return fail(st, "stag_cg_multishift: %s", st == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged");
-    return STAG_OK;
-}
-
-// |b - (M + m_k^2 - m^2) x|^2 into the host, r stored to r_out (precision hi)
-static int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, double mk, void *r_out,
-                            double *rr) {
-    CgWork &H = lat->cg[hi];
-    cudaStream_t s = lat->stream;
-    DslashArgs a1 = dslash_args(lat, hi, STAG_ODD, x, H.t);
-    CUDA_TRY(launch_dslash(hi, EPI_NONE, a1, lat->dslash_block[hi], s));
-    DslashArgs a2 = dslash_args(lat, hi, STAG_EVEN, H.t, r_out);
-    a2.p = x;
-    a2.b = b;
-    a2.m2 = make_dpair(mk * mk);
-    a2.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(hi, r_out ? EPI_RESID_STORE : EPI_RESID, a2, 0, s));
-    CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    *rr = lat->sc_host->true_rr;
-    return STAG_OK;
-}
-
-extern "C" int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,
-                                        const stag_field b, double mass, double rel_tol, int max_iter,
-                                        int inner_prec, double delta, stag_solve_info *infos) {
-    STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift_mixed"));
-    const int hi = b->prec;
-    if (hi != STAG_F64 && hi != STAG_DF64)
-        return fail(STAG_ERR_STATE, "stag_cg_multishift_mixed: fields must be F64 or DF64");
-    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
-        return fail(STAG_ERR_ARG, "stag_cg_multishift_mixed: inner precision must be F32 or F16");
-    if (!(delta > 0 && delta < 1))
-        return fail(STAG_ERR_ARG, "stag_cg_multishift_mixed: delta must be in (0, 1)");
-    if (!lat->has_gauge || !lat->links[hi] || !lat->links[STAG_F32] || !lat->links[inner_prec])
-        return fail(STAG_ERR_STATE, "stag_cg_multishift_mixed: needs %s, F32 and %s gauge copies",
-                    prec_name(hi), prec_name(inner_prec));
-    DEVICE_SCOPE(lat->device);
-    const auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t s = lat->stream;
-    const Geom &g = lat->geom;
-    STAG_TRY(ensure_cg_work(lat, hi));
-    STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_blo));
-    for (int k = 0; k < n; k++)
-        STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_xlo[k]));
-    STAG_TRY(alloc_vec(lat, hi, &lat->ms_rhi[hi]));
-    STAG_TRY(alloc_vec(lat, hi, &lat->ms_ehi[hi]));
-    // |b|^2 in the high precision: the residual of x = 0
-    CUDA_TRY(cudaMemsetAsync(lat->ms_ehi[hi], 0, field_bytes(lat, hi), s));
-    double bb = 0;
-    STAG_TRY(shifted_residual(lat, hi, lat->ms_ehi[hi], b->data, mass, nullptr, &bb));
-    // phase 1: all shifts at once in FP32, to max(rel_tol, 1e-5)
-    CUDA_TRY(launch_convert(STAG_F32, hi, g, b->data, lat->ms_blo, s));
-    const double sloppy_tol = rel_tol > 1e-5 ? rel_tol : 1e-5;
-    stag_solve_info lo_info[MS_MAX];
-    int st = ms_solve_raw(lat, STAG_F32, lat->ms_xlo, shifts, n, lat->ms_blo, field_bytes(lat, STAG_F32),
-                          mass, sloppy_tol, max_iter, lo_info, nullptr);
-    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED)
-        return st;
-    // phase 2: per shift, x_k = x_lo, then the mixed solver on its residual
-    int worst = STAG_OK;
-    stag_solve_info out[MS_MAX];
-    for (int k = 0; k < n; k++) {
-        memset(&out[k], 0, sizeof out[k]);
-        CUDA_TRY(launch_convert(hi, STAG_F32, g, lat->ms_xlo[k], xs[k]->data, s));
-        const double mk = std::sqrt(mass * mass + shifts[k]);
-        double rr0 = 0;
-        STAG_TRY(shifted_residual(lat, hi, xs[k]->data, b->data, mk, lat->ms_rhi[hi], &rr0));
-        const double rel0 = bb > 0 ? std::sqrt(rr0 / bb) : 0.0;
-        stag_solve_info ri;
-        memset(&ri, 0, sizeof ri);
-        if (rel0 > rel_tol) {
-            const int rs = mixed_solve_raw(lat, hi, inner_prec, lat->ms_ehi[hi], lat->ms_rhi[hi],
-                                           field_bytes(lat, hi), mk, rel_tol / rel0, max_iter, delta, &ri);
-            if (rs != STAG_OK && rs != STAG_ERR_NOT_CONVERGED && rs != STAG_ERR_BREAKDOWN)
-                return rs;
-            CUDA_TRY(launch_axpy1(hi, g, lat->ms_ehi[hi], xs[k]->data, s));
-        }
-        double rr1 = 0;
-        STAG_TRY(shifted_residual(lat, hi, xs[k]->data, b->data, mk, nullptr, &rr1));
-        out[k].iters = lo_info[k].iters;
-        out[k].restarts = ri.iters;  // refinement iterations (inner precision)
-        out[k].true_rel_resid = bb > 0 ? std::sqrt(rr1 / bb) : 0.0;
-        out[k].iter_rel_resid = rel0;
-        out[k].status = out[k].true_rel_resid <= rel_tol * 1.05 || bb == 0 ? STAG_OK
-                        : ri.status != STAG_OK ? ri.status : STAG_ERR_NOT_CONVERGED;
-        if (out[k].status != STAG_OK && worst == STAG_OK)
-            worst = out[k].status;
-    }
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    for (int k = 0; k < n; k++)
-        out[k].seconds = secs;
-    if (infos)
-        memcpy(infos, out, sizeof(stag_solve_info) * n);
-    if (worst != STAG_OK)
-        return fail(worst, "stag_cg_multishift_mixed: a shift did not reach the tolerance");
-    return STAG_OK;
-}
-
-// --------------------------------------------------------------------------
-// batched CG over many (lattice, right-hand side) systems, one graph
-// --------------------------------------------------------------------------
-struct BatchPlan {
-    BatchArgs a;
-    int nsys = 0;
-    int prec = 0;
-    cudaStream_t stream = nullptr;
-    int block = 128;
-    // device buffers owned by one call
-    CgScalars *sys = nullptr;
-    unsigned *tickets = nullptr;
-    BatchCtl *ctl = nullptr;
-    double *partial = nullptr;
-    void release() {
-        if (sys) cudaFree(sys);
-        if (tickets) cudaFree(tickets);
-        if (ctl) cudaFree(ctl);
-        if (partial) cudaFree(partial);
-        sys = nullptr;
-        tickets = nullptr;
-        ctl = nullptr;
-        partial = nullptr;
-    }
-};
-
-// group systems by lattice (consecutive, at most batch_max_k per group) and
-// allocate work vectors and reduction buffers; x/b are raw buffers
-static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, const void *const *b,
-                      int prec) {
-    const int K = batch_max_k(prec);
-    memset(&P.a, 0, sizeof P.a);
-    P.nsys = n;
-    P.prec = prec;
-    P.stream = lats[0]->stream;
-    P.block = lats[0]->batch_block[prec];
-    int slot_of_lat[BATCH_MAX_G * BATCH_KMAX];
-    int G = 0, blocks = 0;
-    size_t partial_total = 0;
-    for (int i = 0; i < n; i++) {
-        // slot = index of this system among the earlier systems of its lattice
-        int slot = 0;
-        for (int j = 0; j < i; j++)
-            if (lats[j] == lats[i])
-                slot++;
-        slot_of_lat[i] = slot;
-        const bool new_group = G == 0 || lats[i] != lats[i - 1] || P.a.grp[G - 1].K == K;
-        if (new_group) {
-            if (G == BATCH_MAX_G)
-                return fail(STAG_ERR_ARG, "stag_cg_solve_batched: more than %d groups (at most %d "
-                            "systems of one lattice per group; keep systems of a lattice together)",
-                            BATCH_MAX_G, K);
-            BatchGroup &gr = P.a.grp[G];
-            gr.g = lats[i]->geom;
-            gr.K = 0;
-            gr.block0 = blocks;
-            gr.nblocks = (gr.g.Vh + P.block - 1) / P.block;
-            gr.sys0 = i;
-            gr.links[0] = links_of(lats[i], prec, 0);
-            gr.links[1] = links_of(lats[i], prec, 1);
-            gr.link_scale[0] = gr.link_scale[1] = 0.f;
-            blocks += gr.nblocks;
-            partial_total += (size_t)gr.nblocks * BATCH_KMAX;
-            G++;
-        }
-        BatchGroup &gr = P.a.grp[G - 1];
-        const int k = gr.K++;
-        stag_lattice L = lats[i];
-        for (int v = 0; v < 4; v++)
-            STAG_TRY(alloc_vec(L, prec, &L->bwork[prec][slot_of_lat[i]][v]));
-        gr.x[k] = x[i];
-        gr.b[k] = b[i];
-        gr.r[k] = L->bwork[prec][slot_of_lat[i]][0];
-        gr.p[k] = L->bwork[prec][slot_of_lat[i]][1];
-        gr.Ap[k] = L->bwork[prec][slot_of_lat[i]][2];
-        gr.t[k] = L->bwork[prec][slot_of_lat[i]][3];
-    }
-    P.a.G = G;
-    P.a.nblocks = blocks;
-    cudaError_t e;
-    if ((e = cudaMalloc(&P.sys, sizeof(CgScalars) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&P.tickets, sizeof(unsigned) * G)) != cudaSuccess ||
-        (e = cudaMalloc(&P.ctl, sizeof(BatchCtl))) != cudaSuccess ||
-        (e = cudaMalloc(&P.partial, sizeof(double) * partial_total)) != cudaSuccess) {
-        P.release();
-        return fail(STAG_ERR_NOMEM, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
-    }
-    // every system starts as CG_RUNNING (0) until the init kernel decides
-    if ((e = cudaMemsetAsync(P.sys, 0, sizeof(CgScalars) * n, P.stream)) != cudaSuccess) {
-        P.release();
-        return fail(STAG_ERR_CUDA, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
-    }
-    size_t off = 0;
-    for (int gi = 0; gi < G; gi++) {
-        P.a.grp[gi].partial = P.partial + off;
-        off += (size_t)P.a.grp[gi].nblocks * BATCH_KMAX;
-    }
-    P.a.sys = P.sys;
-    P.a.tickets = P.tickets;
-    P.a.ctl = P.ctl;
-    return STAG_OK;
-}
-
-static cudaError_t enqueue_batch_body(const BatchPlan &P) {
-    cudaError_t e;
-    const int w[4] = {BATCH_DSLASH_OE, BATCH_M_PAP, BATCH_UPDATE, BATCH_P};
-    for (int k = 0; k < 4; k++)
-        if ((e = launch_batch(P.prec, w[k], P.a, P.block, P.stream)) != cudaSuccess)
-            return e;
-    return cudaSuccess;
-}
-
-// run the batched CG to completion: init, WHILE(body), true residuals
-static int run_batch(BatchPlan &P, const double *masses, double tol, int max_iter, float *ms_out) {
-    cudaStream_t s = P.stream;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    CUDA_TRY(cudaGraphCreate(&graph, 0));
-    cudaGraphConditionalHandle cond;
-    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 0, 0);
-    auto bail = [&](const char *what, cudaError_t err) {
-        cudaStreamCaptureStatus st;
-        if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(s, &junk);
-        }
-        cudaGetLastError();
-        if (exec)
-            cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        return fail(STAG_ERR_CUDA, "batched CG graph (%s): %s", what, cudaGetErrorString(err));
-    };
-    if (e != cudaSuccess)
-        return bail("conditional handle", e);
-    // scalars: per system m^2, tol^2, max_iter; control block
-    {
-        std::vector<CgScalars> h(P.nsys);
-        memset(h.data(), 0, sizeof(CgScalars) * P.nsys);
-        for (int i = 0; i < P.nsys; i++) {
-            h[i].m2 = make_dpair(masses[i] * masses[i]);
-            h[i].tol2 = tol * tol;
-            h[i].max_iter = max_iter;
-        }
-        BatchCtl c;
-        memset(&c, 0, sizeof c);
-        c.cond = cond;
-        c.has_cond = 1;
-        if ((e = cudaMemcpyAsync(P.sys, h.data(), sizeof(CgScalars) * P.nsys, cudaMemcpyHostToDevice, s)) !=
-                cudaSuccess ||
-            (e = cudaMemcpyAsync(P.ctl, &c, sizeof c, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-            (e = cudaMemsetAsync(P.tickets, 0, sizeof(unsigned) * P.a.G, s)) != cudaSuccess)
-            return bail("scalars", e);
-    }
-    if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin capture", e);
-    if ((e = launch_batch(P.prec, BATCH_INIT, P.a, P.block, s)) != cudaSuccess)
-        return bail("init", e);
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    if ((e = cudaStreamGetCaptureInfo(s, &cst, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
-        return bail("capture info", e);
-    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t loop;
-    if ((e = cudaGraphAddNode(&loop, graph, deps, nullptr, ndeps, &cp)) != cudaSuccess)
-        return bail("add loop node", e);
-    if ((e = cudaStreamUpdateCaptureDependencies(s, &loop, nullptr, 1,
-                                                 cudaStreamSetCaptureDependencies)) != cudaSuccess)
-        return bail("update deps", e);
-    if ((e = launch_batch(P.prec, BATCH_DSLASH_X, P.a, P.block, s)) != cudaSuccess ||
-        (e = launch_batch(P.prec, BATCH_RESID, P.a, P.block, s)) != cudaSuccess)
-        return bail("true residual", e);
-    cudaGraph_t captured = nullptr;
-    if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
-        return bail("end capture", e);
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
-        return bail("begin body capture", e);
-    if ((e = enqueue_batch_body(P)) != cudaSuccess)
-        return bail("body", e);
-    cudaGraph_t body_out = nullptr;
-    if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
-        return bail("end body capture", e);
-    if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
-        return bail("instantiate", e);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, s);
-    e = cudaGraphLaunch(exec, s);
-    cudaEventRecord(e1, s);
-    cudaError_t e2 = cudaStreamSynchronize(s);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (e != cudaSuccess || e2 != cudaSuccess)
-        return bail("run", e != cudaSuccess ? e : e2);
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
-    if (ms_out)
-        *ms_out = ms;
-    return STAG_OK;
-}
-
-static int check_batch(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs, const double *masses,
-                       double rel_tol, int max_iter, const char *who) {
-    if (!lats || !xs || !bs || !masses)
-        return fail(STAG_ERR_ARG, "%s: NULL argument", who);
-    if (n < 1 || n > BATCH_MAX_G * BATCH_KMAX)
-        return fail(STAG_ERR_ARG, "%s: number of systems %d not in [1, %d]", who, n, BATCH_MAX_G * BATCH_KMAX);
-    for (int i = 0; i < n; i++) {
-        if (!lats[i] || !xs[i] || !bs[i])
-            return fail(STAG_ERR_ARG, "%s: NULL lattice or field for system %d", who, i);
-        if (lats[i]->device != lats[0]->device)
-            return fail(STAG_ERR_ARG, "%s: all lattices must be on one device", who);
-        if (xs[i]->lat != lats[i] || bs[i]->lat != lats[i] || xs[i]->parity != STAG_EVEN ||
-            bs[i]->parity != STAG_EVEN)
-            return fail(STAG_ERR_ARG, "%s: system %d needs even fields of its lattice", who, i);
-        if (xs[i]->prec != bs[0]->prec || bs[i]->prec != bs[0]->prec)
-            return fail(STAG_ERR_ARG, "%s: all fields must have one precision", who);
-        if (xs[i] == bs[i])
-            return fail(STAG_ERR_ARG, "%s: x and b of system %d alias", who, i);
-        for (int j = 0; j < i; j++)
-            if (xs[j] == xs[i])
-                return fail(STAG_ERR_ARG, "%s: systems %d and %d share a solution field", who, j, i);
-        if (!(masses[i] > 0) || !std::isfinite(masses[i]))
-            return fail(STAG_ERR_ARG, "%s: mass %d must be positive and finite", who, i);
-        // systems of one lattice must be consecutive
-        for (int j = 0; j + 1 < i; j++)
-            if (lats[j] == lats[i] && lats[j + 1] != lats[i])
-                return fail(STAG_ERR_ARG, "%s: systems of one lattice must be consecutive", who);
-    }
-    if (!(rel_tol >= 0) || !std::isfinite(rel_tol))
-        return fail(STAG_ERR_ARG, "%s: rel_tol must be >= 0", who);
-    if (max_iter < 0)
-        return fail(STAG_ERR_ARG, "%s: max_iter must be >= 0", who);
-    return STAG_OK;
-}
-
-static int batch_solve_raw(int n, stag_lattice *lats, void *const *x, const void *const *b, const double *masses,
-                           int prec, double rel_tol, int max_iter, stag_solve_info *infos) {
-    for (int i = 0; i < n; i++)
-        if (!lats[i]->has_gauge || !lats[i]->links[prec])
-            return fail(STAG_ERR_STATE, "stag_cg_solve_batched: lattice of system %d has no %s gauge copy",
-                        i, prec_name(prec));
-    // work of the other lattices' streams must be done before the batch
-    // runs on the first lattice's stream
-    for (int i = 1; i < n; i++)
-        if (lats[i]->stream != lats[0]->stream)
-            CUDA_TRY(cudaStreamSynchronize(lats[i]->stream));
-    BatchPlan P;
-    STAG_TRY(plan_batch(P, n, lats, x, b, prec));
-    float ms = 0.f;
-    int st = run_batch(P, masses, rel_tol, max_iter, &ms);
-    if (st != STAG_OK) {
-        P.release();
-        return st;
-    }
-    std::vector<CgScalars> h(n);
-    cudaError_t e = cudaMemcpy(h.data(), P.sys, sizeof(CgScalars) * n, cudaMemcpyDeviceToHost);
-    P.release();
-    if (e != cudaSuccess)
-        return fail(STAG_ERR_CUDA, "stag_cg_solve_batched: %s", cudaGetErrorString(e));
-    int worst = STAG_OK;
-    double total_bytes = 0, total_flops = 0;
-    const double rb = prec == STAG_F32 ? 4.0 : 8.0;
-    for (int i = 0; i < n; i++) {
-        stag_solve_info &inf = infos[i];
-        memset(&inf, 0, sizeof inf);
-        inf.iters = h[i].iter;
-        inf.status = h[i].status == CG_CONVERGED ? STAG_OK
-                     : h[i].status == CG_BREAKDOWN ? STAG_ERR_BREAKDOWN
-                                                   : STAG_ERR_NOT_CONVERGED;
-        inf.true_rel_resid = h[i].bb > 0 ? std::sqrt(h[i].true_rr / h[i].bb) : 0.0;
-        inf.iter_rel_resid = h[i].bb > 0 ? std::sqrt(h[i].rr / h[i].bb) : 0.0;
-        inf.seconds = ms * 1e-3;
-        if (inf.status != STAG_OK && worst == STAG_OK)
-            worst = inf.status;
-        total_bytes += (2.0 * 300 + 60) * rb * (double)lats[i]->Vh * h[i].iter;
-        total_flops += (2.0 * 1146 + 72) * (double)lats[i]->Vh * h[i].iter;
-    }
-    if (ms > 0) {
-        // per-system-equivalent rates of the whole batch (links counted once
-        // per system, as if solved alone)
-        infos[0].gbs = total_bytes / (ms * 1e-3) / 1e9;
-        infos[0].gflops = total_flops / (ms * 1e-3) / 1e9;
-    }
-    return worst;
-}
-
-extern "C" int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
-                                     const double *masses, double rel_tol, int max_iter,
-                                     stag_solve_info *infos) {
-    STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched"));
-    const int prec = bs[0]->prec;
-    if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
-        return fail(STAG_ERR_STATE, "stag_cg_solve_batched: fields must be F64, DF64 or F32");
-    DEVICE_SCOPE(lats[0]->device);
-    std::vector<void *> x(n);
-    std::vector<const void *> b(n);
-    for (int i = 0; i < n; i++) {
-        x[i] = xs[i]->data;
-        b[i] = bs[i]->data;
-    }
-    std::vector<stag_solve_info> loc(n);
-    const int st = batch_solve_raw(n, lats, x.data(), b.data(), masses, prec, rel_tol, max_iter, loc.data());
-    if (infos)
-        memcpy(infos, loc.data(), sizeof(stag_solve_info) * n);
-    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED && st != STAG_ERR_BREAKDOWN)
-        return st;
-    if (st != STAG_OK)
-        return fail(st, "stag_cg_solve_batched: a system %s", st == STAG_ERR_BREAKDOWN ? "broke down"
-                                                                                      : "did not converge");
-    return STAG_OK;
-}
-
-extern "C" int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
-                                           const double *masses, double rel_tol, int max_iter, int inner_prec,
-                                           double delta, stag_solve_info *infos) {
-    STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched_mixed"));
-    const int hi = bs[0]->prec;
-    if (hi != STAG_F64 && hi != STAG_DF64)
-        return fail(STAG_ERR_STATE, "stag_cg_solve_batched_mixed: fields must be F64 or DF64");
-    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
-        return fail(STAG_ERR_ARG, "stag_cg_solve_batched_mixed: inner precision must be F32 or F16");
-    if (!(delta > 0 && delta < 1))
-        return fail(STAG_ERR_ARG, "stag_cg_solve_batched_mixed: delta must be in (0, 1)");
-    for (int i = 0; i < n; i++)
-        if (!lats[i]->has_gauge || !lats[i]->links[hi] || !lats[i]->links[STAG_F32] ||
-            !lats[i]->links[inner_prec])
-            return fail(STAG_ERR_STATE, "stag_cg_solve_batched_mixed: every lattice needs %s, F32 and %s "
-                        "gauge copies", prec_name(hi), prec_name(inner_prec));
-    DEVICE_SCOPE(lats[0]->device);
-    const auto t0 = std::chrono::steady_clock::now();
-    // phase 1: every system in FP32 in one batched graph, to max(rel_tol, 1e-5)
-    std::vector<void *> xl(n);
-    std::vector<const void *> bl(n);
-    for (int i = 0; i < n; i++) {
-        int slot = 0;
-        for (int j = 0; j < i; j++)
-            slot += lats[j] == lats[i];
-        STAG_TRY(alloc_vec(lats[i], STAG_F32, &lats[i]->bxlo[slot]));
-        STAG_TRY(alloc_vec(lats[i], STAG_F32, &lats[i]->bblo[slot]));
-        CUDA_TRY(launch_convert(STAG_F32, hi, lats[i]->geom, bs[i]->data, lats[i]->bblo[slot], lats[i]->stream));
-        xl[i] = lats[i]->bxlo[slot];
-        bl[i] = lats[i]->bblo[slot];
-    }
-    const double sloppy = rel_tol > 1e-5 ? rel_tol : 1e-5;
-    std::vector<stag_solve_info> lo(n);
-    int st = batch_solve_raw(n, lats, xl.data(), bl.data(), masses, STAG_F32, sloppy, max_iter, lo.data());
-    if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED)
-        return st;
-    // phase 2: per system, x = x_lo, then reliable-update CG on its residual
-    int worst = STAG_OK;
-    std::vector<stag_solve_info> out(n);
-    for (int i = 0; i < n; i++) {
-        stag_lattice L = lats[i];
-        const Geom &g = L->geom;
-        memset(&out[i], 0, sizeof out[i]);
-        STAG_TRY(ensure_cg_work(L, hi));
-        STAG_TRY(alloc_vec(L, hi, &L->ms_rhi[hi]));
-        STAG_TRY(alloc_vec(L, hi, &L->ms_ehi[hi]));
-        CUDA_TRY(launch_convert(hi, STAG_F32, g, xl[i], xs[i]->data, L->stream));
-        CUDA_TRY(cudaMemsetAsync(L->ms_ehi[hi], 0, field_bytes(L, hi), L->stream));
-        double bb = 0, rr0 = 0, rr1 = 0;
-        STAG_TRY(shifted_residual(L, hi, L->ms_ehi[hi], bs[i]->data, masses[i], nullptr, &bb));
-        STAG_TRY(shifted_residual(L, hi, xs[i]->data, bs[i]->data, masses[i], L->ms_rhi[hi], &rr0));
-        const double rel0 = bb > 0 ? std::sqrt(rr0 / bb) : 0.0;
-        stag_solve_info ri;
-        memset(&ri, 0, sizeof ri);
-        if (rel0 > rel_tol) {
-            const int rs = mixed_solve_raw(L, hi, inner_prec, L->ms_ehi[hi], L->ms_rhi[hi], field_bytes(L, hi),
-                                           masses[i], rel_tol / rel0, max_iter, delta, &ri);
-            if (rs != STAG_OK && rs != STAG_ERR_NOT_CONVERGED && rs != STAG_ERR_BREAKDOWN)
-                return rs;
-            CUDA_TRY(launch_axpy1(hi, g, L->ms_ehi[hi], xs[i]->data, L->stream));
-        }
-        STAG_TRY(shifted_residual(L, hi, xs[i]->data, bs[i]->data, masses[i], nullptr, &rr1));
-        out[i].iters = lo[i].iters;
-        out[i].restarts = ri.iters;
-        out[i].iter_rel_resid = rel0;
-        out[i].true_rel_resid = bb > 0 ? std::sqrt(rr1 / bb) : 0.0;
-        out[i].status = out[i].true_rel_resid <= rel_tol * 1.05 || bb == 0 ? STAG_OK
-                        : ri.status != STAG_OK ? ri.status : STAG_ERR_NOT_CONVERGED;
-        if (out[i].status != STAG_OK && worst == STAG_OK)
-            worst = out[i].status;
-    }
-    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    for (int i = 0; i < n; i++)
-        out[i].seconds = secs;
-    if (infos)
-        memcpy(infos, out.data(), sizeof(stag_solve_info) * n);
-    if (worst != STAG_OK)
-        return fail(worst, "stag_cg_solve_batched_mixed: a system did not reach the tolerance");
-    return STAG_OK;
-}
-
-// --------------------------------------------------------------------------
-// autotuner: time the candidate block sizes, keep the fastest per lattice
-// and precision
-// --------------------------------------------------------------------------
-extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us) {
-    if (!lat)
-        return fail(STAG_ERR_ARG, "stag_lattice_autotune: lattice is NULL");
-    if (!prec_valid(prec))
-        return fail(STAG_ERR_ARG, "stag_lattice_autotune: bad precision %d", prec);
-    if (!lat->has_gauge || !lat->links[prec])
-        return fail(STAG_ERR_STATE, "stag_lattice_autotune: no %s gauge copy uploaded", prec_name(prec));
-    DEVICE_SCOPE(lat->device);
-    STAG_TRY(ensure_cg_work(lat, prec));
-    cudaStream_t s = lat->stream;
-    CgWork &w = lat->cg[prec];
-    const int cand[2] = {128, 256};
-    const int reps = 10;
-    double best = 1e300;
-    int best_b = 128;
-    for (int k = 0; k < 2; k++) {
-        DslashArgs a = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
-        for (int i = 0; i < 2; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        for (int i = 0; i < reps; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
-        CUDA_TRY(cudaEventSynchronize(lat->ev1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
-        const double us = 1e3 * ms / reps;
-        if (dslash_us)
-            dslash_us[k] = us;
-        if (us < best) {
-            best = us;
-            best_b = cand[k];
-        }
-    }
-    lat->dslash_block[prec] = best_b;
-    if (prec == STAG_F16)
-        return STAG_OK;  // no batched kernels in 16-bit storage
-    // batched kernels: one group with the largest K on this lattice
-    const int K = batch_max_k(prec);
-    std::vector<stag_lattice> lats(K, lat);
-    std::vector<void *> x(K);
-    std::vector<const void *> b(K);
-    for (int i = 0; i < K; i++) {
-        STAG_TRY(alloc_vec(lat, prec, &lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0]));
-        x[i] = lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0];
-        b[i] = w.p;
-    }
-    best = 1e300;
-    best_b = 128;
-    for (int k = 0; k < 2; k++) {
-        lat->batch_block[prec] = cand[k];
-        BatchPlan P;
-        STAG_TRY(plan_batch(P, K, lats.data(), x.data(), b.data(), prec));
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < 2 && e == cudaSuccess; i++)
-            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(lat->ev0, s);
-        for (int i = 0; i < reps && e == cudaSuccess; i++)
-            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(lat->ev1, s);
-        if (e == cudaSuccess)
-            e = cudaEventSynchronize(lat->ev1);
-        float ms = 0.f;
-        if (e == cudaSuccess)
-            e = cudaEventElapsedTime(&ms, lat->ev0, lat->ev1);
-        P.release();
-        if (e != cudaSuccess)
-            return fail(STAG_ERR_CUDA, "stag_lattice_autotune: %s", cudaGetErrorString(e));
-        const double us = 1e3 * ms / reps;
-        if (batch_us)
-            batch_us[k] = us;
-        if (us < best) {
-            best = us;
-            best_b = cand[k];
-        }
-    }
-    lat->batch_block[prec] = best_b;
-    return STAG_OK;
-}
-
-// --------------------------------------------------------------------------
 extern "C" const char *stag_strerror(int status) {
     switch (status) {
     case STAG_OK: return "ok";
@@ -2073,3 +780,4 @@ extern "C" const char *stag_strerror(int status) {
 extern "C" const char *stag_last_error_message(void) { return g_last_error.c_str(); }
 
 extern "C" const char *stag_version(void) { return "0.1.0"; }
+
