@@ -266,6 +266,77 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
  * overwrites the lattice's internal work vectors. */
 int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us);
 
+/* ---- learned preconditioner ------------------------------------------------
+ * The paper has no learned preconditioner; this one is a small
+ * gauge-equivariant convolutional network (in the manner of Lehner and
+ * Wettig's preconditioner networks for lattice QCD) trained on the GPU by
+ * the library's own forward and backward kernels and applied inside
+ * flexible CG.  Layers 1 -> C -> C -> 1 channels of colour vectors on the
+ * full lattice, no nonlinearity:
+ *
+ *   y_o(x) = sum_i [ W[0][o][i] psi_i(x)
+ *                    + sum_mu ( W[1+2mu][o][i] U_mu(x) psi_i(x+mu)
+ *                             + W[2+2mu][o][i] U_mu(x-mu)^+ psi_i(x-mu) ) ]
+ *
+ * with the raw fat links U (no phases or coefficients; the lattice's
+ * boundary sign on wrapping hops) and complex colour-blind weights, so the
+ * net is gauge covariant.  As a preconditioner it maps an even residual r
+ * (zero on odd sites) to z = N(r) restricted to the even sites.  Weights:
+ * (re, im) doubles, layer 1 [9][C][1], layer 2 [9][C][C], layer 3 [9][1][C],
+ * concatenated (9 * (2C + C^2) complex numbers).  FP32 activations and
+ * arithmetic; inside the solver the weights are rounded to binary16. */
+typedef struct stag_net_s *stag_net;
+
+/* Create a net with C = channels (1, 2, 4 or 8) on `lat` from the raw fat
+ * links (canonical complex128 [4][V][3][3]).  Initial weights: the identity
+ * map plus seeded N(0, 1e-2) noise.  Counts as a live object of the
+ * lattice: destroy nets before their lattice. */
+int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind, int channels, unsigned seed,
+                    stag_net *out);
+int stag_net_destroy(stag_net n);
+int stag_net_num_weights(const stag_net n, int *count);  /* complex weights */
+int stag_net_set_weights(stag_net n, const double *w);   /* resets the optimiser state */
+int stag_net_get_weights(const stag_net n, double *w);
+
+/* out = N(in) on even fields (F64, DF64 or F32) of the net's lattice;
+ * fp16_weights rounds the weights to binary16 first.  Asynchronous. */
+int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int fp16_weights);
+
+/* Training pairs from the plain CG: solve M x* = b to rel_tol, then rerun
+ * the same iteration and, every `stride` iterations (at most max_pairs
+ * times), store the pair (r_k, e_k = x* - x_k) in FP32 on the device.
+ * b is an even field with a gauge copy of its precision; *collected receives
+ * the number of pairs added.  Pairs accumulate over calls. */
+int stag_net_collect_pairs(stag_net n, const stag_field b, double mass, double rel_tol, int stride,
+                           int max_pairs, int *collected);
+int stag_net_num_pairs(const stag_net n, int *count);
+/* Copy pair k to the host as canonical complex128 [Vh][3] (r and e, FP32
+ * values widened). */
+int stag_net_get_pair(const stag_net n, int k, double *r, double *e);
+
+/* Loss sum over pairs [first, first+count) of |N(r) - e|^2 / |e|^2 and its
+ * gradient dL/dW* (the Wirtinger derivative with respect to the conjugate
+ * weights; dL/dRe W = 2 Re, dL/dIm W = 2 Im of it), same layout as the
+ * weights.  loss or grad may be NULL. */
+int stag_net_loss_grad(stag_net n, int first, int count, double *loss, double *grad);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean loss over mini-batches
+ * of `batch` pairs for `epochs` passes over the collected pairs, shuffled
+ * with `seed`.  epoch_loss (may be NULL) receives the mean loss per epoch. */
+int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss);
+
+/* Flexible CG (Notay; Polak-Ribiere beta on real inner products) for
+ * M x = b with z = N(r) as the preconditioner, from x0 = 0.  A run that
+ * claims convergence is checked against the recomputed residual and
+ * restarted if they drifted apart; after a breakdown (<r, z> <= 0), or the
+ * iteration limit, plain CG (z = r) continues from the current x.
+ * Convergence means |b - M x| <= rel_tol |b| recomputed in the precision of
+ * x and b (F64 or DF64 for an FP64-accurate result).  info->iters counts all
+ * iterations, info->restarts the fallbacks to plain CG, info->seconds is
+ * wall time. */
+int stag_cg_solve_learned(stag_net n, stag_field x_even, const stag_field b_even, double mass,
+                          double rel_tol, int max_iter, stag_solve_info *info);
+
 /* ---- allocation-free M ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory: code invoked while its caller captures

@@ -256,6 +256,9 @@ static inline int alloc_vec(stag_lattice lat, int prec, void **p) {
 }
 
 
+// one plain CG iteration on the lattice stream (stag_api.cu)
+cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done);
+
 // shared between the solver translation units
 int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *b_data, size_t bytes,
                     double mass, double rel_tol, int max_iter, double delta, stag_solve_info *info);

@@ -54,6 +54,8 @@ struct CgScalars {
     int restarts;    // reliable updates so far
     // multi-shift CG: the base CG's previous alpha and beta
     double alpha_prev, beta_prev;
+    // flexible CG: |r|^2 (rr holds <r, z> there)
+    double fcg_rr;
 };
 
 // multi-shift CG

@@ -61,4 +61,44 @@ STAG_D bool grid_sum(double v, double *partial, unsigned *ticket, double *smem, 
     return true;
 }
 
+// Grid-wide sum of two values per thread (same protocol as grid_sum;
+// partial must hold 2 * gridDim.x doubles).
+template <int BLOCK>
+STAG_D bool grid_sum2(double v0, double v1, double *partial, unsigned *ticket, double *smem,
+                      double &t0, double &t1) {
+    __shared__ bool last;
+    const double s0 = block_sum<BLOCK>(v0, smem);
+    const double s1 = block_sum<BLOCK>(v1, smem);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s0;
+        partial[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last)
+        return false;
+    __threadfence();
+    const volatile double *vp = partial;
+    double a0 = 0.0, a1 = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += BLOCK) {
+        a0 += vp[2 * i];
+        a1 += vp[2 * i + 1];
+    }
+    a0 = block_sum<BLOCK>(a0, smem);
+    a1 = block_sum<BLOCK>(a1, smem);
+    __shared__ double res[2];
+    if (threadIdx.x == 0) {
+        res[0] = a0;
+        res[1] = a1;
+        *ticket = 0u;
+    }
+    __syncthreads();
+    t0 = res[0];
+    t1 = res[1];
+    __syncthreads();
+    return true;
+}
+
 }  // namespace stag

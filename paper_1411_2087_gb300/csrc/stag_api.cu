@@ -565,7 +565,7 @@ extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_fi
 //                     x += alpha p, r -= alpha Ap, beta; p = r + beta p }
 //   true residual |b - M x|^2
 // --------------------------------------------------------------------------
-static cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done) {
+cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done) {
     const int prec = w.prec;
     cudaError_t e;
     DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, w.p, w.t);

@@ -51,6 +51,9 @@ EXPORTED = [
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
     "stag_cg_solve", "stag_cg_solve_mixed", "stag_cg_multishift", "stag_cg_multishift_mixed",
     "stag_cg_solve_batched", "stag_cg_solve_batched_mixed", "stag_lattice_autotune",
+    "stag_net_create", "stag_net_destroy", "stag_net_num_weights", "stag_net_set_weights",
+    "stag_net_get_weights", "stag_net_apply", "stag_net_collect_pairs", "stag_net_num_pairs",
+    "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
     "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
@@ -114,6 +117,18 @@ def lib():
             "stag_cg_solve_batched": ([I, P, P, P, P, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_batched_mixed": ([I, P, P, P, P, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_lattice_autotune": ([P, I, P, P], I),
+            "stag_net_create": ([P, P, I, I, ctypes.c_uint, PP], I),
+            "stag_net_destroy": ([P], I),
+            "stag_net_num_weights": ([P, ctypes.POINTER(I)], I),
+            "stag_net_set_weights": ([P, P], I),
+            "stag_net_get_weights": ([P, P], I),
+            "stag_net_apply": ([P, P, P, I], I),
+            "stag_net_collect_pairs": ([P, P, D, D, I, I, ctypes.POINTER(I)], I),
+            "stag_net_num_pairs": ([P, ctypes.POINTER(I)], I),
+            "stag_net_get_pair": ([P, I, P, P], I),
+            "stag_net_loss_grad": ([P, I, I, ctypes.POINTER(D), P], I),
+            "stag_net_train": ([P, I, I, D, ctypes.c_uint, P], I),
+            "stag_cg_solve_learned": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
@@ -339,6 +354,8 @@ class Lattice:
         return {"dslash_us": {128: d[0], 256: d[1]}, "batch_us": {128: b[0], 256: b[1]}}
 
     def close(self):
+        for n in list(getattr(self, "_nets", [])):
+            n.close()
         for f in list(self._fields):
             f.destroy()
         if self.handle:
@@ -396,6 +413,112 @@ def cg_batched(systems, tol: float = 1e-10, max_iter: int = 20000, mixed: Option
     if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
         _check(st)
     return st, [i.as_dict() for i in infos]
+
+
+class Net:
+    """The learned gauge-covariant preconditioner (see stag_net_* in stag.h).
+
+    Weights are exchanged as complex128 arrays: a list of three arrays of
+    shapes [9][C][1], [9][C][C], [9][1][C]."""
+
+    def __init__(self, lattice: "Lattice", fat, channels: int = 8, seed: int = 0):
+        self.lattice = lattice
+        self.C = int(channels)
+        p, kind, keep = _as_buffer(fat, (4, lattice.V, 3, 3))
+        h = ctypes.c_void_p()
+        _check(lib().stag_net_create(lattice.handle, p, kind, self.C, int(seed) & 0xffffffff,
+                                     ctypes.byref(h)))
+        self.handle = h
+        n = ctypes.c_int()
+        _check(lib().stag_net_num_weights(h, ctypes.byref(n)))
+        self.nw = n.value
+        if not hasattr(lattice, "_nets"):
+            lattice._nets = set()
+        lattice._nets.add(self)
+
+    def _shapes(self):
+        C = self.C
+        return [(9, C, 1), (9, C, C), (9, 1, C)]
+
+    def get_weights(self):
+        buf = np.empty(2 * self.nw, dtype=np.float64)
+        _check(lib().stag_net_get_weights(self.handle, buf.ctypes.data_as(ctypes.c_void_p)))
+        z = buf[0::2] + 1j * buf[1::2]
+        out, off = [], 0
+        for sh in self._shapes():
+            n = int(np.prod(sh))
+            out.append(z[off:off + n].reshape(sh).copy())
+            off += n
+        return out
+
+    def set_weights(self, ws):
+        flat = np.concatenate([np.asarray(w, dtype=np.complex128).reshape(-1) for w in ws])
+        if flat.size != self.nw:
+            raise ValueError(f"expected {self.nw} complex weights, got {flat.size}")
+        buf = np.empty(2 * self.nw, dtype=np.float64)
+        buf[0::2] = flat.real
+        buf[1::2] = flat.imag
+        _check(lib().stag_net_set_weights(self.handle, buf.ctypes.data_as(ctypes.c_void_p)))
+
+    def apply(self, out: Field, inp: Field, fp16_weights: bool = False):
+        _check(lib().stag_net_apply(self.handle, out.handle, inp.handle, int(bool(fp16_weights))))
+
+    def collect_pairs(self, b: Field, mass: float, tol: float = 1e-10, stride: int = 10,
+                      max_pairs: int = 64) -> int:
+        n = ctypes.c_int()
+        _check(lib().stag_net_collect_pairs(self.handle, b.handle, float(mass), float(tol), int(stride),
+                                            int(max_pairs), ctypes.byref(n)))
+        return n.value
+
+    def num_pairs(self) -> int:
+        n = ctypes.c_int()
+        _check(lib().stag_net_num_pairs(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def get_pair(self, k: int):
+        Vh = self.lattice.Vh
+        r = np.empty((Vh, 3), dtype=np.complex128)
+        e = np.empty((Vh, 3), dtype=np.complex128)
+        _check(lib().stag_net_get_pair(self.handle, int(k), r.ctypes.data_as(ctypes.c_void_p),
+                                       e.ctypes.data_as(ctypes.c_void_p)))
+        return r, e
+
+    def loss_grad(self, first: int, count: int):
+        """(loss, [dL/dW* per layer]) over pairs [first, first+count)."""
+        loss = ctypes.c_double()
+        buf = np.empty(2 * self.nw, dtype=np.float64)
+        _check(lib().stag_net_loss_grad(self.handle, int(first), int(count), ctypes.byref(loss),
+                                        buf.ctypes.data_as(ctypes.c_void_p)))
+        z = buf[0::2] + 1j * buf[1::2]
+        out, off = [], 0
+        for sh in self._shapes():
+            n = int(np.prod(sh))
+            out.append(z[off:off + n].reshape(sh).copy())
+            off += n
+        return loss.value, out
+
+    def train(self, epochs: int = 10, batch: int = 8, lr: float = 1e-2, seed: int = 0):
+        hist = np.zeros(int(epochs))
+        _check(lib().stag_net_train(self.handle, int(epochs), int(batch), float(lr), int(seed) & 0xffffffff,
+                                    hist.ctypes.data_as(ctypes.c_void_p)))
+        return hist
+
+    def cg(self, x: Field, b: Field, mass: float, tol: float = 1e-10, max_iter: int = 20000,
+           raise_on_failure: bool = False) -> dict:
+        info = SolveInfo()
+        st = lib().stag_cg_solve_learned(self.handle, x.handle, b.handle, float(mass), float(tol),
+                                         int(max_iter), ctypes.byref(info))
+        if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def close(self):
+        if self.handle:
+            _check(lib().stag_net_destroy(self.handle))
+            self.handle = None
+            getattr(self.lattice, "_nets", set()).discard(self)
 
 
 def version() -> str:

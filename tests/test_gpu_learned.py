@@ -1,0 +1,164 @@
+"""The learned gauge-covariant preconditioner on the GPU: the forward pass
+against the oracle's FP64 net, gauge covariance, the training gradient
+against the oracle's finite differences (central, h = 1e-6, FP64), training
+lowering the loss, and flexible CG with the trained net reaching the true
+residual in fewer iterations than without it."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2087_gb300 import stag, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_weights(C, seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    shapes = [(9, C, 1), (9, C, C), (9, 1, C)]
+    return [scale * (rng.standard_normal(s) + 1j * rng.standard_normal(s)) for s in shapes]
+
+
+def shift(field, dims, mu, s):
+    Lx, Ly, Lz, Lt = dims
+    f = field.reshape((Lt, Lz, Ly, Lx) + field.shape[1:])
+    return np.roll(f, -s, axis=3 - mu).reshape(field.shape)
+
+
+@pytest.mark.parametrize("dims,C", [((4, 4, 4, 4), 4), ((6, 4, 6, 10), 8), ((2, 2, 2, 2), 2)])
+def test_forward_matches_oracle(dims, C):
+    U = synth.su3_field(dims, 0.4, 5).numpy()
+    Vh = int(np.prod(dims)) // 2
+    r = synth.gaussian_colour_field(Vh, 6).numpy()
+    Ws = rand_weights(C, 7)
+    want = oracle.net_apply(dims, U, Ws, r)
+    with stag.Lattice(dims) as lat:
+        net = stag.Net(lat, U, channels=C)
+        net.set_weights(Ws)
+        got_w = net.get_weights()
+        assert all(np.array_equal(a, b) for a, b in zip(got_w, Ws))
+        for prec in ("f32", "df64"):
+            fin = lat.field(stag.EVEN, prec, r)
+            fout = lat.field(stag.EVEN, prec)
+            net.apply(fout, fin)
+            err = np.abs(fout.export() - want).max() / np.abs(want).max()
+            assert err < 1e-5, (prec, err)
+        # binary16 weights: error of the rounding only
+        fin = lat.field(stag.EVEN, "f32", r)
+        fout = lat.field(stag.EVEN, "f32")
+        net.apply(fout, fin, fp16_weights=True)
+        err = np.abs(fout.export() - want).max() / np.abs(want).max()
+        assert err < 5e-3
+        net.close()
+
+
+def test_gpu_net_is_gauge_covariant():
+    dims = (4, 4, 4, 6)
+    Vh = int(np.prod(dims)) // 2
+    U = synth.su3_field(dims, 0.5, 8).numpy()
+    g = synth.gauge_transform(dims, 9).numpy()
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[mu] = g @ U[mu] @ shift(g, dims, mu, 1).conj().transpose(0, 2, 1)
+    par = oracle.parity_mask(dims)
+    idx = np.nonzero(par == 0)[0]
+    g_even = np.empty((Vh, 3, 3), complex)
+    g_even[idx // 2] = g[idx]
+    r = synth.gaussian_colour_field(Vh, 10).numpy()
+    Ws = rand_weights(4, 11)
+    outs = []
+    for links, src in ((U, r), (Ug, np.einsum("vab,vb->va", g_even, r))):
+        with stag.Lattice(dims) as lat:
+            net = stag.Net(lat, links, channels=4)
+            net.set_weights(Ws)
+            fin = lat.field(stag.EVEN, "df64", src)
+            fout = lat.field(stag.EVEN, "df64")
+            net.apply(fout, fin)
+            outs.append(fout.export())
+            net.close()
+    want = np.einsum("vab,vb->va", g_even, outs[0])
+    assert np.abs(outs[1] - want).max() < 1e-5 * np.abs(want).max()
+
+
+def test_gradient_against_oracle_finite_differences():
+    dims = (4, 4, 2, 4)
+    mass = 0.1
+    U = synth.su3_field(dims, 0.3, 12).numpy()
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 13).numpy()
+    C = 2
+    Ws = rand_weights(C, 14, scale=0.4)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64",))
+        net = stag.Net(lat, U, channels=C)
+        fb = lat.field(stag.EVEN, "df64", b)
+        assert net.collect_pairs(fb, mass, 1e-10, stride=3, max_pairs=3) == 3
+        net.set_weights(Ws)
+        loss, grads = net.loss_grad(0, 3)
+        pairs = [net.get_pair(k) for k in range(3)]
+        net.close()
+    rs = [p[0] for p in pairs]
+    es = [p[1] for p in pairs]
+    assert abs(loss - oracle.net_loss(dims, U, Ws, rs, es)) <= 1e-5 * loss
+    h = 1e-6
+    fd_all, an_all = [], []
+    for li, W in enumerate(Ws):
+        for idx in np.ndindex(W.shape):
+            for unit in (1.0, 1j):
+                Wp = [w.copy() for w in Ws]
+                Wm = [w.copy() for w in Ws]
+                Wp[li][idx] += unit * h
+                Wm[li][idx] -= unit * h
+                fd = (oracle.net_loss(dims, U, Wp, rs, es) - oracle.net_loss(dims, U, Wm, rs, es)) / (2 * h)
+                an = 2 * (grads[li][idx].real if unit == 1.0 else grads[li][idx].imag)
+                fd_all.append(fd)
+                an_all.append(an)
+    fd_all = np.array(fd_all)
+    an_all = np.array(an_all)
+    # FP32 forward/backward against FP64 finite differences
+    assert np.linalg.norm(fd_all - an_all) <= 2e-4 * np.linalg.norm(fd_all), \
+        np.abs(fd_all - an_all).max()
+
+
+def test_training_lowers_loss_and_net_cuts_iterations():
+    dims = (8, 8, 8, 8)
+    mass = 0.05
+    U = synth.su3_field(dims, 0.3, 1010).numpy()
+    N = oracle.long_links(dims, U)
+    Vh = int(np.prod(dims)) // 2
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("df64",))
+        net = stag.Net(lat, U, channels=8, seed=1)
+        for s in range(4):
+            fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1200 + s).numpy())
+            net.collect_pairs(fb, mass, 1e-10, stride=8, max_pairs=16)
+        assert net.num_pairs() >= 32
+        hist = net.train(epochs=30, batch=8, lr=2e-2, seed=3)
+        assert hist[-1] < 0.8 * hist[0], hist
+        b = synth.gaussian_colour_field(Vh, 1300).numpy()
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        plain = lat.cg(fx, fb, mass, 1e-10, 20000)
+        learned = net.cg(fx, fb, mass, 1e-10, 20000)
+        x = fx.export()
+        net.close()
+    res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
+    assert learned["return"] == stag.OK, learned
+    assert res <= 1.05e-10, res
+    assert learned["iters"] < plain["iters"], (learned, plain)
+
+
+def test_learned_solver_edges():
+    dims = (4, 4, 4, 4)
+    U = synth.su3_field(dims, 0.3, 20).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64",))
+        net = stag.Net(lat, U, channels=4)
+        fz = lat.field(stag.EVEN, "df64", np.zeros((128, 3), complex))
+        fx = lat.field(stag.EVEN, "df64")
+        info = net.cg(fx, fz, 0.1, 1e-10, 100)
+        assert info["return"] == stag.OK and not np.any(fx.export())
+        with pytest.raises(stag.StagError):
+            net.train(epochs=1)  # no pairs yet
+        with pytest.raises(stag.StagError):
+            stag.Net(lat, U, channels=3)
+        net.close()
