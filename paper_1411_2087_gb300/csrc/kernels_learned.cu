@@ -245,7 +245,8 @@ __global__ void pair_loss_kernel(NetGeom g, const float2 *__restrict__ y, const 
         net_coords(g, i, x);
         const bool even = ((x[0] + x[1] + x[2] + x[3]) & 1) == 0;
         const int Vh = g.V / 2;
-        const float inv = (float)(1.0 / *enorm2);
+        // a pair with e = 0 carries no information: no loss, no gradient
+        const float inv = *enorm2 > 0.0 ? (float)(1.0 / *enorm2) : 0.f;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             float2 d = make_float2(0.f, 0.f);
@@ -257,7 +258,7 @@ __global__ void pair_loss_kernel(NetGeom g, const float2 *__restrict__ y, const 
             }
             gout[(size_t)a * g.V + i] = make_float2(d.x * inv, d.y * inv);
         }
-        part *= 1.0 / *enorm2;
+        part *= *enorm2 > 0.0 ? 1.0 / *enorm2 : 0.0;
     }
     for (int s = 16; s > 0; s >>= 1)
         part += __shfl_down_sync(0xffffffffu, part, s);

@@ -322,7 +322,8 @@ extern "C" int stag_net_collect_pairs(stag_net n, const stag_field b, double mas
         return st;
     }
     const int total_iters = info.iters;
-    int want = total_iters / stride;
+    // snapshots strictly before convergence (e_k = 0 at the last iterate)
+    int want = (total_iters - 1) / stride;
     if (want > max_pairs)
         want = max_pairs;
     if (want < 1) {
