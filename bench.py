@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision comparison on the 48^3x96 workload")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-preconditioner comparison on the 32^3x64, m=0.005 workload")
+    ap.add_argument("--learned-pairs", type=int, default=64)
+    ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched / multi-shift comparison (16 RHS on three lattices, 12 shifts)")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
@@ -295,6 +299,9 @@ def run_native(args):
     batched = None
     if not args.no_batched:
         batched = batched_comparison(local, rank)
+    learned = None
+    if not args.no_learned:
+        learned = learned_comparison(local, rank, args.learned_pairs, args.learned_epochs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -340,8 +347,80 @@ def run_native(args):
         "cpu_baseline": cpu,
         "mixed_vs_fp64": mixed,
         "batched_multishift": batched,
+        "learned_vs_fp64": learned,
     }
     return line
+
+
+LEARNED_DIMS = (32, 32, 32, 64)
+LEARNED_MASS = 0.005
+
+
+def learned_comparison(local, rank, n_pairs, epochs):
+    """32^3x64, eps = 0.3, m = 0.005 to a 1e-10 true residual: double-float
+    CG against flexible CG with the trained gauge-covariant net (3 layers,
+    8 channels, residual loss, FP16 weights / FP32 arithmetic in the solve)
+    and against mixed 16-bit CG.  Training pairs (r_k, x* - x_k) come from
+    plain CG on two sources of the same gauge field; the timed solve uses a
+    third source.  Collection and training times are reported separately."""
+    import torch
+    from paper_1411_2087_gb300 import stag, synth
+    dev = torch.device("cuda", local)
+    U = synth.su3_field(LEARNED_DIMS, 0.3, 1010, device=dev)
+    torch.cuda.synchronize()
+    Vh = int(np.prod(LEARNED_DIMS)) // 2
+    out = {"workload": f"{'x'.join(map(str, LEARNED_DIMS))}, m={LEARNED_MASS}, eps=0.3, tol=1e-10"}
+    with stag.Lattice(LEARNED_DIMS, device=local) as lat:
+        lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
+        net = stag.Net(lat, U, channels=8, seed=1)
+        del U
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        per_src = max(1, n_pairs // 2)
+        fx = lat.field(stag.EVEN, "df64")
+        for s in range(2):
+            fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1400 + s))
+            iters = lat.cg(fx, fb, LEARNED_MASS, 1e-10, 20000)["iters"]
+            net.collect_pairs(fb, LEARNED_MASS, 1e-10, stride=max(1, iters // (per_src + 1)),
+                              max_pairs=per_src)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        net.set_loss("residual")
+        hist = net.train(epochs=epochs, batch=8, lr=1e-2, seed=3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        b = synth.gaussian_colour_field(Vh, 1500 + rank)
+        fb = lat.field(stag.EVEN, "df64", b)
+        fr = lat.field(stag.EVEN, "df64")
+
+        def resid():
+            lat.apply_M(fr, fx, LEARNED_MASS)
+            r = fr.export() - b.numpy()
+            return float(np.linalg.norm(r) / np.linalg.norm(b.numpy()))
+
+        runs = {}
+        for name, fn in (("fp64_df64_cg", lambda: lat.cg(fx, fb, LEARNED_MASS, 1e-10, 20000)),
+                         ("mixed_f16_cg", lambda: lat.cg_mixed(fx, fb, LEARNED_MASS, 1e-10, 20000, "f16")),
+                         ("learned_fcg_df64", lambda: net.cg(fx, fb, LEARNED_MASS, 1e-10, 20000))):
+            fn()
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            info = fn()
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
+            res = resid()
+            runs[name] = {"seconds": round(tb - ta, 4), "iters": info["iters"], "true_rel_resid": res,
+                          "ok": info["return"] == stag.OK and res <= 1.05e-10}
+        base = runs["fp64_df64_cg"]
+        for name in ("mixed_f16_cg", "learned_fcg_df64"):
+            runs[name]["speedup_vs_fp64"] = round(base["seconds"] / runs[name]["seconds"], 3)
+            runs[name]["iteration_ratio_vs_fp64"] = round(base["iters"] / max(1, runs[name]["iters"]), 3)
+        out.update(runs)
+        out["training"] = {"pairs": net.num_pairs(), "epochs": epochs, "collect_seconds": round(t1 - t0, 2),
+                           "train_seconds": round(t2 - t1, 2), "loss_first": float(hist[0]),
+                           "loss_last": float(hist[-1]), "loss": "residual |M N r - r|^2/|r|^2"}
+        net.close()
+    return out
 
 
 BATCH_LATTICES = (((16, 16, 16, 16), 6, 1003), ((24, 24, 24, 48), 5, 1004), ((32, 32, 32, 64), 5, 1005))

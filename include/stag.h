@@ -314,7 +314,16 @@ int stag_net_num_pairs(const stag_net n, int *count);
  * values widened). */
 int stag_net_get_pair(const stag_net n, int k, double *r, double *e);
 
-/* Loss sum over pairs [first, first+count) of |N(r) - e|^2 / |e|^2 and its
+/* Training objective.
+ * STAG_NET_LOSS_ERROR (default): sum over pairs of |N(r) - e|^2 / |e|^2.
+ * STAG_NET_LOSS_RESIDUAL: sum over pairs of |M N(r) - r|^2 / |r|^2 with M at
+ *   the mass the pairs were collected with, differentiated through M (FP32
+ *   Dslash; needs an F32 gauge copy).  It weights the upper spectrum, where a
+ *   local operator can compress the condition number of N M. */
+enum { STAG_NET_LOSS_ERROR = 0, STAG_NET_LOSS_RESIDUAL = 1 };
+int stag_net_set_loss(stag_net n, int kind);
+
+/* Loss (the objective above) summed over pairs [first, first+count), and its
  * gradient dL/dW* (the Wirtinger derivative with respect to the conjugate
  * weights; dL/dRe W = 2 Re, dL/dIm W = 2 Im of it), same layout as the
  * weights.  loss or grad may be NULL. */
@@ -322,7 +331,10 @@ int stag_net_loss_grad(stag_net n, int first, int count, double *loss, double *g
 
 /* Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean loss over mini-batches
  * of `batch` pairs for `epochs` passes over the collected pairs, shuffled
- * with `seed`.  epoch_loss (may be NULL) receives the mean loss per epoch. */
+ * with `seed`; the step size decays from lr to lr/10 (cosine) over the
+ * epochs.  With the residual loss, the first training call first rescales
+ * the last layer by the least-squares optimal factor for the pairs.
+ * epoch_loss (may be NULL) receives the mean loss per epoch. */
 int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss);
 
 /* Flexible CG (Notay; Polak-Ribiere beta on real inner products) for

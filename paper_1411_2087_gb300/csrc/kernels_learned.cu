@@ -61,10 +61,14 @@ STAG_D void transport(const float2 *__restrict__ Lp, int V, bool adj, const floa
 
 // one layer; weights [9][COUT][CIN] rounded through binary16 when
 // round_half (the FP16 weight storage of the deployed preconditioner)
+// in_par >= 0: the input is zero off that parity, so a site of that parity
+// needs only its own term and a site of the other parity only the hops;
+// out_par >= 0: only sites of that parity are computed (one thread each)
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128)
 covconv_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__restrict__ W, int round_half,
-               const float2 *__restrict__ in, float2 *__restrict__ out, const int *gate) {
+               const float2 *__restrict__ in, float2 *__restrict__ out, const int *gate, int in_par,
+               int out_par) {
     __shared__ float2 sw[9 * COUT * CIN];
     if (gate && *gate != CG_RUNNING)
         return;
@@ -75,12 +79,31 @@ covconv_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__restric
         sw[k] = w;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.V)
-        return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int V = g.V;
-    int x[4];
-    net_coords(g, i, x);
+    int x[4], i;
+    if (out_par < 0) {
+        i = t;
+        if (i >= V)
+            return;
+        net_coords(g, i, x);
+    } else {
+        if (t >= V / 2)
+            return;
+        // site t of parity out_par in checkerboard order
+        const int lxh = g.L[0] / 2;
+        const int xh = t % lxh;
+        int r = t / lxh;
+        x[1] = r % g.L[1];
+        r /= g.L[1];
+        x[2] = r % g.L[2];
+        x[3] = r / g.L[2];
+        x[0] = 2 * xh + ((out_par + x[1] + x[2] + x[3]) & 1);
+        i = x[0] + g.L[0] * (x[1] + g.L[1] * (x[2] + g.L[2] * x[3]));
+    }
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const bool do_self = in_par < 0 || par == in_par;
+    const bool do_hops = in_par < 0 || par != in_par;
     float2 acc[COUT][3];
 #pragma unroll
     for (int o = 0; o < COUT; o++)
@@ -89,6 +112,8 @@ covconv_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__restric
             acc[o][a] = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int d = 0; d < 9; d++) {
+        if (d == 0 ? !do_self : !do_hops)
+            continue;
         const int mu = (d - 1) >> 1;
         const bool bwd = d > 0 && ((d - 1) & 1);
         const int j = d == 0 ? i : net_hop(g, i, x, mu, bwd ? -1 : 1);
@@ -264,6 +289,77 @@ __global__ void pair_loss_kernel(NetGeom g, const float2 *__restrict__ y, const 
         part += __shfl_down_sync(0xffffffffu, part, s);
     if ((threadIdx.x & 31) == 0 && part != 0.0)
         atomicAdd(loss, part);
+}
+
+// residual loss of one pair: q = M z - r on even sites (mz, r full [3][V]),
+// *loss += |q|^2 / |r|^2, q written over mz (odd sites zero)
+__global__ void resid_loss_kernel(NetGeom g, float2 *mz, const float2 *__restrict__ r, const double *rnorm2,
+                                  double *loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (i < g.V) {
+        int x[4];
+        net_coords(g, i, x);
+        const bool even = ((x[0] + x[1] + x[2] + x[3]) & 1) == 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            float2 q = make_float2(0.f, 0.f);
+            if (even) {
+                const float2 m = mz[(size_t)a * g.V + i], rv = r[(size_t)a * g.V + i];
+                q = make_float2(m.x - rv.x, m.y - rv.y);
+                part += (double)q.x * q.x + (double)q.y * q.y;
+            }
+            mz[(size_t)a * g.V + i] = q;
+        }
+        part *= *rnorm2 > 0.0 ? 1.0 / *rnorm2 : 0.0;
+    }
+    for (int s = 16; s > 0; s >>= 1)
+        part += __shfl_down_sync(0xffffffffu, part, s);
+    if ((threadIdx.x & 31) == 0 && part != 0.0)
+        atomicAdd(loss, part);
+}
+
+// out[0] += Re<a, b>, out[1] += |a|^2 over full [3][V] vectors
+__global__ void dot2_full_kernel(int n, const float2 *__restrict__ a, const float2 *__restrict__ b, double *out) {
+    double p0 = 0.0, p1 = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float2 x = a[k], y = b[k];
+        p0 += (double)x.x * y.x + (double)x.y * y.y;
+        p1 += (double)x.x * x.x + (double)x.y * x.y;
+    }
+    for (int s = 16; s > 0; s >>= 1) {
+        p0 += __shfl_down_sync(0xffffffffu, p0, s);
+        p1 += __shfl_down_sync(0xffffffffu, p1, s);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, p0);
+        atomicAdd(out + 1, p1);
+    }
+}
+
+cudaError_t launch_dot2_full(int n, const float2 *a, const float2 *b, double *out, cudaStream_t s) {
+    dot2_full_kernel<<<256, 256, 0, s>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+// v *= 1 / *n2 (full [3][V])
+__global__ void scale_full_kernel(NetGeom g, float2 *v, const double *n2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * g.V)
+        return;
+    const float f = *n2 > 0.0 ? (float)(1.0 / *n2) : 0.f;
+    v[k] = make_float2(v[k].x * f, v[k].y * f);
+}
+
+cudaError_t launch_resid_loss(const NetGeom &g, float2 *mz, const float2 *r, const double *rnorm2, double *loss,
+                              cudaStream_t s) {
+    resid_loss_kernel<<<(g.V + 255) / 256, 256, 0, s>>>(g, mz, r, rnorm2, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_full(const NetGeom &g, float2 *v, const double *n2, cudaStream_t s) {
+    scale_full_kernel<<<(3 * g.V + 255) / 256, 256, 0, s>>>(g, v, n2);
+    return cudaGetLastError();
 }
 
 // |v|^2 of an even FP32 pair vector into *out (atomic; monitoring only)
@@ -448,15 +544,17 @@ fcg_beta_kernel(Geom g, const typename Fmt<P>::Elem *z, const typename Fmt<P>::E
 // ---- launchers -----------------------------------------------------------
 template <int CIN, int COUT>
 static cudaError_t conv_t(const NetGeom &g, const float2 *NL, const float2 *W, int round_half, const float2 *in,
-                          float2 *out, const int *gate, cudaStream_t s) {
-    covconv_kernel<CIN, COUT><<<(g.V + 127) / 128, 128, 0, s>>>(g, NL, W, round_half, in, out, gate);
+                          float2 *out, const int *gate, int in_par, int out_par, cudaStream_t s) {
+    const int n = out_par < 0 ? g.V : g.V / 2;
+    covconv_kernel<CIN, COUT><<<(n + 127) / 128, 128, 0, s>>>(g, NL, W, round_half, in, out, gate, in_par, out_par);
     return cudaGetLastError();
 }
 
 cudaError_t launch_covconv(int cin, int cout, const NetGeom &g, const float2 *NL, const float2 *W, int round_half,
-                           const float2 *in, float2 *out, const int *gate, cudaStream_t s) {
+                           const float2 *in, float2 *out, const int *gate, cudaStream_t s, int in_par,
+                           int out_par) {
 #define CC(A, B) \
-    if (cin == A && cout == B) return conv_t<A, B>(g, NL, W, round_half, in, out, gate, s);
+    if (cin == A && cout == B) return conv_t<A, B>(g, NL, W, round_half, in, out, gate, in_par, out_par, s);
     CC(1, 4) CC(4, 4) CC(4, 1) CC(1, 8) CC(8, 8) CC(8, 1) CC(1, 2) CC(2, 2) CC(2, 1) CC(1, 1)
 #undef CC
     return cudaErrorInvalidValue;

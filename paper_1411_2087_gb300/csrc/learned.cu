@@ -27,8 +27,13 @@ struct stag_net_s {
     // training pairs: even FP32 [3][Vh] residuals and errors, |e|^2 on the device
     std::vector<float2 *> pr, pe;
     std::vector<float2 *> slabs;
-    double *enorm2 = nullptr;
+    double *enorm2 = nullptr;  // |e_k|^2 per pair
+    double *rnorm2 = nullptr;  // |r_k|^2 per pair
     int enorm_cap = 0;
+    int loss_kind = STAG_NET_LOSS_ERROR;
+    double mass = 0;           // mass of the collected pairs (residual loss)
+    // FP32 solver-layout work vectors of the residual loss: z, Mz / Mq, t (odd)
+    void *fz = nullptr, *fmz = nullptr, *ft = nullptr;
     // flexible CG work vectors per precision
     void *r_old[4] = {};
     void *z[4] = {};
@@ -36,7 +41,8 @@ struct stag_net_s {
 
 static void net_free(stag_net n) {
     void *bufs[] = {n->NL, n->w, n->w32, n->wt, n->grad, n->m, n->v, n->a0, n->a1, n->a2, n->y,
-                    n->g1, n->g2, n->g3, n->wpartial, n->scal, n->enorm2};
+                    n->g1, n->g2, n->g3, n->wpartial, n->scal, n->enorm2, n->rnorm2,
+                    n->fz, n->fmz, n->ft};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
@@ -201,15 +207,17 @@ extern "C" int stag_net_get_weights(const stag_net n, double *w) {
 
 static const float2 *wl(const stag_net n, int layer) { return (const float2 *)n->w32 + n->off[layer]; }
 
-// y = net(a0) through the three layers (a0 must already hold the input)
-static cudaError_t net_forward(stag_net n, int round_half, const int *gate, cudaStream_t s) {
+// y = net(a0) through the three layers (a0 must already hold the input,
+// zero on odd sites).  even_out: only the even sites of y are computed (all
+// a preconditioner needs).
+static cudaError_t net_forward(stag_net n, int round_half, const int *gate, cudaStream_t s, bool even_out = false) {
     cudaError_t e;
     const int C = n->C;
-    if ((e = launch_covconv(1, C, n->ng, n->NL, wl(n, 0), round_half, n->a0, n->a1, gate, s)) != cudaSuccess)
+    if ((e = launch_covconv(1, C, n->ng, n->NL, wl(n, 0), round_half, n->a0, n->a1, gate, s, 0, -1)) != cudaSuccess)
         return e;
     if ((e = launch_covconv(C, C, n->ng, n->NL, wl(n, 1), round_half, n->a1, n->a2, gate, s)) != cudaSuccess)
         return e;
-    return launch_covconv(C, 1, n->ng, n->NL, wl(n, 2), round_half, n->a2, n->y, gate, s);
+    return launch_covconv(C, 1, n->ng, n->NL, wl(n, 2), round_half, n->a2, n->y, gate, s, -1, even_out ? 0 : -1);
 }
 
 // dL/dW* += gradient of the loss of one pair whose output gradient is in g3
@@ -248,7 +256,7 @@ static cudaError_t net_apply_raw(stag_net n, int prec, const void *in, void *out
     cudaError_t e;
     if ((e = launch_solver_to_full(prec, n->ng, n->lat->geom, in, n->a0, gate, s)) != cudaSuccess)
         return e;
-    if ((e = net_forward(n, round_half, gate, s)) != cudaSuccess)
+    if ((e = net_forward(n, round_half, gate, s, true)) != cudaSuccess)
         return e;
     return launch_full_to_solver(prec, n->ng, n->lat->geom, n->y, out, gate, s);
 }
@@ -284,14 +292,52 @@ static int refresh_enorms(stag_net n) {
     if (np > n->enorm_cap) {
         if (n->enorm2)
             cudaFree(n->enorm2);
-        n->enorm2 = nullptr;
+        if (n->rnorm2)
+            cudaFree(n->rnorm2);
+        n->enorm2 = n->rnorm2 = nullptr;
         CUDA_TRY(cudaMalloc(&n->enorm2, sizeof(double) * np));
+        CUDA_TRY(cudaMalloc(&n->rnorm2, sizeof(double) * np));
         n->enorm_cap = np;
     }
     cudaStream_t s = n->lat->stream;
     CUDA_TRY(cudaMemsetAsync(n->enorm2, 0, sizeof(double) * np, s));
-    for (int k = 0; k < np; k++)
+    CUDA_TRY(cudaMemsetAsync(n->rnorm2, 0, sizeof(double) * np, s));
+    for (int k = 0; k < np; k++) {
         CUDA_TRY(launch_pair_norm2((int)(3 * n->lat->Vh), n->pe[k], n->enorm2 + k, s));
+        CUDA_TRY(launch_pair_norm2((int)(3 * n->lat->Vh), n->pr[k], n->rnorm2 + k, s));
+    }
+    return STAG_OK;
+}
+
+// y holds N(r) (full); g3 <- gradient of |M z - r|^2 / |r|^2 with respect to
+// conj(y), z = y on even sites: M (M z - r) / |r|^2 (M Hermitian), FP32
+static int resid_loss_grad(stag_net n, int p, cudaStream_t s) {
+    stag_lattice lat = n->lat;
+    const int P = STAG_F32;
+    const Geom &g = lat->geom;
+    CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->y, n->fz, nullptr, s));
+    // Mz
+    DslashArgs a1 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
+    CUDA_TRY(launch_dslash(P, EPI_NONE, a1, lat->dslash_block[P], s));
+    DslashArgs a2 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
+    a2.p = n->fz;
+    a2.m2 = make_dpair(n->mass * n->mass);
+    a2.m2_in_args = 1;
+    CUDA_TRY(launch_dslash(P, EPI_M, a2, lat->dslash_block[P], s));
+    CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
+    // q = Mz - r (into g3), loss
+    CUDA_TRY(launch_resid_loss(n->ng, n->g3, n->a0, n->rnorm2 + p, n->scal, s));
+    // M q / |r|^2
+    CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->g3, n->fz, nullptr, s));
+    DslashArgs a3 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
+    CUDA_TRY(launch_dslash(P, EPI_NONE, a3, lat->dslash_block[P], s));
+    DslashArgs a4 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
+    a4.p = n->fz;
+    a4.m2 = make_dpair(n->mass * n->mass);
+    a4.m2_in_args = 1;
+    CUDA_TRY(launch_dslash(P, EPI_M, a4, lat->dslash_block[P], s));
+    CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
+    CUDA_TRY(launch_scale_full(n->ng, n->g3, n->rnorm2 + p, s));
     return STAG_OK;
 }
 
@@ -337,6 +383,7 @@ extern "C" int stag_net_collect_pairs(stag_net n, const stag_field b, double mas
         return st;
     }
     const int first = (int)n->pr.size() - want;
+    n->mass = mass;
     // the second run: same kernels, same order, so the same iterates
     CgWork &w = lat->cg[prec];
     cudaStream_t s = lat->stream;
@@ -391,6 +438,24 @@ extern "C" int stag_net_get_pair(const stag_net n, int k, double *r, double *e) 
     return STAG_OK;
 }
 
+extern "C" int stag_net_set_loss(stag_net n, int kind) {
+    if (!n)
+        return fail(STAG_ERR_ARG, "stag_net_set_loss: NULL net");
+    if (kind != STAG_NET_LOSS_ERROR && kind != STAG_NET_LOSS_RESIDUAL)
+        return fail(STAG_ERR_ARG, "stag_net_set_loss: unknown loss %d", kind);
+    if (kind == STAG_NET_LOSS_RESIDUAL) {
+        stag_lattice lat = n->lat;
+        if (!lat->has_gauge || !lat->links[STAG_F32])
+            return fail(STAG_ERR_STATE, "stag_net_set_loss: the residual loss needs an F32 gauge copy");
+        DEVICE_SCOPE(lat->device);
+        STAG_TRY(alloc_vec(lat, STAG_F32, &n->fz));
+        STAG_TRY(alloc_vec(lat, STAG_F32, &n->fmz));
+        STAG_TRY(alloc_vec(lat, STAG_F32, &n->ft));
+    }
+    n->loss_kind = kind;
+    return STAG_OK;
+}
+
 extern "C" int stag_net_num_pairs(const stag_net n, int *count) {
     if (!n || !count)
         return fail(STAG_ERR_ARG, "stag_net_num_pairs: NULL argument");
@@ -408,7 +473,10 @@ static int loss_grad_range(stag_net n, const int *idx, int count, double *loss) 
         const int p = idx[k];
         CUDA_TRY(launch_pair_to_full(n->ng, n->pr[p], n->a0, s));
         CUDA_TRY(net_forward(n, 0, nullptr, s));
-        CUDA_TRY(launch_pair_loss(n->ng, n->y, n->pe[p], n->enorm2 + p, n->g3, n->scal, s));
+        if (n->loss_kind == STAG_NET_LOSS_RESIDUAL)
+            STAG_TRY(resid_loss_grad(n, p, s));
+        else
+            CUDA_TRY(launch_pair_loss(n->ng, n->y, n->pe[p], n->enorm2 + p, n->g3, n->scal, s));
         CUDA_TRY(net_backward(n, s));
     }
     if (loss) {
@@ -437,6 +505,42 @@ extern "C" int stag_net_loss_grad(stag_net n, int first, int count, double *loss
     return STAG_OK;
 }
 
+// Warm start of the residual loss: the scale s minimising sum |s M N(r) - r|^2
+// over the pairs, s = sum Re<M N r, r> / sum |M N r|^2, folded into the last
+// layer's weights
+static int residual_warm_start(stag_net n) {
+    stag_lattice lat = n->lat;
+    cudaStream_t s = lat->stream;
+    const int P = STAG_F32;
+    const Geom &g = lat->geom;
+    CUDA_TRY(cudaMemsetAsync(n->scal + 1, 0, 2 * sizeof(double), s));
+    for (size_t p = 0; p < n->pr.size(); p++) {
+        CUDA_TRY(launch_pair_to_full(n->ng, n->pr[p], n->a0, s));
+        CUDA_TRY(net_forward(n, 0, nullptr, s));
+        CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->y, n->fz, nullptr, s));
+        DslashArgs a1 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
+        CUDA_TRY(launch_dslash(P, EPI_NONE, a1, lat->dslash_block[P], s));
+        DslashArgs a2 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
+        a2.p = n->fz;
+        a2.m2 = make_dpair(n->mass * n->mass);
+        a2.m2_in_args = 1;
+        CUDA_TRY(launch_dslash(P, EPI_M, a2, lat->dslash_block[P], s));
+        CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
+        CUDA_TRY(launch_dot2_full(3 * n->ng.V, n->g3, n->a0, n->scal + 1, s));
+    }
+    double h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, n->scal + 1, sizeof h, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (!(h[1] > 0) || !std::isfinite(h[0]))
+        return STAG_OK;
+    const double scale = h[0] / h[1];
+    std::vector<double> w(2 * (size_t)n->nw);
+    STAG_TRY(stag_net_get_weights(n, w.data()));
+    for (int k = 2 * n->off[2]; k < 2 * n->nw; k++)
+        w[k] *= scale;
+    return stag_net_set_weights(n, w.data());
+}
+
 extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss) {
     if (!n)
         return fail(STAG_ERR_ARG, "stag_net_train: NULL net");
@@ -451,8 +555,12 @@ extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsi
     for (int k = 0; k < np; k++)
         order[k] = k;
     cudaStream_t s = n->lat->stream;
+    if (n->loss_kind == STAG_NET_LOSS_RESIDUAL && n->adam_t == 0)
+        STAG_TRY(residual_warm_start(n));
     for (int ep = 0; ep < epochs; ep++) {
         std::shuffle(order.begin(), order.end(), rng);
+        // cosine decay of the step size from lr to lr / 10
+        const double lr_ep = lr * (0.1 + 0.45 * (1.0 + std::cos(M_PI * ep / epochs)));
         double tot = 0;
         for (int b0 = 0; b0 < np; b0 += batch) {
             const int cnt = std::min(batch, np - b0);
@@ -460,7 +568,7 @@ extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsi
             STAG_TRY(loss_grad_range(n, order.data() + b0, cnt, &l));
             tot += l;
             n->adam_t++;
-            CUDA_TRY(launch_adam(2 * n->nw, n->w, n->grad, n->m, n->v, lr / cnt, n->adam_t, n->w32, s));
+            CUDA_TRY(launch_adam(2 * n->nw, n->w, n->grad, n->m, n->v, lr_ep / cnt, n->adam_t, n->w32, s));
         }
         if (epoch_loss)
             epoch_loss[ep] = tot / np;

@@ -54,6 +54,7 @@ EXPORTED = [
     "stag_net_create", "stag_net_destroy", "stag_net_num_weights", "stag_net_set_weights",
     "stag_net_get_weights", "stag_net_apply", "stag_net_collect_pairs", "stag_net_num_pairs",
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
+    "stag_net_set_loss",
     "stag_apply_M_noalloc",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
@@ -128,6 +129,7 @@ def lib():
             "stag_net_get_pair": ([P, I, P, P], I),
             "stag_net_loss_grad": ([P, I, I, ctypes.POINTER(D), P], I),
             "stag_net_train": ([P, I, I, D, ctypes.c_uint, P], I),
+            "stag_net_set_loss": ([P, I], I),
             "stag_cg_solve_learned": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
@@ -459,6 +461,10 @@ class Net:
         buf[0::2] = flat.real
         buf[1::2] = flat.imag
         _check(lib().stag_net_set_weights(self.handle, buf.ctypes.data_as(ctypes.c_void_p)))
+
+    def set_loss(self, kind: str = "error"):
+        """'error' (|N r - e|^2/|e|^2) or 'residual' (|M N r - r|^2/|r|^2)."""
+        _check(lib().stag_net_set_loss(self.handle, {"error": 0, "residual": 1}[kind]))
 
     def apply(self, out: Field, inp: Field, fp16_weights: bool = False):
         _check(lib().stag_net_apply(self.handle, out.handle, inp.handle, int(bool(fp16_weights))))

@@ -79,7 +79,17 @@ def test_gpu_net_is_gauge_covariant():
     assert np.abs(outs[1] - want).max() < 1e-5 * np.abs(want).max()
 
 
-def test_gradient_against_oracle_finite_differences():
+def resid_loss_oracle(dims, U, N, mass, Ws, rs):
+    tot = 0.0
+    for r in rs:
+        z = oracle.net_apply(dims, U, Ws, r)
+        q = oracle.apply_M(dims, U, N, mass, z) - r
+        tot += float(np.vdot(q, q).real / np.vdot(r, r).real)
+    return tot
+
+
+@pytest.mark.parametrize("kind", ["error", "residual"])
+def test_gradient_against_oracle_finite_differences(kind):
     dims = (4, 4, 2, 4)
     mass = 0.1
     U = synth.su3_field(dims, 0.3, 12).numpy()
@@ -87,18 +97,26 @@ def test_gradient_against_oracle_finite_differences():
     b = synth.gaussian_colour_field(Vh, 13).numpy()
     C = 2
     Ws = rand_weights(C, 14, scale=0.4)
+    N = oracle.long_links(dims, U)
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, None, precisions=("df64",))
+        lat.upload_gauge(U, N, precisions=("df64", "f32"))
         net = stag.Net(lat, U, channels=C)
         fb = lat.field(stag.EVEN, "df64", b)
         assert net.collect_pairs(fb, mass, 1e-10, stride=3, max_pairs=3) == 3
+        net.set_loss(kind)
         net.set_weights(Ws)
         loss, grads = net.loss_grad(0, 3)
         pairs = [net.get_pair(k) for k in range(3)]
         net.close()
     rs = [p[0] for p in pairs]
     es = [p[1] for p in pairs]
-    assert abs(loss - oracle.net_loss(dims, U, Ws, rs, es)) <= 1e-5 * loss
+    if kind == "error":
+        def L(ws):
+            return oracle.net_loss(dims, U, ws, rs, es)
+    else:
+        def L(ws):
+            return resid_loss_oracle(dims, U, N, mass, ws, rs)
+    assert abs(loss - L(Ws)) <= 1e-5 * loss
     h = 1e-6
     fd_all, an_all = [], []
     for li, W in enumerate(Ws):
@@ -108,7 +126,7 @@ def test_gradient_against_oracle_finite_differences():
                 Wm = [w.copy() for w in Ws]
                 Wp[li][idx] += unit * h
                 Wm[li][idx] -= unit * h
-                fd = (oracle.net_loss(dims, U, Wp, rs, es) - oracle.net_loss(dims, U, Wm, rs, es)) / (2 * h)
+                fd = (L(Wp) - L(Wm)) / (2 * h)
                 an = 2 * (grads[li][idx].real if unit == 1.0 else grads[li][idx].imag)
                 fd_all.append(fd)
                 an_all.append(an)
@@ -120,20 +138,23 @@ def test_gradient_against_oracle_finite_differences():
 
 
 def test_training_lowers_loss_and_net_cuts_iterations():
+    """What the trained net gains: flexible CG with it against the same
+    solve without it (plain CG), on a source it was not trained on."""
     dims = (8, 8, 8, 8)
     mass = 0.05
     U = synth.su3_field(dims, 0.3, 1010).numpy()
     N = oracle.long_links(dims, U)
     Vh = int(np.prod(dims)) // 2
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, N, precisions=("df64",))
+        lat.upload_gauge(U, N, precisions=("df64", "f32"))
         net = stag.Net(lat, U, channels=8, seed=1)
         for s in range(4):
             fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1200 + s).numpy())
             net.collect_pairs(fb, mass, 1e-10, stride=8, max_pairs=16)
         assert net.num_pairs() >= 32
-        hist = net.train(epochs=30, batch=8, lr=2e-2, seed=3)
-        assert hist[-1] < 0.8 * hist[0], hist
+        net.set_loss("residual")
+        hist = net.train(epochs=100, batch=8, lr=1e-2, seed=3)
+        assert hist[-1] < 0.9 * hist[0], hist
         b = synth.gaussian_colour_field(Vh, 1300).numpy()
         fb = lat.field(stag.EVEN, "df64", b)
         fx = lat.field(stag.EVEN, "df64")
@@ -144,7 +165,26 @@ def test_training_lowers_loss_and_net_cuts_iterations():
     res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
     assert learned["return"] == stag.OK, learned
     assert res <= 1.05e-10, res
-    assert learned["iters"] < plain["iters"], (learned, plain)
+    # a local degree-one (in the hopping term) preconditioner can at best
+    # halve the condition number: about 1.4x fewer iterations
+    assert learned["iters"] <= 0.8 * plain["iters"], (learned, plain)
+    assert learned["restarts"] == 0
+
+
+def test_error_loss_training_runs():
+    dims = (4, 4, 4, 8)
+    U = synth.su3_field(dims, 0.3, 21).numpy()
+    Vh = int(np.prod(dims)) // 2
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64",))
+        net = stag.Net(lat, U, channels=4, seed=2)
+        fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 22).numpy())
+        net.collect_pairs(fb, 0.1, 1e-10, stride=4, max_pairs=8)
+        hist = net.train(epochs=20, batch=4, lr=1e-2, seed=1)
+        assert np.all(np.isfinite(hist)) and hist[-1] < hist[0]
+        with pytest.raises(stag.StagError):  # the residual loss needs an F32 gauge copy
+            net.set_loss("residual")
+        net.close()
 
 
 def test_learned_solver_edges():
