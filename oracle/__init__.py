@@ -81,6 +81,8 @@ def _load():
         lib.orc_cg.argtypes = [P, P, D, D, P, P, D, P, P, D, I,
                                ctypes.POINTER(I), ctypes.POINTER(D), P]
         lib.orc_cg.restype = I
+        lib.orc_dslash_sites.argtypes = [P, P, D, D, P, P, P, P, ctypes.c_long, P]
+        lib.orc_dslash_sites.restype = None
         lib.orc_covconv.argtypes = [P, P, P, I, I, P, P, P]
         lib.orc_covconv.restype = None
         lib.orc_num_threads.argtypes = []
@@ -158,6 +160,21 @@ def dslash_parity(dims, U, N, out_parity: int, psi_cb, bc=BC_DEFAULT,
     out = np.empty_like(psi)
     _load().orc_dslash_parity(_ptr(d), _ptr(_bc(bc)), c1, c3, _ptr(U), _ptr(N),
                               int(out_parity), _ptr(psi), _ptr(out))
+    return out
+
+
+def dslash_sites(dims, U, N, sites, psi_cb, bc=BC_DEFAULT, c1=C1_NAIK, c3=C3_NAIK) -> np.ndarray:
+    """(D psi)(x) at the full-lattice sites `sites` (all of one parity);
+    psi_cb is the other parity in checkerboard order.  Returns [n][3]."""
+    d = _dims(dims)
+    V = volume(d)
+    U = _c(U, (4, V, 3, 3))
+    N = _c(N, (4, V, 3, 3))
+    psi = _c(psi_cb, (V // 2, 3))
+    idx = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = np.empty((idx.size, 3), dtype=np.complex128)
+    _load().orc_dslash_sites(_ptr(d), _ptr(_bc(bc)), c1, c3, _ptr(U), _ptr(N), _ptr(psi), _ptr(idx),
+                             idx.size, _ptr(out))
     return out
 
 

@@ -236,6 +236,18 @@ void orc_dslash_parity(const int L[4], const double bc[4], double c1, double c3,
     }
 }
 
+/* D at a list of full-lattice sites only (for sampled checks on lattices
+ * too large to compare whole): out[k] = (D psi)(sites[k]), psi given on the
+ * other parity in checkerboard order. */
+void orc_dslash_sites(const int L[4], const double bc[4], double c1, double c3,
+                      const cplx *U, const cplx *N, const cplx *in_cb,
+                      const long *sites, long n, cplx *out)
+{
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < n; k++)
+        dslash_site(L, bc, c1, c3, U, N, in_cb, 1, sites[k], out + k * 3);
+}
+
 /* M = m^2 - D_eo D_oe on the even checkerboard (the even-odd preconditioned
  * normal operator the CG solves). */
 void orc_apply_M(const int L[4], const double bc[4], double c1, double c3,

@@ -1,0 +1,87 @@
+"""Parity at the bench's sizes and launch configuration: the whole 32^3x64
+Dslash against the oracle in both parities and precisions, the CG solve there
+checked by the oracle's residual, and 4096 sampled sites of the 48^3x96
+Dslash."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1411_2087_gb300 import stag, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def gen(dims, eps, seed):
+    dev = torch.device("cuda", 0)
+    U = synth.su3_field(dims, eps, seed, device=dev)
+    torch.cuda.synchronize()
+    return U
+
+
+def test_dslash_32x32x32x64_full():
+    dims = (32, 32, 32, 64)
+    Vh = int(np.prod(dims)) // 2
+    U = gen(dims, 0.3, 1001)
+    Uh = U.cpu().numpy()
+    N = oracle.long_links(dims, Uh)
+    psi_e = synth.gaussian_colour_field(Vh, 1101).numpy()
+    psi_o = synth.gaussian_colour_field(Vh, 1102).numpy()
+    want_o = oracle.dslash_parity(dims, Uh, N, 1, psi_e)
+    want_e = oracle.dslash_parity(dims, Uh, N, 0, psi_o)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64", "f64"))
+        for prec in ("df64", "f64"):
+            fe = lat.field(stag.EVEN, prec, psi_e)
+            fo = lat.field(stag.ODD, prec, psi_o)
+            oo = lat.field(stag.ODD, prec)
+            oe = lat.field(stag.EVEN, prec)
+            lat.dslash(oo, fe)
+            lat.dslash(oe, fo)
+            for got, want in ((oo.export(), want_o), (oe.export(), want_e)):
+                err = np.abs(got - want).max() / np.abs(want).max()
+                assert err <= 1e-12, (prec, err)
+            for f in (fe, fo, oo, oe):
+                f.destroy()
+        # the bench step: CG at m = 0.02 to 1e-10, residual by the oracle
+        b = synth.gaussian_colour_field(Vh, 1101).numpy()
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        info = lat.cg(fx, fb, 0.02, 1e-10, 20000)
+        assert info["return"] == stag.OK
+        x = fx.export()
+    r = np.linalg.norm(b - oracle.apply_M(dims, Uh, N, 0.02, x)) / np.linalg.norm(b)
+    assert r <= 1.05e-10, r
+
+
+def test_dslash_48x48x48x96_sampled():
+    dims = (48, 48, 48, 96)
+    V = int(np.prod(dims))
+    Vh = V // 2
+    U = gen(dims, 0.35, 1002)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64",))
+        N_dev = lat.long_links(U)
+        Uh = U.cpu().numpy()
+        Nh = N_dev.cpu().numpy()
+        del N_dev
+        psi = synth.gaussian_colour_field(Vh, 1103).numpy()
+        fe = lat.field(stag.EVEN, "df64", psi)
+        fo = lat.field(stag.ODD, "df64")
+        lat.dslash(fo, fe)
+        got = fo.export()
+    # the long links the GPU built are checked on sampled sites too
+    rng = np.random.default_rng(7)
+    par = None
+    sites = rng.choice(V, 20000, replace=False)
+    x = sites % 48
+    y = (sites // 48) % 48
+    z = (sites // (48 * 48)) % 48
+    t = sites // (48 * 48 * 48)
+    odd = sites[((x + y + z + t) & 1) == 1][:4096]
+    Noracle = oracle.long_links(dims, Uh)
+    for mu in range(4):
+        assert np.abs(Noracle[mu][odd] - Nh[mu][odd]).max() < 1e-13
+    want = oracle.dslash_sites(dims, Uh, Noracle, odd, psi)
+    err = np.abs(got[odd // 2] - want).max() / np.abs(want).max()
+    assert err <= 1e-12, err

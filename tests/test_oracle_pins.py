@@ -435,3 +435,16 @@ def test_cg_history_consistent():
     true_r = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
     assert abs(true_r - info["true_rel_resid"]) < 1e-14
     assert info["true_rel_resid"] < 1e-10 * 1.5
+
+
+def test_dslash_sites_equals_full_parity():
+    dims = (4, 6, 2, 8)
+    U, N = fields(dims, 0.3, 95)
+    Vh = np.prod(dims) // 2
+    psi = rand_colour(Vh, 96)
+    full = oracle.dslash_parity(dims, U, N, 1, psi)
+    par = oracle.parity_mask(dims)
+    odd = np.nonzero(par == 1)[0]
+    pick = odd[::7]
+    got = oracle.dslash_sites(dims, U, N, pick, psi)
+    assert np.array_equal(got, full[pick // 2])
