@@ -78,6 +78,7 @@ enum {
  */
 enum { STAG_F64 = 0, STAG_F32 = 1, STAG_F16 = 2, STAG_DF64 = 3 };
 #define STAG_PREC_BIT(p) (1u << (p))
+#define STAG_COMPRESS12 (1u << 16)
 
 enum { STAG_EVEN = 0, STAG_ODD = 1 };
 enum { STAG_PTR_HOST = 0, STAG_PTR_DEVICE = 1 };
@@ -126,7 +127,15 @@ int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk);
  * The library folds c1, c3, the Kogut-Susskind phases and the boundary signs
  * into its own copies and re-lays them out per parity (structure of arrays).
  * prec_mask: OR of STAG_PREC_BIT(p) for each precision to build a copy for
- *            (0 means F64 | DF64).  A later upload replaces all copies.
+ *            (0 means F64 | DF64), optionally with STAG_COMPRESS12: the F32
+ *            and F16 Dslash then read "two-row" 12-real links (the paper's
+ *            gauge compression, Sec. 4) and rebuild row 3 as
+ *            conj(row1 x row2) / (c eta b): 2/3 of the link bytes and wider
+ *            loads.  Only valid for special unitary links (checked: a link
+ *            deviating from SU(3) by more than 1e-6 gives STAG_ERR_ARG, e.g.
+ *            smeared fat links, which the paper notes are not in SU(3));
+ *            the full copies are kept for the batched solver.
+ *            A later upload replaces all copies.
  * Blocks until the copies are built. */
 int stag_gauge_upload(stag_lattice lat, const double *fat, const double *lng,
                       double c1, double c3, int ptr_kind, unsigned prec_mask);

@@ -108,6 +108,7 @@ struct stag_lattice_s {
     long long V = 0, Vh = 0;
     Geom geom;
     void *links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision [2][8][9][stride]
+    void *links_c12[4] = {nullptr, nullptr, nullptr, nullptr};  // 12-real copies (FP32, 16-bit)
     bool has_gauge = false;
     double c1 = 0, c3 = 0;
     int live_fields = 0;
@@ -203,6 +204,17 @@ static inline DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, co
     if (prec == STAG_F16) {
         a.link_scale[0] = lat->link_scale[0];
         a.link_scale[1] = lat->link_scale[1];
+    }
+    if (lat->links_c12[prec]) {
+        // the 12-real copy replaces the full one for this precision
+        const size_t half = c12_link_bytes(prec, (size_t)lat->geom.stride) / 2;
+        a.links_out = (const char *)lat->links_c12[prec] + (size_t)out_par * half;
+        a.links_in = (const char *)lat->links_c12[prec] + (size_t)(1 - out_par) * half;
+        a.compressed = 1;
+        a.inv_c[0] = (float)(1.0 / lat->c1);
+        a.inv_c[1] = (float)(1.0 / lat->c3);
+        for (int k = 0; k < 4; k++)
+            a.bc_neg[k] = lat->bc[k] < 0 ? 1 : 0;
     }
     return a;
 }

@@ -41,38 +41,90 @@ struct DslashArgs {
     int skip_if_done;       // return at once when sc->status is no longer CG_RUNNING
     const int *gate;        // if set, return at once unless *gate != 0 (uniform flag)
     float link_scale[2];    // 16-bit links: value = q * scale (one-link, three-link)
+    int compressed;         // links in the 12-real layout (FP32, 16-bit)
+    float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
+    int bc_neg[4];          // boundary sign of direction mu is -1
 };
 
-// acc += D psi at checkerboard site c of parity par
-template <int P>
-STAG_D void dslash_site(const Geom &g, int par, int c,
-                        const typename Fmt<P>::Elem *__restrict__ Gout,
-                        const typename Fmt<P>::Elem *__restrict__ Gin,
-                        const typename Fmt<P>::Elem *__restrict__ in,
-                        const float link_scale[2], cplx<typename Fmt<P>::R> acc[3]) {
+// rebuild row 2 of L = s U (U in SU(3)) from rows 0 and 1: conj(r0 x r1) / s
+template <class R>
+STAG_D void reconstruct_row2(cplx<R> L[9], float inv_s) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        // r0_k r1_l - r0_l r1_k
+        const float re = L[k].re * L[3 + l].re - L[k].im * L[3 + l].im - (L[l].re * L[3 + k].re - L[l].im * L[3 + k].im);
+        const float im = L[k].re * L[3 + l].im + L[k].im * L[3 + l].re - (L[l].re * L[3 + k].im + L[l].im * L[3 + k].re);
+        L[6 + j] = cplx<R>{re * inv_s, -im * inv_s};
+    }
+}
+
+// number of times a hop of s steps from coordinate v wraps (L >= 2, |s| <= 3)
+STAG_D int hop_wraps(int v, int s, int L) {
+    int y = v + s, w = 0;
+    if (y >= L) { y -= L; w++; }
+    if (y >= L) { y -= L; w++; }
+    if (y < 0) { y += L; w++; }
+    if (y < 0) { y += L; w++; }
+    return w;
+}
+
+// the nine entries of one link: either stored whole, or rows 0 and 1 of the
+// 12-real layout with row 2 rebuilt (inv_s = 1/(c eta b) of that link)
+template <int P, bool COMP>
+STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float inv_s,
+                      cplx<typename Fmt<P>::R> L[9]) {
     using F = Fmt<P>;
-    using R = typename F::R;
+    if constexpr (COMP) {
+        const char *kb = (const char *)G + (size_t)kind * C12<P>::kind_bytes((size_t)S);
+        C12<P>::load(kb, S, idx, ls, L);
+        reconstruct_row2(L, inv_s);
+    } else {
+        const typename F::Elem *Lp = (const typename F::Elem *)G + kind * 9 * S + idx;
+#pragma unroll
+        for (int e = 0; e < 9; e++)
+            L[e] = F::unpack_link(ld_stream(Lp + e * S), ls);
+    }
+}
+
+// acc += D psi at checkerboard site c of parity par
+template <int P, bool COMP = false>
+STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ Gout,
+                        const void *__restrict__ Gin, const typename Fmt<P>::Elem *__restrict__ in,
+                        const DslashArgs &a, cplx<typename Fmt<P>::R> acc[3]) {
+    using R = typename Fmt<P>::R;
     const int S = g.stride;
     int x[4];
     cb_coords(g, c, par, x);
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
+        // Kogut-Susskind phase of direction mu at x (equal at x - s mu)
+        int esum = 0;
+#pragma unroll
+        for (int nu = 0; nu < mu; nu++)
+            esum += x[nu];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int s = h ? 3 : 1;
             const int kind = 4 * h + mu;
-            const float ls = link_scale[h];
+            const float ls = a.link_scale[h];
             // forward: + L(x) psi(x + s mu)
             {
                 const int j = cb_hop(g, c, x, mu, +s);
                 cplx<R> v[3];
                 load_vec<P>(in, S, j, v);
-                const typename F::Elem *Lp = Gout + kind * 9 * S + c;
+                float inv_s = 0.f;
+                if (COMP) {
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
+                    inv_s = flip ? -a.inv_c[h] : a.inv_c[h];
+                }
+                cplx<R> L[9];
+                load_link<P, COMP>(Gout, kind, S, c, ls, inv_s, L);
 #pragma unroll
-                for (int a = 0; a < 3; a++)
+                for (int r = 0; r < 3; r++)
 #pragma unroll
                     for (int b = 0; b < 3; b++)
-                        cmac(acc[a], F::unpack_link(ld_stream(Lp + (3 * a + b) * S), ls), v[b]);
+                        cmac(acc[r], L[3 * r + b], v[b]);
             }
             // backward: - L(x - s mu)^+ psi(x - s mu)
             {
@@ -82,12 +134,18 @@ STAG_D void dslash_site(const Geom &g, int par, int c,
 #pragma unroll
                 for (int b = 0; b < 3; b++)
                     v[b] = cneg(v[b]);
-                const typename F::Elem *Lp = Gin + kind * 9 * S + j;
+                float inv_s = 0.f;
+                if (COMP) {
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
+                    inv_s = flip ? -a.inv_c[h] : a.inv_c[h];
+                }
+                cplx<R> L[9];
+                load_link<P, COMP>(Gin, kind, S, j, ls, inv_s, L);
 #pragma unroll
-                for (int a = 0; a < 3; a++)
+                for (int r = 0; r < 3; r++)
 #pragma unroll
                     for (int b = 0; b < 3; b++)
-                        cmac_conj(acc[a], F::unpack_link(ld_stream(Lp + (3 * b + a) * S), ls), v[b]);
+                        cmac_conj(acc[r], L[3 * b + r], v[b]);
             }
         }
     }
@@ -103,7 +161,7 @@ template <class R> STAG_D double re_dot3(const cplx<R> a[3], const cplx<R> b[3])
     return to_double<R>(rnorm<R>(s));
 }
 
-template <int P, int EPI, int BLOCK>
+template <int P, int EPI, int BLOCK, bool COMP = false>
 __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     using F = Fmt<P>;
     using R = typename F::R;
@@ -119,8 +177,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     double dot = 0.0;
     if (c < a.g.Vh) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
-        dslash_site<P>(a.g, a.out_par, c, (const E *)a.links_out, (const E *)a.links_in,
-                       (const E *)a.in, a.link_scale, acc);
+        dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
         if (EPI == EPI_NONE) {
 #pragma unroll
             for (int k = 0; k < 3; k++) {

@@ -6,20 +6,33 @@
 
 namespace stag {
 
-template <int P, int BLOCK>
-static cudaError_t launch_p_b(int epi, const DslashArgs &a, cudaStream_t s) {
+template <int P, int BLOCK, bool COMP>
+static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
     const int grid = dslash_grid(a.g, BLOCK);
     if (grid == 0)
         return cudaSuccess;
     switch (epi) {
-    case EPI_NONE: dslash_kernel<P, EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_M: dslash_kernel<P, EPI_M, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_NONE: dslash_kernel<P, EPI_NONE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_M: dslash_kernel<P, EPI_M, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// the 12-real layout exists for FP32 and 16-bit links only
+template <int P, int BLOCK>
+static cudaError_t launch_p_b(int epi, const DslashArgs &a, cudaStream_t s) {
+    if constexpr (P == P_F32 || P == P_F16) {
+        if (a.compressed)
+            return launch_p_b_c<P, BLOCK, true>(epi, a, s);
+    } else {
+        if (a.compressed)
+            return cudaErrorInvalidValue;
+    }
+    return launch_p_b_c<P, BLOCK, false>(epi, a, s);
 }
 
 template <int P> cudaError_t launch_dslash_p(int epi, const DslashArgs &a, int block, cudaStream_t s) {

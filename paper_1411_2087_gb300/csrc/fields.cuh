@@ -77,6 +77,59 @@ template <> struct Fmt<P_F16> {
     }
 };
 
+// --------------------------------------------------------------------------
+// 12-real ("two-row") compressed links (the paper's gauge compression,
+// Sec. 4): rows 0 and 1 of the folded link L = s U, U in SU(3), s = c eta b;
+// row 2 = conj(row0 x row1) / s is rebuilt in the kernel.  Per parity and
+// kind, entries e0..e5 (row-major rows 0, 1):
+//   FP32:   float4 [3][stride], chunk k holds e(2k), e(2k+1)  (48 B per link)
+//   16-bit: int4 [stride] (e0..e3) then int2 [stride] (e4, e5) (24 B per link)
+// --------------------------------------------------------------------------
+template <int P> struct C12;
+
+template <> struct C12<P_F32> {
+    STAG_HD static size_t kind_bytes(size_t S) { return 3 * S * 16; }
+    STAG_D static void load(const char *kind_base, int S, int idx, float, cplx<float> L[6]) {
+        const float4 *p = (const float4 *)kind_base;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float4 v = ld_stream(p + k * S + idx);
+            L[2 * k] = cplx<float>{v.x, v.y};
+            L[2 * k + 1] = cplx<float>{v.z, v.w};
+        }
+    }
+    STAG_D static void store(char *kind_base, size_t S, size_t idx, int e, double re, double im, float) {
+        float2 *p = (float2 *)((float4 *)kind_base + (e / 2) * S + idx) + (e % 2);
+        *p = make_float2((float)re, (float)im);
+    }
+};
+
+template <> struct C12<P_F16> {
+    STAG_HD static size_t kind_bytes(size_t S) { return 24 * S; }
+    STAG_D static cplx<float> q(int v, float scale) {
+        return cplx<float>{(float)(short)(v & 0xffff) * scale, (float)(v >> 16) * scale};
+    }
+    STAG_D static void load(const char *kind_base, int S, int idx, float scale, cplx<float> L[6]) {
+        const int4 a = ld_stream((const int4 *)kind_base + idx);
+        const int2 b = ld_stream((const int2 *)(kind_base + (size_t)16 * S) + idx);
+        L[0] = q(a.x, scale);
+        L[1] = q(a.y, scale);
+        L[2] = q(a.z, scale);
+        L[3] = q(a.w, scale);
+        L[4] = q(b.x, scale);
+        L[5] = q(b.y, scale);
+    }
+    STAG_D static void store(char *kind_base, size_t S, size_t idx, int e, double re, double im, float inv_scale) {
+        short2 *p = e < 4 ? (short2 *)kind_base + idx * 4 + e : (short2 *)(kind_base + 16 * S) + idx * 2 + (e - 4);
+        *p = make_short2(q16((float)re * inv_scale), q16((float)im * inv_scale));
+    }
+};
+
+inline size_t c12_link_bytes(int p, size_t stride) {  // both parities, 8 kinds
+    return p == P_F32 ? 2 * 8 * C12<P_F32>::kind_bytes(stride)
+         : p == P_F16 ? 2 * 8 * C12<P_F16>::kind_bytes(stride) : 0;
+}
+
 // bytes of one colour-vector field / one complex link entry
 inline size_t prec_vec_bytes(int p, size_t stride) {
     switch (p) {

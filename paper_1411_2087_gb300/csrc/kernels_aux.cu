@@ -278,6 +278,110 @@ __global__ void fold_kernel(FoldArgs fa, const double *__restrict__ fat, const d
             Fmt<P>::pack_link(coef * src[2 * j], coef * src[2 * j + 1], fa.inv_scale[three ? 1 : 0]);
 }
 
+// the same folding into the 12-real layout (rows 0 and 1 only)
+template <int P>
+__global__ void fold_c12_kernel(FoldArgs fa, const double *__restrict__ fat, const double *__restrict__ lng,
+                                char *G) {
+    const Geom &g = fa.g;
+    const long long V = 2LL * g.Vh;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 8 * V)
+        return;
+    const int kind = (int)(t / V);
+    const long long i = t % V;
+    const int mu = kind & 3;
+    const bool three = kind >= 4;
+    int x[4];
+    full_coords(g, i, x);
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const size_t cb = (size_t)(i >> 1);
+    int eta_sum = 0;
+    for (int nu = 0; nu < mu; nu++)
+        eta_sum += x[nu];
+    const int s = three ? 3 : 1;
+    const int wraps = (x[mu] + s) / g.L[mu];
+    double coef = three ? fa.c3 : fa.c1;
+    if (eta_sum & 1)
+        coef = -coef;
+    if ((wraps & 1) && fa.bc[mu] < 0)
+        coef = -coef;
+    const double *src = (three ? lng : fat) + ((size_t)mu * V + i) * 18;
+    const size_t S = (size_t)g.stride;
+    char *kb = G + ((size_t)par * 8 + kind) * C12<P>::kind_bytes(S);
+    for (int e = 0; e < 6; e++)
+        C12<P>::store(kb, S, cb, e, coef * src[2 * e], coef * src[2 * e + 1], fa.inv_scale[three ? 1 : 0]);
+}
+
+cudaError_t launch_fold_links_c12(int prec, const Geom &g, const double bc[4], double c1, double c3,
+                                  const double *fat, const double *lng, void *links, const float inv_scale[2],
+                                  cudaStream_t s) {
+    FoldArgs fa;
+    fa.g = g;
+    for (int k = 0; k < 4; k++)
+        fa.bc[k] = bc[k];
+    fa.c1 = c1;
+    fa.c3 = c3;
+    fa.inv_scale[0] = inv_scale ? inv_scale[0] : 0.f;
+    fa.inv_scale[1] = inv_scale ? inv_scale[1] : 0.f;
+    const long long n = 16LL * g.Vh;
+    const int grid = (int)((n + 255) / 256);
+    if (prec == P_F32)
+        fold_c12_kernel<P_F32><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links);
+    else if (prec == P_F16)
+        fold_c12_kernel<P_F16><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// largest deviation of a link field from SU(3): max over links of
+// |U U^+ - 1| (entry-wise) and |det U - 1|, as float bits in *out
+__global__ void su3_dev_kernel(const double2 *__restrict__ U, long long nlinks, unsigned *out) {
+    float m = 0.f;
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nlinks;
+         l += (long long)gridDim.x * blockDim.x) {
+        double2 A[9];
+        for (int e = 0; e < 9; e++)
+            A[e] = U[l * 9 + e];
+        double dev = 0.0;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) {
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k < 3; k++) {  // (U U^+)_ab = sum_k U_ak conj(U_bk)
+                    re += A[3 * a + k].x * A[3 * b + k].x + A[3 * a + k].y * A[3 * b + k].y;
+                    im += A[3 * a + k].y * A[3 * b + k].x - A[3 * a + k].x * A[3 * b + k].y;
+                }
+                dev = fmax(dev, fabs(re - (a == b ? 1.0 : 0.0)));
+                dev = fmax(dev, fabs(im));
+            }
+        // det by the first row's cofactors
+        double dre = 0.0, dim = 0.0;
+        for (int j = 0; j < 3; j++) {
+            const int k = (j + 1) % 3, q = (j + 2) % 3;
+            const double2 p = A[3 + k], r = A[6 + q], u = A[3 + q], v = A[6 + k];
+            const double cre = (p.x * r.x - p.y * r.y) - (u.x * v.x - u.y * v.y);
+            const double cim = (p.x * r.y + p.y * r.x) - (u.x * v.y + u.y * v.x);
+            dre += A[j].x * cre - A[j].y * cim;
+            dim += A[j].x * cim + A[j].y * cre;
+        }
+        dev = fmax(dev, fabs(dre - 1.0));
+        dev = fmax(dev, fabs(dim));
+        m = fmaxf(m, (float)dev);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_su3_deviation(const double *U, long long nlinks, unsigned *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    su3_dev_kernel<<<1024, 256, 0, s>>>((const double2 *)U, nlinks, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], double c1, double c3,
                               const double *fat, const double *lng, void *links,
                               const float inv_scale[2], cudaStream_t s) {

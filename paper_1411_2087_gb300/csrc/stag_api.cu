@@ -125,6 +125,8 @@ extern "C" int stag_lattice_destroy(stag_lattice lat) {
         free_cg(lat->cg[p]);
         if (lat->links[p])
             cudaFree(lat->links[p]);
+        if (lat->links_c12[p])
+            cudaFree(lat->links_c12[p]);
     }
     if (lat->partial)
         cudaFree(lat->partial);
@@ -244,6 +246,8 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         return fail(STAG_ERR_ARG, "stag_gauge_upload: bad ptr_kind %d", ptr_kind);
     if (!std::isfinite(c1) || !std::isfinite(c3))
         return fail(STAG_ERR_ARG, "stag_gauge_upload: coefficients must be finite");
+    const bool compress = (prec_mask & STAG_COMPRESS12) != 0;
+    prec_mask &= ~(unsigned)STAG_COMPRESS12;
     if (prec_mask == 0)
         prec_mask = STAG_PREC_BIT(STAG_F64) | STAG_PREC_BIT(STAG_DF64);
     for (int p = 0; p < 32; p++)
@@ -251,6 +255,10 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
             if (!prec_valid(p))
                 return fail(STAG_ERR_ARG, "stag_gauge_upload: precision %d (%s) not available", p,
                             prec_name(p));
+    if (compress && !(prec_mask & (STAG_PREC_BIT(STAG_F32) | STAG_PREC_BIT(STAG_F16))))
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: 12-real compression applies to F32 and F16 copies only");
+    if (compress && (c1 == 0.0 || c3 == 0.0))
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: 12-real compression needs c1 != 0 and c3 != 0");
     DEVICE_SCOPE(lat->device);
     // device sources may have been written on any stream of the caller
     if (ptr_kind == STAG_PTR_DEVICE)
@@ -290,8 +298,40 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
             cudaFree(lat->links[p]);
             lat->links[p] = nullptr;
         }
+        if (lat->links_c12[p]) {
+            cudaFree(lat->links_c12[p]);
+            lat->links_c12[p] = nullptr;
+        }
     }
     drop_mixed_graphs(lat);
+    if (compress) {
+        // the 12-real form rebuilds row 3 from rows 1 and 2: only valid for
+        // links in SU(3) (the paper's Sec. 4 notes smeared links are not)
+        unsigned *dev_bits = nullptr;
+        cudaError_t e = cudaMalloc(&dev_bits, 2 * sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = launch_su3_deviation(fat_d, 4LL * lat->V, dev_bits, lat->stream);
+        if (e == cudaSuccess)
+            e = launch_su3_deviation(lng_d, 4LL * lat->V, dev_bits + 1, lat->stream);
+        unsigned bits[2] = {0u, 0u};
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bits, dev_bits, sizeof bits, cudaMemcpyDeviceToHost, lat->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(lat->stream);
+        if (dev_bits)
+            cudaFree(dev_bits);
+        if (e != cudaSuccess) {
+            release();
+            return fail(STAG_ERR_CUDA, "SU(3) check: %s", cudaGetErrorString(e));
+        }
+        float dev[2];
+        memcpy(dev, bits, sizeof dev);
+        if (!(dev[0] <= 1e-6f) || !(dev[1] <= 1e-6f)) {
+            release();
+            return fail(STAG_ERR_ARG, "stag_gauge_upload: links deviate from SU(3) by %.2e (fat) / %.2e (long); "
+                        "12-real compression needs special unitary links", dev[0], dev[1]);
+        }
+    }
     lat->has_gauge = false;
     float inv_scale[2] = {0.f, 0.f};
     if ((prec_mask >> STAG_F16) & 1u) {
@@ -329,6 +369,15 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         if (e == cudaSuccess)
             e = launch_fold_links(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links[p], inv_scale,
                                   lat->stream);
+        if (e == cudaSuccess && compress && (p == STAG_F32 || p == STAG_F16)) {
+            const size_t cb = c12_link_bytes(p, (size_t)lat->geom.stride);
+            e = cudaMalloc(&lat->links_c12[p], cb);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(lat->links_c12[p], 0, cb, lat->stream);
+            if (e == cudaSuccess)
+                e = launch_fold_links_c12(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links_c12[p],
+                                          inv_scale, lat->stream);
+        }
         if (e != cudaSuccess) {
             release();
             return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,

@@ -33,6 +33,7 @@ ERR_NOMEM = -7
 
 F64, F32, F16, DF64 = 0, 1, 2, 3
 PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
+COMPRESS12 = 1 << 16
 EVEN, ODD = 0, 1
 CG_LAUNCH_GRAPH, CG_LAUNCH_HOST = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
@@ -257,7 +258,8 @@ class Lattice:
         _check(lib().stag_lattice_set_cg_launch(self.handle, m, int(chunk)))
 
     # gauge -----------------------------------------------------------------
-    def upload_gauge(self, fat, lng=None, c1=C1_NAIK, c3=C3_NAIK, precisions=("f64", "df64")):
+    def upload_gauge(self, fat, lng=None, c1=C1_NAIK, c3=C3_NAIK, precisions=("f64", "df64"),
+                     compress12: bool = False):
         shape = (4, self.V, 3, 3)
         pf, kind, keep_f = _as_buffer(fat, shape)
         if lng is not None:
@@ -266,7 +268,7 @@ class Lattice:
                 raise ValueError("fat and long links must both be on the host or both on the device")
         else:
             pl = None
-        mask = 0
+        mask = COMPRESS12 if compress12 else 0
         for p in precisions:
             mask |= 1 << (PREC[p] if isinstance(p, str) else int(p))
         _check(lib().stag_gauge_upload(self.handle, pf, pl, float(c1), float(c3), kind, mask))

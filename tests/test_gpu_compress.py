@@ -1,0 +1,72 @@
+"""12-real ("two-row") link compression of the FP32 and 16-bit copies: the
+Dslash with the third row rebuilt from conj(row1 x row2) / (c eta b) against
+the oracle, for boundary conditions and lattice sizes that exercise every
+sign of the rebuild (including hops that wrap twice on L = 2), the SU(3)
+check at upload, and a mixed-precision solve on compressed 16-bit links."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1411_2087_gb300 import stag, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 2e-6, "f16": 3e-4}
+
+
+def rel_err(got, want):
+    return np.abs(got - want).max() / np.abs(want).max()
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 6, 8), (8, 8, 8, 8), (6, 4, 6, 10)])
+@pytest.mark.parametrize("bc", [(1.0, 1.0, 1.0, -1.0), (-1.0, 1.0, -1.0, -1.0), (1.0, 1.0, 1.0, 1.0)])
+def test_compressed_dslash(dims, bc):
+    Vh = int(np.prod(dims)) // 2
+    U = synth.su3_field(dims, 0.5, 31).numpy()
+    N = oracle.long_links(dims, U)
+    psi_e = synth.gaussian_colour_field(Vh, 32).numpy()
+    psi_o = synth.gaussian_colour_field(Vh, 33).numpy()
+    want_o = oracle.dslash_parity(dims, U, N, 1, psi_e, bc=bc, c1=1.2, c3=-0.07)
+    want_e = oracle.dslash_parity(dims, U, N, 0, psi_o, bc=bc, c1=1.2, c3=-0.07)
+    with stag.Lattice(dims, bc=bc) as lat:
+        lat.upload_gauge(U, N, c1=1.2, c3=-0.07, precisions=("f32", "f16"), compress12=True)
+        for prec in ("f32", "f16"):
+            fe = lat.field(stag.EVEN, prec, psi_e)
+            fo = lat.field(stag.ODD, prec, psi_o)
+            oo = lat.field(stag.ODD, prec)
+            oe = lat.field(stag.EVEN, prec)
+            lat.dslash(oo, fe)
+            lat.dslash(oe, fo)
+            e1 = rel_err(oo.export(), want_o)
+            e2 = rel_err(oe.export(), want_e)
+            assert e1 <= TOL[prec] and e2 <= TOL[prec], (prec, e1, e2)
+
+
+def test_compression_rejects_non_su3_links():
+    dims = (4, 4, 4, 4)
+    U = synth.su3_field(dims, 0.3, 34).numpy()
+    with stag.Lattice(dims) as lat:
+        with pytest.raises(stag.StagError) as ei:
+            lat.upload_gauge(1.01 * U, None, precisions=("f32",), compress12=True)
+        assert ei.value.status == stag.ERR_ARG
+        with pytest.raises(stag.StagError):  # DF64 copies are never compressed
+            lat.upload_gauge(U, None, precisions=("df64",), compress12=True)
+        # without compression the same links are accepted
+        lat.upload_gauge(1.01 * U, None, precisions=("f32",))
+
+
+def test_mixed_cg_on_compressed_links():
+    dims, mass = (8, 8, 8, 8), 0.02
+    U = synth.su3_field(dims, 0.35, 35).numpy()
+    N = oracle.long_links(dims, U)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 36).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("df64", "f32", "f16"), compress12=True)
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        for inner in ("f32", "f16"):
+            info = lat.cg_mixed(fx, fb, mass, 1e-10, 20000, inner=inner)
+            assert info["return"] == stag.OK, info
+            r = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, fx.export())) / np.linalg.norm(b)
+            assert r <= 1.05e-10, (inner, r)
