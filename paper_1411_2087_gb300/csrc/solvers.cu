@@ -482,7 +482,7 @@ int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, dou
     a2.b = b;
     a2.m2 = make_dpair(mk * mk);
     a2.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(hi, r_out ? EPI_RESID_STORE : EPI_RESID, a2, 0, s));
+    CUDA_TRY(launch_dslash(hi, r_out ? EPI_RESID_STORE : EPI_RESID, a2, lat->dslash_block[hi], s));
     CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     *rr = lat->sc_host->true_rr;

@@ -566,7 +566,7 @@ static int dslash_impl(stag_lattice lat, stag_field out, const stag_field in, in
     STAG_TRY(check_pair(lat, out, in, out_par, who));
     DEVICE_SCOPE(lat->device);
     DslashArgs a = dslash_args(lat, out->prec, out_par, in->data, out->data);
-    CUDA_TRY(launch_dslash(out->prec, EPI_NONE, a, 0, lat->stream));
+    CUDA_TRY(launch_dslash(out->prec, EPI_NONE, a, lat->dslash_block[out->prec], lat->stream));
     return STAG_OK;
 }
 
