@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched / multi-shift comparison (16 RHS on three lattices, 12 shifts)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="time the Dslash kernels of every precision on --dims (autotuner launches) and exit")
+    ap.add_argument("--compress12", action="store_true",
+                    help="with --kernels-only: 12-real links for the FP32 and 16-bit copies")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
                     help="host: the same CG kernels launched one by one (per-kernel profiling)")
     return ap.parse_args()
@@ -648,8 +652,41 @@ def run_reference(args):
     }
 
 
+def run_kernels_only(args):
+    """Dslash kernel timings per precision (and of the batched multi-RHS
+    kernel) on one lattice: the autotuner's CUDA-event timings of both block
+    sizes, with GB/s from the algorithmic bytes per site."""
+    import torch
+    from paper_1411_2087_gb300 import metrics, stag, synth
+    dims = tuple(int(v) for v in args.dims.split(",")) if args.dims else DIMS
+    Vh = int(np.prod(dims)) // 2
+    dev = torch.device("cuda", 0)
+    U = synth.su3_field(dims, EPS, SEED_LINKS, device=dev)
+    torch.cuda.synchronize()
+    out = {"kernels_only": True, "lattice": list(dims), "compress12": bool(args.compress12)}
+    link_reals = 12 if args.compress12 else 18
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("f64", "df64", "f32", "f16"), compress12=args.compress12)
+        for prec, rb in (("f64", 8), ("df64", 8), ("f32", 4), ("f16", 2)):
+            t = lat.autotune(prec)
+            best = min(t["dslash_us"].values())
+            if prec == "f16":
+                byts = metrics.dslash_half_bytes_per_site() if not args.compress12 else 16 * 24 + 32
+            elif prec in ("f32",):
+                byts = metrics.dslash_bytes_per_site(rb, reals_per_link=link_reals)
+            else:
+                byts = metrics.dslash_bytes_per_site(rb)
+            out[prec] = {"us": {str(k): round(v, 2) for k, v in t["dslash_us"].items()},
+                         "gbs": round(byts * Vh / (best * 1e-6) / 1e9, 1),
+                         "batched_us": {str(k): round(v, 2) for k, v in t["batch_us"].items()}}
+    return out
+
+
 def main():
     args = parse()
+    if args.kernels_only:
+        print(json.dumps(run_kernels_only(args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args)
     else:
