@@ -177,6 +177,20 @@ def make_inputs(dims, device, rank):
     return U, b
 
 
+def aggregate_ranks(pg, times, work):
+    """Whole-job figures: the largest time of each kind over the ranks and
+    the sum of the work, through torch.distributed `pg` (None: one rank).
+    Returns times followed by work, as floats."""
+    import torch
+    if pg is None:
+        return [float(t) for t in times] + [float(w) for w in work]
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64)
+    w = torch.tensor([float(v) for v in work], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(w, op=pg.ReduceOp.SUM)
+    return [float(v) for v in t] + [float(v) for v in w]
+
+
 def cg_bytes_per_iter_site(prec):
     from paper_1411_2087_gb300 import metrics
     return metrics.cg_bytes_per_iteration_per_site(8)
@@ -277,16 +291,8 @@ def run_native(args):
 
     # ---- aggregate over ranks (max time, sum of work)
     bpi = cg_bytes_per_iter_site(prec) * Vh
-    work_bytes = sum(iters) * bpi
-    e2e_bytes = e2e_iters * bpi
-    vals = torch.tensor([total_ms, e2e_s, work_bytes, e2e_bytes, dslash_ms], dtype=torch.float64)
-    if pg is not None:
-        mx = vals.clone()
-        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
-        sm = vals.clone()
-        pg.all_reduce(sm, op=pg.ReduceOp.SUM)
-        total_ms, e2e_s, dslash_ms = mx[0].item(), mx[1].item(), mx[4].item()
-        work_bytes, e2e_bytes = sm[2].item(), sm[3].item()
+    total_ms, e2e_s, dslash_ms, work_bytes, e2e_bytes = aggregate_ranks(
+        pg, [total_ms, e2e_s, dslash_ms], [sum(iters) * bpi, e2e_iters * bpi])
     value = work_bytes / (total_ms * 1e-3) / 1e9
     e2e_value = e2e_bytes / e2e_s / 1e9
 
