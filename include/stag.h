@@ -387,6 +387,33 @@ int stag_apply_M_noalloc(const int dims[4], const double bc[4], double c1, doubl
                          const double *fat, const double *lng, double mass,
                          const double *in_even, double *out_even, void *cuda_stream);
 
+/* ---- domain decomposition, emulated on one GPU ---------------------------
+ * The paper's multi-node runs (Sec. 2 and 3) split the lattice over ranks,
+ * each applying Dslash to its part after exchanging the boundary sites of
+ * the input with its neighbours.  These calls reproduce that data movement
+ * on one device: the t direction is cut into `ndomains` slabs of
+ * Lt / ndomains slices (the first Lt % ndomains slabs one more); each slab's
+ * Dslash reads a private copy of the input that holds the slab and the three
+ * slices on either side (the reach of the three-link term), filled by
+ * device-to-device copies as a halo exchange would, and writes the outputs
+ * of its slab only.  The global sums of the CG are per-slab partial sums
+ * added on the host in slab order, as an allreduce would.  The results equal
+ * the single-domain calls up to the order of the summation.
+ * 1 <= ndomains <= Lt, else STAG_ERR_ARG.  Each call allocates one field per
+ * slab on the device and frees it before returning. */
+
+/* out = D in, as stag_dslash_eo / stag_dslash_oe (out's parity selects
+ * which), computed slab by slab.  Fields of opposite parity, one precision
+ * (any), with a gauge copy of that precision; synchronous. */
+int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, const stag_field in);
+
+/* stag_cg_solve computed slab by slab with host-reduced inner products (one
+ * host round trip per reduction: a model of the multi-node solver's data
+ * flow, not a fast path).  Same fields, arguments and return values as
+ * stag_cg_solve; info->seconds is wall time, gflops and gbs are 0. */
+int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x_even, const stag_field b_even,
+                     double mass, double rel_tol, int max_iter, stag_solve_info *info);
+
 /* ---- errors -------------------------------------------------------------- */
 const char *stag_strerror(int status);
 const char *stag_last_error_message(void);

@@ -42,6 +42,7 @@ struct DslashArgs {
     const int *gate;        // if set, return at once unless *gate != 0 (uniform flag)
     float link_scale[2];    // 16-bit links: value = q * scale (one-link, three-link)
     int compressed;         // links in the 12-real layout (FP32, 16-bit)
+    int c0, cn;             // output sites c0 .. c0+cn-1 (cn = 0: all Vh)
     float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
     int bc_neg[4];          // boundary sign of direction mu is -1
 };
@@ -172,10 +173,10 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
         return;
     if (a.gate && *a.gate == 0)
         return;
-    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    const int c = a.c0 + blockIdx.x * BLOCK + threadIdx.x;
     const int S = a.g.stride;
     double dot = 0.0;
-    if (c < a.g.Vh) {
+    if (c < a.c0 + (a.cn ? a.cn : a.g.Vh)) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
         dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
         if (EPI == EPI_NONE) {

@@ -8,7 +8,8 @@ namespace stag {
 
 template <int P, int BLOCK, bool COMP>
 static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
-    const int grid = dslash_grid(a.g, BLOCK);
+    const int n = a.cn ? a.cn : a.g.Vh;
+    const int grid = (n + BLOCK - 1) / BLOCK;
     if (grid == 0)
         return cudaSuccess;
     switch (epi) {

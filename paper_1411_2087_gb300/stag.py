@@ -57,6 +57,7 @@ EXPORTED = [
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
     "stag_net_set_loss",
     "stag_apply_M_noalloc",
+    "stag_dd_dslash", "stag_dd_cg_solve",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -135,6 +136,8 @@ def lib():
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
+            "stag_dd_dslash": ([P, I, P, P], I),
+            "stag_dd_cg_solve": ([P, I, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
             "stag_version": ([], ctypes.c_char_p),
@@ -311,6 +314,22 @@ class Lattice:
         info = SolveInfo()
         st = lib().stag_cg_solve(self.handle, x.handle, b.handle, float(mass), float(tol),
                                  int(max_iter), ctypes.byref(info))
+        if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def dd_dslash(self, out: Field, inp: Field, ndomains: int):
+        """Dslash computed on `ndomains` t-slabs with depth-3 halo copies."""
+        _check(lib().stag_dd_dslash(self.handle, int(ndomains), out.handle, inp.handle))
+
+    def dd_cg(self, x: Field, b: Field, mass: float, ndomains: int, tol: float = 1e-10,
+              max_iter: int = 20000, raise_on_failure: bool = False) -> dict:
+        """CG on `ndomains` t-slabs with host-reduced inner products."""
+        info = SolveInfo()
+        st = lib().stag_dd_cg_solve(self.handle, int(ndomains), x.handle, b.handle, float(mass),
+                                    float(tol), int(max_iter), ctypes.byref(info))
         if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(st)
         d = info.as_dict()
