@@ -194,6 +194,19 @@ typedef struct {
 int stag_cg_solve(stag_lattice lat, stag_field x_even, const stag_field b_even,
                   double mass, double rel_tol, int max_iter, stag_solve_info *info);
 
+/* stag_cg_solve with a record of the iteration: trace[3k + 0..2] receives
+ * alpha_k = |r_k|^2 / <p_k, M p_k>, beta_k = |r_{k+1}|^2 / |r_k|^2 and
+ * |r_{k+1}|^2 for k < min(iterations, trace_len) (host memory, caller-owned,
+ * 3 * trace_len doubles; entries past the last iteration are not written).
+ * The first trace_len iterations run host-driven, one launch sequence and
+ * one host wait each, so that the device scalars can be read between them;
+ * the arithmetic is that of stag_cg_solve.  This exposes the CG's scalar
+ * recurrence for checking against an independent implementation.
+ * trace NULL or trace_len < 0: STAG_ERR_ARG.  Otherwise as stag_cg_solve. */
+int stag_cg_solve_traced(stag_lattice lat, stag_field x_even, const stag_field b_even,
+                         double mass, double rel_tol, int max_iter, double *trace, int trace_len,
+                         stag_solve_info *info);
+
 /* Mixed-precision CG with reliable updates (Sleijpen & van der Vorst;
  * Clark et al. for lattice QCD): the iteration runs in `inner_prec`
  * (STAG_F32, or STAG_F16 = 16-bit fixed-point storage with float arithmetic),

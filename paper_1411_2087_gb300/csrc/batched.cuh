@@ -60,8 +60,8 @@ STAG_D int group_of(const BatchArgs &a, int blk) {
 
 // Sum K values per thread over the blocks of one group.  Returns true in
 // the group's last block; there tot[k] holds the sums (all threads).
-template <int BLOCK, int K>
-STAG_D bool group_sum(const double (&v)[K], int Kact, double *partial, int lblk, int nblk, unsigned *ticket,
+template <int BLOCK, int K, class T>
+STAG_D bool group_sum(const T (&v)[K], int Kact, double *partial, int lblk, int nblk, unsigned *ticket,
                       double *smem, double (&tot)[K]) {
     __shared__ bool last;
     __shared__ double res[K];

@@ -152,14 +152,20 @@ STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ 
     }
 }
 
-template <class R> STAG_D double re_dot3(const cplx<R> a[3], const cplx<R> b[3]) {
+// Re <a, b> of one site, in the reduction type of R (FP64 for FP64, else
+// double-float: exact for an FP32 sum, the double-float sum itself for DF64)
+STAG_D double to_red(double s) { return s; }
+STAG_D df to_red(float s) { return df_make(s, 0.f); }
+STAG_D df to_red(df s) { return df_norm(s); }
+
+template <class R> STAG_D red_t<R> re_dot3(const cplx<R> a[3], const cplx<R> b[3]) {
     R s = rzero<R>();
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         mac(s, a[k].re, b[k].re);
         mac(s, a[k].im, b[k].im);
     }
-    return to_double<R>(rnorm<R>(s));
+    return to_red(s);
 }
 
 template <int P, int EPI, int BLOCK, bool COMP = false>
@@ -175,7 +181,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
         return;
     const int c = a.c0 + blockIdx.x * BLOCK + threadIdx.x;
     const int S = a.g.stride;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (c < a.c0 + (a.cn ? a.cn : a.g.Vh)) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
         dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);

@@ -26,7 +26,7 @@ cg_init_kernel(Geom g, typename Fmt<P>::Elem *x, typename Fmt<P>::Elem *r,
     using R = typename F::R;
     __shared__ double smem[32];
     const int c = blockIdx.x * BLOCK + threadIdx.x;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (c < g.Vh) {
         cplx<R> bv[3], z[3];
         load_vec<P>(b, g.stride, c, bv);
@@ -69,7 +69,7 @@ cg_update_kernel(Geom g, typename Fmt<P>::Elem *x, typename Fmt<P>::Elem *r,
     __shared__ double smem[32];
     const int c = blockIdx.x * BLOCK + threadIdx.x;
     const bool run = sc->status == CG_RUNNING;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (run && c < g.Vh) {
         const R alpha = scalar_as<R>(sc->alpha);
         const R malpha = -alpha;

@@ -32,10 +32,10 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_kernel(BatchArgs a, int ou
     const int c = lblk * BLOCK + threadIdx.x;
     const Geom &g = G.g;
     const int S = g.stride;
-    double dot[K];
+    red_t<R> dot[K];
 #pragma unroll
     for (int k = 0; k < K; k++)
-        dot[k] = 0.0;
+        dot[k] = red_zero<red_t<R>>();
     if (c < g.Vh) {
         cplx<R> acc[K][3];
 #pragma unroll
@@ -164,10 +164,10 @@ __global__ void __launch_bounds__(BLOCK) batch_init_kernel(BatchArgs a) {
     const int lblk = blockIdx.x - G.block0;
     const int c = lblk * BLOCK + threadIdx.x;
     const int S = G.g.stride;
-    double dot[K];
+    red_t<R> dot[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        dot[k] = 0.0;
+        dot[k] = red_zero<red_t<R>>();
         if (k < G.K && c < G.g.Vh) {
             cplx<R> bv[3], z[3];
             load_vec<P>((const E *)G.b[k], S, c, bv);
@@ -224,10 +224,10 @@ __global__ void __launch_bounds__(BLOCK) batch_update_kernel(BatchArgs a) {
     const int lblk = blockIdx.x - G.block0;
     const int c = lblk * BLOCK + threadIdx.x;
     const int S = G.g.stride;
-    double dot[K];
+    red_t<R> dot[K];
 #pragma unroll
     for (int k = 0; k < K; k++) {
-        dot[k] = 0.0;
+        dot[k] = red_zero<red_t<R>>();
         if (act[k] && c < G.g.Vh) {
             const R alpha = scalar_as<R>(a.sys[G.sys0 + k].alpha);
             const R malpha = -alpha;

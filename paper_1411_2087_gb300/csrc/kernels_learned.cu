@@ -470,7 +470,7 @@ fcg_update_kernel(Geom g, typename Fmt<P>::Elem *x, typename Fmt<P>::Elem *r, ty
     __shared__ double smem[32];
     const bool run = sc->status == CG_RUNNING;
     const int c = blockIdx.x * BLOCK + threadIdx.x;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (run && c < g.Vh) {
         const R alpha = scalar_as<R>(sc->alpha);
         const R malpha = -alpha;
@@ -520,7 +520,7 @@ fcg_beta_kernel(Geom g, const typename Fmt<P>::Elem *z, const typename Fmt<P>::E
     if (sc->status != CG_RUNNING)
         return;
     const int c = blockIdx.x * BLOCK + threadIdx.x;
-    double d0 = 0.0, d1 = 0.0;
+    red_t<R> d0 = red_zero<red_t<R>>(), d1 = red_zero<red_t<R>>();
     if (c < g.Vh) {
         cplx<R> zv[3], rv[3], ov[3];
         load_vec<P>(z, g.stride, c, zv);

@@ -41,7 +41,7 @@ mixed_init_kernel(Geom g, typename Fmt<PH>::Elem *x, typename Fmt<PH>::Elem *r,
     using RL = typename Fmt<PL>::R;
     __shared__ double smem[32];
     const int c = blockIdx.x * MB + threadIdx.x;
-    double dot = 0.0;
+    red_t<RH> dot = red_zero<red_t<RH>>();
     if (c < g.Vh) {
         cplx<RH> bv[3], zh[3];
         cplx<RL> bl[3];
@@ -93,7 +93,7 @@ mixed_update_kernel(Geom g, float2 *xs, typename Fmt<PL>::Elem *rs, const typena
     __shared__ double smem[32];
     const int c = blockIdx.x * MB + threadIdx.x;
     const bool run = sc->status == CG_RUNNING;
-    double dot = 0.0;
+    red_t<RL> dot = red_zero<red_t<RL>>();
     if (run && c < g.Vh) {
         const float alpha = scalar_as<float>(sc->alpha);
         cplx<float> xv[3];

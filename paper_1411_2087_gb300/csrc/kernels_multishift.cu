@@ -43,7 +43,7 @@ ms_init_kernel(Geom g, MsArgs a, double *partial, CgScalars *sc, ShiftState *st)
     using E = typename F::Elem;
     __shared__ double smem[32];
     const int c = blockIdx.x * MSB + threadIdx.x;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (c < g.Vh) {
         cplx<R> bv[3], z[3];
         load_vec<P>((const E *)a.b, g.stride, c, bv);
@@ -121,7 +121,7 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
         active[threadIdx.x] = threadIdx.x < a.n ? st[threadIdx.x].active : 0;
     __syncthreads();
     const int c = blockIdx.x * MSB + threadIdx.x;
-    double dot = 0.0;
+    red_t<R> dot = red_zero<red_t<R>>();
     if (run && c < g.Vh) {
         const R alpha = scalar_as<R>(sc->alpha);
         cplx<R> rv[3], av[3];

@@ -735,8 +735,11 @@ static void fill_info(stag_lattice lat, int prec, const CgScalars &h, float ms,
     }
 }
 
-extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b, double mass,
-                             double rel_tol, int max_iter, stag_solve_info *info) {
+// trace (may be NULL): (alpha_k, beta_k, |r_{k+1}|^2) of the first trace_len
+// iterations; tracing runs those iterations host-driven, one at a time
+static int cg_solve_impl(stag_lattice lat, stag_field x, const stag_field b, double mass,
+                         double rel_tol, int max_iter, stag_solve_info *info, double *trace,
+                         int trace_len) {
     if (info)
         memset(info, 0, sizeof *info);
     if (!lat || !x || !b)
@@ -766,7 +769,7 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
     CgWork &w = lat->cg[prec];
     cudaStream_t s = lat->stream;
     CUDA_TRY(cudaMemcpyAsync(w.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
-    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
+    if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH && !trace) {
         if (!w.exec)
             STAG_TRY(build_cg_graph(lat, w));
         STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, w.cond));
@@ -780,6 +783,18 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
         STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0));
         CUDA_TRY(cudaEventRecord(lat->ev0, s));
         CUDA_TRY(launch_cg_init(prec, lat->geom, w.xw, w.r, w.p, w.bw, lat->partial, lat->sc, s));
+        for (int k = 0; trace && k < trace_len && k < max_iter; k++) {
+            CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            if (lat->sc_host->status != CG_RUNNING)
+                break;
+            CUDA_TRY(enqueue_cg_body(lat, w, s, true));
+            CUDA_TRY(cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            trace[3 * k + 0] = lat->sc_host->alpha.d;
+            trace[3 * k + 1] = lat->sc_host->beta.d;
+            trace[3 * k + 2] = lat->sc_host->rr;
+        }
         const int chunk = lat->cg_chunk;
         const long long max_chunks = (long long)max_iter / chunk + 2;
         for (long long k = 0; k < max_chunks; k++) {
@@ -808,6 +823,21 @@ extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b,
                     local.status == STAG_ERR_BREAKDOWN ? "breakdown" : "not converged", local.iters,
                     local.iter_rel_resid);
     return STAG_OK;
+}
+
+extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b, double mass,
+                             double rel_tol, int max_iter, stag_solve_info *info) {
+    return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, nullptr, 0);
+}
+
+extern "C" int stag_cg_solve_traced(stag_lattice lat, stag_field x, const stag_field b, double mass,
+                                    double rel_tol, int max_iter, double *trace, int trace_len,
+                                    stag_solve_info *info) {
+    if (info)
+        memset(info, 0, sizeof *info);
+    if (!trace || trace_len < 0)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_traced: need a trace buffer and trace_len >= 0");
+    return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, trace, trace_len);
 }
 
 

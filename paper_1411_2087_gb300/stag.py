@@ -57,7 +57,7 @@ EXPORTED = [
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
     "stag_net_set_loss",
     "stag_apply_M_noalloc",
-    "stag_dd_dslash", "stag_dd_cg_solve",
+    "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -136,6 +136,7 @@ def lib():
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
+            "stag_cg_solve_traced": ([P, P, P, D, D, I, P, I, ctypes.POINTER(SolveInfo)], I),
             "stag_dd_dslash": ([P, I, P, P], I),
             "stag_dd_cg_solve": ([P, I, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
@@ -319,6 +320,21 @@ class Lattice:
         d = info.as_dict()
         d["return"] = st
         return d
+
+    def cg_traced(self, x: Field, b: Field, mass: float, n_trace: int, tol: float = 1e-10,
+                  max_iter: int = 20000):
+        """CG recording (alpha_k, beta_k, |r_{k+1}|^2) of the first n_trace
+        iterations; returns (info, trace[min(iters, n_trace)][3])."""
+        trace = np.zeros((max(int(n_trace), 1), 3))
+        info = SolveInfo()
+        st = lib().stag_cg_solve_traced(self.handle, x.handle, b.handle, float(mass), float(tol),
+                                        int(max_iter), trace.ctypes.data_as(ctypes.c_void_p),
+                                        int(n_trace), ctypes.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d, trace[: min(d["iters"], int(n_trace))].copy()
 
     def dd_dslash(self, out: Field, inp: Field, ndomains: int):
         """Dslash computed on `ndomains` t-slabs with depth-3 halo copies."""

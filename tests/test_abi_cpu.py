@@ -72,6 +72,9 @@ def test_null_handles_rejected(L):
     assert L.stag_dslash_oe(None, None, None) == stag.ERR_ARG
     assert L.stag_apply_M(None, None, None, 0.1) == stag.ERR_ARG
     assert L.stag_cg_solve(None, None, None, 0.1, 1e-10, 10, None) == stag.ERR_ARG
+    assert L.stag_cg_solve_traced(None, None, None, 0.1, 1e-10, 10, None, 5, None) == stag.ERR_ARG
+    assert L.stag_dd_dslash(None, 2, None, None) == stag.ERR_ARG
+    assert L.stag_dd_cg_solve(None, 2, None, None, 0.1, 1e-10, 10, None) == stag.ERR_ARG
     assert L.stag_field_import(None, None, 0) == stag.ERR_ARG
     assert L.stag_field_export(None, None, 0) == stag.ERR_ARG
     assert L.stag_field_zero(None) == stag.ERR_ARG

@@ -42,6 +42,52 @@ def test_cg_matches_oracle(dims, mass, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "df64"])
+@pytest.mark.parametrize("dims,mass", [((8, 8, 8, 8), 0.1), ((6, 4, 6, 10), 0.05)])
+def test_cg_first_iterations_match_oracle(prec, dims, mass):
+    """The scalar recurrence itself: alpha_k, beta_k and |r_{k+1}|^2 of the
+    first 20 iterations agree with the oracle's to 1e-12 relative."""
+    U, N = fields(dims, 0.3, 1000)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 1100).numpy()
+    _, info_o = oracle.cg(dims, U, N, mass, b, tol=1e-10, history=True)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=(prec,))
+        fb = lat.field(stag.EVEN, prec, b)
+        fx = lat.field(stag.EVEN, prec)
+        info, trace = lat.cg_traced(fx, fb, mass, 20, 1e-10, 5000)
+        fy = lat.field(stag.EVEN, prec)
+        info_g = lat.cg(fy, fb, mass, 1e-10, 5000)
+        same = np.array_equal(fx.export(), fy.export())
+    assert info["return"] == stag.OK and trace.shape == (20, 3)
+    want = info_o["history"][:20]
+    rel = np.abs(trace - want) / np.abs(want)
+    assert rel.max() <= 1e-12, rel.max(axis=0)
+    # tracing changes how the iterations are launched, not their arithmetic
+    assert info["iters"] == info_g["iters"] and same
+
+
+def test_cg_trace_shorter_than_solve_and_arguments():
+    dims, mass = (4, 4, 4, 4), 0.5
+    U, N = fields(dims, 0.3, 9)
+    Vh = int(np.prod(dims)) // 2
+    b = synth.gaussian_colour_field(Vh, 10).numpy()
+    _, info_o = oracle.cg(dims, U, N, mass, b, tol=1e-10, history=True)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("f64",))
+        fb = lat.field(stag.EVEN, "f64", b)
+        fx = lat.field(stag.EVEN, "f64")
+        # a trace longer than the solve holds every iteration
+        info, trace = lat.cg_traced(fx, fb, mass, 1000, 1e-10, 5000)
+        assert info["return"] == stag.OK and len(trace) == info["iters"]
+        assert np.abs(trace - info_o["history"]).max() <= 1e-12 * np.abs(info_o["history"]).max()
+        # trace_len 0: a plain host-driven solve
+        info0, trace0 = lat.cg_traced(fx, fb, mass, 0, 1e-10, 5000)
+        assert info0["iters"] == info["iters"] and len(trace0) == 0
+        with pytest.raises(stag.StagError):
+            lat.cg_traced(fx, fb, mass, -1)
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
 def test_cg_tight_solution_agrees(prec):
     dims, mass = (4, 4, 4, 8), 0.1
     U, N = fields(dims, 0.3, 77)
