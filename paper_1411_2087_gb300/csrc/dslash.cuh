@@ -22,7 +22,8 @@ enum Epi {
     EPI_M = 1,      // out = m^2 p - D in                (M p with in = D_oe p)
     EPI_M_PAP = 2,  // as EPI_M, plus <p, out> -> alpha = rr / <p, M p>
     EPI_RESID = 3,  // r = b - (m^2 p - D in), |r|^2 -> true residual (r not stored)
-    EPI_RESID_STORE = 4  // as EPI_RESID, and r stored to out
+    EPI_RESID_STORE = 4, // as EPI_RESID, and r stored to out
+    EPI_M_PART = 5  // as EPI_M, plus one partial of <p, out> per block (summed by pap_finish)
 };
 
 struct DslashArgs {
@@ -217,10 +218,16 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
                     store_vec<P>((E *)a.out, S, c, o);
             } else {
                 store_vec<P>((E *)a.out, S, c, o);
-                if (EPI == EPI_M_PAP)
+                if (EPI == EPI_M_PAP || EPI == EPI_M_PART)
                     dot = re_dot3<R>(p, o);
             }
         }
+    }
+    if (EPI == EPI_M_PART) {
+        // no ticket: the block's partial is all this kernel contributes
+        const double s = block_sum<BLOCK>(dot, smem);
+        if (threadIdx.x == 0)
+            a.partial[blockIdx.x] = s;
     }
     if (EPI == EPI_M_PAP || EPI == EPI_RESID || EPI == EPI_RESID_STORE) {
         double total;

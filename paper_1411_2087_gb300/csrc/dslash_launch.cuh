@@ -18,6 +18,7 @@ static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
     case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
     case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
     case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+    case EPI_M_PART: dslash_kernel<P, EPI_M_PART, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -22,6 +22,11 @@ cudaError_t launch_cg_update(int prec, const Geom &g, void *x, void *r, const vo
                              const void *Ap, double *partial, CgScalars *sc, cudaStream_t s);
 cudaError_t launch_cg_p_update(int prec, const Geom &g, const void *r, void *p,
                                const CgScalars *sc, cudaStream_t s);
+// <p, M p> from the n block partials of a Dslash with EPI_M_PART, summed in
+// block order; then alpha = |r|^2 / <p, M p> and the breakdown test (as the
+// EPI_M_PAP epilogue).  Returns at once when skip_if_done and the solve has
+// stopped.
+cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s);
 
 // canonical complex128 [Vh][3] (device) <-> internal field layout
 cudaError_t launch_import(int prec, const Geom &g, const double *canon, void *field, cudaStream_t s);

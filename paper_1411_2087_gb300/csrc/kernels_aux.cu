@@ -137,6 +137,39 @@ cg_p_kernel(Geom g, const typename Fmt<P>::Elem *r, typename Fmt<P>::Elem *p, co
     store_vec<P>(p, g.stride, c, rv);
 }
 
+// one block: sum of the block partials of an EPI_M_PART Dslash, then alpha
+constexpr int FINISH_BLOCK = 1024;
+
+__global__ void __launch_bounds__(FINISH_BLOCK)
+pap_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int skip_if_done) {
+    __shared__ double smem[32];
+    if (skip_if_done && sc->status != CG_RUNNING)
+        return;
+    // four independent sums per thread over a fixed assignment, then the block tree
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int i = threadIdx.x;
+    for (; i + 3 * FINISH_BLOCK < n; i += 4 * FINISH_BLOCK) {
+        a0 += partial[i];
+        a1 += partial[i + FINISH_BLOCK];
+        a2 += partial[i + 2 * FINISH_BLOCK];
+        a3 += partial[i + 3 * FINISH_BLOCK];
+    }
+    for (; i < n; i += FINISH_BLOCK)
+        a0 += partial[i];
+    const double total = block_sum<FINISH_BLOCK>((a0 + a1) + (a2 + a3), smem);
+    if (threadIdx.x == 0) {
+        sc->pAp = total;
+        if (sc->status == CG_RUNNING && !(total > 0.0 && total < INFINITY))
+            sc->status = CG_BREAKDOWN;
+        sc->alpha = make_dpair(sc->status == CG_RUNNING ? sc->rr / total : 0.0);
+    }
+}
+
+cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s) {
+    pap_finish_kernel<<<1, FINISH_BLOCK, 0, s>>>(partial, n, sc, skip_if_done ? 1 : 0);
+    return cudaGetLastError();
+}
+
 static int cg_grid(const Geom &g) { return (g.Vh + CG_BLOCK - 1) / CG_BLOCK; }
 
 #define STAG_PREC_SWITCH(prec, ...)                                   \
