@@ -125,7 +125,8 @@ struct stag_lattice_s {
     struct MixedGraph {
         cudaGraphExec_t exec = nullptr;
         cudaGraph_t graph = nullptr;
-        cudaGraphConditionalHandle cond = 0;
+        cudaGraphConditionalHandle cond = 0;      // WHILE: the iteration loop
+        cudaGraphConditionalHandle rel_cond = 0;  // IF: the reliable update
     } mixed[4][4];
     // multi-shift CG
     ShiftState *ms_state = nullptr;        // device, MS_MAX entries
@@ -143,6 +144,7 @@ struct stag_lattice_s {
     void *bblo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 right-hand sides of that phase
     int batch_block[4] = {128, 128, 128, 128};  // block size of the batched kernels (autotuned)
     int dslash_block[4] = {0, 0, 0, 0};         // block size of the Dslash kernels (0 = default)
+    int mdslash_block[4] = {0, 0, 0, 0};        // block size of the M Dslash with <p, Mp> partials (0 = as above)
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
     int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
 };
@@ -239,7 +241,8 @@ static inline int ensure_cg_work(stag_lattice lat, int prec) {
 }
 
 static inline int upload_scalars(stag_lattice lat, double mass, double tol, int max_iter, bool has_cond,
-                          cudaGraphConditionalHandle cond, double delta = 0.0) {
+                          cudaGraphConditionalHandle cond, double delta = 0.0,
+                          bool has_rel_cond = false, cudaGraphConditionalHandle rel_cond = 0) {
     // pageable source: the copy has read it when cudaMemcpyAsync returns
     CgScalars h;
     memset(&h, 0, sizeof h);
@@ -249,6 +252,8 @@ static inline int upload_scalars(stag_lattice lat, double mass, double tol, int 
     h.has_cond = has_cond ? 1 : 0;
     h.cond = cond;
     h.delta = delta;
+    h.has_rel_cond = has_rel_cond ? 1 : 0;
+    h.rel_cond = rel_cond;
     CUDA_TRY(cudaMemcpyAsync(lat->sc, &h, sizeof h, cudaMemcpyHostToDevice, lat->stream));
     return STAG_OK;
 }
@@ -267,6 +272,27 @@ static inline int alloc_vec(stag_lattice lat, int prec, void **p) {
     return STAG_OK;
 }
 
+
+// block size of the M Dslash that writes <p, Mp> partials (EPI_M_PART)
+static inline int m_block(const stag_lattice lat, int prec) {
+    if (lat->mdslash_block[prec] > 0)
+        return lat->mdslash_block[prec];
+    return lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
+}
+
+// Ap = m^2 p - D_eo t with <p, Ap> summed by pap_finish: alpha and the
+// breakdown test in sc (skip_if_done: both return at once after the solve)
+static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *t, void *Ap, const void *p,
+                                        bool skip_if_done, cudaStream_t s) {
+    DslashArgs a = dslash_args(lat, prec, STAG_EVEN, t, Ap);
+    a.p = p;
+    a.skip_if_done = skip_if_done;
+    const int block = m_block(lat, prec);
+    cudaError_t e = launch_dslash(prec, EPI_M_PART, a, block, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s);
+}
 
 // one plain CG iteration on the lattice stream (stag_api.cu)
 cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done);

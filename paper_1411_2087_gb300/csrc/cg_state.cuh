@@ -56,6 +56,10 @@ struct CgScalars {
     double alpha_prev, beta_prev;
     // flexible CG: |r|^2 (rr holds <r, z> there)
     double fcg_rr;
+    // mixed precision in a graph: condition of the reliable-update branch
+    cudaGraphConditionalHandle rel_cond;
+    int has_rel_cond;
+    int pad3;
 };
 
 // multi-shift CG

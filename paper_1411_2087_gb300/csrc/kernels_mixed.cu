@@ -16,6 +16,8 @@
 //   if reliable: x += x_s, x_s = 0                        (mixed_accum, gated)
 //                r = b - M x, |r|^2                        (hi Dslash kernels, gated)
 //                r_s = r, beta = |r|^2/rr                  (mixed_restart, gated)
+//   (in a graph the four gated kernels sit in a conditional IF node that
+//   mixed_update opens, so that iterations without an update launch none)
 //   p = r_s + beta p                                      (cg_p_kernel)
 #include "dslash.cuh"
 #include "kernels.h"
@@ -121,6 +123,10 @@ mixed_update_kernel(Geom g, float2 *xs, typename Fmt<PL>::Elem *rs, const typena
             const double rn = sqrt(total);
             if (!(total < INFINITY)) {
                 sc->status = CG_BREAKDOWN;
+            } else if (sc->iter > sc->max_iter) {
+                // the update requested at max_iter ends the solve; this only
+                // guards the loop if that update did not run
+                sc->status = CG_MAXITER;
             } else if (rn < sc->delta * sc->rmax || total <= sc->rr_stop || sc->iter >= sc->max_iter) {
                 sc->reliable = 1;
             } else {
@@ -129,6 +135,8 @@ mixed_update_kernel(Geom g, float2 *xs, typename Fmt<PL>::Elem *rs, const typena
                 sc->rmax = fmax(sc->rmax, rn);
             }
         }
+        if (sc->has_rel_cond)
+            cudaGraphSetConditional(sc->rel_cond, sc->reliable ? 1u : 0u);
         set_loop_condition_m(sc);
     }
 }

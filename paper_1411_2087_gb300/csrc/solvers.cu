@@ -10,25 +10,12 @@ static const int *reliable_flag(stag_lattice lat) {
     return (const int *)((const char *)lat->sc + offsetof(CgScalars, reliable));
 }
 
-static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool host_mode) {
+// the four kernels of a reliable update; each returns at once unless it is due
+static cudaError_t enqueue_reliable_update(stag_lattice lat, int hi, int lo, cudaStream_t s) {
     CgWork &H = lat->cg[hi];
     CgWork &L = lat->cg[lo];
-    cudaStream_t s = lat->stream;
     const Geom &g = lat->geom;
     cudaError_t e;
-    // low precision: t_s = D_oe p; Ap = m^2 p - D_eo t_s, alpha
-    DslashArgs a1 = dslash_args(lat, lo, STAG_ODD, L.p, L.t);
-    a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_NONE, a1, lat->dslash_block[lo], s)) != cudaSuccess)
-        return e;
-    DslashArgs a2 = dslash_args(lat, lo, STAG_EVEN, L.t, L.Ap);
-    a2.p = L.p;
-    a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(lo, EPI_M_PAP, a2, lat->dslash_block[lo], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_mixed_update(lo, g, lat->xs, L.r, L.p, L.Ap, lat->partial, lat->sc, s)) != cudaSuccess)
-        return e;
-    // reliable update (every kernel returns at once unless it is due)
     if ((e = launch_mixed_accum(hi, g, H.xw, lat->xs, lat->sc, s)) != cudaSuccess)
         return e;
     DslashArgs a3 = dslash_args(lat, hi, STAG_ODD, H.xw, H.t);
@@ -41,8 +28,61 @@ static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool hos
     a4.gate = reliable_flag(lat);
     if ((e = launch_dslash(hi, EPI_RESID_STORE, a4, lat->dslash_block[hi], s)) != cudaSuccess)
         return e;
-    if ((e = launch_mixed_restart(hi, lo, g, H.r, L.r, lat->sc, s)) != cudaSuccess)
+    return launch_mixed_restart(hi, lo, g, H.r, L.r, lat->sc, s);
+}
+
+// One iteration.  Host mode: all kernels launched on the lattice stream.
+// Graph capture (side != nullptr): the reliable update goes into a
+// conditional IF node whose handle (*rel_cond, created on the loop-body
+// graph) mixed_update sets, captured on the second stream `side`.
+static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool host_mode, cudaStream_t side = nullptr,
+                                      cudaGraphConditionalHandle *rel_cond = nullptr) {
+    CgWork &L = lat->cg[lo];
+    cudaStream_t s = lat->stream;
+    const Geom &g = lat->geom;
+    cudaError_t e;
+    // low precision: t_s = D_oe p; Ap = m^2 p - D_eo t_s, alpha
+    DslashArgs a1 = dslash_args(lat, lo, STAG_ODD, L.p, L.t);
+    a1.skip_if_done = host_mode;
+    if ((e = launch_dslash(lo, EPI_NONE, a1, lat->dslash_block[lo], s)) != cudaSuccess)
         return e;
+    if ((e = enqueue_m_pap(lat, lo, L.t, L.Ap, L.p, host_mode, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_mixed_update(lo, g, lat->xs, L.r, L.p, L.Ap, lat->partial, lat->sc, s)) != cudaSuccess)
+        return e;
+    if (!side) {
+        if ((e = enqueue_reliable_update(lat, hi, lo, s)) != cudaSuccess)
+            return e;
+    } else {
+        cudaStreamCaptureStatus st;
+        cudaGraph_t body = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t ndeps = 0;
+        if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, &body, &deps, nullptr, &ndeps)) != cudaSuccess)
+            return e;
+        if ((e = cudaGraphConditionalHandleCreate(rel_cond, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return e;
+        cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+        ip.conditional.handle = *rel_cond;
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t branch;
+        if ((e = cudaGraphAddNode(&branch, body, deps, nullptr, ndeps, &ip)) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamUpdateCaptureDependencies(s, &branch, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaStreamBeginCaptureToGraph(side, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return e;
+        cudaError_t e2 = enqueue_reliable_update(lat, hi, lo, side);
+        cudaGraph_t branch_out = nullptr;
+        e = cudaStreamEndCapture(side, &branch_out);
+        if (e2 != cudaSuccess)
+            return e2;
+        if (e != cudaSuccess)
+            return e;
+    }
     return launch_cg_p_update(lo, g, L.r, L.p, lat->sc, s);
 }
 
@@ -98,10 +138,18 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
     if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
         return bail("end capture", e);
     cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t side = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail("side stream", e);
     if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        cudaStreamDestroy(side);
         return bail("begin body capture", e);
-    if ((e = enqueue_mixed_body(lat, hi, lo, false)) != cudaSuccess)
+    }
+    cudaGraphConditionalHandle rel_cond = 0;
+    e = enqueue_mixed_body(lat, hi, lo, false, side, &rel_cond);
+    cudaStreamDestroy(side);
+    if (e != cudaSuccess)
         return bail("body", e);
     cudaGraph_t body_out = nullptr;
     if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
@@ -112,6 +160,7 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
     mg.graph = graph;
     mg.exec = exec;
     mg.cond = cond;
+    mg.rel_cond = rel_cond;
     return STAG_OK;
 }
 
@@ -133,7 +182,7 @@ int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *
         auto &mg = lat->mixed[hi][lo];
         if (!mg.exec)
             STAG_TRY(build_mixed_graph(lat, hi, lo));
-        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta));
+        STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta, true, mg.rel_cond));
         CUDA_TRY(cudaEventRecord(lat->ev0, s));
         CUDA_TRY(cudaGraphLaunch(mg.exec, s));
         CUDA_TRY(cudaEventRecord(lat->ev1, s));
@@ -244,10 +293,7 @@ static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, 
     a1.skip_if_done = host_mode;
     if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
-    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
-    a2.p = a.p[a.base];
-    a2.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_M_PAP, a2, lat->dslash_block[prec], s)) != cudaSuccess)
+    if ((e = enqueue_m_pap(lat, prec, w.t, w.Ap, a.p[a.base], host_mode, s)) != cudaSuccess)
         return e;
     if ((e = launch_ms_update(prec, lat->geom, a, w.Ap, lat->partial, lat->sc, lat->ms_state, s)) !=
         cudaSuccess)
@@ -1007,6 +1053,28 @@ extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_
         }
     }
     lat->dslash_block[prec] = best_b;
+    // the M Dslash with <p, Mp> partials of the solvers' iterations
+    best = 1e300;
+    best_b = 128;
+    for (int k = 0; k < 2; k++) {
+        DslashArgs a = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
+        a.p = w.p;
+        for (int i = 0; i < 2; i++)
+            CUDA_TRY(launch_dslash(prec, EPI_M_PART, a, cand[k], s));
+        CUDA_TRY(cudaEventRecord(lat->ev0, s));
+        for (int i = 0; i < reps; i++)
+            CUDA_TRY(launch_dslash(prec, EPI_M_PART, a, cand[k], s));
+        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+        CUDA_TRY(cudaEventSynchronize(lat->ev1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+        const double us = 1e3 * ms / reps;
+        if (us < best) {
+            best = us;
+            best_b = cand[k];
+        }
+    }
+    lat->mdslash_block[prec] = best_b;
     if (prec == STAG_F16)
         return STAG_OK;  // no batched kernels in 16-bit storage
     // batched kernels: one group with the largest K on this lattice

@@ -621,16 +621,9 @@ cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool sk
     a1.skip_if_done = skip_if_done;
     if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
         return e;
-    DslashArgs a2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
-    a2.p = w.p;
-    a2.skip_if_done = skip_if_done;
     // Ap = M p with one partial of <p, Ap> per block; a one-block kernel sums
     // them (cheaper at these grid sizes than a last-block ticket in the Dslash)
-    const int block = lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
-    if ((e = launch_dslash(prec, EPI_M_PART, a2, block, s)) != cudaSuccess)
-        return e;
-    if ((e = launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s)) !=
-        cudaSuccess)
+    if ((e = enqueue_m_pap(lat, prec, w.t, w.Ap, w.p, skip_if_done, s)) != cudaSuccess)
         return e;
     if ((e = launch_cg_update(prec, lat->geom, w.xw, w.r, w.p, w.Ap, lat->partial, lat->sc, s)) !=
         cudaSuccess)
