@@ -299,7 +299,9 @@ def run_native(args):
     peak, peak_kind = measured_peak()
     alg_dslash = metrics.dslash_bytes_per_site(8) * Vh
     achieved = alg_dslash / (dslash_ms * 1e-3) / 1e9
-    launches_per_solve = [4 * k + 3 for k in iters]
+    # per iteration: D_oe, M with <p, Mp> partials, their sum, update, p update;
+    # per solve: init and the two kernels of the true residual
+    launches_per_solve = [5 * k + 3 for k in iters]
     gpu_launches = sum(launches_per_solve) + args.dslash_launches
 
     lat.close()
