@@ -2,7 +2,12 @@
 // lock step inside one graph.  Systems on the same lattice form a group that
 // shares every link load: the multi-RHS Dslash streams each link matrix from
 // HBM once and applies it to all K vectors of the group, so the link bytes
-// per right-hand side drop by K.  One grouped launch covers all groups
+// per right-hand side drop by K.  In FP32 one thread holds a link and applies
+// it to the K vectors.  In double-float and FP64 the arithmetic per site is
+// K times that of a single Dslash and a thread holding K accumulators runs
+// out of registers, so there one thread handles one (site, system) pair and
+// the K lanes of a site load the same link in one coalesced request (the
+// lane-mapped Dslash).  One grouped launch covers all groups
 // (lattices of different sizes): block b belongs to the group whose block
 // range contains it.  Each system keeps its own CG scalars and stops on its
 // own; the loop ends when none is running.
@@ -20,11 +25,13 @@ struct BatchGroup {
     int block0;       // first block of this group in the grouped launch
     int nblocks;      // blocks of this group
     int sys0;         // index of the group's first system
+    int dblock0;      // first block of this group in a lane-mapped Dslash launch
+    int dnblocks;     // its blocks there: one thread per (site, system), K lanes per site
     const void *links[2];  // per parity [8][9][stride]
     float link_scale[2];
     void *x[BATCH_KMAX], *r[BATCH_KMAX], *p[BATCH_KMAX], *Ap[BATCH_KMAX], *t[BATCH_KMAX];
     const void *b[BATCH_KMAX];
-    double *partial;  // this group's partial sums, [nblocks][K]
+    double *partial;  // this group's partial sums, [max(nblocks, dnblocks)][BATCH_KMAX]
 };
 
 struct BatchCtl {
@@ -38,6 +45,7 @@ struct BatchCtl {
 struct BatchArgs {
     int G;
     int nblocks;  // total blocks of the grouped launch
+    int dnblocks; // total blocks of a lane-mapped Dslash launch
     BatchGroup grp[BATCH_MAX_G];
     CgScalars *sys;    // one per system
     unsigned *tickets; // one per group
@@ -54,6 +62,16 @@ STAG_D int group_of(const BatchArgs &a, int blk) {
 #pragma unroll 1
     for (int k = 1; k < a.G; k++)
         if (blk >= a.grp[k].block0)
+            gi = k;
+    return gi;
+}
+
+// the same for a lane-mapped Dslash launch
+STAG_D int group_of_lanes(const BatchArgs &a, int blk) {
+    int gi = 0;
+#pragma unroll 1
+    for (int k = 1; k < a.G; k++)
+        if (blk >= a.grp[k].dblock0)
             gi = k;
     return gi;
 }

@@ -152,6 +152,93 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_kernel(BatchArgs a, int ou
     }
 }
 
+// Lane-mapped multi-RHS Dslash (double-float and FP64): thread t of the
+// group's range handles site t / GK for system t % GK (GK = systems in the
+// group), with the single-site stencil; epilogues as batch_dslash_kernel.
+template <int P, int EPI, int BLOCK, int K>
+__global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, int out_par, int src_x) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    using E = typename F::Elem;
+    __shared__ double smem[32];
+    __shared__ int act[K];
+    const int gi = group_of_lanes(a, blockIdx.x);
+    const BatchGroup &G = a.grp[gi];
+    load_active<K>(a, G, act, EPI != EPI_RESID && !src_x);
+    const int lblk = blockIdx.x - G.dblock0;
+    const int t = lblk * BLOCK + threadIdx.x;
+    const int k = t % G.K;
+    const int c = t / G.K;
+    const Geom &g = G.g;
+    const int S = g.stride;
+    red_t<R> dk = red_zero<red_t<R>>();
+    if (c < g.Vh && act[k]) {
+        DslashArgs da;
+        da.link_scale[0] = G.link_scale[0];
+        da.link_scale[1] = G.link_scale[1];
+        cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
+        // EPI_NONE: D_oe of p (or of x for the true residual); otherwise D_eo of the odd t
+        const E *vin = (const E *)(EPI == EPI_NONE ? (src_x ? G.x[k] : G.p[k]) : G.t[k]);
+        dslash_site<P, false>(g, out_par, c, G.links[out_par], G.links[1 - out_par], vin, da, acc);
+        if (EPI == EPI_NONE) {
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                acc[r].re = rnorm<R>(acc[r].re);
+                acc[r].im = rnorm<R>(acc[r].im);
+            }
+            store_vec<P>((E *)G.t[k], S, c, acc);
+        } else {
+            const R m2 = scalar_as<R>(a.sys[G.sys0 + k].m2);
+            cplx<R> pv[3], o[3];
+            load_vec<P>((const E *)(EPI == EPI_RESID ? G.x[k] : G.p[k]), S, c, pv);
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+                o[r] = cneg(acc[r]);
+                mac(o[r].re, m2, pv[r].re);
+                mac(o[r].im, m2, pv[r].im);
+                o[r].re = rnorm<R>(o[r].re);
+                o[r].im = rnorm<R>(o[r].im);
+            }
+            if (EPI == EPI_RESID) {
+                cplx<R> bv[3];
+                load_vec<P>((const E *)G.b[k], S, c, bv);
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    o[r].re = rsub(bv[r].re, o[r].re);
+                    o[r].im = rsub(bv[r].im, o[r].im);
+                }
+                dk = re_dot3<R>(o, o);
+            } else {
+                store_vec<P>((E *)G.Ap[k], S, c, o);
+                dk = re_dot3<R>(pv, o);
+            }
+        }
+    }
+    if (EPI == EPI_M_PAP || EPI == EPI_RESID) {
+        red_t<R> dot[K];
+#pragma unroll
+        for (int kk = 0; kk < K; kk++)
+            dot[kk] = kk == k ? dk : red_zero<red_t<R>>();
+        double tot[K];
+        if (group_sum<BLOCK, K>(dot, G.K, G.partial, lblk, G.dnblocks, &a.tickets[gi], smem, tot) &&
+            threadIdx.x == 0) {
+            for (int kk = 0; kk < G.K; kk++) {
+                if (!act[kk])
+                    continue;
+                CgScalars &sc = a.sys[G.sys0 + kk];
+                if (EPI == EPI_RESID) {
+                    sc.true_rr = tot[kk];
+                } else {
+                    sc.pAp = tot[kk];
+                    if (!(tot[kk] > 0.0 && tot[kk] < INFINITY))
+                        sc.status = CG_BREAKDOWN;
+                    sc.alpha = make_dpair(sc.status == CG_RUNNING ? sc.rr / tot[kk] : 0.0);
+                }
+            }
+        }
+    }
+}
+
 // x = 0, r = b, p = b, |b|^2 per system
 template <int P, int BLOCK, int K>
 __global__ void __launch_bounds__(BLOCK) batch_init_kernel(BatchArgs a) {
@@ -328,6 +415,16 @@ template <int P, int BLOCK>
 static cudaError_t launch_batch_p(int what, const BatchArgs &a, cudaStream_t s) {
     constexpr int K = batch_k<P>();
     const int grid = a.nblocks;
+    if constexpr (P != P_F32) {
+        const int dgrid = a.dnblocks;
+        switch (what) {
+        case BATCH_DSLASH_OE: batch_dslash_lanes_kernel<P, EPI_NONE, BLOCK, K><<<dgrid, BLOCK, 0, s>>>(a, 1, 0); return cudaGetLastError();
+        case BATCH_DSLASH_X: batch_dslash_lanes_kernel<P, EPI_NONE, BLOCK, K><<<dgrid, BLOCK, 0, s>>>(a, 1, 1); return cudaGetLastError();
+        case BATCH_M_PAP: batch_dslash_lanes_kernel<P, EPI_M_PAP, BLOCK, K><<<dgrid, BLOCK, 0, s>>>(a, 0, 0); return cudaGetLastError();
+        case BATCH_RESID: batch_dslash_lanes_kernel<P, EPI_RESID, BLOCK, K><<<dgrid, BLOCK, 0, s>>>(a, 0, 0); return cudaGetLastError();
+        default: break;
+        }
+    }
     switch (what) {
     case BATCH_INIT: batch_init_kernel<P, BLOCK, K><<<grid, BLOCK, 0, s>>>(a); break;
     case BATCH_DSLASH_OE: batch_dslash_kernel<P, EPI_NONE, BLOCK, K><<<grid, BLOCK, 0, s>>>(a, 1, 0); break;

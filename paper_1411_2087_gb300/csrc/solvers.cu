@@ -3,6 +3,8 @@
 // autotuner.  Documentation in include/stag.h.
 #include "api_internal.h"
 
+#include <algorithm>
+
 // --------------------------------------------------------------------------
 // mixed-precision CG with reliable updates (kernels_mixed.cu has the method)
 // --------------------------------------------------------------------------
@@ -673,7 +675,6 @@ static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, c
             gr.links[1] = links_of(lats[i], prec, 1);
             gr.link_scale[0] = gr.link_scale[1] = 0.f;
             blocks += gr.nblocks;
-            partial_total += (size_t)gr.nblocks * BATCH_KMAX;
             G++;
         }
         BatchGroup &gr = P.a.grp[G - 1];
@@ -690,6 +691,16 @@ static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, c
     }
     P.a.G = G;
     P.a.nblocks = blocks;
+    // lane-mapped Dslash (double-float, FP64): one thread per (site, system)
+    int dblocks = 0;
+    for (int gi = 0; gi < G; gi++) {
+        BatchGroup &gr = P.a.grp[gi];
+        gr.dblock0 = dblocks;
+        gr.dnblocks = (int)(((long long)gr.g.Vh * gr.K + P.block - 1) / P.block);
+        dblocks += gr.dnblocks;
+        partial_total += (size_t)std::max(gr.nblocks, gr.dnblocks) * BATCH_KMAX;
+    }
+    P.a.dnblocks = dblocks;
     cudaError_t e;
     if ((e = cudaMalloc(&P.sys, sizeof(CgScalars) * n)) != cudaSuccess ||
         (e = cudaMalloc(&P.tickets, sizeof(unsigned) * G)) != cudaSuccess ||
@@ -706,7 +717,7 @@ static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, c
     size_t off = 0;
     for (int gi = 0; gi < G; gi++) {
         P.a.grp[gi].partial = P.partial + off;
-        off += (size_t)P.a.grp[gi].nblocks * BATCH_KMAX;
+        off += (size_t)std::max(P.a.grp[gi].nblocks, P.a.grp[gi].dnblocks) * BATCH_KMAX;
     }
     P.a.sys = P.sys;
     P.a.tickets = P.tickets;
