@@ -631,10 +631,7 @@ static int fcg_run(stag_net n, int prec, bool use_net, double mass, double tol2b
             DslashArgs b1 = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
             b1.skip_if_done = 1;
             CUDA_TRY(launch_dslash(prec, EPI_NONE, b1, lat->dslash_block[prec], s));
-            DslashArgs b2 = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
-            b2.p = w.p;
-            b2.skip_if_done = 1;
-            CUDA_TRY(launch_dslash(prec, EPI_M_PAP, b2, lat->dslash_block[prec], s));
+            CUDA_TRY(enqueue_m_pap(lat, prec, w.t, w.Ap, w.p, true, s));
             CUDA_TRY(launch_fcg_update(prec, g, w.xw, w.r, n->r_old[prec], w.p, w.Ap, lat->partial, lat->sc, s));
             CUDA_TRY(precondition(n, prec, use_net, w.r, n->z[prec], gate, s));
             CUDA_TRY(launch_fcg_beta(prec, g, n->z[prec], w.r, n->r_old[prec], lat->partial, lat->sc, 0, s));
