@@ -614,15 +614,38 @@ class OracleWorkload:
         x, info = self.oracle.cg(self.dims, self.U, self.N, MASS, self.b, tol=TOL, max_iter=n_iter)
         return info["iters"], time.perf_counter() - t0, self.oracle.num_threads()
 
+    def dslash_ms(self, reps=3):
+        """Median time of one oracle D_oe on the source."""
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            self.oracle.dslash_parity(self.dims, self.U, self.N, 1, self.b)
+            ts.append(time.perf_counter() - t0)
+        return 1e3 * float(np.median(ts))
 
-def cpu_baseline(dims, rank, n_iter=150):
+
+def cpu_baseline(dims, rank, n_iter=150, n_iter_1=5):
+    """The oracle on the host cores: n_iter CG iterations with every core,
+    n_iter_1 with one thread, and the median of three Dslash applications."""
     Vh = int(np.prod(dims)) // 2
-    it, dt, cores = OracleWorkload(dims, rank).run(n_iter)
+    wl = OracleWorkload(dims, rank)
+    it, dt, cores = wl.run(n_iter)
     gbs = it * cg_bytes_per_iter_site("f64") * Vh / dt / 1e9
+    dslash_ms = wl.dslash_ms()
+    wl.oracle.set_num_threads(1)
+    try:
+        it1, dt1, _ = wl.run(n_iter_1)
+    finally:
+        wl.oracle.set_num_threads(cores)
+    gbs1 = it1 * cg_bytes_per_iter_site("f64") * Vh / dt1 / 1e9
     return {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
             "sample": f"{it} CG iterations of the FP64 oracle on the same {'x'.join(map(str, dims))} "
                       f"workload ({dt:.1f} s incl. the final true-residual check), "
-                      f"rate = iterations * bytes/iteration / time"}
+                      f"rate = iterations * bytes/iteration / time",
+            "single_thread": {"value": round(gbs1, 3), "unit": "GB/s", "cores": 1,
+                              "sample": f"{it1} CG iterations ({dt1:.1f} s incl. the true-residual check)"},
+            "dslash_ms": {"value": round(dslash_ms, 1), "cores": cores,
+                          "sample": "median of 3 oracle D_oe applications on the workload's source"}}
 
 
 def run_reference(args):
