@@ -136,6 +136,8 @@ int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk);
  *            smeared fat links, which the paper notes are not in SU(3));
  *            the full copies are kept for the batched solver.
  *            A later upload replaces all copies.
+ * Links holding a NaN, an infinity or an entry beyond the FP32 range give
+ * STAG_ERR_ARG (the lattice then has no gauge field).
  * Blocks until the copies are built. */
 int stag_gauge_upload(stag_lattice lat, const double *fat, const double *lng,
                       double c1, double c3, int ptr_kind, unsigned prec_mask);
@@ -426,6 +428,19 @@ int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, const stag_fi
  * stag_cg_solve; info->seconds is wall time, gflops and gbs are 0. */
 int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x_even, const stag_field b_even,
                      double mass, double rel_tol, int max_iter, stag_solve_info *info);
+
+/* ---- diagnostics ----------------------------------------------------------
+ * The neighbour arithmetic of the Dslash kernels, run on the host: the
+ * checkerboard index of the site reached from site `cb` of parity `parity`
+ * by `steps` (+-1 or +-3) hops along direction mu (0..3 = x, y, z, t) on a
+ * lattice `dims` (each even, >= 2), periodic in index space, and the number
+ * of times that hop wraps around the lattice (the exponent of the boundary
+ * sign).  Site order: full index i = x + Lx (y + Ly (z + Lz t)), cb = i / 2
+ * within a parity, parity = (x + y + z + t) mod 2.  Lets a test check every
+ * hop the kernels take against a brute-force table without a GPU.  The paper
+ * has no counterpart.  Bad arguments: STAG_ERR_ARG. */
+int stag_cb_neighbor(const int dims[4], int parity, long long cb, int mu, int steps,
+                     long long *out_cb, int *out_wraps);
 
 /* ---- errors -------------------------------------------------------------- */
 const char *stag_strerror(int status);

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/stag.h"
 #include "batched.cuh"
 #include "dslash.cuh"
@@ -45,6 +47,16 @@ static inline int fail(int code, const char *fmt, ...) {
                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
                         __LINE__);                                                         \
     } while (0)
+
+// NVTX range named after a C-ABI call, so that profiler timelines show the
+// library's calls (a no-op unless a profiling tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define STAG_NVTX(name) NvtxRange nvtx_range_(name)
 
 #define STAG_TRY(call)           \
     do {                         \
@@ -156,6 +168,21 @@ struct stag_field_s {
     void *data = nullptr;
     size_t bytes = 0;
 };
+
+// lattice geometry of the kernels (dims even and >= 2; stride >= V/2)
+static inline Geom geom_of(const int dims[4], long long stride) {
+    Geom g;
+    for (int k = 0; k < 4; k++)
+        g.L[k] = dims[k];
+    g.Lxh = dims[0] / 2;
+    g.Vh = (int)((long long)dims[0] * dims[1] * dims[2] * dims[3] / 2);
+    g.stride = (int)stride;
+    g.plane[0] = 0;
+    g.plane[1] = dims[0] / 2;
+    g.plane[2] = dims[0] * dims[1] / 2;
+    g.plane[3] = dims[0] * dims[1] * dims[2] / 2;
+    return g;
+}
 
 static inline size_t field_bytes(const stag_lattice lat, int prec) {
     return prec_vec_bytes(prec, (size_t)lat->geom.stride);

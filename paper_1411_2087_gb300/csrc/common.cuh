@@ -130,7 +130,7 @@ struct Geom {
 };
 
 // coordinates of checkerboard site c of parity par
-STAG_D void cb_coords(const Geom &g, int c, int par, int x[4]) {
+STAG_HD void cb_coords(const Geom &g, int c, int par, int x[4]) {
     int xh = c % g.Lxh;
     int r = c / g.Lxh;
     x[1] = r % g.L[1];
@@ -142,7 +142,7 @@ STAG_D void cb_coords(const Geom &g, int c, int par, int x[4]) {
 
 // checkerboard index of the site reached from (c, x) by s steps along mu
 // (periodic in index space; the parity flips for odd s)
-STAG_D int cb_hop(const Geom &g, int c, const int x[4], int mu, int s) {
+STAG_HD int cb_hop(const Geom &g, int c, const int x[4], int mu, int s) {
     int L = g.L[mu];
     int y = x[mu] + s;
     // |s| <= 3 and L >= 2: at most two wraps

@@ -157,6 +157,7 @@ int host_sum(const Domains &D, size_t field_off, double *out) {
 }  // namespace
 
 extern "C" int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, const stag_field in) {
+    STAG_NVTX("stag_dd_dslash");
     if (!lat || !out || !in)
         return fail(STAG_ERR_ARG, "stag_dd_dslash: NULL argument");
     if (out->lat != lat || in->lat != lat)
@@ -179,6 +180,7 @@ extern "C" int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, co
 
 extern "C" int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x, const stag_field b, double mass,
                                 double rel_tol, int max_iter, stag_solve_info *info) {
+    STAG_NVTX("stag_dd_cg_solve");
     if (info)
         memset(info, 0, sizeof *info);
     if (!lat || !x || !b)

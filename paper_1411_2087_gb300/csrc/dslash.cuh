@@ -62,7 +62,7 @@ STAG_D void reconstruct_row2(cplx<R> L[9], float inv_s) {
 }
 
 // number of times a hop of s steps from coordinate v wraps (L >= 2, |s| <= 3)
-STAG_D int hop_wraps(int v, int s, int L) {
+STAG_HD int hop_wraps(int v, int s, int L) {
     int y = v + s, w = 0;
     if (y >= L) { y -= L; w++; }
     if (y >= L) { y -= L; w++; }

@@ -48,7 +48,8 @@ cudaError_t launch_fold_links_c12(int prec, const Geom &g, const double bc[4], d
 // matrices, as float bits in *out (device)
 cudaError_t launch_su3_deviation(const double *U, long long nlinks, unsigned *out, cudaStream_t s);
 
-// largest |re| / |im| over n doubles, as float bits in *out (device)
+// largest |re| / |im| over n doubles, as float bits in *out (device); a
+// NaN, an infinity or a value beyond the FP32 range gives +infinity
 cudaError_t launch_absmax(const double *a, long long n, unsigned *out, cudaStream_t s);
 
 // three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu), canonical layout

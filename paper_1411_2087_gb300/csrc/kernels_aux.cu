@@ -3,6 +3,8 @@
 #include "dslash.cuh"
 #include "kernels.h"
 
+#include <cfloat>
+
 namespace stag {
 
 // --------------------------------------------------------------------------
@@ -442,8 +444,12 @@ cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], doubl
 __global__ void absmax_kernel(const double *__restrict__ a, long long n, unsigned *out) {
     float m = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        m = fmaxf(m, (float)fabs(a[i]));
+         i += (long long)gridDim.x * blockDim.x) {
+        float v = (float)fabs(a[i]);
+        if (!(v <= FLT_MAX))  // NaN, infinity and FP32 overflow all count as infinite
+            v = INFINITY;
+        m = fmaxf(m, v);
+    }
     for (int o = 16; o > 0; o >>= 1)
         m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0)

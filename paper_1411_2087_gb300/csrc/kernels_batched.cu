@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, 
     const int S = g.stride;
     red_t<R> dk = red_zero<red_t<R>>();
     if (c < g.Vh && act[k]) {
-        DslashArgs da;
+        DslashArgs da = {};
         da.link_scale[0] = G.link_scale[0];
         da.link_scale[1] = G.link_scale[1];
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};

@@ -262,6 +262,7 @@ static cudaError_t net_apply_raw(stag_net n, int prec, const void *in, void *out
 }
 
 extern "C" int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int fp16_weights) {
+    STAG_NVTX("stag_net_apply");
     if (!n)
         return fail(STAG_ERR_ARG, "stag_net_apply: NULL net");
     STAG_TRY(check_net_field(n, out_even, "stag_net_apply"));
@@ -346,6 +347,7 @@ static int resid_loss_grad(stag_net n, int p, cudaStream_t s) {
 // every `stride` iterations to record the pair.
 extern "C" int stag_net_collect_pairs(stag_net n, const stag_field b, double mass, double rel_tol, int stride,
                                       int max_pairs, int *collected) {
+    STAG_NVTX("stag_net_collect_pairs");
     if (collected)
         *collected = 0;
     if (!n || !b)
@@ -542,6 +544,7 @@ static int residual_warm_start(stag_net n) {
 }
 
 extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss) {
+    STAG_NVTX("stag_net_train");
     if (!n)
         return fail(STAG_ERR_ARG, "stag_net_train: NULL net");
     const int np = (int)n->pr.size();
@@ -649,6 +652,7 @@ static int fcg_run(stag_net n, int prec, bool use_net, double mass, double tol2b
 
 extern "C" int stag_cg_solve_learned(stag_net n, stag_field x, const stag_field b, double mass, double rel_tol,
                                      int max_iter, stag_solve_info *info) {
+    STAG_NVTX("stag_cg_solve_learned");
     if (info)
         memset(info, 0, sizeof *info);
     if (!n || !x || !b)

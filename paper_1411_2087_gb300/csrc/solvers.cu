@@ -243,6 +243,7 @@ int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *
 extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_field b, double mass,
                                    double rel_tol, int max_iter, int inner_prec, double delta,
                                    stag_solve_info *info) {
+    STAG_NVTX("stag_cg_solve_mixed");
     if (info)
         memset(info, 0, sizeof *info);
     if (!lat || !x || !b)
@@ -496,6 +497,7 @@ static int check_ms_args(stag_lattice lat, stag_field *xs, const double *shifts,
 extern "C" int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double *shifts, int n,
                                   const stag_field b, double mass, double rel_tol, int max_iter,
                                   stag_solve_info *infos) {
+    STAG_NVTX("stag_cg_multishift");
     STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift"));
     const int prec = b->prec;
     if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
@@ -540,6 +542,7 @@ int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, dou
 extern "C" int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,
                                         const stag_field b, double mass, double rel_tol, int max_iter,
                                         int inner_prec, double delta, stag_solve_info *infos) {
+    STAG_NVTX("stag_cg_multishift_mixed");
     STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift_mixed"));
     const int hi = b->prec;
     if (hi != STAG_F64 && hi != STAG_DF64)
@@ -921,6 +924,7 @@ static int batch_solve_raw(int n, stag_lattice *lats, void *const *x, const void
 extern "C" int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
                                      const double *masses, double rel_tol, int max_iter,
                                      stag_solve_info *infos) {
+    STAG_NVTX("stag_cg_solve_batched");
     STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched"));
     const int prec = bs[0]->prec;
     if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
@@ -947,6 +951,7 @@ extern "C" int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, 
 extern "C" int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
                                            const double *masses, double rel_tol, int max_iter, int inner_prec,
                                            double delta, stag_solve_info *infos) {
+    STAG_NVTX("stag_cg_solve_batched_mixed");
     STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched_mixed"));
     const int hi = bs[0]->prec;
     if (hi != STAG_F64 && hi != STAG_DF64)
@@ -1030,6 +1035,7 @@ extern "C" int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field
 // and precision
 // --------------------------------------------------------------------------
 extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us) {
+    STAG_NVTX("stag_lattice_autotune");
     if (!lat)
         return fail(STAG_ERR_ARG, "stag_lattice_autotune: lattice is NULL");
     if (!prec_valid(prec))

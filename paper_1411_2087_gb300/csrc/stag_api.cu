@@ -76,16 +76,7 @@ extern "C" int stag_lattice_create(stag_lattice *out, const int dims[4], const d
     }
     lat->V = V;
     lat->Vh = Vh;
-    Geom &g = lat->geom;
-    for (int k = 0; k < 4; k++)
-        g.L[k] = dims[k];
-    g.Lxh = dims[0] / 2;
-    g.Vh = (int)Vh;
-    g.stride = (int)stride;
-    g.plane[0] = 0;
-    g.plane[1] = dims[0] / 2;
-    g.plane[2] = dims[0] * dims[1] / 2;
-    g.plane[3] = dims[0] * dims[1] * dims[2] / 2;
+    lat->geom = geom_of(dims, stride);
 
     auto cleanup = [&](int code) {
         stag_lattice_destroy(lat);
@@ -240,6 +231,7 @@ static int gauge_to_device(stag_lattice lat, const double *src, int ptr_kind, do
 
 extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const double *lng, double c1,
                                  double c3, int ptr_kind, unsigned prec_mask) {
+    STAG_NVTX("stag_gauge_upload");
     if (!lat || !fat)
         return fail(STAG_ERR_ARG, "stag_gauge_upload: lattice or fat links NULL");
     if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
@@ -290,8 +282,10 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         release();
         return st;
     }
-    // drop old copies and solver graphs
+    // drop old copies and solver graphs; until the new copies exist the
+    // lattice has no gauge field
     cudaStreamSynchronize(lat->stream);
+    lat->has_gauge = false;
     for (int p = 0; p < 4; p++) {
         free_cg(lat->cg[p]);
         if (lat->links[p]) {
@@ -334,8 +328,9 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
     }
     lat->has_gauge = false;
     float inv_scale[2] = {0.f, 0.f};
-    if ((prec_mask >> STAG_F16) & 1u) {
-        // 16-bit links: one scale per field, the largest |entry| after folding
+    {
+        // largest |entry| of each field: rejects non-finite links, and is the
+        // scale of the 16-bit copy (one per field, after folding)
         cudaError_t e = lat->absmax ? cudaSuccess : cudaMalloc(&lat->absmax, 2 * sizeof(unsigned));
         const long long n = 4LL * lat->V * 18;
         if (e == cudaSuccess)
@@ -355,9 +350,16 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         for (int h = 0; h < 2; h++) {
             float m;
             memcpy(&m, &bits[h], sizeof m);
-            const double mx = (double)m * cf[h];
-            lat->link_scale[h] = mx > 0 ? (float)(mx / 32767.0) : 0.f;
-            inv_scale[h] = mx > 0 ? (float)(32767.0 / mx) : 0.f;
+            if (!std::isfinite(m)) {
+                release();
+                return fail(STAG_ERR_ARG, "stag_gauge_upload: the %s links hold NaN, infinite or out-of-range "
+                            "entries", h ? "long" : "fat");
+            }
+            if ((prec_mask >> STAG_F16) & 1u) {
+                const double mx = (double)m * cf[h];
+                lat->link_scale[h] = mx > 0 ? (float)(mx / 32767.0) : 0.f;
+                inv_scale[h] = mx > 0 ? (float)(32767.0 / mx) : 0.f;
+            }
         }
     }
     for (int p = 0; p < 4; p++) {
@@ -395,6 +397,7 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
 }
 
 extern "C" int stag_long_links_build(stag_lattice lat, const double *fat, double *lng, int ptr_kind) {
+    STAG_NVTX("stag_long_links_build");
     if (!lat || !fat || !lng)
         return fail(STAG_ERR_ARG, "stag_long_links_build: NULL argument");
     if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
@@ -506,6 +509,7 @@ static int field_io(stag_field f, const double *src, double *dst, int ptr_kind) 
 }
 
 extern "C" int stag_field_import(stag_field f, const double *src, int ptr_kind) {
+    STAG_NVTX("stag_field_import");
     if (!f || !src)
         return fail(STAG_ERR_ARG, "stag_field_import: NULL argument");
     if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
@@ -514,6 +518,7 @@ extern "C" int stag_field_import(stag_field f, const double *src, int ptr_kind) 
 }
 
 extern "C" int stag_field_export(const stag_field f, double *dst, int ptr_kind) {
+    STAG_NVTX("stag_field_export");
     if (!f || !dst)
         return fail(STAG_ERR_ARG, "stag_field_export: NULL argument");
     if (ptr_kind != STAG_PTR_HOST && ptr_kind != STAG_PTR_DEVICE)
@@ -571,16 +576,19 @@ static int dslash_impl(stag_lattice lat, stag_field out, const stag_field in, in
 }
 
 extern "C" int stag_dslash_eo(stag_lattice lat, stag_field out_even, const stag_field in_odd) {
+    STAG_NVTX("stag_dslash_eo");
     return dslash_impl(lat, out_even, in_odd, STAG_EVEN, "stag_dslash_eo");
 }
 
 extern "C" int stag_dslash_oe(stag_lattice lat, stag_field out_odd, const stag_field in_even) {
+    STAG_NVTX("stag_dslash_oe");
     return dslash_impl(lat, out_odd, in_even, STAG_ODD, "stag_dslash_oe");
 }
 
 // odd temporary of the CG workspace of one precision
 extern "C" int stag_apply_M(stag_lattice lat, stag_field out_even, const stag_field in_even,
                             double mass) {
+    STAG_NVTX("stag_apply_M");
     if (!lat || !out_even || !in_even)
         return fail(STAG_ERR_ARG, "stag_apply_M: NULL argument");
     if (out_even->parity != STAG_EVEN || in_even->parity != STAG_EVEN)
@@ -826,12 +834,14 @@ static int cg_solve_impl(stag_lattice lat, stag_field x, const stag_field b, dou
 
 extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b, double mass,
                              double rel_tol, int max_iter, stag_solve_info *info) {
+    STAG_NVTX("stag_cg_solve");
     return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, nullptr, 0);
 }
 
 extern "C" int stag_cg_solve_traced(stag_lattice lat, stag_field x, const stag_field b, double mass,
                                     double rel_tol, int max_iter, double *trace, int trace_len,
                                     stag_solve_info *info) {
+    STAG_NVTX("stag_cg_solve_traced");
     if (info)
         memset(info, 0, sizeof *info);
     if (!trace || trace_len < 0)
@@ -839,6 +849,30 @@ extern "C" int stag_cg_solve_traced(stag_lattice lat, stag_field x, const stag_f
     return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, trace, trace_len);
 }
 
+
+// --------------------------------------------------------------------------
+extern "C" int stag_cb_neighbor(const int dims[4], int parity, long long cb, int mu, int steps,
+                                long long *out_cb, int *out_wraps) {
+    if (!dims || !out_cb || !out_wraps)
+        return fail(STAG_ERR_ARG, "stag_cb_neighbor: NULL argument");
+    long long V = 1;
+    for (int k = 0; k < 4; k++) {
+        if (dims[k] < 2 || dims[k] % 2 != 0 || dims[k] > 4096)
+            return fail(STAG_ERR_ARG, "stag_cb_neighbor: dims[%d] = %d must be even, 2..4096", k, dims[k]);
+        V *= dims[k];
+    }
+    if (V / 2 > (1LL << 30))
+        return fail(STAG_ERR_ARG, "stag_cb_neighbor: volume too large");
+    if ((parity != 0 && parity != 1) || cb < 0 || cb >= V / 2 || mu < 0 || mu > 3 ||
+        (steps != 1 && steps != -1 && steps != 3 && steps != -3))
+        return fail(STAG_ERR_ARG, "stag_cb_neighbor: parity 0/1, 0 <= cb < V/2, mu 0..3, steps +-1 or +-3");
+    const Geom g = geom_of(dims, V / 2);
+    int x[4];
+    cb_coords(g, (int)cb, parity, x);
+    *out_cb = cb_hop(g, (int)cb, x, mu, steps);
+    *out_wraps = hop_wraps(x[mu], steps, g.L[mu]);
+    return STAG_OK;
+}
 
 // --------------------------------------------------------------------------
 extern "C" const char *stag_strerror(int status) {

@@ -57,7 +57,7 @@ EXPORTED = [
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
     "stag_net_set_loss",
     "stag_apply_M_noalloc",
-    "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced",
+    "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced", "stag_cb_neighbor",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -138,6 +138,8 @@ def lib():
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_traced": ([P, P, P, D, D, I, P, I, ctypes.POINTER(SolveInfo)], I),
             "stag_dd_dslash": ([P, I, P, P], I),
+            "stag_cb_neighbor": ([P, I, ctypes.c_longlong, I, I, ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(I)], I),
             "stag_dd_cg_solve": ([P, I, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
@@ -413,6 +415,16 @@ class Lattice:
                 self.close()
         except Exception:
             pass
+
+
+def cb_neighbor(dims, parity: int, cb: int, mu: int, steps: int):
+    """(neighbour cb index, wraps) as the Dslash kernels compute them (host)."""
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    j = ctypes.c_longlong()
+    w = ctypes.c_int()
+    _check(lib().stag_cb_neighbor(d, int(parity), int(cb), int(mu), int(steps), ctypes.byref(j),
+                                  ctypes.byref(w)))
+    return j.value, w.value
 
 
 def apply_M_noalloc(dims, fat, lng, mass, in_even, out_even, bc=BC_DEFAULT, c1=C1_NAIK,

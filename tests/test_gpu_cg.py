@@ -163,6 +163,31 @@ def test_cg_repeated_solves_reuse_graph():
         assert iters[0] == iters[2]  # deterministic reductions
 
 
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf, 1e39])
+def test_corrupted_gauge_field_is_rejected(prec, bad):
+    """A NaN, an infinity or an FP32-overflowing entry in either link field is
+    an argument error at upload (not a silent 16-bit clamp, not a trap), and
+    the lattice keeps no gauge field."""
+    dims = (4, 4, 4, 4)
+    U, N = fields(dims, 0.3, 5)
+    for which in ("fat", "long"):
+        Ub, Nb = U.copy(), N.copy()
+        (Ub if which == "fat" else Nb)[2, 17, 1, 2] = complex(bad, 0.0)
+        with stag.Lattice(dims) as lat:
+            with pytest.raises(stag.StagError) as e:
+                lat.upload_gauge(Ub, Nb, precisions=(prec,))
+            assert e.value.status == stag.ERR_ARG and which in str(e.value)
+            fe = lat.field(stag.EVEN, prec)
+            fo = lat.field(stag.ODD, prec)
+            with pytest.raises(stag.StagError) as e2:
+                lat.dslash(fo, fe)
+            assert e2.value.status == stag.ERR_STATE
+            # a clean upload afterwards works
+            lat.upload_gauge(U, N, precisions=(prec,))
+            lat.dslash(fo, fe)
+
+
 @pytest.mark.parametrize("prec", ["f64", "df64"])
 def test_host_launch_mode_is_identical(prec):
     """The host-driven launch mode runs the same kernels in the same order:
