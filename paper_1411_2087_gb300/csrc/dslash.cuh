@@ -89,12 +89,123 @@ STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float i
     }
 }
 
+// --------------------------------------------------------------------------
+// 16-bit storage in raw units.  A link entry is ls q (ls = the field's
+// scale), a vector component (n / 32767) q (n = the site's norm), q the
+// stored integers.  The products run on the integers (exact in float) and one
+// coefficient per hop, ls n / 32767, carries the scales; row 2 of a 12-real
+// link, conj(row0 x row1) in raw units, carries the extra factor ls / s of
+// the rebuild.  This saves the 24 scale multiplies of every hop.
+// --------------------------------------------------------------------------
+STAG_D float load_vec_raw16(const short2 *__restrict__ v, int S, int j, cplx<float> w[3]) {
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const short2 q = ld_keep(v + b * S + j);
+        w[b] = cplx<float>{(float)q.x, (float)q.y};
+    }
+    return ld_keep((const float *)(v + 3 * S) + j);
+}
+
+// the nine raw entries of one 16-bit link; for the 12-real layout row 2 is
+// conj(row0 x row1) without the 1/s factor
+template <bool COMP>
+STAG_D void load_link_raw16(const void *G, int kind, int S, int idx, cplx<float> L[9]) {
+    if constexpr (COMP) {
+        const char *kb = (const char *)G + (size_t)kind * C12<P_F16>::kind_bytes((size_t)S);
+        C12<P_F16>::load(kb, S, idx, 1.f, L);
+        reconstruct_row2(L, 1.f);
+    } else {
+        const short2 *Lp = (const short2 *)G + kind * 9 * S + idx;
+#pragma unroll
+        for (int e = 0; e < 9; e++) {
+            const short2 q = ld_stream(Lp + e * S);
+            L[e] = cplx<float>{(float)q.x, (float)q.y};
+        }
+    }
+}
+
+template <bool COMP>
+STAG_D void dslash_site_f16(const Geom &g, int par, int c, const void *__restrict__ Gout,
+                            const void *__restrict__ Gin, const short2 *__restrict__ in, const DslashArgs &a,
+                            cplx<float> acc[3]) {
+    const int S = g.stride;
+    int x[4];
+    cb_coords(g, c, par, x);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int esum = 0;
+#pragma unroll
+        for (int nu = 0; nu < mu; nu++)
+            esum += x[nu];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int s = h ? 3 : 1;
+            const int kind = 4 * h + mu;
+            const float ls = a.link_scale[h];
+            const float lsq = ls * (1.f / kQ16);
+            // forward: + L(x) psi(x + s mu)
+            {
+                const int j = cb_hop(g, c, x, mu, +s);
+                cplx<float> v[3];
+                const float cf = load_vec_raw16(in, S, j, v) * lsq;
+                float cf2 = cf;
+                if (COMP) {
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
+                    cf2 = cf * ls * (flip ? -a.inv_c[h] : a.inv_c[h]);
+                }
+                cplx<float> L[9];
+                load_link_raw16<COMP>(Gout, kind, S, c, L);
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    cplx<float> t = czero<float>();
+#pragma unroll
+                    for (int b = 0; b < 3; b++)
+                        cmac(t, L[3 * r + b], v[b]);
+                    const float k = r == 2 ? cf2 : cf;
+                    acc[r].re = fmaf(k, t.re, acc[r].re);
+                    acc[r].im = fmaf(k, t.im, acc[r].im);
+                }
+            }
+            // backward: - L(x - s mu)^+ psi(x - s mu)
+            {
+                const int j = cb_hop(g, c, x, mu, -s);
+                cplx<float> v[3];
+                const float cf = -load_vec_raw16(in, S, j, v) * lsq;
+                if (COMP) {
+                    // row 2 of L meets component 2 of psi in L^+ psi
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
+                    const float k2 = ls * (flip ? -a.inv_c[h] : a.inv_c[h]);
+                    v[2].re *= k2;
+                    v[2].im *= k2;
+                }
+                cplx<float> L[9];
+                load_link_raw16<COMP>(Gin, kind, S, j, L);
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    cplx<float> t = czero<float>();
+#pragma unroll
+                    for (int b = 0; b < 3; b++)
+                        cmac_conj(t, L[3 * b + r], v[b]);
+                    acc[r].re = fmaf(cf, t.re, acc[r].re);
+                    acc[r].im = fmaf(cf, t.im, acc[r].im);
+                }
+            }
+        }
+    }
+}
+
 // acc += D psi at checkerboard site c of parity par
 template <int P, bool COMP = false>
 STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ Gout,
                         const void *__restrict__ Gin, const typename Fmt<P>::Elem *__restrict__ in,
                         const DslashArgs &a, cplx<typename Fmt<P>::R> acc[3]) {
     using R = typename Fmt<P>::R;
+    if constexpr (P == P_F16 && COMP) {
+        // the 18-real 16-bit stencil keeps its scaled form: in raw units the
+        // compiler hoists its loads into 255 registers and it runs no faster
+        dslash_site_f16<COMP>(g, par, c, Gout, Gin, in, a, acc);
+        return;
+    }
     const int S = g.stride;
     int x[4];
     cb_coords(g, c, par, x);
@@ -169,8 +280,8 @@ template <class R> STAG_D red_t<R> re_dot3(const cplx<R> a[3], const cplx<R> b[3
     return to_red(s);
 }
 
-template <int P, int EPI, int BLOCK, bool COMP = false>
-__global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
+template <int P, int EPI, int BLOCK, bool COMP>
+STAG_D void dslash_body(const DslashArgs &a) {
     using F = Fmt<P>;
     using R = typename F::R;
     using E = typename F::Elem;
@@ -243,6 +354,20 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
             }
         }
     }
+}
+
+// One launch of the stencil.  The compressed 16-bit stencil gets its own
+// kernel with a register cap (at least 1024 resident threads per SM): left
+// free, the compiler hoists loads into more registers and the kernel runs
+// slower at the lower occupancy.  The others keep the compiler's choice.
+template <int P, int EPI, int BLOCK, bool COMP = false>
+__global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
+    dslash_body<P, EPI, BLOCK, COMP>(a);
+}
+
+template <int P, int EPI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(DslashArgs a) {
+    dslash_body<P, EPI, BLOCK, true>(a);
 }
 
 }  // namespace stag

@@ -12,14 +12,26 @@ static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
     const int grid = (n + BLOCK - 1) / BLOCK;
     if (grid == 0)
         return cudaSuccess;
-    switch (epi) {
-    case EPI_NONE: dslash_kernel<P, EPI_NONE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_M: dslash_kernel<P, EPI_M, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    case EPI_M_PART: dslash_kernel<P, EPI_M_PART, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    if constexpr (P == P_F16 && COMP) {
+        switch (epi) {
+        case EPI_NONE: dslash_kernel_capped<P, EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M: dslash_kernel_capped<P, EPI_M, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M_PAP: dslash_kernel_capped<P, EPI_M_PAP, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_RESID: dslash_kernel_capped<P, EPI_RESID, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_RESID_STORE: dslash_kernel_capped<P, EPI_RESID_STORE, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M_PART: dslash_kernel_capped<P, EPI_M_PART, BLOCK><<<grid, BLOCK, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (epi) {
+        case EPI_NONE: dslash_kernel<P, EPI_NONE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M: dslash_kernel<P, EPI_M, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M_PAP: dslash_kernel<P, EPI_M_PAP, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_RESID: dslash_kernel<P, EPI_RESID, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_RESID_STORE: dslash_kernel<P, EPI_RESID_STORE, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        case EPI_M_PART: dslash_kernel<P, EPI_M_PART, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     return cudaGetLastError();
 }
