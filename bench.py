@@ -307,14 +307,16 @@ def run_native(args):
     lat.close()
     torch.cuda.empty_cache()
 
+    # the comparison sections are single-GPU measurements: reported on the
+    # one-GPU line, skipped when several ranks run (the scaling runs)
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and world == 1:
         mixed = mixed_comparison(local, rank, args.cg_launch)
     batched = None
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         batched = batched_comparison(local, rank)
     learned = None
-    if not args.no_learned:
+    if not args.no_learned and world == 1:
         learned = learned_comparison(local, rank, args.learned_pairs, args.learned_epochs)
 
     cpu = None
