@@ -152,7 +152,10 @@ int stag_long_links_build(stag_lattice lat, const double *fat, double *lng, int 
 /* ---- colour fields (one parity, internal layout, owned by the library) -- */
 int stag_field_create(stag_lattice lat, int parity, int prec, stag_field *out);
 int stag_field_destroy(stag_field f);
-/* Import/export canonical complex128 [Vh][3]; blocks until complete. */
+/* Import/export canonical complex128 [Vh][3] (host or device memory per
+ * ptr_kind; the caller owns src/dst); blocks until complete.  A device source
+ * is read after all work already queued on the device has finished, so a
+ * buffer just written on another stream may be passed directly. */
 int stag_field_import(stag_field f, const double *src, int ptr_kind);
 int stag_field_export(const stag_field f, double *dst, int ptr_kind);
 /* Set a field to zero (asynchronous). */

@@ -130,7 +130,7 @@ struct stag_lattice_s {
     CgScalars *sc_host = nullptr;  // pinned mirror
     CgWork cg[4];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double *staging = nullptr;
+    double *staging = nullptr;             // canonical [Vh][3] complex128 for host import/export
     float link_scale[2] = {0.f, 0.f};      // 16-bit links: field max / 32767 (one-link, three-link)
     float *xs = nullptr;                   // F32 correction x_sloppy of the mixed solver
     unsigned *absmax = nullptr;            // scratch for the 16-bit link scales
@@ -158,7 +158,7 @@ struct stag_lattice_s {
     int dslash_block[4] = {0, 0, 0, 0};         // block size of the Dslash kernels (0 = default)
     int mdslash_block[4] = {0, 0, 0, 0};        // block size of the M Dslash with <p, Mp> partials (0 = as above)
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
-    int cg_chunk = 32;                     // iterations between status polls (host mode)  // canonical [Vh][3] complex128 for host import/export
+    int cg_chunk = 32;                     // iterations between status polls (host mode)
 };
 
 struct stag_field_s {

@@ -487,6 +487,10 @@ static int field_io(stag_field f, const double *src, double *dst, int ptr_kind) 
     cudaError_t e = cudaSuccess;
     if (ptr_kind == STAG_PTR_DEVICE) {
         canon = src ? (double *)src : dst;
+        // a device source may still be written by work on another stream
+        // (the caller's): let all of it finish before the lattice stream reads
+        if (src)
+            e = cudaDeviceSynchronize();
     } else {
         if (!lat->staging)
             e = cudaMalloc(&lat->staging, bytes);
