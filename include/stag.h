@@ -163,6 +163,18 @@ int stag_field_zero(stag_field f);
 /* Device address and size in bytes of the field's internal storage (for
  * zero-copy views; layout is internal). */
 int stag_field_storage(const stag_field f, void **dev_ptr, unsigned long long *bytes);
+/* Bytes of one field of precision `prec` on this lattice (the size that
+ * stag_field_wrap needs). */
+int stag_field_bytes(stag_lattice lat, int prec, unsigned long long *bytes);
+/* A field that views caller-owned device memory (e.g. a torch tensor) in the
+ * library's internal layout, for zero-copy use: `dev_ptr` must be device (or
+ * managed) memory of the lattice's device, 16-byte aligned, with at least
+ * stag_field_bytes bytes; its contents are used as they are.  The caller
+ * keeps ownership: stag_field_destroy releases the view, not the memory, and
+ * the memory must outlive the view.  Bad pointer, size or alignment:
+ * STAG_ERR_ARG. */
+int stag_field_wrap(stag_lattice lat, int parity, int prec, void *dev_ptr, unsigned long long bytes,
+                    stag_field *out);
 
 /* ---- Dslash --------------------------------------------------------------
  * out = D_eo in  (out even, in odd)    stag_dslash_eo

@@ -167,6 +167,7 @@ struct stag_field_s {
     int prec = 0;
     void *data = nullptr;
     size_t bytes = 0;
+    bool owned = true;   // false: a view of caller memory (stag_field_wrap)
 };
 
 // lattice geometry of the kernels (dims even and >= 2; stride >= V/2)

@@ -4,6 +4,8 @@
 // include/stag.h.
 #include "api_internal.h"
 
+#include <cstdint>
+
 // --------------------------------------------------------------------------
 // errors
 // --------------------------------------------------------------------------
@@ -468,12 +470,60 @@ extern "C" int stag_field_create(stag_lattice lat, int parity, int prec, stag_fi
     return STAG_OK;
 }
 
+extern "C" int stag_field_bytes(stag_lattice lat, int prec, unsigned long long *bytes) {
+    if (!lat || !bytes)
+        return fail(STAG_ERR_ARG, "stag_field_bytes: NULL argument");
+    if (!prec_valid(prec))
+        return fail(STAG_ERR_ARG, "stag_field_bytes: bad precision %d", prec);
+    *bytes = field_bytes(lat, prec);
+    return STAG_OK;
+}
+
+extern "C" int stag_field_wrap(stag_lattice lat, int parity, int prec, void *dev_ptr, unsigned long long bytes,
+                               stag_field *out) {
+    if (!out)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: out is NULL");
+    *out = nullptr;
+    if (!lat || !dev_ptr)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: NULL argument");
+    if (parity != STAG_EVEN && parity != STAG_ODD)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: bad parity %d", parity);
+    if (!prec_valid(prec))
+        return fail(STAG_ERR_ARG, "stag_field_wrap: bad precision %d", prec);
+    const size_t need = field_bytes(lat, prec);
+    if (bytes < need)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: %llu bytes given, %zu needed", bytes, need);
+    if ((uintptr_t)dev_ptr % 16 != 0)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: the buffer must be 16-byte aligned");
+    DEVICE_SCOPE(lat->device);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, dev_ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STAG_ERR_ARG, "stag_field_wrap: not a CUDA pointer");
+    }
+    if ((attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) || attr.device != lat->device)
+        return fail(STAG_ERR_ARG, "stag_field_wrap: the buffer is not device memory of device %d", lat->device);
+    stag_field f = new (std::nothrow) stag_field_s();
+    if (!f)
+        return fail(STAG_ERR_NOMEM, "stag_field_wrap: host allocation failed");
+    f->lat = lat;
+    f->parity = parity;
+    f->prec = prec;
+    f->bytes = need;
+    f->data = dev_ptr;
+    f->owned = false;
+    lat->live_fields++;
+    *out = f;
+    return STAG_OK;
+}
+
 extern "C" int stag_field_destroy(stag_field f) {
     if (!f)
         return STAG_OK;
     DEVICE_SCOPE(f->lat->device);
     cudaStreamSynchronize(f->lat->stream);
-    cudaFree(f->data);
+    if (f->owned)
+        cudaFree(f->data);
     f->lat->live_fields--;
     delete f;
     return STAG_OK;

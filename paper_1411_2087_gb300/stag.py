@@ -58,6 +58,7 @@ EXPORTED = [
     "stag_net_set_loss",
     "stag_apply_M_noalloc",
     "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced", "stag_cb_neighbor",
+    "stag_field_bytes", "stag_field_wrap",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -138,6 +139,8 @@ def lib():
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_traced": ([P, P, P, D, D, I, P, I, ctypes.POINTER(SolveInfo)], I),
             "stag_dd_dslash": ([P, I, P, P], I),
+            "stag_field_bytes": ([P, I, ctypes.POINTER(ctypes.c_ulonglong)], I),
+            "stag_field_wrap": ([P, I, I, P, ctypes.c_ulonglong, PP], I),
             "stag_cb_neighbor": ([P, I, ctypes.c_longlong, I, I, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(I)], I),
             "stag_dd_cg_solve": ([P, I, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
@@ -199,12 +202,22 @@ def _as_buffer(a, shape, writable=False):
 class Field:
     """One-parity colour field in the library's internal layout."""
 
-    def __init__(self, lattice: "Lattice", parity: int, prec="df64"):
+    def __init__(self, lattice: "Lattice", parity: int, prec="df64", wrap=None):
+        """wrap: a contiguous CUDA tensor to view (stag_field_wrap) instead
+        of library-owned storage; the tensor must outlive the field."""
         self.lattice = lattice
         self.parity = int(parity)
         self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         h = ctypes.c_void_p()
-        _check(lib().stag_field_create(lattice.handle, self.parity, self.prec, ctypes.byref(h)))
+        if wrap is None:
+            _check(lib().stag_field_create(lattice.handle, self.parity, self.prec, ctypes.byref(h)))
+        else:
+            if not getattr(wrap, "is_cuda", False) or not wrap.is_contiguous():
+                raise ValueError("wrap needs a contiguous CUDA tensor")
+            nbytes = wrap.numel() * wrap.element_size()
+            _check(lib().stag_field_wrap(lattice.handle, self.parity, self.prec, ctypes.c_void_p(wrap.data_ptr()),
+                                         nbytes, ctypes.byref(h)))
+        self._wrapped = wrap
         self.handle = h
         lattice._fields.add(self)
 
@@ -301,6 +314,17 @@ class Lattice:
         if data is not None:
             f.import_(data)
         return f
+
+    def field_bytes(self, prec="df64") -> int:
+        n = ctypes.c_ulonglong()
+        _check(lib().stag_field_bytes(self.handle, PREC[prec] if isinstance(prec, str) else int(prec),
+                                      ctypes.byref(n)))
+        return n.value
+
+    def wrap_field(self, tensor, parity: int, prec="df64") -> Field:
+        """A field viewing `tensor` (CUDA, contiguous, >= field_bytes(prec)
+        bytes, internal layout): zero-copy with torch."""
+        return Field(self, parity, prec, wrap=tensor)
 
     # operators -------------------------------------------------------------
     def dslash(self, out: Field, inp: Field):

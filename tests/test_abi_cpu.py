@@ -74,6 +74,11 @@ def test_null_handles_rejected(L):
     assert L.stag_cg_solve(None, None, None, 0.1, 1e-10, 10, None) == stag.ERR_ARG
     assert L.stag_cg_solve_traced(None, None, None, 0.1, 1e-10, 10, None, 5, None) == stag.ERR_ARG
     assert L.stag_dd_dslash(None, 2, None, None) == stag.ERR_ARG
+    n = ctypes.c_ulonglong()
+    assert L.stag_field_bytes(None, 0, ctypes.byref(n)) == stag.ERR_ARG
+    hw = ctypes.c_void_p()
+    assert L.stag_field_wrap(None, 0, 0, None, 0, ctypes.byref(hw)) == stag.ERR_ARG
+    assert L.stag_field_wrap(None, 0, 0, None, 0, None) == stag.ERR_ARG
     assert L.stag_dd_cg_solve(None, 2, None, None, 0.1, 1e-10, 10, None) == stag.ERR_ARG
     assert L.stag_field_import(None, None, 0) == stag.ERR_ARG
     assert L.stag_field_export(None, None, 0) == stag.ERR_ARG
