@@ -59,7 +59,8 @@ struct CgScalars {
     // mixed precision in a graph: condition of the reliable-update branch
     cudaGraphConditionalHandle rel_cond;
     int has_rel_cond;
-    int pad3;
+    // multi-shift CG: the iteration whose solution updates have been applied
+    int ms_xdone;
 };
 
 // multi-shift CG

@@ -67,6 +67,7 @@ ms_init_kernel(Geom g, MsArgs a, double *partial, CgScalars *sc, ShiftState *st)
         sc->beta = make_dpair(0.0);
         sc->alpha_prev = 1.0;
         sc->beta_prev = 0.0;
+        sc->ms_xdone = 0;
         const bool done = total <= sc->rr_stop;
         for (int s = 0; s < a.n; s++) {
             st[s].zeta_prev = 1.0;
@@ -104,7 +105,8 @@ STAG_D void ms_shift_scalars(const MsArgs &a, const CgScalars *sc, const ShiftSt
     }
 }
 
-// r -= alpha Ap, |r|^2; x_s += alpha^s p_s for the active shifts
+// r -= alpha Ap, |r|^2; the shift scalars of this iteration (the solution
+// updates x_s += alpha^s p_s run in ms_p_kernel, which reads p_s anyway)
 template <int P>
 __global__ void __launch_bounds__(MSB)
 ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *sc, ShiftState *st) {
@@ -114,6 +116,11 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
     __shared__ double smem[32];
     __shared__ double zeta_next[MS_MAX], alpha_s[MS_MAX];
     __shared__ int active[MS_MAX];
+    // the previous iteration's solution updates are done (ms_p_kernel has
+    // finished); written before this block's ticket, so before the last
+    // block below advances the iteration count
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        sc->ms_xdone = sc->iter;
     const bool run = sc->status == CG_RUNNING;
     if (run)
         ms_shift_scalars(a, sc, st, zeta_next, alpha_s);
@@ -136,22 +143,6 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
         }
         store_vec<P>((E *)a.r, g.stride, c, rv);
         dot = re_dot3<R>(rv, rv);
-        for (int s = 0; s < a.n; s++) {
-            if (!active[s])
-                continue;
-            const R as = scalar_as<R>(make_dpair(alpha_s[s]));
-            cplx<R> xv[3], pv[3];
-            load_vec<P>((const E *)a.x[s], g.stride, c, xv);
-            load_vec<P>((const E *)a.p[s], g.stride, c, pv);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                mac(xv[k].re, as, pv[k].re);
-                mac(xv[k].im, as, pv[k].im);
-                xv[k].re = rnorm<R>(xv[k].re);
-                xv[k].im = rnorm<R>(xv[k].im);
-            }
-            store_vec<P>((E *)a.x[s], g.stride, c, xv);
-        }
     }
     double total;
     if (grid_sum<MSB>(dot, partial, &sc->ticket, smem, total) && threadIdx.x == 0) {
@@ -165,13 +156,15 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
                     continue;
                 const double zn = zeta_next[s], z = st[s].zeta;
                 const double ratio = zn / z;
+                st[s].alpha_s = make_dpair(alpha_s[s]);
                 st[s].beta_s = make_dpair(beta * ratio * ratio);
                 st[s].zeta_next = make_dpair(zn);
                 st[s].zeta_prev = z;
                 st[s].zeta = zn;
                 st[s].iters = sc->iter;
                 // the shifted residual zeta r meets the tolerance: freeze
-                // after this iteration's x update (p_s is not needed again)
+                // after this iteration's x update (iters == iter marks it
+                // for ms_p_kernel; p_s is not needed again)
                 if (zn * zn * total <= sc->rr_stop)
                     st[s].active = 0;
                 else
@@ -191,27 +184,53 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
     }
 }
 
-// p_s = zeta_{k+1} r + beta^s p_s for the active shifts
+// x_s += alpha^s p_s for the shifts active in this iteration, then
+// p_s = zeta_{k+1} r + beta^s p_s for those still active
 template <int P>
 __global__ void __launch_bounds__(MSB)
 ms_p_kernel(Geom g, MsArgs a, const CgScalars *sc, const ShiftState *st) {
     using F = Fmt<P>;
     using R = typename F::R;
     using E = typename F::Elem;
-    if (sc->status != CG_RUNNING)
+    // this iteration's solution updates are due unless already applied (a
+    // host-driven launch after the solve ended finds them done)
+    const int it = sc->iter;
+    const bool xdue = sc->ms_xdone != it;
+    const bool running = sc->status == CG_RUNNING;
+    if (!xdue && !running)
         return;
     const int c = blockIdx.x * MSB + threadIdx.x;
     if (c >= g.Vh)
         return;
     cplx<R> rv[3];
-    load_vec<P>((const E *)a.r, g.stride, c, rv);
+    if (running)
+        load_vec<P>((const E *)a.r, g.stride, c, rv);
     for (int s = 0; s < a.n; s++) {
-        if (!st[s].active)
+        const bool xs = xdue && st[s].iters == it;   // was active in this iteration
+        const bool ps = running && st[s].active;     // still active
+        if (!xs && !ps)
+            continue;
+        cplx<R> pv[3];
+        load_vec<P>((const E *)a.p[s], g.stride, c, pv);
+        if (xs) {
+            // x_s += alpha^s p_s with the direction of this iteration
+            const R as = scalar_as<R>(st[s].alpha_s);
+            cplx<R> xv[3];
+            load_vec<P>((const E *)a.x[s], g.stride, c, xv);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                mac(xv[k].re, as, pv[k].re);
+                mac(xv[k].im, as, pv[k].im);
+                xv[k].re = rnorm<R>(xv[k].re);
+                xv[k].im = rnorm<R>(xv[k].im);
+            }
+            store_vec<P>((E *)a.x[s], g.stride, c, xv);
+        }
+        if (!ps)
             continue;
         const R z = scalar_as<R>(st[s].zeta_next);
         const R bs = scalar_as<R>(st[s].beta_s);
-        cplx<R> pv[3], o[3];
-        load_vec<P>((const E *)a.p[s], g.stride, c, pv);
+        cplx<R> o[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             o[k].re = rzero<R>();
