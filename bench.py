@@ -123,9 +123,22 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, device_index: int):
-        self.dev = device_index
+        self.dev = self.smi_id(device_index)
         self.proc = None
         self.tmp = None
+
+    @staticmethod
+    def smi_id(device_index: int) -> str:
+        """The GPU's UUID for nvidia-smi (the CUDA index differs from
+        nvidia-smi's when CUDA_VISIBLE_DEVICES remaps devices)."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+            if u:
+                return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            pass
+        return str(device_index)
 
     def __enter__(self):
         self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -717,6 +730,10 @@ def run_kernels_only(args):
 
 def main():
     args = parse()
+    world = dist_env()[1]
+    if args.gpus != world:
+        sys.exit(f"bench.py: --gpus {args.gpus} needs that many ranks (torch.distributed.run "
+                 f"--nproc-per-node {args.gpus}); this launch has WORLD_SIZE={world}")
     if args.kernels_only:
         print(json.dumps(run_kernels_only(args)), flush=True)
         return
