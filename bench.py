@@ -149,6 +149,16 @@ class ClockSampler:
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # nvidia-smi's start-up (process, NVML) must not overlap the timed
+        # region: wait for its first sample (at most 3 s)
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 3.0:
+            if self.proc.poll() is not None:
+                break
+            self.tmp.flush()
+            if os.path.getsize(self.tmp.name) > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
