@@ -36,16 +36,23 @@ STAG_D int net_hop(const NetGeom &g, int i, const int x[4], int mu, int s) {
     return i + d * g.step[mu];
 }
 
-STAG_D float2 cmulf(float2 w, float2 h) {
-    return make_float2(w.x * h.x - w.y * h.y, w.x * h.y + w.y * h.x);
+// acc += w h (complex, four FMAs)
+STAG_D void cmacf(float2 &acc, float2 w, float2 h) {
+    acc.x = fmaf(w.x, h.x, acc.x);
+    acc.x = fmaf(-w.y, h.y, acc.x);
+    acc.y = fmaf(w.x, h.y, acc.y);
+    acc.y = fmaf(w.y, h.x, acc.y);
 }
 
-// h = U v (fwd) or U^+ v, U at Lp[e * V]
-STAG_D void transport(const float2 *__restrict__ Lp, int V, bool adj, const float2 v[3], float2 h[3]) {
-    float2 U[9];
+// the link of one hop, U at Lp[e * V]
+STAG_D void load_link9(const float2 *__restrict__ Lp, int V, float2 U[9]) {
 #pragma unroll
     for (int e = 0; e < 9; e++)
         U[e] = __ldg(Lp + (size_t)e * V);
+}
+
+// h = U v (fwd) or U^+ v
+STAG_D void apply_link(const float2 U[9], bool adj, const float2 v[3], float2 h[3]) {
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         float re = 0.f, im = 0.f;
@@ -117,27 +124,70 @@ covconv_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__restric
         const int mu = (d - 1) >> 1;
         const bool bwd = d > 0 && ((d - 1) & 1);
         const int j = d == 0 ? i : net_hop(g, i, x, mu, bwd ? -1 : 1);
+        // the hop's link, loaded once for all channels
+        float2 U[9];
+        if (d > 0)
+            load_link9(NL + (size_t)mu * 9 * V + (bwd ? j : i), V, U);
+        if constexpr (COUT < CIN) {
+            // transports commute with the colour-blind weights: mix the
+            // input channels at the neighbour, then move COUT vectors
+            float2 m[COUT][3];
 #pragma unroll
-        for (int c = 0; c < CIN; c++) {
-            float2 v[3], h[3];
-#pragma unroll
-            for (int a = 0; a < 3; a++)
-                v[a] = __ldg(in + ((size_t)c * 3 + a) * V + j);
-            if (d == 0) {
+            for (int o = 0; o < COUT; o++)
 #pragma unroll
                 for (int a = 0; a < 3; a++)
-                    h[a] = v[a];
-            } else {
-                transport(NL + (size_t)mu * 9 * V + (bwd ? j : i), V, bwd, v, h);
+                    m[o][a] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < CIN; c++) {
+                float2 v[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    v[a] = __ldg(in + ((size_t)c * 3 + a) * V + j);
+#pragma unroll
+                for (int o = 0; o < COUT; o++) {
+                    const float2 w = sw[(d * COUT + o) * CIN + c];
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+                        cmacf(m[o][a], w, v[a]);
+                }
             }
 #pragma unroll
             for (int o = 0; o < COUT; o++) {
-                const float2 w = sw[(d * COUT + o) * CIN + c];
+                float2 h[3];
+                if (d == 0) {
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+                        h[a] = m[o][a];
+                } else {
+                    apply_link(U, bwd, m[o], h);
+                }
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
-                    const float2 t = cmulf(w, h[a]);
-                    acc[o][a].x += t.x;
-                    acc[o][a].y += t.y;
+                    acc[o][a].x += h[a].x;
+                    acc[o][a].y += h[a].y;
+                }
+            }
+        } else {
+            // move each input channel, then mix into the outputs
+#pragma unroll
+            for (int c = 0; c < CIN; c++) {
+                float2 v[3], h[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+                    v[a] = __ldg(in + ((size_t)c * 3 + a) * V + j);
+                if (d == 0) {
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+                        h[a] = v[a];
+                } else {
+                    apply_link(U, bwd, v, h);
+                }
+#pragma unroll
+                for (int o = 0; o < COUT; o++) {
+                    const float2 w = sw[(d * COUT + o) * CIN + c];
+#pragma unroll
+                    for (int a = 0; a < 3; a++)
+                        cmacf(acc[o][a], w, h[a]);
                 }
             }
         }
@@ -177,6 +227,9 @@ covconv_wgrad_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__r
 #pragma unroll
             for (int a = 0; a < 3; a++)
                 gv[o][a] = o0 + o < COUT ? __ldg(gout + ((size_t)(o0 + o) * 3 + a) * V + i) : make_float2(0.f, 0.f);
+        float2 U[9];
+        if (d > 0)
+            load_link9(NL + (size_t)mu * 9 * V + (bwd ? j : i), V, U);
 #pragma unroll
         for (int c = 0; c < CIN; c++) {
             float2 v[3], h[3];
@@ -188,7 +241,7 @@ covconv_wgrad_kernel(NetGeom g, const float2 *__restrict__ NL, const float2 *__r
                 for (int a = 0; a < 3; a++)
                     h[a] = v[a];
             } else {
-                transport(NL + (size_t)mu * 9 * V + (bwd ? j : i), V, bwd, v, h);
+                apply_link(U, bwd, v, h);
             }
 #pragma unroll
             for (int o = 0; o < OB; o++)
