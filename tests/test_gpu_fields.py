@@ -82,3 +82,56 @@ def test_wrap_rejects_bad_buffers():
         st = stag.lib().stag_field_wrap(lat.handle, 0, stag.PREC["df64"],
                                         host.ctypes.data_as(stag.ctypes.c_void_p), nb, stag.ctypes.byref(h))
         assert st == stag.ERR_ARG
+
+
+def test_lattice_on_caller_stream_is_identical():
+    """A lattice bound to the caller's CUDA stream (a torch stream) runs the
+    same kernels, graphs included, as one on the library's own stream."""
+    dims, mass = (6, 4, 6, 10), 0.05
+    Vh = int(np.prod(dims)) // 2
+    U = synth.su3_field(dims, 0.3, 95).numpy()
+    N = oracle.long_links(dims, U)
+    b = synth.gaussian_colour_field(Vh, 96).numpy()
+    user = torch.cuda.Stream()
+    results = []
+    for stream in (None, user.cuda_stream):
+        with stag.Lattice(dims, stream=stream) as lat:
+            lat.upload_gauge(U, N, precisions=("df64", "f16"))
+            fb = lat.field(stag.EVEN, "df64", b)
+            fo = lat.field(stag.ODD, "df64")
+            lat.dslash(fo, fb)
+            fx = lat.field(stag.EVEN, "df64")
+            i1 = lat.cg(fx, fb, mass, 1e-10, 5000)
+            fy = lat.field(stag.EVEN, "df64")
+            i2 = lat.cg_mixed(fy, fb, mass, 1e-10, 5000, inner="f16")
+            results.append((fo.export(), fx.export(), fy.export(), i1["iters"], i2["iters"]))
+    a, c = results
+    assert all(np.array_equal(u, v) for u, v in zip(a[:3], c[:3])) and a[3:] == c[3:]
+    res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, c[1])) / np.linalg.norm(b)
+    assert res <= 1.05e-10
+
+
+def test_two_lattices_interleaved():
+    """Two lattices of different sizes, used alternately, keep separate
+    graphs, scalars and workspaces."""
+    specs = [((4, 4, 4, 8), 0.1, 97), ((6, 4, 6, 10), 0.05, 98)]
+    lats, data = [], []
+    for dims, mass, seed in specs:
+        Vh = int(np.prod(dims)) // 2
+        U = synth.su3_field(dims, 0.3, seed).numpy()
+        N = oracle.long_links(dims, U)
+        b = synth.gaussian_colour_field(Vh, seed + 1).numpy()
+        lat = stag.Lattice(dims)
+        lat.upload_gauge(U, N, precisions=("df64",))
+        lats.append(lat)
+        data.append((dims, mass, U, N, b, lat.field(stag.EVEN, "df64", b), lat.field(stag.EVEN, "df64")))
+    try:
+        for _ in range(2):
+            for lat, (dims, mass, U, N, b, fb, fx) in zip(lats, data):
+                info = lat.cg(fx, fb, mass, 1e-10, 5000)
+                assert info["return"] == stag.OK
+                res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, fx.export())) / np.linalg.norm(b)
+                assert res <= 1.05e-10
+    finally:
+        for lat in lats:
+            lat.close()
