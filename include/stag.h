@@ -297,12 +297,15 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
                                 double delta, stag_solve_info *infos);
 
 /* Autotuner: time the candidate block sizes (128, 256 threads) of the Dslash
- * kernel and of the batched multi-right-hand-side Dslash in precision `prec`
+ * kernel, of the solvers' M Dslash (m^2 p - D t with one <p, Mp> partial per
+ * block) and of the batched multi-right-hand-side Dslash in precision `prec`
  * on this lattice (10 launches each after 2 warm-ups, CUDA events on the
- * lattice stream) and keep the fastest for every later call on this lattice.
- * dslash_us[2] and batch_us[2] (may be NULL) receive the measured
- * microseconds per launch for 128 and 256.  Needs a gauge copy of `prec`;
- * overwrites the lattice's internal work vectors. */
+ * lattice stream) and keep the fastest of each for every later call on this
+ * lattice.  dslash_us[2] and batch_us[2] (may be NULL) receive the measured
+ * microseconds per launch for 128 and 256 of the Dslash and the batched
+ * Dslash (the batched entries are 0 for STAG_F16, which has no batched
+ * kernels).  Needs a gauge copy of `prec`; overwrites the lattice's internal
+ * work vectors. */
 int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us);
 
 /* ---- learned preconditioner ------------------------------------------------
