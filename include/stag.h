@@ -273,7 +273,9 @@ int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shi
  * one CUDA graph launch.  Systems on the same lattice (which must be
  * consecutive in the arrays) share every link load: the multi-right-hand-side
  * Dslash streams each link matrix once per site and applies it to up to 8
- * (FP32) or 4 (F64/DF64) vectors.  Each system has its own mass, scalars and
+ * (FP32: one thread per site) or 4 (F64/DF64: one thread per site and
+ * system, the threads of a site loading the link in one coalesced request)
+ * vectors.  Each system has its own mass, scalars and
  * stopping test; the loop ends when none is running.  All fields have one
  * precision (F64, DF64 or F32) with gauge copies of it on every lattice.
  * Work runs on lats[0]'s stream (the others' streams are synchronized
