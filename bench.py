@@ -622,7 +622,11 @@ def mixed_comparison(local, rank, cg_launch):
         def run_all(tag, which):
             for name, fn in which:
                 fn()
+                # an NVTX range per timed solve, e.g. "mixed_f16_c12", so that a
+                # profiler can select one solve's kernels
+                torch.cuda.nvtx.range_push(name + tag)
                 info = fn()
+                torch.cuda.nvtx.range_pop()
                 lat.apply_M(fr, fx, MIXED_MASS)
                 r = fr.export() - b.numpy()
                 res = float(np.linalg.norm(r) / np.linalg.norm(b.numpy()))
