@@ -85,3 +85,50 @@ def test_dslash_48x48x48x96_sampled():
     want = oracle.dslash_sites(dims, Uh, Noracle, odd, psi)
     err = np.abs(got[odd // 2] - want).max() / np.abs(want).max()
     assert err <= 1e-12, err
+
+
+def test_mixed_f16_c12_48x48x48x96_oracle_residual():
+    """The mixed-precision bench configuration (16-bit inner iterations on
+    12-real links, double-float reliable updates, 48^3x96, m = 0.01): the
+    returned solution's true residual recomputed by the oracle."""
+    dims, mass = (48, 48, 48, 96), 0.01
+    Vh = int(np.prod(dims)) // 2
+    U = gen(dims, 0.35, 1002)
+    b = synth.gaussian_colour_field(Vh, 1102).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"), compress12=True)
+        Uh = U.cpu().numpy()
+        del U
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        info = lat.cg_mixed(fx, fb, mass, 1e-10, 20000, inner="f16")
+        x = fx.export()
+    assert info["return"] == stag.OK, info
+    N = oracle.long_links(dims, Uh)
+    r = np.linalg.norm(b - oracle.apply_M(dims, Uh, N, mass, x)) / np.linalg.norm(b)
+    assert r <= 1.05e-10, r
+    assert abs(info["true_rel_resid"] - r) <= 1e-2 * r
+
+
+def test_multishift_24x24x24x48_oracle_residuals():
+    """The multishift bench configuration (12 shifts geomspace(1e-4, 0.5) on
+    24^3x48, m = 0.02): every shifted solution's true residual recomputed by
+    the oracle."""
+    dims, mass = (24, 24, 24, 48), 0.02
+    Vh = int(np.prod(dims)) // 2
+    shifts = list(np.geomspace(1e-4, 0.5, 12))
+    U = gen(dims, 0.3, 1004)
+    b = synth.gaussian_colour_field(Vh, 3000).numpy()
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64",))
+        Uh = U.cpu().numpy()
+        fb = lat.field(stag.EVEN, "df64", b)
+        xs = [lat.field(stag.EVEN, "df64") for _ in shifts]
+        st, infos = lat.cg_multishift(xs, fb, shifts, mass, 1e-10, 20000)
+        sols = [x.export() for x in xs]
+    assert st == stag.OK, infos
+    N = oracle.long_links(dims, Uh)
+    nb = np.linalg.norm(b)
+    for sh, x in zip(shifts, sols):
+        r = np.linalg.norm(b - oracle.apply_M(dims, Uh, N, mass, x) - sh * x) / nb
+        assert r <= 1.05e-10, (sh, r)
