@@ -132,3 +132,37 @@ def test_multishift_24x24x24x48_oracle_residuals():
     for sh, x in zip(shifts, sols):
         r = np.linalg.norm(b - oracle.apply_M(dims, Uh, N, mass, x) - sh * x) / nb
         assert r <= 1.05e-10, (sh, r)
+
+
+def test_batched_bench_configuration_oracle_residuals():
+    """The batched bench configuration (16 right-hand sides: 6 on 16^4, 5 on
+    24^3x48, 5 on 32^3x64, m = 0.02, double-float, one graph launch): every
+    solution's true residual recomputed by the oracle."""
+    specs = [((16, 16, 16, 16), 6, 1003), ((24, 24, 24, 48), 5, 1004), ((32, 32, 32, 64), 5, 1005)]
+    mass = 0.02
+    lats, systems, host = [], [], []
+    try:
+        for dims, nrhs, seed in specs:
+            U = gen(dims, 0.3, seed)
+            lat = stag.Lattice(dims)
+            lat.upload_gauge(U, None, precisions=("df64",))
+            lats.append(lat)
+            Uh = U.cpu().numpy()
+            del U
+            Vh = int(np.prod(dims)) // 2
+            for k in range(nrhs):
+                b = synth.gaussian_colour_field(Vh, 3000 + 17 * seed + k).numpy()
+                systems.append((lat, lat.field(stag.EVEN, "df64"), lat.field(stag.EVEN, "df64", b), mass))
+                host.append((dims, Uh, b))
+        st, infos = stag.cg_batched(systems, 1e-10, 20000)
+        assert st == stag.OK, infos
+        sols = [s[1].export() for s in systems]
+    finally:
+        for lat in lats:
+            lat.close()
+    longs = {}
+    for (dims, Uh, b), x in zip(host, sols):
+        if dims not in longs:
+            longs[dims] = oracle.long_links(dims, Uh)
+        r = np.linalg.norm(b - oracle.apply_M(dims, Uh, longs[dims], mass, x)) / np.linalg.norm(b)
+        assert r <= 1.05e-10, (dims, r)
