@@ -28,7 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
-import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -116,7 +116,8 @@ def ncu_traffic(prec: str, dims):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region
+    (read through a pipe by a background thread)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -125,7 +126,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = self.smi_id(device_index)
         self.proc = None
-        self.tmp = None
+        self.reader = None
+        self.lines = []
+        self.first = threading.Event()
 
     @staticmethod
     def smi_id(device_index: int) -> str:
@@ -140,25 +143,26 @@ class ClockSampler:
             pass
         return str(device_index)
 
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line)
+            self.first.set()
+        self.first.set()
+
     def __enter__(self):
-        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.tmp, stderr=subprocess.DEVNULL)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
-        # nvidia-smi's start-up (process, NVML) must not overlap the timed
-        # region: wait for its first sample (at most 3 s)
-        t0 = time.perf_counter()
-        while self.proc is not None and time.perf_counter() - t0 < 3.0:
-            if self.proc.poll() is not None:
-                break
-            self.tmp.flush()
-            if os.path.getsize(self.tmp.name) > 0:
-                break
-            time.sleep(0.02)
+        if self.proc is not None:
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            # nvidia-smi's start-up (process, NVML) must not overlap the timed
+            # region: wait for its first sample (at most 3 s)
+            self.first.wait(timeout=3.0)
         return self
 
     def __exit__(self, *exc):
@@ -168,18 +172,15 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+            if self.reader is not None:
+                self.reader.join(timeout=5)
 
     def summary(self):
-        if self.tmp is None:
-            return None
-        self.tmp.flush()
         rows = []
-        with open(self.tmp.name) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.tmp.name)
+        for line in list(self.lines):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
