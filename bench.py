@@ -418,13 +418,20 @@ def learned_comparison(local, rank, n_pairs, epochs):
         del U
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
-        per_src = max(1, n_pairs // 2)
+        # half the pairs from each of two sources, spread over the solve; a
+        # request beyond what two solves hold (one pair per iteration) draws
+        # further sources
+        per_src = max(1, (n_pairs + 1) // 2)
         fx = lat.field(stag.EVEN, "df64")
-        for s in range(2):
-            fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1400 + s))
+        left, src = n_pairs, 0
+        while left > 0 and src < 64:
+            fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1400 + src))
             iters = lat.cg(fx, fb, LEARNED_MASS, 1e-10, 20000)["iters"]
-            net.collect_pairs(fb, LEARNED_MASS, 1e-10, stride=max(1, iters // (per_src + 1)),
-                              max_pairs=per_src)
+            want = min(left, per_src)
+            left -= net.collect_pairs(fb, LEARNED_MASS, 1e-10, stride=max(1, iters // (want + 1)),
+                                      max_pairs=want)
+            fb.destroy()
+            src += 1
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         net.set_loss("residual")
