@@ -9,11 +9,14 @@
 // owners' slices.  The Dslash kernel then writes the outputs of the slab only
 // and reads nothing of the input outside slab + halo (the rest of the private
 // buffer stays zero, so a deeper reach would change the result).  Links are
-// static and read in place: a rank would hold those of its slab and of the
-// three slices below it.  The CG's global sums are per-domain partial sums
-// added on the host in domain order, the allreduce of a multi-GPU run.
+// static: a rank holds those of its slab and of the three slices below it,
+// and each domain here gets a private copy of exactly those (zero
+// elsewhere), filled once per call as the exchange at upload would be.  The
+// CG's global sums are per-domain partial sums added on the host in domain
+// order, the allreduce of a multi-GPU run.
 #include "api_internal.h"
 
+#include <algorithm>
 #include <climits>
 
 namespace {
@@ -21,6 +24,7 @@ namespace {
 struct Domain {
     int t0 = 0, nt = 0;            // owned slices [t0, t0 + nt)
     void *buf = nullptr;           // assembled input (slab + halo, zero elsewhere)
+    void *links = nullptr;         // links of slices [t0 - 3, t0 + nt), zero elsewhere
     CgScalars *sc = nullptr;       // this domain's scalars (partial sums)
 };
 
@@ -34,11 +38,70 @@ struct Domains {
         for (auto &x : d) {
             if (x.buf)
                 cudaFree(x.buf);
+            if (x.links)
+                cudaFree(x.links);
             if (x.sc)
                 cudaFree(x.sc);
         }
     }
 };
+
+// the active link layout of the domain precision: bytes of one parity
+size_t link_half_bytes(const Domains &D) {
+    stag_lattice lat = D.lat;
+    if (lat->links_c12[D.prec])
+        return c12_link_bytes(D.prec, (size_t)lat->geom.stride) / 2;
+    return link_bytes(lat, D.prec) / 2;
+}
+const void *link_base(const Domains &D) {
+    return D.lat->links_c12[D.prec] ? D.lat->links_c12[D.prec] : D.lat->links[D.prec];
+}
+
+// copy the links of slices [t, t + n) (one contiguous range) of both
+// parities: every component plane of the layout, one 2-D copy per plane kind
+int copy_link_range(const Domains &D, void *dst, int t, int n) {
+    stag_lattice lat = D.lat;
+    const size_t S = (size_t)lat->geom.stride;
+    const size_t per = (size_t)lat->geom.plane[3];
+    const size_t half = link_half_bytes(D);
+    const char *src = (const char *)link_base(D);
+    struct Planes { size_t base, pitch, elem, count; };
+    Planes pl[2];
+    int np = 0;
+    if (!lat->links_c12[D.prec]) {
+        pl[np++] = {0, S * prec_link_elem_bytes(D.prec), prec_link_elem_bytes(D.prec), 72};
+    } else if (D.prec == STAG_F32) {
+        pl[np++] = {0, S * 16, 16, 24};          // float4 [8 kinds][3][S]
+    } else {
+        pl[np++] = {0, S * 24, 16, 8};           // int4 [S] of each kind
+        pl[np++] = {S * 16, S * 24, 8, 8};       // int2 [S] of each kind
+    }
+    for (int par = 0; par < 2; par++)
+        for (int q = 0; q < np; q++) {
+            const size_t off = par * half + pl[q].base + (size_t)t * per * pl[q].elem;
+            CUDA_TRY(cudaMemcpy2DAsync((char *)dst + off, pl[q].pitch, src + off, pl[q].pitch,
+                                       (size_t)n * per * pl[q].elem, pl[q].count, cudaMemcpyDeviceToDevice,
+                                       lat->stream));
+        }
+    return STAG_OK;
+}
+
+// domain i's links: slices [t0 - 3, t0 + nt) (periodic), zero elsewhere
+int fill_links(const Domains &D, int i) {
+    const Domain &x = D.d[i];
+    const int Lt = D.lat->geom.L[3];
+    int t = x.t0 - kHalo, n = x.nt + kHalo;
+    if (n >= Lt) {
+        t = 0;
+        n = Lt;
+    }
+    t = (t % Lt + Lt) % Lt;
+    const int first = std::min(n, Lt - t);  // up to the end of the lattice, then from slice 0
+    STAG_TRY(copy_link_range(D, x.links, t, first));
+    if (n > first)
+        STAG_TRY(copy_link_range(D, x.links, 0, n - first));
+    return STAG_OK;
+}
 
 int make_domains(Domains &D, int k) {
     stag_lattice lat = D.lat;
@@ -53,16 +116,22 @@ int make_domains(Domains &D, int k) {
         x.t0 = t;
         x.nt = Lt / k + (i < Lt % k ? 1 : 0);
         t += x.nt;
+        const size_t lb = 2 * link_half_bytes(D);
         cudaError_t e = cudaMalloc(&x.buf, fb);
+        if (e == cudaSuccess)
+            e = cudaMalloc(&x.links, lb);
         if (e == cudaSuccess)
             e = cudaMalloc(&x.sc, sizeof(CgScalars));
         if (e == cudaSuccess)
             e = cudaMemsetAsync(x.buf, 0, fb, lat->stream);
         if (e == cudaSuccess)
+            e = cudaMemsetAsync(x.links, 0, lb, lat->stream);
+        if (e == cudaSuccess)
             e = cudaMemsetAsync(x.sc, 0, sizeof(CgScalars), lat->stream);
         if (e != cudaSuccess)
             return fail(e == cudaErrorMemoryAllocation ? STAG_ERR_NOMEM : STAG_ERR_CUDA,
                         "domain decomposition: %s", cudaGetErrorString(e));
+        STAG_TRY(fill_links(D, i));
     }
     return STAG_OK;
 }
@@ -105,6 +174,10 @@ int domain_dslash(const Domains &D, int i, int out_par, int epi, void *out, cons
     const Domain &x = D.d[i];
     stag_lattice lat = D.lat;
     DslashArgs a = dslash_args(lat, D.prec, out_par, x.buf, out);
+    // the domain's own copy of the links, same layout
+    const size_t half = link_half_bytes(D);
+    a.links_out = (const char *)x.links + (size_t)out_par * half;
+    a.links_in = (const char *)x.links + (size_t)(1 - out_par) * half;
     a.c0 = x.t0 * lat->geom.plane[3];
     a.cn = x.nt * lat->geom.plane[3];
     a.p = p;
