@@ -434,8 +434,11 @@ int stag_apply_M_noalloc(const int dims[4], const double bc[4], double c1, doubl
  * of its slab only.  The global sums of the CG are per-slab partial sums
  * added on the host in slab order, as an allreduce would.  The results equal
  * the single-domain calls up to the order of the summation.
- * 1 <= ndomains <= Lt, else STAG_ERR_ARG.  Each call allocates one field per
- * slab on the device and frees it before returning. */
+ * Each slab also reads its links from a private copy holding only its own
+ * link slices and the three below it (the exchange a multi-GPU upload does
+ * once).  1 <= ndomains <= Lt, else STAG_ERR_ARG.  Each call allocates one
+ * field and one link copy per slab on the device and frees them before
+ * returning. */
 
 /* out = D in, as stag_dslash_eo / stag_dslash_oe (out's parity selects
  * which), computed slab by slab.  Fields of opposite parity, one precision
