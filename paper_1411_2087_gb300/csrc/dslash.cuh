@@ -356,18 +356,19 @@ STAG_D void dslash_body(const DslashArgs &a) {
     }
 }
 
-// One launch of the stencil.  The compressed 16-bit stencil gets its own
-// kernel with a register cap (at least 1024 resident threads per SM): left
-// free, the compiler hoists loads into more registers and the kernel runs
-// slower at the lower occupancy.  The others keep the compiler's choice.
+// One launch of the stencil.  The capped form asks for at least 1024 resident
+// threads per SM (at most 64 registers): the 16-bit kernels with an epilogue
+// and the compressed 16-bit stencil run faster under it; left free, the
+// compiler either hoists loads into more registers at a lower occupancy or
+// keeps too few loads in flight.  The others keep the compiler's choice.
 template <int P, int EPI, int BLOCK, bool COMP = false>
 __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     dslash_body<P, EPI, BLOCK, COMP>(a);
 }
 
-template <int P, int EPI, int BLOCK>
+template <int P, int EPI, int BLOCK, bool COMP>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(DslashArgs a) {
-    dslash_body<P, EPI, BLOCK, true>(a);
+    dslash_body<P, EPI, BLOCK, COMP>(a);
 }
 
 }  // namespace stag
