@@ -12,6 +12,7 @@ from paper_1411_2087_gb300 import stag, synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 2e-6, "f16": 3e-4}
+TOL_M = {"f32": 5e-6, "f16": 8e-4}  # two stencils and one stored intermediate
 
 
 def rel_err(got, want):
@@ -40,6 +41,11 @@ def test_compressed_dslash(dims, bc):
             e1 = rel_err(oo.export(), want_o)
             e2 = rel_err(oe.export(), want_e)
             assert e1 <= TOL[prec] and e2 <= TOL[prec], (prec, e1, e2)
+            # M = m^2 - D_eo D_oe on the same links (the fused m^2 p - D t epilogue)
+            om = lat.field(stag.EVEN, prec)
+            lat.apply_M(om, fe, 0.3)
+            em = rel_err(om.export(), oracle.apply_M(dims, U, N, 0.3, psi_e, bc=bc, c1=1.2, c3=-0.07))
+            assert em <= TOL_M[prec], (prec, "M", em)
 
 
 def test_compression_rejects_non_su3_links():

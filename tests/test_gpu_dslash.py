@@ -56,7 +56,13 @@ def test_dslash_both_parities(setup, prec):
     assert e1 <= TOL[prec] and e2 <= TOL[prec], f"{prec}: D_oe err {e1:.3e}, D_eo err {e2:.3e}"
 
 
-@pytest.mark.parametrize("prec", ["f64", "df64"])
+# M = m^2 - D_eo D_oe applies two stencils with the odd intermediate stored in
+# the field's precision: the reduced-precision bounds are twice the Dslash
+# bounds plus one rounding of the intermediate
+TOL_M = {"f64": 1e-12, "df64": 1e-12, "f32": 5e-6, "f16": 8e-4}
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "f16"])
 def test_apply_M(setup, prec):
     dims, U, N, psi_e, psi_o, lat = setup
     mass = 0.1
@@ -66,7 +72,7 @@ def test_apply_M(setup, prec):
     err = rel_err(out.export(), oracle.apply_M(dims, U, N, mass, psi_e))
     fe.destroy()
     out.destroy()
-    assert err <= TOL[prec], f"{prec}: M err {err:.3e}"
+    assert err <= TOL_M[prec], f"{prec}: M err {err:.3e}"
 
 
 def test_import_export_roundtrip(setup):
