@@ -357,10 +357,11 @@ STAG_D void dslash_body(const DslashArgs &a) {
 }
 
 // One launch of the stencil.  The capped form asks for at least 1024 resident
-// threads per SM (at most 64 registers): the 16-bit kernels with an epilogue
-// and the compressed 16-bit stencil run faster under it; left free, the
-// compiler either hoists loads into more registers at a lower occupancy or
-// keeps too few loads in flight.  The others keep the compiler's choice.
+// threads per SM (at most 64 registers).  Left free, the compiler hoists the
+// compressed 16-bit stencil's loads into 255 registers at a low occupancy,
+// and gives the uncompressed FP32 and 16-bit epilogue kernels so few
+// registers (32-44) that too few loads are in flight; the launcher picks the
+// capped form for those (kCapped) and the free one for the rest.
 template <int P, int EPI, int BLOCK, bool COMP = false>
 __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
     dslash_body<P, EPI, BLOCK, COMP>(a);

@@ -6,13 +6,21 @@
 
 namespace stag {
 
-// 16-bit kernels with an epilogue (and the compressed 16-bit stencil) run
-// under the register cap; the others keep the compiler's choice.  Measured at
-// 48^3x96: uncompressed 16-bit M with <p, Mp> partials 635 -> 557 us capped,
-// while the plain uncompressed 16-bit D_oe is 530 us free and 540 us capped.
+// Which kernels run under the register cap, by measurement (48^3x96, kernel
+// times inside the mixed solves).  Left free, the compiler gives these 32-44
+// registers and keeps too few stencil loads in flight:
+//   16-bit with an epilogue    M with <p, Mp> partials 635 -> 557 us
+//   FP32 uncompressed          D_oe 947 -> 901 us, M with partials 954 -> 913 us
+//   16-bit compressed          see dslash_kernel_capped
+// The plain uncompressed 16-bit D_oe stays free (530 us, 540 us capped); FP32
+// compressed (56-62 registers free) and the FP64 and double-float kernels
+// (HBM-bound at their free choice) keep the compiler's choice.
+template <int P, int EPI, bool COMP>
+constexpr bool kCapped = (P == P_F16 && (COMP || EPI != EPI_NONE)) || (P == P_F32 && !COMP);
+
 template <int P, int EPI, int BLOCK, bool COMP>
 static void launch_one(int grid, const DslashArgs &a, cudaStream_t s) {
-    if constexpr (P == P_F16 && (COMP || EPI != EPI_NONE))
+    if constexpr (kCapped<P, EPI, COMP>)
         dslash_kernel_capped<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
     else
         dslash_kernel<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
