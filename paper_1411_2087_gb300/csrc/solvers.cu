@@ -174,8 +174,10 @@ int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *
     STAG_TRY(ensure_cg_work(lat, hi));
     STAG_TRY(ensure_cg_work(lat, lo));
     if (!lat->xs) {
-        CUDA_TRY(cudaMalloc(&lat->xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
-        CUDA_TRY(cudaMemsetAsync(lat->xs, 0, prec_vec_bytes(STAG_F32, lat->geom.stride), lat->stream));
+        // the init kernel of every solve zeroes x_s
+        float *xs = nullptr;
+        CUDA_TRY(cudaMalloc(&xs, prec_vec_bytes(STAG_F32, lat->geom.stride)));
+        lat->xs = xs;
     }
     CgWork &H = lat->cg[hi];
     cudaStream_t s = lat->stream;
@@ -279,12 +281,16 @@ extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_fi
 // multi-shift CG (kernels_multishift.cu has the recurrences)
 // --------------------------------------------------------------------------
 static int ensure_ms_state(stag_lattice lat) {
-    if (lat->ms_state)
-        return STAG_OK;
-    CUDA_TRY(cudaMalloc(&lat->ms_state, sizeof(ShiftState) * MS_MAX));
-    CUDA_TRY(cudaMallocHost(&lat->ms_state_host, sizeof(ShiftState) * MS_MAX));
-    CUDA_TRY(cudaMalloc(&lat->ms_true, sizeof(double) * MS_MAX));
-    CUDA_TRY(cudaMallocHost(&lat->ms_true_host, sizeof(double) * MS_MAX));
+    // each buffer on its own: an allocation that failed in an earlier call
+    // is retried here instead of leaving the others in use without it
+    if (!lat->ms_state)
+        CUDA_TRY(cudaMalloc(&lat->ms_state, sizeof(ShiftState) * MS_MAX));
+    if (!lat->ms_state_host)
+        CUDA_TRY(cudaMallocHost(&lat->ms_state_host, sizeof(ShiftState) * MS_MAX));
+    if (!lat->ms_true)
+        CUDA_TRY(cudaMalloc(&lat->ms_true, sizeof(double) * MS_MAX));
+    if (!lat->ms_true_host)
+        CUDA_TRY(cudaMallocHost(&lat->ms_true_host, sizeof(double) * MS_MAX));
     return STAG_OK;
 }
 
