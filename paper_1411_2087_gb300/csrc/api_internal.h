@@ -290,13 +290,16 @@ static inline int alloc_vec(stag_lattice lat, int prec, void **p) {
     if (*p)
         return STAG_OK;
     const size_t b = field_bytes(lat, prec);
-    cudaError_t e = cudaMalloc(p, b);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(*p, 0, b, lat->stream);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return fail(STAG_ERR_NOMEM, "vector allocation (%s): %s", prec_name(prec), cudaGetErrorString(e));
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, b);
+    if (e == cudaSuccess) {
+        e = cudaMemsetAsync(q, 0, b, lat->stream);
+        if (e != cudaSuccess)
+            cudaFree(q);
     }
+    if (e != cudaSuccess)
+        return fail(STAG_ERR_NOMEM, "vector allocation (%s): %s", prec_name(prec), cudaGetErrorString(e));
+    *p = q;
     return STAG_OK;
 }
 
