@@ -33,7 +33,7 @@ using stag::Geom;
 // loads the library until the process exits.
 constexpr long long kNoAllocMaxVh = 65536;
 
-__device__ __align__(256) double2 g_noalloc_scratch[3 * kNoAllocMaxVh];
+static __device__ __align__(256) double2 g_noalloc_scratch[3 * kNoAllocMaxVh];
 
 struct NoAllocArgs {
     Geom g;
@@ -127,13 +127,17 @@ __global__ void noalloc_dslash_kernel(NoAllocArgs a, int out_par) {
 std::mutex g_scratch_mutex;
 double2 *g_scratch_addr[64] = {nullptr};
 
-bool is_device_pointer(const void *p) {
+// device memory of device `dev` (managed memory is reachable from any
+// device; plain device memory of another GPU is not without peer access)
+bool is_device_pointer_of(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged)
+        return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -167,17 +171,18 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double bc[4], doubl
         return stag::set_error(STAG_ERR_ARG, "stag_apply_M_noalloc: c1, c3, mass must be finite");
     if (in_even == out_even)
         return stag::set_error(STAG_ERR_ARG, "stag_apply_M_noalloc: in and out must differ");
-    const void *ptrs[4] = {fat, lng, in_even, out_even};
-    for (const void *p : ptrs)
-        if (!is_device_pointer(p))
-            return stag::set_error(STAG_ERR_ARG,
-                                   "stag_apply_M_noalloc: every buffer must be device memory");
-
-    // set-up, once per device, with that device current: the device address
-    // of the scratch array (its host-side name is only a stand-in)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return stag::set_error(STAG_ERR_CUDA, "stag_apply_M_noalloc: no current CUDA device");
+    const void *ptrs[4] = {fat, lng, in_even, out_even};
+    for (const void *p : ptrs)
+        if (!is_device_pointer_of(p, dev))
+            return stag::set_error(STAG_ERR_ARG,
+                                   "stag_apply_M_noalloc: every buffer must be device memory of the "
+                                   "current device (%d)", dev);
+
+    // set-up, once per device, with that device current: the device address
+    // of the scratch array (its host-side name is only a stand-in)
     double2 *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_scratch_mutex);

@@ -454,12 +454,16 @@ def cb_neighbor(dims, parity: int, cb: int, mu: int, steps: int):
 def apply_M_noalloc(dims, fat, lng, mass, in_even, out_even, bc=BC_DEFAULT, c1=C1_NAIK,
                     c3=C3_NAIK, stream=None):
     """stag_apply_M_noalloc on CUDA tensors the caller owns (see stag.h)."""
+    import torch
     V = int(np.prod(dims))
     for t, shape in ((fat, (4, V, 3, 3)), (lng, (4, V, 3, 3)), (in_even, (V // 2, 3)),
                      (out_even, (V // 2, 3))):
         p, kind, keep = _as_buffer(t, shape)
         if kind != PTR_DEVICE:
             raise ValueError("stag_apply_M_noalloc needs device tensors")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("stag_apply_M_noalloc needs tensors on the current CUDA device "
+                             f"(cuda:{torch.cuda.current_device()}), got {t.device}")
     d = (ctypes.c_int * 4)(*[int(v) for v in dims])
     b = (ctypes.c_double * 4)(*[float(v) for v in bc]) if bc is not None else None
     _check(lib().stag_apply_M_noalloc(d, b, float(c1), float(c3), ctypes.c_void_p(fat.data_ptr()),

@@ -106,3 +106,41 @@ def test_binding_checks_shapes():
         stag._as_buffer(np.zeros((4, 3), dtype=np.float64), (4, 3))
     p, kind, keep = stag._as_buffer(np.zeros((4, 3), dtype=np.complex128), (4, 3))
     assert kind == stag.PTR_HOST
+
+
+def test_noalloc_argument_checks_before_cuda(L):
+    """stag_apply_M_noalloc rejects bad arguments before any CUDA call (dummy
+    non-NULL pointers: none is dereferenced before the checks fail)."""
+    dummy = ctypes.c_void_p(0x1000)
+    other = ctypes.c_void_p(0x2000)
+    d = (ctypes.c_int * 4)(4, 4, 4, 4)
+
+    def call(dims=d, bc=None, c1=1.125, c3=-1 / 24, fat=dummy, lng=dummy, mass=0.1, i=dummy, o=other):
+        st = L.stag_apply_M_noalloc(dims, bc, c1, c3, fat, lng, mass, i, o, None)
+        return st, L.stag_last_error_message()
+
+    for args in ({"dims": None}, {"fat": None}, {"lng": None}, {"i": None}, {"o": None}):
+        st, msg = call(**args)
+        assert st == stag.ERR_ARG and b"NULL" in msg, args
+    for dims in ((4, 4, 4, 3), (4, 0, 4, 4), (1, 4, 4, 4), (4, 4, -2, 4)):
+        st, msg = call(dims=(ctypes.c_int * 4)(*dims))
+        assert st == stag.ERR_ARG and b"even" in msg, dims
+    st, msg = call(dims=(ctypes.c_int * 4)(16, 16, 16, 64))
+    assert st == stag.ERR_ARG and b"65536" in msg
+    st, msg = call(bc=(ctypes.c_double * 4)(1, 1, 0.5, -1))
+    assert st == stag.ERR_ARG and b"bc" in msg
+    for kw in ({"c1": float("nan")}, {"c3": float("inf")}, {"mass": float("nan")}):
+        st, msg = call(**kw)
+        assert st == stag.ERR_ARG and b"finite" in msg, kw
+    st, msg = call(o=dummy)
+    assert st == stag.ERR_ARG and b"differ" in msg
+
+
+def test_noalloc_binding_refuses_host_tensors():
+    import torch
+    dims = (4, 4, 4, 4)
+    V = 256
+    fat = torch.zeros((4, V, 3, 3), dtype=torch.complex128)
+    vec = torch.zeros((V // 2, 3), dtype=torch.complex128)
+    with pytest.raises(ValueError, match="device tensors"):
+        stag.apply_M_noalloc(dims, fat, fat, 0.1, vec, vec.clone())

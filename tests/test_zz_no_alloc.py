@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1411_2087_gb300 import stag, synth
 
 pytestmark = pytest.mark.gpu
@@ -56,6 +57,32 @@ def test_noalloc_matches_apply_M_twice(dims):
             assert err <= TOL, f"call with seed {seed}: rel err {err:.3e}"
             fin.destroy()
             fout.destroy()
+
+
+@pytest.mark.parametrize("dims,bc", [((4, 2, 6, 4), (-1.0, 1.0, 1.0, -1.0)),
+                                     ((2, 4, 4, 2), (1.0, -1.0, -1.0, 1.0))])
+def test_noalloc_matches_oracle_wraps_and_bc(dims, bc):
+    """Extents of 2 (a three-link hop wraps twice) and non-default boundary
+    signs and coefficients: the kernel's own wrap counting against the CPU
+    oracle's M, twice in a row."""
+    dev = torch.device("cuda", 0)
+    Vh = int(np.prod(dims)) // 2
+    c1, c3, mass = 1.25, -0.1, 0.3
+    U = synth.su3_field(dims, 0.3, 2025).numpy()
+    N = oracle.long_links(dims, U)
+    U_d = torch.from_numpy(U).to(dev)
+    N_d = torch.from_numpy(N).to(dev)
+    out_d = torch.empty((Vh, 3), dtype=torch.complex128, device=dev)
+    for seed in (9, 10):
+        src = synth.gaussian_colour_field(Vh, seed).numpy()
+        want = oracle.apply_M(dims, U, N, mass, src, bc=bc, c1=c1, c3=c3)
+        in_d = torch.from_numpy(src).to(dev)
+        out_d.fill_(float("nan"))
+        torch.cuda.synchronize()
+        stag.apply_M_noalloc(dims, U_d, N_d, mass, in_d, out_d, bc=bc, c1=c1, c3=c3)
+        torch.cuda.synchronize()
+        err = rel_err(out_d.cpu().numpy(), want)
+        assert err <= TOL, f"seed {seed}: rel err {err:.3e}"
 
 
 def test_noalloc_rejects_oversize_and_host_memory():
