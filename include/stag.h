@@ -327,12 +327,25 @@ int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double 
  * net is gauge covariant.  As a preconditioner it maps an even residual r
  * (zero on odd sites) to z = N(r) restricted to the even sites.  Weights:
  * (re, im) doubles, layer 1 [9][C][1], layer 2 [9][C][C], layer 3 [9][1][C],
- * concatenated (9 * (2C + C^2) complex numbers).  FP32 activations and
- * arithmetic; inside the solver the weights are rounded to binary16. */
+ * concatenated (9 * (2C + C^2) complex numbers).
+ *
+ * Evaluation.  The net is linear and its weights commute with the
+ * transports, so on an even input with even outputs kept it equals the
+ * two-hop path sum
+ *   z(x) = c0 r(x) + sum_{a,b} C[a][b] T_a T_b r(x),  T_d one hop d (or 1),
+ *   c0 = W3[0] W2[0] W1[0],
+ *   C[a][b] = W3[0] W2[a] W1[b] + W3[a] W2[0] W1[b] + W3[a] W2[b] W1[0]
+ * (products over the channels).  The library evaluates the net in that form
+ * (two stencil kernels: 16 link matrices and about 1.4k multiply-adds per
+ * even site) and trains the layer weights through it (the chain rule from
+ * dL/dC* to dL/dW*).  FP32 arithmetic; inside the solver the weights are
+ * rounded to binary16 and the links read from a 16-bit copy (fixed point,
+ * one scale for the field). */
 typedef struct stag_net_s *stag_net;
 
 /* Create a net with C = channels (1, 2, 4 or 8) on `lat` from the raw fat
- * links (canonical complex128 [4][V][3][3]).  Initial weights: the identity
+ * links (canonical complex128 [4][V][3][3]; a NaN, an infinity or an entry
+ * beyond the FP32 range gives STAG_ERR_ARG).  Initial weights: the identity
  * map plus seeded N(0, 1e-2) noise.  Counts as a live object of the
  * lattice: destroy nets before their lattice. */
 int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind, int channels, unsigned seed,
@@ -342,9 +355,13 @@ int stag_net_num_weights(const stag_net n, int *count);  /* complex weights */
 int stag_net_set_weights(stag_net n, const double *w);   /* resets the optimiser state */
 int stag_net_get_weights(const stag_net n, double *w);
 
-/* out = N(in) on even fields (F64, DF64 or F32) of the net's lattice;
- * fp16_weights rounds the weights to binary16 first.  Asynchronous. */
-int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int fp16_weights);
+/* out = N(in) on distinct even fields of one precision (F64, DF64 or F32)
+ * of the net's lattice.  flags: 0, or an OR of STAG_NET_FP16_WEIGHTS (round
+ * the weights to binary16 first) and STAG_NET_LINKS16 (read the 16-bit link
+ * copy), which together are the form the learned solver applies; other bits
+ * give STAG_ERR_ARG.  Asynchronous. */
+enum { STAG_NET_FP16_WEIGHTS = 1, STAG_NET_LINKS16 = 2 };
+int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int flags);
 
 /* Training pairs from the plain CG: solve M x* = b to rel_tol, then rerun
  * the same iteration and, every `stride` iterations (at most max_pairs
@@ -382,7 +399,8 @@ int stag_net_loss_grad(stag_net n, int first, int count, double *loss, double *g
 int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss);
 
 /* Flexible CG (Notay; Polak-Ribiere beta on real inner products) for
- * M x = b with z = N(r) as the preconditioner, from x0 = 0.  A run that
+ * M x = b with z = N(r) as the preconditioner (binary16 weights, 16-bit
+ * links), from x0 = 0.  A run that
  * claims convergence is checked against the recomputed residual and
  * restarted if they drifted apart; after a breakdown (<r, z> <= 0), or the
  * iteration limit, plain CG (z = r) continues from the current x.

@@ -1,0 +1,762 @@
+// The learned preconditioner evaluated in path form.
+//
+// The net (three gauge-covariant convolution layers 1 -> C -> C -> 1, no
+// nonlinearity; include/stag.h) is linear in its input, and its colour-blind
+// weights commute with the link transports.  Each layer applies at most one
+// hop, T_0 = 1 or T_d psi(x) = U_mu(x) psi(x+mu) (d = +mu) or
+// U_mu(x-mu)^+ psi(x-mu) (d = -mu), so the whole net is a sum over hop
+// sequences (d1, d2, d3) of (W3[d3] W2[d2] W1[d1]) T_d3 T_d2 T_d1.  As a
+// preconditioner its input r lives on the even sites and only its even
+// outputs are kept, which leaves the sequences with zero or two hops:
+//
+//   z(x) = c0 r(x) + sum_{a,b} C[a][b] (T_a T_b r)(x)          (x even)
+//   c0      = W3[0] W2[0] W1[0]
+//   C[a][b] = W3[0] W2[a] W1[b] + W3[a] W2[0] W1[b] + W3[a] W2[b] W1[0]
+//
+// (row . matrix . column products over the channels).  Two kernels evaluate
+// it: net_mid_kernel forms chi_a(y) = sum_b C[a][b] (T_b r)(y) on the odd
+// sites (eight link transports and an 8 x 8 complex mixing per site), and
+// net_out_kernel adds the eight transports T_a chi_a on the even sites.
+// That is 16 link matrices and about 1.4k multiply-adds per even site,
+// against 27 link loads and about 12k multiply-adds per site for the three
+// layers one after another.  Training differentiates the same form: the
+// gradient with respect to C[a][b] is <T_b r, T_a^+ g> summed over the odd
+// sites (g = dL/dz*), and the chain rule through the products above gives
+// the gradient of every layer weight.
+#include "kernels.h"
+#include "learned.cuh"
+#include "reduce.cuh"
+
+namespace stag {
+
+// ---- links -----------------------------------------------------------------
+// Net links per parity in structure-of-arrays form: element e (row*3+col) of
+// U_mu at checkerboard site c of parity par at ((par*4 + mu)*9 + e)*S + c,
+// the boundary sign of a wrapping forward hop folded into the last-slice link.
+// FP32 (float2) or 16-bit (short2, value = q * scale).
+STAG_D cplx<float> nl_get(float2 v) { return cplx<float>{v.x, v.y}; }
+STAG_D cplx<float> nl_get(short2 v) { return cplx<float>{(float)v.x, (float)v.y}; }
+
+template <class LT>
+STAG_D void nl_load(const LT *__restrict__ NL, int S, int par, int mu, int c, cplx<float> U[9]) {
+    const LT *p = NL + (size_t)((par * 4 + mu) * 9) * S + c;
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        U[e] = nl_get(ld_stream(p + (size_t)e * S));
+}
+
+// h = U v (adj = false) or U^+ v
+STAG_D void nl_apply(const cplx<float> U[9], bool adj, const cplx<float> v[3], cplx<float> h[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        cplx<float> t = czero<float>();
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (adj)
+                cmac_conj(t, U[3 * b + a], v[b]);
+            else
+                cmac(t, U[3 * a + b], v[b]);
+        }
+        h[a] = t;
+    }
+}
+
+// canonical raw fat links complex128 [4][V][3][3] -> net links of both
+// parities; one thread per (mu, site).  inv_scale: 16-bit only.
+template <class LT> STAG_D LT nl_pack(double re, double im, float inv_scale);
+template <> STAG_D float2 nl_pack<float2>(double re, double im, float) { return make_float2((float)re, (float)im); }
+template <> STAG_D short2 nl_pack<short2>(double re, double im, float inv) {
+    return make_short2(q16((float)re * inv), q16((float)im * inv));
+}
+
+template <class LT>
+__global__ void net_links_cb_kernel(Geom g, double bc0, double bc1, double bc2, double bc3,
+                                    const double2 *__restrict__ fat, LT *NL, float inv_scale) {
+    const long long V = 2LL * g.Vh;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V)
+        return;
+    const int mu = (int)(t / V);
+    const int i = (int)(t % V);
+    int x[4];
+    x[0] = i % g.L[0];
+    int rr = i / g.L[0];
+    x[1] = rr % g.L[1];
+    rr /= g.L[1];
+    x[2] = rr % g.L[2];
+    x[3] = rr / g.L[2];
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const double bc[4] = {bc0, bc1, bc2, bc3};
+    const double sgn = (x[mu] == g.L[mu] - 1 && bc[mu] < 0) ? -1.0 : 1.0;
+    const int S = g.stride;
+    LT *dst = NL + (size_t)((par * 4 + mu) * 9) * S + (i >> 1);
+#pragma unroll 1
+    for (int e = 0; e < 9; e++) {
+        const double2 u = fat[((size_t)mu * V + i) * 9 + e];
+        dst[(size_t)e * S] = nl_pack<LT>(sgn * u.x, sgn * u.y, inv_scale);
+    }
+}
+
+cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double *fat, float2 *NL32, short2 *NL16,
+                                float inv_scale16, cudaStream_t s) {
+    const long long n = 8LL * g.Vh;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (NL32)
+        net_links_cb_kernel<float2><<<grid, 256, 0, s>>>(g, bc[0], bc[1], bc[2], bc[3], (const double2 *)fat,
+                                                         NL32, 1.f);
+    if (NL16)
+        net_links_cb_kernel<short2><<<grid, 256, 0, s>>>(g, bc[0], bc[1], bc[2], bc[3], (const double2 *)fat,
+                                                         NL16, inv_scale16);
+    return cudaGetLastError();
+}
+
+// ---- path coefficients from the layer weights ------------------------------
+// w: the weights as FP32 (re, im) pairs, layers at complex offsets off[0..2]
+// (W1 [9][C][1], W2 [9][C][C], W3 [9][1][C]); round_half rounds each weight
+// through binary16 first (the deployed preconditioner's weight storage).
+struct NetW {
+    const float2 *w;
+    int C, off1, off2, round_half;
+    STAG_D double2 get(int k) const {
+        float2 v = w[k];
+        if (round_half)
+            v = make_float2(__half2float(__float2half_rn(v.x)), __half2float(__float2half_rn(v.y)));
+        return make_double2((double)v.x, (double)v.y);
+    }
+    STAG_D double2 w1(int d, int i) const { return get(d * C + i); }
+    STAG_D double2 w2(int d, int j, int i) const { return get(off1 + (d * C + j) * C + i); }
+    STAG_D double2 w3(int d, int j) const { return get(off2 + d * C + j); }
+};
+
+STAG_D double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+STAG_D double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+STAG_D double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// W3[d3] . W2[d2] . W1[d1]
+STAG_D double2 triple(const NetW &W, int d3, int d2, int d1) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int j = 0; j < W.C; j++) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int i = 0; i < W.C; i++)
+            t = zadd(t, zmul(W.w2(d2, j, i), W.w1(d1, i)));
+        s = zadd(s, zmul(W.w3(d3, j), t));
+    }
+    return s;
+}
+
+// one block of 65 threads: thread a*8+b computes C[a][b], thread 64 c0
+__global__ void net_path_coef_kernel(NetW W, NetPath *out) {
+    const int q = threadIdx.x;
+    if (q < 64) {
+        const int a = q >> 3, b = q & 7;
+        const double2 v = zadd(zadd(triple(W, 0, a + 1, b + 1), triple(W, a + 1, 0, b + 1)), triple(W, a + 1, b + 1, 0));
+        out->C[q] = make_float2((float)v.x, (float)v.y);
+    } else if (q == 64) {
+        const double2 v = triple(W, 0, 0, 0);
+        out->c0 = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int round_half, NetPath *out,
+                                 cudaStream_t s) {
+    NetW W{(const float2 *)w32, C, off[1], off[2], round_half};
+    net_path_coef_kernel<<<1, 96, 0, s>>>(W, out);
+    return cudaGetLastError();
+}
+
+// dL/dW* of every complex weight from G[a*8+b] = dL/dC[a][b]* and G[64] =
+// dL/dc0* (C holomorphic in W: dL/dW* = sum conj(dC/dW) dL/dC*); added to grad
+__global__ void net_path_chain_kernel(NetW W, int nw, const double2 *__restrict__ G, double2 *grad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nw)
+        return;
+    const int C = W.C;
+    const double2 G0 = G[64];
+    double2 acc = make_double2(0.0, 0.0);
+    auto add = [&](double2 coef, double2 gv) { acc = zadd(acc, zmul(zconj(coef), gv)); };
+    if (k < W.off1) {  // W1[d][i]
+        const int d = k / C, i = k % C;
+        // sum_j W3[d3][j] W2[d2][j][i]
+        auto s32 = [&](int d3, int d2) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int j = 0; j < C; j++)
+                t = zadd(t, zmul(W.w3(d3, j), W.w2(d2, j, i)));
+            return t;
+        };
+        if (d == 0) {
+            add(s32(0, 0), G0);
+            for (int a = 0; a < 8; a++)
+                for (int b = 0; b < 8; b++)
+                    add(s32(a + 1, b + 1), G[a * 8 + b]);
+        } else {
+            const int b = d - 1;
+            for (int a = 0; a < 8; a++)
+                add(zadd(s32(0, a + 1), s32(a + 1, 0)), G[a * 8 + b]);
+        }
+    } else if (k < W.off2) {  // W2[d][j][i]
+        const int q = k - W.off1;
+        const int d = q / (C * C), j = (q / C) % C, i = q % C;
+        if (d == 0) {
+            add(zmul(W.w3(0, j), W.w1(0, i)), G0);
+            for (int a = 0; a < 8; a++)
+                for (int b = 0; b < 8; b++)
+                    add(zmul(W.w3(a + 1, j), W.w1(b + 1, i)), G[a * 8 + b]);
+        } else {
+            const int e = d - 1;
+            for (int b = 0; b < 8; b++)  // W2 as the outer hop, layer 3 idle
+                add(zmul(W.w3(0, j), W.w1(b + 1, i)), G[e * 8 + b]);
+            for (int a = 0; a < 8; a++)  // W2 as the inner hop, layer 1 idle
+                add(zmul(W.w3(a + 1, j), W.w1(0, i)), G[a * 8 + e]);
+        }
+    } else {  // W3[d][j]
+        const int q = k - W.off2;
+        const int d = q / C, j = q % C;
+        // sum_i W2[d2][j][i] W1[d1][i]
+        auto s21 = [&](int d2, int d1) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int i = 0; i < C; i++)
+                t = zadd(t, zmul(W.w2(d2, j, i), W.w1(d1, i)));
+            return t;
+        };
+        if (d == 0) {
+            add(s21(0, 0), G0);
+            for (int a = 0; a < 8; a++)
+                for (int b = 0; b < 8; b++)
+                    add(s21(a + 1, b + 1), G[a * 8 + b]);
+        } else {
+            const int a = d - 1;
+            for (int b = 0; b < 8; b++)
+                add(zadd(s21(0, b + 1), s21(b + 1, 0)), G[a * 8 + b]);
+        }
+    }
+    grad[k] = zadd(grad[k], acc);
+}
+
+cudaError_t launch_net_path_chain(int C, const float *w32, const int off[3], const double2 *G, double2 *grad,
+                                  cudaStream_t s) {
+    NetW W{(const float2 *)w32, C, off[1], off[2], 0};
+    const int nw = 9 * (2 * C + C * C);
+    net_path_chain_kernel<<<(nw + 127) / 128, 128, 0, s>>>(W, nw, G, grad);
+    return cudaGetLastError();
+}
+
+// ---- the two stencil passes --------------------------------------------------
+constexpr int NET_BLOCK = 128;
+
+template <class R> STAG_D cplx<float> to_f(const cplx<R> &v) { return cconv<float, R>(v); }
+
+// chi_a(y) = sum_b C[a][b] (T_b r)(y) on the odd sites; r even (precision P,
+// component stride rs), chi float2 [8][3][S].  Hop index b = 2 mu (+mu) or
+// 2 mu + 1 (-mu).  ls: the links' scale (1 for FP32).
+template <int P, class LT>
+__global__ void __launch_bounds__(NET_BLOCK)
+net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
+               const typename Fmt<P>::Elem *__restrict__ r, int rs, float2 *__restrict__ chi, const int *gate) {
+    __shared__ cplx<float> sC[64];
+    if (gate && *gate != CG_RUNNING)
+        return;
+    if (threadIdx.x < 64) {
+        const float2 v = path->C[threadIdx.x];
+        sC[threadIdx.x] = cplx<float>{v.x * ls, v.y * ls};
+    }
+    __syncthreads();
+    const int c = blockIdx.x * NET_BLOCK + threadIdx.x;
+    if (c >= g.Vh)
+        return;
+    const int S = g.stride;
+    int x[4];
+    cb_coords(g, c, 1, x);
+    cplx<float> ch[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            ch[a][k] = czero<float>();
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+        for (int bw = 0; bw < 2; bw++) {
+            // +mu: U_mu(y) r(y+mu), the link of this odd site;
+            // -mu: U_mu(y-mu)^+ r(y-mu), the link of the even neighbour
+            const int j = cb_hop(g, c, x, mu, bw ? -1 : 1);
+            cplx<typename Fmt<P>::R> vr[3];
+            load_vec<P>(r, rs, j, vr);
+            cplx<float> v[3], U[9], h[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                v[k] = to_f(vr[k]);
+            nl_load(NL, S, bw ? 0 : 1, mu, bw ? j : c, U);
+            nl_apply(U, bw, v, h);
+            const int b = 2 * mu + bw;
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const cplx<float> w = sC[a * 8 + b];
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    cmac(ch[a][k], w, h[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            __stcs(chi + (size_t)(a * 3 + k) * S + c, make_float2(ch[a][k].re, ch[a][k].im));
+}
+
+// z(x) = c0 r(x) + sum_a (T_a chi_a)(x) on the even sites.  NET_OUT_DOTS
+// adds per-block partials of Re<z, r> (partial[blk]) and Re<z, Ap>
+// (partial[nblk + blk]; 0 without Ap) for the flexible CG.
+enum { NET_OUT_PLAIN = 0, NET_OUT_DOTS = 1 };
+
+template <int PI, int PO, class LT, int EPI>
+__global__ void __launch_bounds__(NET_BLOCK)
+net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
+               const float2 *__restrict__ chi, const typename Fmt<PI>::Elem *__restrict__ r, int rs,
+               typename Fmt<PO>::Elem *__restrict__ z, int zs, const typename Fmt<PO>::Elem *__restrict__ Ap,
+               double *partial, const int *gate) {
+    using RO = typename Fmt<PO>::R;
+    __shared__ double smem[32];
+    if (gate && *gate != CG_RUNNING)
+        return;
+    const int c = blockIdx.x * NET_BLOCK + threadIdx.x;
+    const int S = g.stride;
+    red_t<RO> d0 = red_zero<red_t<RO>>(), d1 = red_zero<red_t<RO>>();
+    if (c < g.Vh) {
+        int x[4];
+        cb_coords(g, c, 0, x);
+        cplx<float> acc[3] = {czero<float>(), czero<float>(), czero<float>()};
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+            for (int bw = 0; bw < 2; bw++) {
+                // +mu: U_mu(x) chi_{+mu}(x+mu); -mu: U_mu(x-mu)^+ chi_{-mu}(x-mu)
+                const int j = cb_hop(g, c, x, mu, bw ? -1 : 1);
+                const int a = 2 * mu + bw;
+                cplx<float> v[3], U[9], h[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float2 t = __ldg(chi + (size_t)(a * 3 + k) * S + j);
+                    v[k] = cplx<float>{t.x, t.y};
+                }
+                nl_load(NL, S, bw ? 1 : 0, mu, bw ? j : c, U);
+                nl_apply(U, bw, v, h);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    acc[k].re += h[k].re;
+                    acc[k].im += h[k].im;
+                }
+            }
+        }
+        const float2 c0 = path->c0;
+        cplx<typename Fmt<PI>::R> rv[3];
+        load_vec<PI>(r, rs, c, rv);
+        cplx<RO> zo[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const cplx<float> rf = to_f(rv[k]);
+            cplx<float> zf = cplx<float>{acc[k].re * ls, acc[k].im * ls};
+            cmac(zf, cplx<float>{c0.x, c0.y}, rf);
+            zo[k] = cplx<RO>{rconv<RO, float>(zf.re), rconv<RO, float>(zf.im)};
+        }
+        store_vec<PO>(z, zs, c, zo);
+        if (EPI == NET_OUT_DOTS) {
+            cplx<RO> ro[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                ro[k] = cconv<RO, typename Fmt<PI>::R>(rv[k]);
+            d0 = re_dot3<RO>(zo, ro);
+            if (Ap) {
+                cplx<RO> av[3];
+                load_vec<PO>(Ap, zs, c, av);
+                d1 = re_dot3<RO>(zo, av);
+            }
+        }
+    }
+    if (EPI == NET_OUT_DOTS) {
+        const double s0 = block_sum<NET_BLOCK>(d0, smem);
+        const double s1 = block_sum<NET_BLOCK>(d1, smem);
+        if (threadIdx.x == 0) {
+            partial[blockIdx.x] = s0;
+            partial[gridDim.x + blockIdx.x] = s1;
+        }
+    }
+}
+
+int net_grid(const Geom &g) { return (g.Vh + NET_BLOCK - 1) / NET_BLOCK; }
+
+#define NP_IN_SWITCH(prec, ...)                                            \
+    switch (prec) {                                                        \
+    case P_F64: { constexpr int P = P_F64; __VA_ARGS__; } break;           \
+    case P_DF64: { constexpr int P = P_DF64; __VA_ARGS__; } break;         \
+    case P_F32: { constexpr int P = P_F32; __VA_ARGS__; } break;           \
+    case P_F16: { constexpr int P = P_F16; __VA_ARGS__; } break;           \
+    default: return cudaErrorInvalidValue;                                 \
+    }
+
+cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const NetPath *path, const void *r,
+                           int rs, float2 *chi, const int *gate, cudaStream_t s) {
+    NP_IN_SWITCH(prec, {
+        using E = typename Fmt<P>::Elem;
+        if (nl.l16)
+            net_mid_kernel<P, short2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l16, nl.scale16, path,
+                                                                         (const E *)r, rs, chi, gate);
+        else
+            net_mid_kernel<P, float2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l32, 1.f, path, (const E *)r, rs,
+                                                                         chi, gate);
+    });
+    return cudaGetLastError();
+}
+
+template <int PI, int PO, int EPI>
+static void net_out_t(const Geom &g, const NetLinkSet &nl, const NetPath *path, const float2 *chi, const void *r,
+                      int rs, void *z, int zs, const void *Ap, double *partial, const int *gate, cudaStream_t s) {
+    using EI = typename Fmt<PI>::Elem;
+    using EO = typename Fmt<PO>::Elem;
+    if (nl.l16)
+        net_out_kernel<PI, PO, short2, EPI><<<net_grid(g), NET_BLOCK, 0, s>>>(
+            g, nl.l16, nl.scale16, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial, gate);
+    else
+        net_out_kernel<PI, PO, float2, EPI><<<net_grid(g), NET_BLOCK, 0, s>>>(
+            g, nl.l32, 1.f, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial, gate);
+}
+
+// input and output of one precision (the solver's), or FP32 pair input with
+// FP32 output (training)
+cudaError_t launch_net_out(int prec_in, int prec_out, const Geom &g, const NetLinkSet &nl, const NetPath *path,
+                           const float2 *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
+                           double *partial, const int *gate, cudaStream_t s) {
+    if (prec_in != prec_out)
+        return cudaErrorInvalidValue;
+    NP_IN_SWITCH(prec_in, {
+        if (dots)
+            net_out_t<P, P, NET_OUT_DOTS>(g, nl, path, chi, r, rs, z, zs, Ap, partial, gate, s);
+        else
+            net_out_t<P, P, NET_OUT_PLAIN>(g, nl, path, chi, r, rs, z, zs, nullptr, nullptr, gate, s);
+    });
+    return cudaGetLastError();
+}
+
+// ---- training: dL/dC[a][b]* and dL/dc0* ----------------------------------------
+// Per odd site y: h_b = (T_b r)(y), k_a = (T_a^+ g)(y); the block gathers a
+// tile of NET_BLOCK sites in shared memory (site index fastest) and warp w
+// adds the 4 x 4 pairs (a in 4 (w >> 1) .. +3, b in 4 (w & 1) .. +3) of
+// conj(h_b) k_a over the tile; each thread also adds conj(r) g of the even
+// site with its checkerboard index (the c0 term).  One partial per block and
+// pair, in double: partial[blk * 65 + q].
+constexpr int GRAD_BLOCKS = 1024;
+
+__global__ void __launch_bounds__(NET_BLOCK)
+net_grad_kernel(Geom g, const float2 *__restrict__ NL, const float2 *__restrict__ r, int rs,
+                const float2 *__restrict__ gv, int gs, double2 *partial) {
+    static_assert(NET_BLOCK == 128, "four warps: one per 4 x 4 block of hop pairs");
+    __shared__ float2 H[8][3][NET_BLOCK];
+    __shared__ float2 K[8][3][NET_BLOCK];
+    const int S = g.stride;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int a0 = 4 * (warp >> 1), b0 = 4 * (warp & 1);
+    cplx<float> acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            acc[i][j] = czero<float>();
+    cplx<float> acc0 = czero<float>();
+    for (int base = blockIdx.x * NET_BLOCK; base < g.Vh; base += gridDim.x * NET_BLOCK) {
+        const int c = base + threadIdx.x;
+        if (c < g.Vh) {
+            int x[4];
+            cb_coords(g, c, 1, x);
+#pragma unroll
+            for (int mu = 0; mu < 4; mu++) {
+                const int jf = cb_hop(g, c, x, mu, 1), jb = cb_hop(g, c, x, mu, -1);
+                cplx<float> Uf[9], Ub[9], v[3], h[3];
+                nl_load(NL, S, 1, mu, c, Uf);
+                nl_load(NL, S, 0, mu, jb, Ub);
+                // h_{+mu} = Uf r(y+mu), h_{-mu} = Ub^+ r(y-mu)
+                // k_{+mu} = T_{-mu} g = Ub^+ g(y-mu), k_{-mu} = T_{+mu} g = Uf g(y+mu)
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const bool bwd = q & 1;
+                    const float2 *src = q < 2 ? r : gv;
+                    const int st = q < 2 ? rs : gs;
+                    const int j = ((q == 0) || (q == 3)) ? jf : jb;
+                    const bool use_b = (q == 1) || (q == 2);
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        const float2 t = __ldg(src + (size_t)k * st + j);
+                        v[k] = cplx<float>{t.x, t.y};
+                    }
+                    nl_apply(use_b ? Ub : Uf, use_b, v, h);
+                    // q: 0 h_{+mu}, 1 h_{-mu}, 2 k_{+mu}, 3 k_{-mu}
+                    const int idx = 2 * mu + (bwd ? 1 : 0);
+                    float2(*dst)[3][NET_BLOCK] = q < 2 ? H : K;
+#pragma unroll
+                    for (int k = 0; k < 3; k++)
+                        dst[idx][k][threadIdx.x] = make_float2(h[k].re, h[k].im);
+                }
+            }
+            // c0 term on the even site with this checkerboard index
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float2 rv = __ldg(r + (size_t)k * rs + c), gg = __ldg(gv + (size_t)k * gs + c);
+                cmac_conj(acc0, cplx<float>{rv.x, rv.y}, cplx<float>{gg.x, gg.y});
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 8; b++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    H[b][k][threadIdx.x] = make_float2(0.f, 0.f);
+                    K[b][k][threadIdx.x] = make_float2(0.f, 0.f);
+                }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int s = lane; s < NET_BLOCK; s += 32) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                cplx<float> hb[4], ka[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const float2 t = H[b0 + i][k][s];
+                    hb[i] = cplx<float>{t.x, t.y};
+                    const float2 u = K[a0 + i][k][s];
+                    ka[i] = cplx<float>{u.x, u.y};
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        cmac_conj(acc[i][j], hb[j], ka[i]);
+            }
+        }
+        __syncthreads();
+    }
+    // warp sums in double, fixed order; acc[i][j] is the pair (a0 + i, b0 + j)
+    double2 *out = partial + (size_t)blockIdx.x * 65;
+#pragma unroll 1
+    for (int i = 0; i < 4; i++)
+#pragma unroll 1
+        for (int j = 0; j < 4; j++) {
+            double re = acc[i][j].re, im = acc[i][j].im;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_down_sync(0xffffffffu, re, o);
+                im += __shfl_down_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0)
+                out[(a0 + i) * 8 + b0 + j] = make_double2(re, im);
+        }
+    double re0 = acc0.re, im0 = acc0.im;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re0 += __shfl_down_sync(0xffffffffu, re0, o);
+        im0 += __shfl_down_sync(0xffffffffu, im0, o);
+    }
+    // the tile is no longer read (the loop ended with a barrier)
+    double2 *red = reinterpret_cast<double2 *>(&H[0][0][0]);
+    if (lane == 0)
+        red[warp] = make_double2(re0, im0);
+    __syncthreads();
+    if (threadIdx.x == 0)
+        out[64] = make_double2((red[0].x + red[1].x) + (red[2].x + red[3].x),
+                               (red[0].y + red[1].y) + (red[2].y + red[3].y));
+}
+
+// G[q] += sum over blocks of partial[blk * 65 + q], in block order
+__global__ void net_grad_finish_kernel(const double2 *__restrict__ partial, int nblk, double2 *G) {
+    const int q = threadIdx.x;
+    if (q >= 65)
+        return;
+    double2 t = make_double2(0.0, 0.0);
+    for (int b = 0; b < nblk; b++) {
+        const double2 v = partial[(size_t)b * 65 + q];
+        t.x += v.x;
+        t.y += v.y;
+    }
+    G[q].x += t.x;
+    G[q].y += t.y;
+}
+
+int net_grad_blocks(const Geom &g) {
+    const int need = (g.Vh + NET_BLOCK - 1) / NET_BLOCK;
+    return need < GRAD_BLOCKS ? need : GRAD_BLOCKS;
+}
+
+cudaError_t launch_net_grad(const Geom &g, const float2 *NL32, const float2 *r, int rs, const float2 *gv, int gs,
+                            double2 *partial, double2 *G, cudaStream_t s) {
+    const int nb = net_grad_blocks(g);
+    net_grad_kernel<<<nb, NET_BLOCK, 0, s>>>(g, NL32, r, rs, gv, gs, partial);
+    net_grad_finish_kernel<<<1, 96, 0, s>>>(partial, nb, G);
+    return cudaGetLastError();
+}
+
+// ---- losses on the even sites (FP32) -----------------------------------------
+// error loss: g = (z - e) / |e|^2, *loss += |z - e|^2 / |e|^2 (z, g: stride zs;
+// e: stride es)
+__global__ void net_error_loss_kernel(int Vh, const float2 *__restrict__ z, int zs, const float2 *__restrict__ e,
+                                      int es, const double *enorm2, float2 *gv, double *loss) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (c < Vh) {
+        const double n2 = *enorm2;
+        // a pair with e = 0 carries no information: no loss, no gradient
+        const float inv = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float2 zv = z[(size_t)k * zs + c], ev = e[(size_t)k * es + c];
+            const float2 d = make_float2(zv.x - ev.x, zv.y - ev.y);
+            part += (double)d.x * d.x + (double)d.y * d.y;
+            gv[(size_t)k * zs + c] = make_float2(d.x * inv, d.y * inv);
+        }
+        part *= n2 > 0.0 ? 1.0 / n2 : 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part != 0.0)
+        atomicAdd(loss, part);
+}
+
+// residual loss: q = (Mz - r) / |r|^2 written over mz, *loss += |Mz - r|^2 / |r|^2
+__global__ void net_resid_loss_kernel(int Vh, float2 *mz, int ms, const float2 *__restrict__ r, int rs,
+                                      const double *rnorm2, double *loss) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (c < Vh) {
+        const double n2 = *rnorm2;
+        const float inv = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float2 m = mz[(size_t)k * ms + c], rv = r[(size_t)k * rs + c];
+            const float2 q = make_float2(m.x - rv.x, m.y - rv.y);
+            part += (double)q.x * q.x + (double)q.y * q.y;
+            mz[(size_t)k * ms + c] = make_float2(q.x * inv, q.y * inv);
+        }
+        part *= n2 > 0.0 ? 1.0 / n2 : 0.0;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part != 0.0)
+        atomicAdd(loss, part);
+}
+
+// out[0] += Re<a, b>, out[1] += |a|^2 (even FP32 vectors of strides as, bs)
+__global__ void net_dot2_kernel(int Vh, const float2 *__restrict__ a, int as, const float2 *__restrict__ b, int bs,
+                                double *out) {
+    double p0 = 0.0, p1 = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Vh; c += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float2 x = a[(size_t)k * as + c], y = b[(size_t)k * bs + c];
+            p0 += (double)x.x * y.x + (double)x.y * y.y;
+            p1 += (double)x.x * x.x + (double)x.y * x.y;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        p0 += __shfl_down_sync(0xffffffffu, p0, o);
+        p1 += __shfl_down_sync(0xffffffffu, p1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out, p0);
+        atomicAdd(out + 1, p1);
+    }
+}
+
+cudaError_t launch_net_error_loss(int Vh, const float2 *z, int zs, const float2 *e, int es, const double *enorm2,
+                                  float2 *gv, double *loss, cudaStream_t s) {
+    net_error_loss_kernel<<<(Vh + 255) / 256, 256, 0, s>>>(Vh, z, zs, e, es, enorm2, gv, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_resid_loss(int Vh, float2 *mz, int ms, const float2 *r, int rs, const double *rnorm2,
+                                  double *loss, cudaStream_t s) {
+    net_resid_loss_kernel<<<(Vh + 255) / 256, 256, 0, s>>>(Vh, mz, ms, r, rs, rnorm2, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_net_dot2(int Vh, const float2 *a, int as, const float2 *b, int bs, double *out, cudaStream_t s) {
+    net_dot2_kernel<<<256, 256, 0, s>>>(Vh, a, as, b, bs, out);
+    return cudaGetLastError();
+}
+
+// ---- flexible CG ---------------------------------------------------------------
+// After z = N(r) with the partials of Re<z, r> and Re<z, Ap> (net_out_kernel
+// NET_OUT_DOTS or fcg_copy_dots_kernel): beta (Polak-Ribiere,
+// <z_new, r_new - r_old> / <z_old, r_old> with r_new - r_old = -alpha Ap; or
+// Fletcher-Reeves <z_new, r_new> / <z_old, r_old> after a reliable update,
+// where r_new is the recomputed residual; 0 on the first step), rr = <z, r>.
+constexpr int FCG_FINISH = 256;
+
+__global__ void __launch_bounds__(FCG_FINISH)
+fcg_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int first) {
+    __shared__ double smem[32];
+    if (sc->status != CG_RUNNING)
+        return;
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = threadIdx.x; i < n; i += FCG_FINISH) {
+        a0 += partial[i];
+        a1 += partial[n + i];
+    }
+    const double zr = block_sum<FCG_FINISH>(a0, smem);
+    const double zap = block_sum<FCG_FINISH>(a1, smem);
+    if (threadIdx.x == 0) {
+        double beta = 0.0;
+        if (!first)
+            beta = sc->reliable ? zr / sc->rr : -sc->alpha.d * zap / sc->rr;
+        sc->beta = make_dpair(beta);
+        sc->rr = zr;
+        if (!(zr > 0.0 && zr < INFINITY)) {
+            // the preconditioned residual lost positivity
+            sc->status = CG_BREAKDOWN;
+            if (sc->has_cond)
+                cudaGraphSetConditional(sc->cond, 0u);
+        }
+    }
+}
+
+cudaError_t launch_fcg_finish(const double *partial, int n, CgScalars *sc, int first, cudaStream_t s) {
+    fcg_finish_kernel<<<1, FCG_FINISH, 0, s>>>(partial, n, sc, first);
+    return cudaGetLastError();
+}
+
+// z = r with the partials of Re<z, r> and Re<z, Ap> (the flexible CG without
+// the net: plain CG)
+template <int P>
+__global__ void __launch_bounds__(NET_BLOCK)
+fcg_copy_dots_kernel(Geom g, const typename Fmt<P>::Elem *__restrict__ r, typename Fmt<P>::Elem *__restrict__ z,
+                     const typename Fmt<P>::Elem *__restrict__ Ap, double *partial, const int *gate) {
+    using R = typename Fmt<P>::R;
+    __shared__ double smem[32];
+    if (gate && *gate != CG_RUNNING)
+        return;
+    const int c = blockIdx.x * NET_BLOCK + threadIdx.x;
+    red_t<R> d0 = red_zero<red_t<R>>(), d1 = red_zero<red_t<R>>();
+    if (c < g.Vh) {
+        cplx<R> rv[3], av[3];
+        load_vec<P>(r, g.stride, c, rv);
+        store_vec<P>(z, g.stride, c, rv);
+        d0 = re_dot3<R>(rv, rv);
+        if (Ap) {
+            load_vec<P>(Ap, g.stride, c, av);
+            d1 = re_dot3<R>(rv, av);
+        }
+    }
+    const double s0 = block_sum<NET_BLOCK>(d0, smem);
+    const double s1 = block_sum<NET_BLOCK>(d1, smem);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s0;
+        partial[gridDim.x + blockIdx.x] = s1;
+    }
+}
+
+cudaError_t launch_fcg_copy_dots(int prec, const Geom &g, const void *r, void *z, const void *Ap, double *partial,
+                                 const int *gate, cudaStream_t s) {
+    NP_IN_SWITCH(prec, {
+        using E = typename Fmt<P>::Elem;
+        fcg_copy_dots_kernel<P><<<net_grid(g), NET_BLOCK, 0, s>>>(g, (const E *)r, (E *)z, (const E *)Ap, partial,
+                                                                   gate);
+    });
+    return cudaGetLastError();
+}
+
+}  // namespace stag

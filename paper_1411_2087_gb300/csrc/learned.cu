@@ -1,7 +1,10 @@
 // Learned gauge-covariant preconditioner (host side): the net object,
 // training-pair collection from CG, training with the project's own forward
 // and backward kernels and Adam, and the flexible CG that applies the net.
-// Documentation in include/stag.h; the kernels are in kernels_learned.cu.
+// Documentation in include/stag.h.  The net is evaluated and differentiated
+// in its path form (kernels_netpath.cu): its weights are the three layers',
+// and every forward pass first turns them into the 65 coefficients of the
+// two-hop path sum that the layers compose to on even fields.
 #include <algorithm>
 #include <random>
 
@@ -10,21 +13,22 @@
 
 struct stag_net_s {
     stag_lattice lat = nullptr;
-    int C = 8;        // hidden channels: layers 1 -> C -> C -> 1
-    NetGeom ng;
-    float2 *NL = nullptr;         // net links [4][9][V]
+    int C = 8;                    // hidden channels: layers 1 -> C -> C -> 1
+    float2 *NL32 = nullptr;       // net links, FP32 [2][4][9][stride]
+    short2 *NL16 = nullptr;       // the same in 16-bit fixed point
+    float scale16 = 0.f;          // 16-bit value = q * scale16
     int nw = 0;                   // complex weights in all layers
     int off[3] = {0, 0, 0};       // complex offset of each layer's weights
     double *w = nullptr;          // master weights (re, im), device
     float *w32 = nullptr;         // FP32 copy used by the kernels
-    float2 *wt = nullptr;         // adjoint weights of layers 2 and 3 (backward pass)
     double *grad = nullptr, *m = nullptr, *v = nullptr;
     int adam_t = 0;
-    float2 *a0 = nullptr, *a1 = nullptr, *a2 = nullptr, *y = nullptr;  // activations
-    float2 *g1 = nullptr, *g2 = nullptr, *g3 = nullptr;                 // output gradients
-    double2 *wpartial = nullptr;
-    double *scal = nullptr;       // [0] loss accumulator
-    // training pairs: even FP32 [3][Vh] residuals and errors, |e|^2 on the device
+    NetPath *path = nullptr;      // path coefficients of the current weights
+    float2 *chi = nullptr;        // odd-site intermediate [8][3][stride]
+    double2 *G = nullptr;         // dL/dC* (64) and dL/dc0* (1), summed over pairs
+    double2 *gpartial = nullptr;  // per-block partials of G
+    double *scal = nullptr;       // [0] loss accumulator, [1..2] warm-start sums
+    // training pairs: even FP32 [3][Vh] residuals and errors
     std::vector<float2 *> pr, pe;
     std::vector<float2 *> slabs;
     double *enorm2 = nullptr;  // |e_k|^2 per pair
@@ -32,28 +36,23 @@ struct stag_net_s {
     int enorm_cap = 0;
     int loss_kind = STAG_NET_LOSS_ERROR;
     double mass = 0;           // mass of the collected pairs (residual loss)
-    // FP32 solver-layout work vectors of the residual loss: z, Mz / Mq, t (odd)
+    // FP32 solver-layout work vectors of the losses: z, Mz / g, t (odd)
     void *fz = nullptr, *fmz = nullptr, *ft = nullptr;
-    // flexible CG work vectors per precision
-    void *r_old[4] = {};
+    // flexible CG: preconditioned residual per precision
     void *z[4] = {};
 };
 
 static void net_free(stag_net n) {
-    void *bufs[] = {n->NL, n->w, n->w32, n->wt, n->grad, n->m, n->v, n->a0, n->a1, n->a2, n->y,
-                    n->g1, n->g2, n->g3, n->wpartial, n->scal, n->enorm2, n->rnorm2,
-                    n->fz, n->fmz, n->ft};
+    void *bufs[] = {n->NL32, n->NL16, n->w, n->w32, n->grad, n->m, n->v, n->path, n->chi, n->G, n->gpartial,
+                    n->scal, n->enorm2, n->rnorm2, n->fz, n->fmz, n->ft};
     for (void *b : bufs)
         if (b)
             cudaFree(b);
     for (float2 *p : n->slabs)
         cudaFree(p);
-    for (int q = 0; q < 4; q++) {
-        if (n->r_old[q])
-            cudaFree(n->r_old[q]);
+    for (int q = 0; q < 4; q++)
         if (n->z[q])
             cudaFree(n->z[q]);
-    }
 }
 
 extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind, int channels, unsigned seed,
@@ -73,19 +72,13 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
         return fail(STAG_ERR_NOMEM, "stag_net_create: host allocation failed");
     n->lat = lat;
     n->C = channels;
-    for (int k = 0; k < 4; k++)
-        n->ng.L[k] = lat->dims[k];
-    n->ng.V = (int)lat->V;
-    n->ng.step[0] = 1;
-    n->ng.step[1] = lat->dims[0];
-    n->ng.step[2] = lat->dims[0] * lat->dims[1];
-    n->ng.step[3] = lat->dims[0] * lat->dims[1] * lat->dims[2];
     const int C = channels;
     n->off[0] = 0;
     n->off[1] = 9 * C;
     n->off[2] = 9 * C + 9 * C * C;
     n->nw = 9 * C + 9 * C * C + 9 * C;
     const size_t V = (size_t)lat->V;
+    const size_t S = (size_t)lat->geom.stride;
     cudaStream_t s = lat->stream;
     auto bail = [&](cudaError_t e) {
         cudaStreamSynchronize(s);
@@ -98,23 +91,34 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
     if (ptr_kind == STAG_PTR_DEVICE && (e = cudaDeviceSynchronize()) != cudaSuccess)
         return bail(e);
     const size_t nr = 2 * (size_t)n->nw;
-    if ((e = cudaMalloc(&n->NL, sizeof(float2) * 36 * V)) != cudaSuccess ||
+    if ((e = cudaMalloc(&n->NL32, sizeof(float2) * 2 * 4 * 9 * S)) != cudaSuccess ||
+        (e = cudaMalloc(&n->NL16, sizeof(short2) * 2 * 4 * 9 * S)) != cudaSuccess ||
         (e = cudaMalloc(&n->w, sizeof(double) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&n->w32, sizeof(float) * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&n->wt, sizeof(float2) * n->nw)) != cudaSuccess ||
         (e = cudaMalloc(&n->grad, sizeof(double) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&n->m, sizeof(double) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&n->v, sizeof(double) * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&n->a0, sizeof(float2) * 3 * V)) != cudaSuccess ||
-        (e = cudaMalloc(&n->a1, sizeof(float2) * 3 * V * C)) != cudaSuccess ||
-        (e = cudaMalloc(&n->a2, sizeof(float2) * 3 * V * C)) != cudaSuccess ||
-        (e = cudaMalloc(&n->y, sizeof(float2) * 3 * V)) != cudaSuccess ||
-        (e = cudaMalloc(&n->g1, sizeof(float2) * 3 * V * C)) != cudaSuccess ||
-        (e = cudaMalloc(&n->g2, sizeof(float2) * 3 * V * C)) != cudaSuccess ||
-        (e = cudaMalloc(&n->g3, sizeof(float2) * 3 * V)) != cudaSuccess ||
-        (e = cudaMalloc(&n->wpartial, sizeof(double2) * wgrad_partial_blocks() * 9 * C * C)) != cudaSuccess ||
+        (e = cudaMalloc(&n->path, sizeof(NetPath))) != cudaSuccess ||
+        (e = cudaMalloc(&n->chi, sizeof(float2) * 8 * 3 * S)) != cudaSuccess ||
+        (e = cudaMalloc(&n->G, sizeof(double2) * 65)) != cudaSuccess ||
+        (e = cudaMalloc(&n->gpartial, sizeof(double2) * 65 * net_grad_blocks(lat->geom))) != cudaSuccess ||
         (e = cudaMalloc(&n->scal, sizeof(double) * 4)) != cudaSuccess)
         return bail(e);
+    // the padding sites of the link planes are never read; zero them anyway
+    if ((e = cudaMemsetAsync(n->NL32, 0, sizeof(float2) * 2 * 4 * 9 * S, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(n->NL16, 0, sizeof(short2) * 2 * 4 * 9 * S, s)) != cudaSuccess)
+        return bail(e);
+    {
+        int st = alloc_vec(lat, STAG_F32, &n->fz);
+        if (st == STAG_OK)
+            st = alloc_vec(lat, STAG_F32, &n->fmz);
+        if (st != STAG_OK) {
+            cudaStreamSynchronize(s);
+            net_free(n);
+            delete n;
+            return st;
+        }
+    }
     // net links from the raw fat links
     double *fat_d = (double *)fat;
     bool owned = false;
@@ -128,7 +132,28 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
             return bail(e);
         }
     }
-    e = launch_net_links(n->ng, lat->bc, fat_d, n->NL, s);
+    // the 16-bit copy's scale: the largest |re| or |im| of the field
+    unsigned *amax_d = (unsigned *)(n->scal + 3);
+    e = launch_absmax(fat_d, (long long)(4 * V * 18), amax_d, s);
+    float amax = 0.f;
+    if (e == cudaSuccess) {
+        unsigned bits = 0;
+        e = cudaMemcpyAsync(&bits, amax_d, sizeof bits, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        memcpy(&amax, &bits, sizeof amax);
+    }
+    if (e == cudaSuccess && !(amax < INFINITY)) {
+        if (owned)
+            cudaFree(fat_d);
+        cudaStreamSynchronize(s);
+        net_free(n);
+        delete n;
+        return fail(STAG_ERR_ARG, "stag_net_create: links hold a NaN, an infinity or an entry beyond FP32");
+    }
+    n->scale16 = amax > 0.f ? amax / kQ16 : 1.f;
+    if (e == cudaSuccess)
+        e = launch_net_links_cb(lat->geom, lat->bc, fat_d, n->NL32, n->NL16, amax > 0.f ? kQ16 / amax : 0.f, s);
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (owned)
         cudaFree(fat_d);
@@ -189,6 +214,7 @@ extern "C" int stag_net_set_weights(stag_net n, const double *w) {
         if (!std::isfinite(w[k]))
             return fail(STAG_ERR_ARG, "stag_net_set_weights: weight %zu is not finite", k);
     std::vector<float> w32(w, w + nr);
+    CUDA_TRY(cudaStreamSynchronize(n->lat->stream));
     CUDA_TRY(cudaMemcpy(n->w, w, sizeof(double) * nr, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(n->w32, w32.data(), sizeof(float) * nr, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemset(n->m, 0, sizeof(double) * nr));
@@ -201,48 +227,40 @@ extern "C" int stag_net_get_weights(const stag_net n, double *w) {
     if (!n || !w)
         return fail(STAG_ERR_ARG, "stag_net_get_weights: NULL argument");
     DEVICE_SCOPE(n->lat->device);
+    CUDA_TRY(cudaStreamSynchronize(n->lat->stream));
     CUDA_TRY(cudaMemcpy(w, n->w, sizeof(double) * 2 * n->nw, cudaMemcpyDeviceToHost));
     return STAG_OK;
 }
 
-static const float2 *wl(const stag_net n, int layer) { return (const float2 *)n->w32 + n->off[layer]; }
-
-// y = net(a0) through the three layers (a0 must already hold the input,
-// zero on odd sites).  even_out: only the even sites of y are computed (all
-// a preconditioner needs).
-static cudaError_t net_forward(stag_net n, int round_half, const int *gate, cudaStream_t s, bool even_out = false) {
-    cudaError_t e;
-    const int C = n->C;
-    if ((e = launch_covconv(1, C, n->ng, n->NL, wl(n, 0), round_half, n->a0, n->a1, gate, s, 0, -1)) != cudaSuccess)
-        return e;
-    if ((e = launch_covconv(C, C, n->ng, n->NL, wl(n, 1), round_half, n->a1, n->a2, gate, s)) != cudaSuccess)
-        return e;
-    return launch_covconv(C, 1, n->ng, n->NL, wl(n, 2), round_half, n->a2, n->y, gate, s, -1, even_out ? 0 : -1);
+// ---- applying the net ------------------------------------------------------
+static NetLinkSet net_links(const stag_net n, bool links16) {
+    NetLinkSet s;
+    s.l32 = n->NL32;
+    if (links16) {
+        s.l16 = n->NL16;
+        s.scale16 = n->scale16;
+    }
+    return s;
 }
 
-// dL/dW* += gradient of the loss of one pair whose output gradient is in g3
-static cudaError_t net_backward(stag_net n, cudaStream_t s) {
-    cudaError_t e;
-    const int C = n->C;
-    double2 *gr = (double2 *)n->grad;
-    // adjoint weights of layers 3 and 2
-    float2 *wt3 = n->wt + n->off[2];
-    float2 *wt2 = n->wt + n->off[1];
-    if ((e = launch_net_adjoint(C, 1, wl(n, 2), wt3, s)) != cudaSuccess ||
-        (e = launch_net_adjoint(C, C, wl(n, 1), wt2, s)) != cudaSuccess)
-        return e;
-    if ((e = launch_covconv_wgrad(C, 1, n->ng, n->NL, n->a2, n->g3, n->wpartial, gr + n->off[2], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_covconv(1, C, n->ng, n->NL, wt3, 0, n->g3, n->g2, nullptr, s)) != cudaSuccess)
-        return e;
-    if ((e = launch_covconv_wgrad(C, C, n->ng, n->NL, n->a1, n->g2, n->wpartial, gr + n->off[1], s)) != cudaSuccess)
-        return e;
-    if ((e = launch_covconv(C, C, n->ng, n->NL, wt2, 0, n->g2, n->g1, nullptr, s)) != cudaSuccess)
-        return e;
-    return launch_covconv_wgrad(1, C, n->ng, n->NL, n->a0, n->g1, n->wpartial, gr + n->off[0], s);
+// the path coefficients of the current weights (round_half: binary16 weights)
+static cudaError_t net_coefficients(stag_net n, int round_half, cudaStream_t s) {
+    return launch_net_path_coef(n->C, n->w32, n->off, round_half, n->path, s);
 }
 
-// ---- applying the net to solver fields --------------------------------
+// z = N(r) on even vectors with the coefficients in n->path: r of precision
+// prec_in and component stride rs, z of prec_out and stride zs; dots: the
+// partials of Re<z, r>, Re<z, Ap> for the flexible CG
+static cudaError_t net_apply_path(stag_net n, int prec, const void *r, int rs, void *z, int zs, bool links16,
+                                  bool dots, const void *Ap, const int *gate, cudaStream_t s) {
+    stag_lattice lat = n->lat;
+    const NetLinkSet nl = net_links(n, links16);
+    cudaError_t e = launch_net_mid(prec, lat->geom, nl, n->path, r, rs, n->chi, gate, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_net_out(prec, prec, lat->geom, nl, n->path, n->chi, r, rs, z, zs, dots, Ap, lat->partial, gate, s);
+}
+
 static int check_net_field(const stag_net n, const stag_field f, const char *who) {
     if (!f || f->lat != n->lat || f->parity != STAG_EVEN)
         return fail(STAG_ERR_ARG, "%s: fields must be even fields of the net's lattice", who);
@@ -251,17 +269,7 @@ static int check_net_field(const stag_net n, const stag_field f, const char *who
     return STAG_OK;
 }
 
-static cudaError_t net_apply_raw(stag_net n, int prec, const void *in, void *out, int round_half, const int *gate,
-                                 cudaStream_t s) {
-    cudaError_t e;
-    if ((e = launch_solver_to_full(prec, n->ng, n->lat->geom, in, n->a0, gate, s)) != cudaSuccess)
-        return e;
-    if ((e = net_forward(n, round_half, gate, s, true)) != cudaSuccess)
-        return e;
-    return launch_full_to_solver(prec, n->ng, n->lat->geom, n->y, out, gate, s);
-}
-
-extern "C" int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int fp16_weights) {
+extern "C" int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int flags) {
     STAG_NVTX("stag_net_apply");
     if (!n)
         return fail(STAG_ERR_ARG, "stag_net_apply: NULL net");
@@ -269,9 +277,16 @@ extern "C" int stag_net_apply(stag_net n, stag_field out_even, const stag_field 
     STAG_TRY(check_net_field(n, in_even, "stag_net_apply"));
     if (out_even->prec != in_even->prec)
         return fail(STAG_ERR_ARG, "stag_net_apply: precision mismatch");
+    if (out_even == in_even)
+        return fail(STAG_ERR_ARG, "stag_net_apply: in and out must differ");
+    if (flags & ~(STAG_NET_FP16_WEIGHTS | STAG_NET_LINKS16))
+        return fail(STAG_ERR_ARG, "stag_net_apply: unknown flags 0x%x", flags);
     DEVICE_SCOPE(n->lat->device);
-    CUDA_TRY(net_apply_raw(n, in_even->prec, in_even->data, out_even->data, fp16_weights ? 1 : 0, nullptr,
-                           n->lat->stream));
+    cudaStream_t s = n->lat->stream;
+    const int S = n->lat->geom.stride;
+    CUDA_TRY(net_coefficients(n, (flags & STAG_NET_FP16_WEIGHTS) ? 1 : 0, s));
+    CUDA_TRY(net_apply_path(n, in_even->prec, in_even->data, S, out_even->data, S, (flags & STAG_NET_LINKS16) != 0,
+                            false, nullptr, nullptr, s));
     return STAG_OK;
 }
 
@@ -296,6 +311,7 @@ static int refresh_enorms(stag_net n) {
         if (n->rnorm2)
             cudaFree(n->rnorm2);
         n->enorm2 = n->rnorm2 = nullptr;
+        n->enorm_cap = 0;
         CUDA_TRY(cudaMalloc(&n->enorm2, sizeof(double) * np));
         CUDA_TRY(cudaMalloc(&n->rnorm2, sizeof(double) * np));
         n->enorm_cap = np;
@@ -307,38 +323,6 @@ static int refresh_enorms(stag_net n) {
         CUDA_TRY(launch_pair_norm2((int)(3 * n->lat->Vh), n->pe[k], n->enorm2 + k, s));
         CUDA_TRY(launch_pair_norm2((int)(3 * n->lat->Vh), n->pr[k], n->rnorm2 + k, s));
     }
-    return STAG_OK;
-}
-
-// y holds N(r) (full); g3 <- gradient of |M z - r|^2 / |r|^2 with respect to
-// conj(y), z = y on even sites: M (M z - r) / |r|^2 (M Hermitian), FP32
-static int resid_loss_grad(stag_net n, int p, cudaStream_t s) {
-    stag_lattice lat = n->lat;
-    const int P = STAG_F32;
-    const Geom &g = lat->geom;
-    CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->y, n->fz, nullptr, s));
-    // Mz
-    DslashArgs a1 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
-    CUDA_TRY(launch_dslash(P, EPI_NONE, a1, lat->dslash_block[P], s));
-    DslashArgs a2 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
-    a2.p = n->fz;
-    a2.m2 = make_dpair(n->mass * n->mass);
-    a2.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(P, EPI_M, a2, lat->dslash_block[P], s));
-    CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
-    // q = Mz - r (into g3), loss
-    CUDA_TRY(launch_resid_loss(n->ng, n->g3, n->a0, n->rnorm2 + p, n->scal, s));
-    // M q / |r|^2
-    CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->g3, n->fz, nullptr, s));
-    DslashArgs a3 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
-    CUDA_TRY(launch_dslash(P, EPI_NONE, a3, lat->dslash_block[P], s));
-    DslashArgs a4 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
-    a4.p = n->fz;
-    a4.m2 = make_dpair(n->mass * n->mass);
-    a4.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(P, EPI_M, a4, lat->dslash_block[P], s));
-    CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
-    CUDA_TRY(launch_scale_full(n->ng, n->g3, n->rnorm2 + p, s));
     return STAG_OK;
 }
 
@@ -428,6 +412,7 @@ extern "C" int stag_net_get_pair(const stag_net n, int k, double *r, double *e) 
     DEVICE_SCOPE(n->lat->device);
     const size_t Vh = (size_t)n->lat->Vh;
     std::vector<float2> h(3 * Vh);
+    CUDA_TRY(cudaStreamSynchronize(n->lat->stream));
     for (int which = 0; which < 2; which++) {
         CUDA_TRY(cudaMemcpy(h.data(), which ? n->pe[k] : n->pr[k], sizeof(float2) * 3 * Vh, cudaMemcpyDeviceToHost));
         double *dst = which ? e : r;
@@ -450,8 +435,6 @@ extern "C" int stag_net_set_loss(stag_net n, int kind) {
         if (!lat->has_gauge || !lat->links[STAG_F32])
             return fail(STAG_ERR_STATE, "stag_net_set_loss: the residual loss needs an F32 gauge copy");
         DEVICE_SCOPE(lat->device);
-        STAG_TRY(alloc_vec(lat, STAG_F32, &n->fz));
-        STAG_TRY(alloc_vec(lat, STAG_F32, &n->fmz));
         STAG_TRY(alloc_vec(lat, STAG_F32, &n->ft));
     }
     n->loss_kind = kind;
@@ -466,21 +449,54 @@ extern "C" int stag_net_num_pairs(const stag_net n, int *count) {
 }
 
 // ---- training -------------------------------------------------------------
-// loss and dL/dW* summed over pairs [first, first + count)
+// out = M in = m^2 in - D_eo D_oe in on FP32 solver-layout vectors (t: odd)
+static int apply_M_f32(stag_net n, const void *in, void *t, void *out, cudaStream_t s) {
+    stag_lattice lat = n->lat;
+    const int P = STAG_F32;
+    DslashArgs a1 = dslash_args(lat, P, STAG_ODD, in, t);
+    CUDA_TRY(launch_dslash(P, EPI_NONE, a1, lat->dslash_block[P], s));
+    DslashArgs a2 = dslash_args(lat, P, STAG_EVEN, t, out);
+    a2.p = in;
+    a2.m2 = make_dpair(n->mass * n->mass);
+    a2.m2_in_args = 1;
+    CUDA_TRY(launch_dslash(P, EPI_M, a2, lat->dslash_block[P], s));
+    return STAG_OK;
+}
+
+// loss of pair p added to scal[0] and its dL/dC*, dL/dc0* to G; the path
+// coefficients must be current.  z = N(r) -> fz; then the output gradient g:
+//   error loss:    g = (z - e) / |e|^2                  -> fmz
+//   residual loss: q = (M z - r) / |r|^2 -> fmz, g = M q -> fz (M Hermitian)
+static int pair_loss_grad(stag_net n, int p, cudaStream_t s) {
+    stag_lattice lat = n->lat;
+    const Geom &g = lat->geom;
+    const int S = g.stride, Vh = g.Vh;
+    CUDA_TRY(net_apply_path(n, STAG_F32, n->pr[p], Vh, n->fz, S, false, false, nullptr, nullptr, s));
+    const float2 *gv;
+    if (n->loss_kind == STAG_NET_LOSS_RESIDUAL) {
+        STAG_TRY(apply_M_f32(n, n->fz, n->ft, n->fmz, s));
+        CUDA_TRY(launch_net_resid_loss(Vh, (float2 *)n->fmz, S, n->pr[p], Vh, n->rnorm2 + p, n->scal, s));
+        STAG_TRY(apply_M_f32(n, n->fmz, n->ft, n->fz, s));
+        gv = (const float2 *)n->fz;
+    } else {
+        CUDA_TRY(launch_net_error_loss(Vh, (const float2 *)n->fz, S, n->pe[p], Vh, n->enorm2 + p, (float2 *)n->fmz,
+                                       n->scal, s));
+        gv = (const float2 *)n->fmz;
+    }
+    CUDA_TRY(launch_net_grad(g, n->NL32, n->pr[p], Vh, gv, S, n->gpartial, n->G, s));
+    return STAG_OK;
+}
+
+// loss and dL/dW* summed over the pairs idx[0..count)
 static int loss_grad_range(stag_net n, const int *idx, int count, double *loss) {
     cudaStream_t s = n->lat->stream;
     CUDA_TRY(cudaMemsetAsync(n->grad, 0, sizeof(double) * 2 * n->nw, s));
+    CUDA_TRY(cudaMemsetAsync(n->G, 0, sizeof(double2) * 65, s));
     CUDA_TRY(cudaMemsetAsync(n->scal, 0, sizeof(double), s));
-    for (int k = 0; k < count; k++) {
-        const int p = idx[k];
-        CUDA_TRY(launch_pair_to_full(n->ng, n->pr[p], n->a0, s));
-        CUDA_TRY(net_forward(n, 0, nullptr, s));
-        if (n->loss_kind == STAG_NET_LOSS_RESIDUAL)
-            STAG_TRY(resid_loss_grad(n, p, s));
-        else
-            CUDA_TRY(launch_pair_loss(n->ng, n->y, n->pe[p], n->enorm2 + p, n->g3, n->scal, s));
-        CUDA_TRY(net_backward(n, s));
-    }
+    CUDA_TRY(net_coefficients(n, 0, s));
+    for (int k = 0; k < count; k++)
+        STAG_TRY(pair_loss_grad(n, idx[k], s));
+    CUDA_TRY(launch_net_path_chain(n->C, n->w32, n->off, n->G, (double2 *)n->grad, s));
     if (loss) {
         CUDA_TRY(cudaMemcpyAsync(loss, n->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -513,22 +529,13 @@ extern "C" int stag_net_loss_grad(stag_net n, int first, int count, double *loss
 static int residual_warm_start(stag_net n) {
     stag_lattice lat = n->lat;
     cudaStream_t s = lat->stream;
-    const int P = STAG_F32;
-    const Geom &g = lat->geom;
+    const int S = lat->geom.stride, Vh = lat->geom.Vh;
     CUDA_TRY(cudaMemsetAsync(n->scal + 1, 0, 2 * sizeof(double), s));
+    CUDA_TRY(net_coefficients(n, 0, s));
     for (size_t p = 0; p < n->pr.size(); p++) {
-        CUDA_TRY(launch_pair_to_full(n->ng, n->pr[p], n->a0, s));
-        CUDA_TRY(net_forward(n, 0, nullptr, s));
-        CUDA_TRY(launch_full_to_solver(P, n->ng, g, n->y, n->fz, nullptr, s));
-        DslashArgs a1 = dslash_args(lat, P, STAG_ODD, n->fz, n->ft);
-        CUDA_TRY(launch_dslash(P, EPI_NONE, a1, lat->dslash_block[P], s));
-        DslashArgs a2 = dslash_args(lat, P, STAG_EVEN, n->ft, n->fmz);
-        a2.p = n->fz;
-        a2.m2 = make_dpair(n->mass * n->mass);
-        a2.m2_in_args = 1;
-        CUDA_TRY(launch_dslash(P, EPI_M, a2, lat->dslash_block[P], s));
-        CUDA_TRY(launch_solver_to_full(P, n->ng, g, n->fmz, n->g3, nullptr, s));
-        CUDA_TRY(launch_dot2_full(3 * n->ng.V, n->g3, n->a0, n->scal + 1, s));
+        CUDA_TRY(net_apply_path(n, STAG_F32, n->pr[p], Vh, n->fz, S, false, false, nullptr, nullptr, s));
+        STAG_TRY(apply_M_f32(n, n->fz, n->ft, n->fmz, s));
+        CUDA_TRY(launch_net_dot2(Vh, (const float2 *)n->fmz, S, n->pr[p], Vh, n->scal + 1, s));
     }
     double h[2];
     CUDA_TRY(cudaMemcpyAsync(h, n->scal + 1, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -585,12 +592,17 @@ static const int *status_flag(stag_lattice lat) {
     return (const int *)((const char *)lat->sc + offsetof(CgScalars, status));
 }
 
-// enqueue z = N(r) (or z = r without the net)
-static cudaError_t precondition(stag_net n, int prec, bool use_net, const void *r, void *z, const int *gate,
-                                cudaStream_t s) {
-    if (use_net)
-        return net_apply_raw(n, prec, r, z, 1, gate, s);
-    return cudaMemcpyAsync(z, r, field_bytes(n->lat, prec), cudaMemcpyDeviceToDevice, s);
+// z = N(r) (or z = r without the net) with the partials of Re<z, r> and
+// Re<z, Ap> (Ap may be NULL), then beta and <z, r> in the scalars
+static cudaError_t precondition(stag_net n, int prec, bool use_net, const void *r, void *z, const void *Ap,
+                                int first, const int *gate, cudaStream_t s) {
+    stag_lattice lat = n->lat;
+    const int S = lat->geom.stride;
+    cudaError_t e = use_net ? net_apply_path(n, prec, r, S, z, S, true, true, Ap, gate, s)
+                            : launch_fcg_copy_dots(prec, lat->geom, r, z, Ap, lat->partial, gate, s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_fcg_finish(lat->partial, net_grid(lat->geom), lat->sc, first, s);
 }
 
 // one run of flexible CG from the current x (r = b - M x recomputed):
@@ -620,8 +632,7 @@ static int fcg_run(stag_net n, int prec, bool use_net, double mass, double tol2b
     a2.b = w.bw;
     CUDA_TRY(launch_dslash(prec, EPI_RESID_STORE, a2, lat->dslash_block[prec], s));
     // z = N(r); rr = <z, r>; p = z
-    CUDA_TRY(precondition(n, prec, use_net, w.r, n->z[prec], gate, s));
-    CUDA_TRY(launch_fcg_beta(prec, g, n->z[prec], w.r, nullptr, lat->partial, lat->sc, 1, s));
+    CUDA_TRY(precondition(n, prec, use_net, w.r, n->z[prec], nullptr, 1, gate, s));
     CUDA_TRY(cudaMemcpyAsync(w.p, n->z[prec], field_bytes(lat, prec), cudaMemcpyDeviceToDevice, s));
     const long long max_chunks = (long long)max_iter / chunk + 2;
     for (long long k = 0; k < max_chunks; k++) {
@@ -635,9 +646,10 @@ static int fcg_run(stag_net n, int prec, bool use_net, double mass, double tol2b
             b1.skip_if_done = 1;
             CUDA_TRY(launch_dslash(prec, EPI_NONE, b1, lat->dslash_block[prec], s));
             CUDA_TRY(enqueue_m_pap(lat, prec, w.t, w.Ap, w.p, true, s));
-            CUDA_TRY(launch_fcg_update(prec, g, w.xw, w.r, n->r_old[prec], w.p, w.Ap, lat->partial, lat->sc, s));
-            CUDA_TRY(precondition(n, prec, use_net, w.r, n->z[prec], gate, s));
-            CUDA_TRY(launch_fcg_beta(prec, g, n->z[prec], w.r, n->r_old[prec], lat->partial, lat->sc, 0, s));
+            // x += alpha p, r -= alpha Ap, |r|^2 and the stopping test
+            CUDA_TRY(launch_fcg_update(prec, g, w.xw, w.r, w.p, w.Ap, lat->partial, lat->sc, s));
+            // z = N(r), beta = -alpha <z, Ap> / <z_old, r_old>, p = z + beta p
+            CUDA_TRY(precondition(n, prec, use_net, w.r, n->z[prec], w.Ap, 0, gate, s));
             CUDA_TRY(launch_cg_p_update(prec, g, n->z[prec], w.p, lat->sc, s));
         }
     }
@@ -670,12 +682,13 @@ extern "C" int stag_cg_solve_learned(stag_net n, stag_field x, const stag_field 
     DEVICE_SCOPE(lat->device);
     const auto t0 = std::chrono::steady_clock::now();
     STAG_TRY(ensure_cg_work(lat, prec));
-    STAG_TRY(alloc_vec(lat, prec, &n->r_old[prec]));
     STAG_TRY(alloc_vec(lat, prec, &n->z[prec]));
     CgWork &w = lat->cg[prec];
     cudaStream_t s = lat->stream;
     CUDA_TRY(cudaMemcpyAsync(w.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemsetAsync(w.xw, 0, field_bytes(lat, prec), s));
+    // the deployed preconditioner: binary16 weights, 16-bit links
+    CUDA_TRY(net_coefficients(n, 1, s));
     // |b|^2: the residual of x = 0
     double bb = 0;
     STAG_TRY(shifted_residual(lat, prec, w.xw, w.bw, mass, nullptr, &bb));
@@ -692,7 +705,7 @@ extern "C" int stag_cg_solve_learned(stag_net n, stag_field x, const stag_field 
         int it = 0;
         bool use_net = true;
         for (int attempt = 0; attempt < 4 && iters <= max_iter; attempt++) {
-            status = fcg_run(n, prec, use_net, mass, tol2bb, max_iter - iters, use_net ? 8 : 32, &it, &rr);
+            status = fcg_run(n, prec, use_net, mass, tol2bb, max_iter - iters, use_net ? 16 : 32, &it, &rr);
             if (status < 0)
                 return status;
             iters += it;

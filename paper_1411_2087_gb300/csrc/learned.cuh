@@ -1,45 +1,60 @@
 // Shared declarations of the learned preconditioner (kernels_learned.cu,
-// learned.cu): full-lattice geometry and kernel launchers.
+// kernels_netpath.cu, learned.cu): path coefficients, link sets and kernel
+// launchers.
 #pragma once
 #include "dslash.cuh"
 
 namespace stag {
 
-struct NetGeom {
-    int L[4];
-    int V;        // sites of the full lattice
-    int step[4];  // lexicographic index step of one hop: 1, Lx, Lx*Ly, Lx*Ly*Lz
+// The net's action on even fields as a two-hop path sum (kernels_netpath.cu):
+// z = c0 r + sum_{a,b} C[a*8+b] T_a T_b r, hop index 2 mu (+mu) or 2 mu + 1 (-mu)
+struct NetPath {
+    float2 C[64];
+    float2 c0;
 };
 
-// in_par / out_par: parity where the input is non-zero / of the outputs
-// needed (-1: all sites)
-cudaError_t launch_covconv(int cin, int cout, const NetGeom &g, const float2 *NL, const float2 *W, int round_half,
-                           const float2 *in, float2 *out, const int *gate, cudaStream_t s, int in_par = -1,
-                           int out_par = -1);
-cudaError_t launch_covconv_wgrad(int cin, int cout, const NetGeom &g, const float2 *NL, const float2 *in,
-                                 const float2 *gout, double2 *partial, double2 *grad, cudaStream_t s);
-int wgrad_partial_blocks();
-cudaError_t launch_pair_to_full(const NetGeom &g, const float2 *ev, float2 *full, cudaStream_t s);
-cudaError_t launch_pair_loss(const NetGeom &g, const float2 *y, const float2 *e, const double *enorm2,
-                             float2 *gout, double *loss, cudaStream_t s);
+// the net's link copies: FP32, and optionally 16-bit (used when l16 is set)
+struct NetLinkSet {
+    const float2 *l32 = nullptr;
+    const short2 *l16 = nullptr;
+    float scale16 = 0.f;  // 16-bit value = q * scale16
+};
+
+cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double *fat, float2 *NL32, short2 *NL16,
+                                float inv_scale16, cudaStream_t s);
+cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int round_half, NetPath *out,
+                                 cudaStream_t s);
+cudaError_t launch_net_path_chain(int C, const float *w32, const int off[3], const double2 *G, double2 *grad,
+                                  cudaStream_t s);
+// chi [8][3][stride] (odd sites) from the even input r (precision prec, stride rs)
+cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const NetPath *path, const void *r,
+                           int rs, float2 *chi, const int *gate, cudaStream_t s);
+// z = c0 r + sum_a T_a chi_a (even); dots adds the per-block partials of
+// Re<z, r> and Re<z, Ap> (0 without Ap): 2 * net_grid doubles
+cudaError_t launch_net_out(int prec_in, int prec_out, const Geom &g, const NetLinkSet &nl, const NetPath *path,
+                           const float2 *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
+                           double *partial, const int *gate, cudaStream_t s);
+int net_grid(const Geom &g);
+int net_grad_blocks(const Geom &g);
+// G[0..63] += dL/dC*, G[64] += dL/dc0* for input r and output gradient g (FP32)
+cudaError_t launch_net_grad(const Geom &g, const float2 *NL32, const float2 *r, int rs, const float2 *gv, int gs,
+                            double2 *partial, double2 *G, cudaStream_t s);
+cudaError_t launch_net_error_loss(int Vh, const float2 *z, int zs, const float2 *e, int es, const double *enorm2,
+                                  float2 *gv, double *loss, cudaStream_t s);
+cudaError_t launch_net_resid_loss(int Vh, float2 *mz, int ms, const float2 *r, int rs, const double *rnorm2,
+                                  double *loss, cudaStream_t s);
+cudaError_t launch_net_dot2(int Vh, const float2 *a, int as, const float2 *b, int bs, double *out, cudaStream_t s);
+cudaError_t launch_fcg_finish(const double *partial, int n, CgScalars *sc, int first, cudaStream_t s);
+cudaError_t launch_fcg_copy_dots(int prec, const Geom &g, const void *r, void *z, const void *Ap, double *partial,
+                                 const int *gate, cudaStream_t s);
+
+// kernels_learned.cu
 cudaError_t launch_pair_norm2(int n, const float2 *v, double *out, cudaStream_t s);
 cudaError_t launch_adam(int n, double *w, const double *grad, double *m, double *v, double lr, int t, float *w32,
                         cudaStream_t s);
-cudaError_t launch_solver_to_full(int prec, const NetGeom &g, const Geom &sg, const void *f, float2 *full,
-                                  const int *gate, cudaStream_t s);
-cudaError_t launch_full_to_solver(int prec, const NetGeom &g, const Geom &sg, const float2 *full, void *f,
-                                  const int *gate, cudaStream_t s);
 cudaError_t launch_solver_to_pair(int prec, const Geom &sg, const void *f, const void *sub, float2 *pair,
                                   cudaStream_t s);
-cudaError_t launch_fcg_update(int prec, const Geom &g, void *x, void *r, void *r_old, const void *p,
-                              const void *Ap, double *partial, CgScalars *sc, cudaStream_t s);
-cudaError_t launch_fcg_beta(int prec, const Geom &g, const void *z, const void *r, const void *r_old,
-                            double *partial, CgScalars *sc, int first, cudaStream_t s);
-cudaError_t launch_resid_loss(const NetGeom &g, float2 *mz, const float2 *r, const double *rnorm2, double *loss,
-                              cudaStream_t s);
-cudaError_t launch_dot2_full(int n, const float2 *a, const float2 *b, double *out, cudaStream_t s);
-cudaError_t launch_scale_full(const NetGeom &g, float2 *v, const double *n2, cudaStream_t s);
-cudaError_t launch_net_links(const NetGeom &g, const double bc[4], const double *fat, float2 *NL, cudaStream_t s);
-cudaError_t launch_net_adjoint(int cin, int cout, const float2 *W, float2 *WT, cudaStream_t s);
+cudaError_t launch_fcg_update(int prec, const Geom &g, void *x, void *r, const void *p, const void *Ap,
+                              double *partial, CgScalars *sc, cudaStream_t s);
 
 }  // namespace stag

@@ -35,6 +35,7 @@ F64, F32, F16, DF64 = 0, 1, 2, 3
 PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
 COMPRESS12 = 1 << 16
 EVEN, ODD = 0, 1
+NET_FP16_WEIGHTS, NET_LINKS16 = 1, 2
 CG_LAUNCH_GRAPH, CG_LAUNCH_HOST = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 
@@ -543,8 +544,10 @@ class Net:
         """'error' (|N r - e|^2/|e|^2) or 'residual' (|M N r - r|^2/|r|^2)."""
         _check(lib().stag_net_set_loss(self.handle, {"error": 0, "residual": 1}[kind]))
 
-    def apply(self, out: Field, inp: Field, fp16_weights: bool = False):
-        _check(lib().stag_net_apply(self.handle, out.handle, inp.handle, int(bool(fp16_weights))))
+    def apply(self, out: Field, inp: Field, fp16_weights: bool = False, links16: bool = False):
+        """out = N(inp); fp16_weights and links16 together are the solver's form."""
+        flags = (NET_FP16_WEIGHTS if fp16_weights else 0) | (NET_LINKS16 if links16 else 0)
+        _check(lib().stag_net_apply(self.handle, out.handle, inp.handle, flags))
 
     def collect_pairs(self, b: Field, mass: float, tol: float = 1e-10, stride: int = 10,
                       max_pairs: int = 64) -> int:

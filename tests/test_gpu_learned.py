@@ -42,12 +42,24 @@ def test_forward_matches_oracle(dims, C):
             net.apply(fout, fin)
             err = np.abs(fout.export() - want).max() / np.abs(want).max()
             assert err < 1e-5, (prec, err)
-        # binary16 weights: error of the rounding only
+        # binary16 weights: error of the rounding only; with the 16-bit
+        # links as well (the solver's form), 1/32767 of the largest entry more
         fin = lat.field(stag.EVEN, "f32", r)
         fout = lat.field(stag.EVEN, "f32")
         net.apply(fout, fin, fp16_weights=True)
         err = np.abs(fout.export() - want).max() / np.abs(want).max()
         assert err < 5e-3
+        for prec in ("f32", "df64"):
+            fin = lat.field(stag.EVEN, prec, r)
+            fout = lat.field(stag.EVEN, prec)
+            net.apply(fout, fin, fp16_weights=True, links16=True)
+            err = np.abs(fout.export() - want).max() / np.abs(want).max()
+            assert err < 5e-3, (prec, err)
+        fin = lat.field(stag.EVEN, "f32", r)
+        fout = lat.field(stag.EVEN, "f32")
+        net.apply(fout, fin, links16=True)
+        err = np.abs(fout.export() - want).max() / np.abs(want).max()
+        assert err < 5e-4, err
         net.close()
 
 
