@@ -60,8 +60,10 @@ def parse():
                     help="skip the mixed-precision comparison on the 48^3x96 workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner comparison on the 32^3x64, m=0.005 workload")
-    ap.add_argument("--learned-pairs", type=int, default=64)
-    ap.add_argument("--learned-epochs", type=int, default=30)
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the IEEE FP64 and reduced-precision-error sections")
+    ap.add_argument("--learned-pairs", type=int, default=4096)
+    ap.add_argument("--learned-epochs", type=int, default=2)
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched / multi-shift comparison (16 RHS on three lattices, 12 shifts)")
     ap.add_argument("--kernels-only", action="store_true",
@@ -340,6 +342,11 @@ def run_native(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = batched_comparison(local, rank)
+    fp64 = None
+    precision = None
+    if not args.no_precision and world == 1:
+        fp64 = fp64_ieee_section(local, rank)
+        precision = precision_error_section(local, rank)
     learned = None
     if not args.no_learned and world == 1:
         learned = learned_comparison(local, rank, args.learned_pairs, args.learned_epochs)
@@ -390,8 +397,101 @@ def run_native(args):
         "mixed_vs_fp64": mixed,
         "batched_multishift": batched,
         "learned_vs_fp64": learned,
+        "fp64_ieee": fp64,
+        "precision_error": precision,
     }
     return line
+
+
+# nominal GB300 FP64 rate (FLOP/s); the stencil needs 576 FP64 multiply-adds
+# (1146 flops with the sums) per site
+FP64_NOMINAL_FLOPS = 1.25e12
+
+
+def fp64_ieee_section(local, rank):
+    """The main workload (32^3x64, m = 0.02, to 1e-10) in IEEE FP64 storage
+    and arithmetic: CG seconds and iterations, and the Dslash rate against
+    both the HBM roof and the FP64-pipe bound (1146 flops per site at the
+    nominal 1.25 TFLOP/s)."""
+    import torch
+    from paper_1411_2087_gb300 import metrics, stag
+    dev = torch.device("cuda", local)
+    U, b_host = make_inputs(DIMS, dev, rank)
+    torch.cuda.synchronize()
+    Vh = int(np.prod(DIMS)) // 2
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": f"{'x'.join(map(str, DIMS))}, m={MASS}, tol={TOL}, IEEE FP64"}
+    with stag.Lattice(DIMS, device=local, stream=stream.cuda_stream) as lat:
+        lat.upload_gauge(U, None, precisions=("f64",))
+        del U
+        torch.cuda.empty_cache()
+        tuned = lat.autotune("f64")
+        fb = lat.field(stag.EVEN, "f64", b_host)
+        fx = lat.field(stag.EVEN, "f64")
+        fo = lat.field(stag.ODD, "f64")
+        lat.cg(fx, fb, MASS, TOL, 20000)
+        info = lat.cg(fx, fb, MASS, TOL, 20000)
+        for _ in range(5):
+            lat.dslash(fo, fb)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(50):
+            lat.dslash(fo, fb)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        us = ev0.elapsed_time(ev1) / 50 * 1e3
+    peak, peak_kind = measured_peak()
+    gbs = metrics.dslash_bytes_per_site(8) * Vh / (us * 1e-6) / 1e9
+    flops = 1146 * Vh / (us * 1e-6)
+    out["cg"] = {"seconds": round(info["seconds"], 4), "iters": info["iters"],
+                 "true_rel_resid": info["true_rel_resid"], "ok": info["return"] == stag.OK}
+    out["dslash"] = {"us_per_launch": round(us, 2), "gbs": round(gbs, 1),
+                     "frac_hbm": round(gbs / peak, 4), "hbm_peak_source": peak_kind,
+                     "tflops": round(flops / 1e12, 3),
+                     "frac_fp64_pipe": round(flops / FP64_NOMINAL_FLOPS, 4),
+                     "fp64_pipe_peak_tflops": FP64_NOMINAL_FLOPS / 1e12,
+                     "fp64_pipe_peak_source": "nominal",
+                     "block": min(tuned["dslash_us"], key=tuned["dslash_us"].get)}
+    return out
+
+
+def precision_error_section(local, rank):
+    """Error of every reduced-precision operator against the double-float
+    one on the main workload's lattice and source (32^3x64): max-norm
+    relative error of D_oe b and of M b = m^2 b - D_eo D_oe b, for FP32 and
+    16-bit storage with full and 12-real (two-row) links, against double
+    float (itself within 1e-12 of the FP64 oracle in the GPU tests)."""
+    import torch
+    from paper_1411_2087_gb300 import stag
+    dev = torch.device("cuda", local)
+    U, b_host = make_inputs(DIMS, dev, rank)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(dev)
+    out = {"workload": f"{'x'.join(map(str, DIMS))}, eps={EPS}, Gaussian source; reference: double-float",
+           "norm": "max |got - ref| / max |ref|"}
+    with stag.Lattice(DIMS, device=local, stream=stream.cuda_stream) as lat:
+        ref = {}
+        for compress in (False, True):
+            lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"), compress12=compress)
+            for prec in (("df64", "f32", "f16") if not compress else ("f32", "f16")):
+                fb = lat.field(stag.EVEN, prec, b_host)
+                fo = lat.field(stag.ODD, prec)
+                fm = lat.field(stag.EVEN, prec)
+                lat.dslash(fo, fb)
+                lat.apply_M(fm, fb, MASS)
+                d, m = fo.export(), fm.export()
+                for f in (fb, fo, fm):
+                    f.destroy()
+                if prec == "df64":
+                    ref = {"dslash": d, "M": m}
+                    continue
+                key = prec + ("_c12" if compress else "")
+                out[key] = {op: float(np.abs(v - ref[op]).max() / np.abs(ref[op]).max())
+                            for op, v in (("dslash", d), ("M", m))}
+    del U
+    torch.cuda.empty_cache()
+    return out
 
 
 LEARNED_DIMS = (32, 32, 32, 64)
@@ -401,10 +501,13 @@ LEARNED_MASS = 0.005
 def learned_comparison(local, rank, n_pairs, epochs):
     """32^3x64, eps = 0.3, m = 0.005 to a 1e-10 true residual: double-float
     CG against flexible CG with the trained gauge-covariant net (3 layers,
-    8 channels, residual loss, FP16 weights / FP32 arithmetic in the solve)
-    and against mixed 16-bit CG.  Training pairs (r_k, x* - x_k) come from
-    plain CG on two sources of the same gauge field; the timed solve uses a
-    third source.  Collection and training times are reported separately."""
+    8 channels, residual loss; in the solve binary16 weights, 16-bit links,
+    FP32 arithmetic), and mixed 16-bit CG against the same mixed iteration
+    with the net (flexible, double-float reliable updates).  Training pairs
+    (r_k, x* - x_k) come from plain CG on as many sources of the same gauge
+    field as the pair count needs; the timed solves use another source.
+    Collection and training times are reported separately, and the net's
+    application time (CUDA events, solver form) beside them."""
     import torch
     from paper_1411_2087_gb300 import stag, synth
     dev = torch.device("cuda", local)
@@ -412,8 +515,11 @@ def learned_comparison(local, rank, n_pairs, epochs):
     torch.cuda.synchronize()
     Vh = int(np.prod(LEARNED_DIMS)) // 2
     out = {"workload": f"{'x'.join(map(str, LEARNED_DIMS))}, m={LEARNED_MASS}, eps=0.3, tol=1e-10"}
-    with stag.Lattice(LEARNED_DIMS, device=local) as lat:
+    stream = torch.cuda.Stream(dev)
+    with stag.Lattice(LEARNED_DIMS, device=local, stream=stream.cuda_stream) as lat:
         lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
+        for p in ("df64", "f16"):
+            lat.autotune(p)
         net = stag.Net(lat, U, channels=8, seed=1)
         del U
         torch.cuda.empty_cache()
@@ -447,10 +553,25 @@ def learned_comparison(local, rank, n_pairs, epochs):
             r = fr.export() - b.numpy()
             return float(np.linalg.norm(r) / np.linalg.norm(b.numpy()))
 
+        # one application of the net in the solver's form (DF64 in and out)
+        fz = lat.field(stag.EVEN, "df64")
+        for _ in range(3):
+            net.apply(fz, fb, fp16_weights=True, links16=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(20):
+            net.apply(fz, fb, fp16_weights=True, links16=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out["net_apply_ms"] = round(ev0.elapsed_time(ev1) / 20, 4)
+        fz.destroy()
         runs = {}
         for name, fn in (("fp64_df64_cg", lambda: lat.cg(fx, fb, LEARNED_MASS, 1e-10, 20000)),
                          ("mixed_f16_cg", lambda: lat.cg_mixed(fx, fb, LEARNED_MASS, 1e-10, 20000, "f16")),
-                         ("learned_fcg_df64", lambda: net.cg(fx, fb, LEARNED_MASS, 1e-10, 20000))):
+                         ("learned_fcg_df64", lambda: net.cg(fx, fb, LEARNED_MASS, 1e-10, 20000)),
+                         ("learned_mixed_f16",
+                          lambda: net.cg_mixed(fx, fb, LEARNED_MASS, 1e-10, 20000, "f16"))):
             fn()
             torch.cuda.synchronize()
             ta = time.perf_counter()
@@ -461,9 +582,12 @@ def learned_comparison(local, rank, n_pairs, epochs):
             runs[name] = {"seconds": round(tb - ta, 4), "iters": info["iters"], "true_rel_resid": res,
                           "ok": info["return"] == stag.OK and res <= 1.05e-10}
         base = runs["fp64_df64_cg"]
-        for name in ("mixed_f16_cg", "learned_fcg_df64"):
+        for name in ("mixed_f16_cg", "learned_fcg_df64", "learned_mixed_f16"):
             runs[name]["speedup_vs_fp64"] = round(base["seconds"] / runs[name]["seconds"], 3)
             runs[name]["iteration_ratio_vs_fp64"] = round(base["iters"] / max(1, runs[name]["iters"]), 3)
+        # what the net adds to the mixed iteration by itself
+        runs["learned_mixed_f16"]["speedup_vs_mixed_f16"] = round(
+            runs["mixed_f16_cg"]["seconds"] / runs["learned_mixed_f16"]["seconds"], 3)
         out.update(runs)
         out["training"] = {"pairs": net.num_pairs(), "epochs": epochs, "collect_seconds": round(t1 - t0, 2),
                            "train_seconds": round(t2 - t1, 2), "loss_first": float(hist[0]),

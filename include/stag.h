@@ -70,6 +70,14 @@ enum {
  *            exponent range); arithmetic in error-free float operations.
  *            GB300's FP64 pipe is far narrower than its FP32 pipes, and this
  *            form keeps FP64-level accuracy at FP32 throughput.
+ *            Range: imports into DF64, F32 and F16 fields refuse finite
+ *            entries beyond the FP32 range (STAG_ERR_ARG, field unchanged);
+ *            entries below about 1e-30 lose relative precision in DF64 (the
+ *            low float of the pair leaves the normal range).  Every solver
+ *            on DF64 or F32 fields first checks the exponent k of b's largest
+ *            entry: when |k| > 16 it solves with a copy b 2^-k (allocated for
+ *            the call) and multiplies the solutions by 2^k, both exact, so
+ *            the scale of b does not matter within that range.
  * STAG_F32   float storage and arithmetic.
  * STAG_F16   16-bit storage ("half" in the lattice-QCD sense): signed
  *            fixed point, links with one scale per field (the largest folded
@@ -410,6 +418,21 @@ int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, 
  * wall time. */
 int stag_cg_solve_learned(stag_net n, stag_field x_even, const stag_field b_even, double mass,
                           double rel_tol, int max_iter, stag_solve_info *info);
+
+/* Mixed-precision flexible CG with the net: the iteration of
+ * stag_cg_solve_mixed (inner_prec STAG_F32 or STAG_F16 storage, reliable
+ * updates at `delta` in the precision of x and b, F64 or DF64) with
+ * z = N(r_s) as the preconditioner, applied in inner_prec (binary16 weights,
+ * 16-bit links), Polak-Ribiere beta, and Fletcher-Reeves beta after a
+ * reliable update (r_s replaced by the recomputed residual).  Convergence is
+ * declared on a recomputed true residual, as in stag_cg_solve_mixed.  Needs
+ * gauge copies of x's precision and inner_prec.  If the flexible iteration
+ * breaks down or does not converge, stag_cg_solve_mixed runs from x = 0;
+ * info->iters and info->restarts then count both runs.  info->seconds is
+ * wall time. */
+int stag_cg_solve_learned_mixed(stag_net n, stag_field x_even, const stag_field b_even, double mass,
+                                double rel_tol, int max_iter, int inner_prec, double delta,
+                                stag_solve_info *info);
 
 /* ---- allocation-free M ---------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -325,11 +325,33 @@ static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *
     return launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s);
 }
 
+// Source normalisation (stag_api.cu): when the exponent k of b's largest
+// entry is far from 0 (double-float and FP32 fields), `scaled` is a copy
+// b 2^-k to solve with, and rhs_scale_end multiplies the n solutions by 2^k
+// and frees it (call it on every path once begin succeeded).
+struct RhsScale {
+    int k = 0;
+    stag_field scaled = nullptr;
+};
+int rhs_scale_begin(const stag_field b, RhsScale *rs);
+int rhs_scale_end(RhsScale *rs, stag_field const *xs, int n);
+
 // one plain CG iteration on the lattice stream (stag_api.cu)
 cudaError_t enqueue_cg_body(stag_lattice lat, CgWork &w, cudaStream_t s, bool skip_if_done);
 
+// A flexible preconditioner inside the mixed solver (learned.cu): enqueue
+// z = N(r_s) in the low precision with the block partials of Re<z, r_s> and
+// Re<z, Ap> (Ap NULL on the first call), then beta and rr = <r_s, z> into the
+// scalars (first: beta = 0).  Kernels return at once unless the solve runs.
+struct MixedPrecond {
+    cudaError_t (*enqueue)(void *ctx, int lo, const void *rs, void *z, const void *Ap, int first, cudaStream_t s);
+    void *ctx = nullptr;
+    void *z = nullptr;  // low-precision buffer for z
+};
+
 // shared between the solver translation units
 int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *b_data, size_t bytes,
-                    double mass, double rel_tol, int max_iter, double delta, stag_solve_info *info);
+                    double mass, double rel_tol, int max_iter, double delta, stag_solve_info *info,
+                    const MixedPrecond *pc = nullptr);
 int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, double mk, void *r_out,
                      double *rr);

@@ -61,6 +61,9 @@ struct CgScalars {
     int has_rel_cond;
     // multi-shift CG: the iteration whose solution updates have been applied
     int ms_xdone;
+    // mixed precision with a flexible preconditioner: rr holds <r_s, z> and
+    // beta comes from the preconditioner step, not from |r_s|^2
+    int fcg;
 };
 
 // multi-shift CG

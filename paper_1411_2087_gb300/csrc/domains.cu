@@ -251,9 +251,23 @@ extern "C" int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, co
     return STAG_OK;
 }
 
+static int dd_cg_impl(stag_lattice lat, int ndomains, stag_field x, const stag_field b, double mass,
+                      double rel_tol, int max_iter, stag_solve_info *info);
+
 extern "C" int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x, const stag_field b, double mass,
                                 double rel_tol, int max_iter, stag_solve_info *info) {
     STAG_NVTX("stag_dd_cg_solve");
+    if (!lat || !x || !b || x == b || b->lat != lat || b->parity != STAG_EVEN || x->prec != b->prec)
+        return dd_cg_impl(lat, ndomains, x, b, mass, rel_tol, max_iter, info);  // reports the error
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const int st = dd_cg_impl(lat, ndomains, x, rs.scaled ? rs.scaled : b, mass, rel_tol, max_iter, info);
+    STAG_TRY(rhs_scale_end(&rs, &x, 1));
+    return st;
+}
+
+static int dd_cg_impl(stag_lattice lat, int ndomains, stag_field x, const stag_field b, double mass,
+                      double rel_tol, int max_iter, stag_solve_info *info) {
     if (info)
         memset(info, 0, sizeof *info);
     if (!lat || !x || !b)

@@ -52,6 +52,14 @@ cudaError_t launch_su3_deviation(const double *U, long long nlinks, unsigned *ou
 // NaN, an infinity or a value beyond the FP32 range gives +infinity
 cudaError_t launch_absmax(const double *a, long long n, unsigned *out, cudaStream_t s);
 
+// *flag = 1 if a finite entry of n doubles lies beyond the FP32 range (device)
+cudaError_t launch_finite_overflow(const double *a, long long n, unsigned *flag, cudaStream_t s);
+
+// largest |component| of a field (F64, DF64: hi parts, F32) as float bits in
+// *out (device); v *= 2^e exactly (results in the normal range)
+cudaError_t launch_field_absmax(int prec, const Geom &g, const void *v, unsigned *out, cudaStream_t s);
+cudaError_t launch_field_ldexp(int prec, const Geom &g, void *v, int e, cudaStream_t s);
+
 // three-link products N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu), canonical layout
 cudaError_t launch_long_links(const Geom &g, const double *fat, double *lng, cudaStream_t s);
 

@@ -464,6 +464,88 @@ cudaError_t launch_absmax(const double *a, long long n, unsigned *out, cudaStrea
     return cudaGetLastError();
 }
 
+// *flag = 1 if a finite entry lies beyond the FP32 range (NaN and infinity
+// pass: the solvers report them as breakdowns)
+__global__ void finite_overflow_kernel(const double *__restrict__ a, long long n, unsigned *flag) {
+    int bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = fabs(a[i]);
+        bad |= v > (double)FLT_MAX && v < INFINITY;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+        atomicOr(flag, 1u);
+}
+
+cudaError_t launch_finite_overflow(const double *a, long long n, unsigned *flag, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    finite_overflow_kernel<<<1024, 256, 0, s>>>(a, n, flag);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------
+// exact power-of-two rescaling of a colour field (the solvers' source
+// normalisation): the largest |component| (double-float: of the hi parts)
+// as float bits, and v *= 2^e
+// --------------------------------------------------------------------------
+template <int P> STAG_D float elem_absmax(typename Fmt<P>::Elem v);
+template <> STAG_D float elem_absmax<P_F64>(double2 v) { return (float)fmax(fabs(v.x), fabs(v.y)); }
+template <> STAG_D float elem_absmax<P_DF64>(float4 v) { return fmaxf(fabsf(v.x), fabsf(v.z)); }
+template <> STAG_D float elem_absmax<P_F32>(float2 v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+
+template <int P> STAG_D typename Fmt<P>::Elem elem_ldexp(typename Fmt<P>::Elem v, int e);
+template <> STAG_D double2 elem_ldexp<P_F64>(double2 v, int e) { return make_double2(ldexp(v.x, e), ldexp(v.y, e)); }
+template <> STAG_D float4 elem_ldexp<P_DF64>(float4 v, int e) {
+    return make_float4(ldexpf(v.x, e), ldexpf(v.y, e), ldexpf(v.z, e), ldexpf(v.w, e));
+}
+template <> STAG_D float2 elem_ldexp<P_F32>(float2 v, int e) { return make_float2(ldexpf(v.x, e), ldexpf(v.y, e)); }
+
+template <int P>
+__global__ void field_absmax_kernel(Geom g, const typename Fmt<P>::Elem *__restrict__ v, unsigned *out) {
+    float m = 0.f;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.Vh; c += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            m = fmaxf(m, elem_absmax<P>(v[(size_t)a * g.stride + c]));  // fmaxf drops NaN
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, __float_as_uint(m));
+}
+
+template <int P>
+__global__ void field_ldexp_kernel(Geom g, typename Fmt<P>::Elem *v, int e) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= g.Vh)
+        return;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        v[(size_t)a * g.stride + c] = elem_ldexp<P>(v[(size_t)a * g.stride + c], e);
+}
+
+#define STAG_SRC_SWITCH(prec, ...)                                    \
+    switch (prec) {                                                   \
+    case P_F64: { constexpr int P = P_F64; __VA_ARGS__; } break;      \
+    case P_DF64: { constexpr int P = P_DF64; __VA_ARGS__; } break;    \
+    case P_F32: { constexpr int P = P_F32; __VA_ARGS__; } break;      \
+    default: return cudaErrorInvalidValue;                            \
+    }
+
+cudaError_t launch_field_absmax(int prec, const Geom &g, const void *v, unsigned *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess)
+        return e;
+    STAG_SRC_SWITCH(prec, field_absmax_kernel<P><<<512, 256, 0, s>>>(g, (const typename Fmt<P>::Elem *)v, out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_ldexp(int prec, const Geom &g, void *v, int e, cudaStream_t s) {
+    STAG_SRC_SWITCH(prec, field_ldexp_kernel<P><<<(g.Vh + 255) / 256, 256, 0, s>>>(g, (typename Fmt<P>::Elem *)v, e));
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------------------
 // three-link products (FP64): N_mu(x) = U_mu(x) U_mu(x+mu) U_mu(x+2mu)
 // --------------------------------------------------------------------------

@@ -19,6 +19,9 @@
 //   (in a graph the four gated kernels sit in a conditional IF node that
 //   mixed_update opens, so that iterations without an update launch none)
 //   p = r_s + beta p                                      (cg_p_kernel)
+// With a flexible preconditioner (sc->fcg) the direction update is
+// p = z + beta p, z = N(r_s), and the preconditioner step sets beta and
+// rr = <r_s, z>; mixed_update and mixed_restart then leave both alone.
 #include "dslash.cuh"
 #include "kernels.h"
 
@@ -130,8 +133,12 @@ mixed_update_kernel(Geom g, float2 *xs, typename Fmt<PL>::Elem *rs, const typena
             } else if (rn < sc->delta * sc->rmax || total <= sc->rr_stop || sc->iter >= sc->max_iter) {
                 sc->reliable = 1;
             } else {
-                sc->beta = make_dpair(total / sc->rr);
-                sc->rr = total;
+                if (sc->fcg) {
+                    sc->fcg_rr = total;
+                } else {
+                    sc->beta = make_dpair(total / sc->rr);
+                    sc->rr = total;
+                }
                 sc->rmax = fmax(sc->rmax, rn);
             }
         }
@@ -194,8 +201,12 @@ mixed_restart_kernel(Geom g, const typename Fmt<PH>::Elem *r, typename Fmt<PL>::
             sc->status = CG_CONVERGED;
         else if (sc->iter >= sc->max_iter)
             sc->status = CG_MAXITER;
-        sc->beta = make_dpair(rt / sc->rr);
-        sc->rr = rt;
+        if (sc->fcg) {
+            sc->fcg_rr = rt;
+        } else {
+            sc->beta = make_dpair(rt / sc->rr);
+            sc->rr = rt;
+        }
         sc->rmax = sqrt(rt);
         set_loop_condition_m(sc);
     }

@@ -117,12 +117,14 @@ cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double 
 struct NetW {
     const float2 *w;
     int C, off1, off2, round_half;
-    STAG_D double2 get(int k) const {
+    const double2 *sw = nullptr;  // the weights staged in shared memory, if set
+    STAG_D double2 load(int k) const {
         float2 v = w[k];
         if (round_half)
             v = make_float2(__half2float(__float2half_rn(v.x)), __half2float(__float2half_rn(v.y)));
         return make_double2((double)v.x, (double)v.y);
     }
+    STAG_D double2 get(int k) const { return sw ? sw[k] : load(k); }
     STAG_D double2 w1(int d, int i) const { return get(d * C + i); }
     STAG_D double2 w2(int d, int j, int i) const { return get(off1 + (d * C + j) * C + i); }
     STAG_D double2 w3(int d, int j) const { return get(off2 + d * C + j); }
@@ -144,8 +146,17 @@ STAG_D double2 triple(const NetW &W, int d3, int d2, int d1) {
     return s;
 }
 
-// one block of 65 threads: thread a*8+b computes C[a][b], thread 64 c0
+// one block: the weights go to shared memory, then thread a*8+b computes
+// C[a][b] and thread 64 c0
+constexpr int NET_MAX_W = 9 * (2 * 8 + 8 * 8);
+
 __global__ void net_path_coef_kernel(NetW W, NetPath *out) {
+    __shared__ double2 sw[NET_MAX_W];
+    const int nw = 9 * (2 * W.C + W.C * W.C);
+    for (int k = threadIdx.x; k < nw; k += blockDim.x)
+        sw[k] = W.load(k);
+    __syncthreads();
+    W.sw = sw;
     const int q = threadIdx.x;
     if (q < 64) {
         const int a = q >> 3, b = q & 7;
@@ -245,14 +256,69 @@ constexpr int NET_BLOCK = 128;
 
 template <class R> STAG_D cplx<float> to_f(const cplx<R> &v) { return cconv<float, R>(v); }
 
+// The odd-site intermediate chi: FP32 (float2 [8][3][S]) with FP32 links,
+// and 16-bit with 16-bit links: short2 [8][3][S] followed by one float norm
+// per site and channel, float [8][S] (value = q * norm / 32767; the norm is
+// the channel's largest |component| at that site).
+template <class LT> struct Chi;
+template <> struct Chi<float2> {
+    STAG_D static void store(void *chi, int S, int a, int c, const cplx<float> v[3]) {
+        float2 *p = (float2 *)chi;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            __stcs(p + (size_t)(a * 3 + k) * S + c, make_float2(v[k].re, v[k].im));
+    }
+    // v = chi_a at site j; returns the factor that turns v into values
+    STAG_D static float load(const void *chi, int S, int a, int j, cplx<float> v[3]) {
+        const float2 *p = (const float2 *)chi;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float2 t = __ldcs(p + (size_t)(a * 3 + k) * S + j);
+            v[k] = cplx<float>{t.x, t.y};
+        }
+        return 1.f;
+    }
+};
+template <> struct Chi<short2> {
+    STAG_D static void store(void *chi, int S, int a, int c, const cplx<float> v[3]) {
+        short2 *p = (short2 *)chi;
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+        const float inv = m > 0.f ? kQ16 / m : 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            __stcs(p + (size_t)(a * 3 + k) * S + c, make_short2(q16(v[k].re * inv), q16(v[k].im * inv)));
+        __stcs((float *)(p + (size_t)24 * S) + (size_t)a * S + c, m);
+    }
+    STAG_D static float load(const void *chi, int S, int a, int j, cplx<float> v[3]) {
+        const short2 *p = (const short2 *)chi;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const short2 t = __ldcs(p + (size_t)(a * 3 + k) * S + j);
+            v[k] = cplx<float>{(float)t.x, (float)t.y};
+        }
+        return __ldcs((const float *)(p + (size_t)24 * S) + (size_t)a * S + j) * (1.f / kQ16);
+    }
+};
+
 // chi_a(y) = sum_b C[a][b] (T_b r)(y) on the odd sites; r even (precision P,
-// component stride rs), chi float2 [8][3][S].  Hop index b = 2 mu (+mu) or
-// 2 mu + 1 (-mu).  ls: the links' scale (1 for FP32).
+// component stride rs).  Hop index b = 2 mu (+mu) or 2 mu + 1 (-mu).  ls: the
+// links' scale (1 for FP32).  The eight transported vectors go to shared
+// memory first (each thread reads back only its own), so that the loads of
+// the transport phase and the mixing's 48 live values never meet.
+// Six resident blocks (at most 80 registers, 24 warps per SM): at eight the
+// 16-bit form spills 96 bytes, and measured at 32^3x64 the solver-form net
+// application took 0.342 ms against 0.308 ms at six.
+constexpr int NET_MID_MINB = 6;
+
 template <int P, class LT>
-__global__ void __launch_bounds__(NET_BLOCK)
+__global__ void __launch_bounds__(NET_BLOCK, NET_MID_MINB)
 net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
-               const typename Fmt<P>::Elem *__restrict__ r, int rs, float2 *__restrict__ chi, const int *gate) {
+               const typename Fmt<P>::Elem *__restrict__ r, int rs, void *__restrict__ chi, const int *gate) {
     __shared__ cplx<float> sC[64];
+    __shared__ float2 sh[8][3][NET_BLOCK];
     if (gate && *gate != CG_RUNNING)
         return;
     if (threadIdx.x < 64) {
@@ -266,12 +332,6 @@ net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
     const int S = g.stride;
     int x[4];
     cb_coords(g, c, 1, x);
-    cplx<float> ch[8][3];
-#pragma unroll
-    for (int a = 0; a < 8; a++)
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            ch[a][k] = czero<float>();
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
 #pragma unroll
@@ -287,21 +347,31 @@ net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
                 v[k] = to_f(vr[k]);
             nl_load(NL, S, bw ? 0 : 1, mu, bw ? j : c, U);
             nl_apply(U, bw, v, h);
-            const int b = 2 * mu + bw;
 #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const cplx<float> w = sC[a * 8 + b];
-#pragma unroll
-                for (int k = 0; k < 3; k++)
-                    cmac(ch[a][k], w, h[k]);
-            }
+            for (int k = 0; k < 3; k++)
+                sh[2 * mu + bw][k][threadIdx.x] = make_float2(h[k].re, h[k].im);
         }
     }
+    cplx<float> h[8][3];
 #pragma unroll
-    for (int a = 0; a < 8; a++)
+    for (int b = 0; b < 8; b++)
 #pragma unroll
-        for (int k = 0; k < 3; k++)
-            __stcs(chi + (size_t)(a * 3 + k) * S + c, make_float2(ch[a][k].re, ch[a][k].im));
+        for (int k = 0; k < 3; k++) {
+            const float2 t = sh[b][k][threadIdx.x];
+            h[b][k] = cplx<float>{t.x, t.y};
+        }
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+        cplx<float> acc[3] = {czero<float>(), czero<float>(), czero<float>()};
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const cplx<float> w = sC[a * 8 + b];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                cmac(acc[k], w, h[b][k]);
+        }
+        Chi<LT>::store(chi, S, a, c, acc);
+    }
 }
 
 // z(x) = c0 r(x) + sum_a (T_a chi_a)(x) on the even sites.  NET_OUT_DOTS
@@ -312,7 +382,7 @@ enum { NET_OUT_PLAIN = 0, NET_OUT_DOTS = 1 };
 template <int PI, int PO, class LT, int EPI>
 __global__ void __launch_bounds__(NET_BLOCK)
 net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
-               const float2 *__restrict__ chi, const typename Fmt<PI>::Elem *__restrict__ r, int rs,
+               const void *__restrict__ chi, const typename Fmt<PI>::Elem *__restrict__ r, int rs,
                typename Fmt<PO>::Elem *__restrict__ z, int zs, const typename Fmt<PO>::Elem *__restrict__ Ap,
                double *partial, const int *gate) {
     using RO = typename Fmt<PO>::R;
@@ -332,19 +402,14 @@ net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
             for (int bw = 0; bw < 2; bw++) {
                 // +mu: U_mu(x) chi_{+mu}(x+mu); -mu: U_mu(x-mu)^+ chi_{-mu}(x-mu)
                 const int j = cb_hop(g, c, x, mu, bw ? -1 : 1);
-                const int a = 2 * mu + bw;
                 cplx<float> v[3], U[9], h[3];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float2 t = __ldg(chi + (size_t)(a * 3 + k) * S + j);
-                    v[k] = cplx<float>{t.x, t.y};
-                }
+                const float f = Chi<LT>::load(chi, S, 2 * mu + bw, j, v);
                 nl_load(NL, S, bw ? 1 : 0, mu, bw ? j : c, U);
                 nl_apply(U, bw, v, h);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
-                    acc[k].re += h[k].re;
-                    acc[k].im += h[k].im;
+                    acc[k].re = fmaf(f, h[k].re, acc[k].re);
+                    acc[k].im = fmaf(f, h[k].im, acc[k].im);
                 }
             }
         }
@@ -395,7 +460,7 @@ int net_grid(const Geom &g) { return (g.Vh + NET_BLOCK - 1) / NET_BLOCK; }
     }
 
 cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const NetPath *path, const void *r,
-                           int rs, float2 *chi, const int *gate, cudaStream_t s) {
+                           int rs, void *chi, const int *gate, cudaStream_t s) {
     NP_IN_SWITCH(prec, {
         using E = typename Fmt<P>::Elem;
         if (nl.l16)
@@ -409,7 +474,7 @@ cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const 
 }
 
 template <int PI, int PO, int EPI>
-static void net_out_t(const Geom &g, const NetLinkSet &nl, const NetPath *path, const float2 *chi, const void *r,
+static void net_out_t(const Geom &g, const NetLinkSet &nl, const NetPath *path, const void *chi, const void *r,
                       int rs, void *z, int zs, const void *Ap, double *partial, const int *gate, cudaStream_t s) {
     using EI = typename Fmt<PI>::Elem;
     using EO = typename Fmt<PO>::Elem;
@@ -424,7 +489,7 @@ static void net_out_t(const Geom &g, const NetLinkSet &nl, const NetPath *path, 
 // input and output of one precision (the solver's), or FP32 pair input with
 // FP32 output (training)
 cudaError_t launch_net_out(int prec_in, int prec_out, const Geom &g, const NetLinkSet &nl, const NetPath *path,
-                           const float2 *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
+                           const void *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
                            double *partial, const int *gate, cudaStream_t s) {
     if (prec_in != prec_out)
         return cudaErrorInvalidValue;
@@ -685,20 +750,28 @@ cudaError_t launch_net_dot2(int Vh, const float2 *a, int as, const float2 *b, in
 // <z_new, r_new - r_old> / <z_old, r_old> with r_new - r_old = -alpha Ap; or
 // Fletcher-Reeves <z_new, r_new> / <z_old, r_old> after a reliable update,
 // where r_new is the recomputed residual; 0 on the first step), rr = <z, r>.
-constexpr int FCG_FINISH = 256;
+constexpr int FCG_FINISH = 1024;
 
 __global__ void __launch_bounds__(FCG_FINISH)
 fcg_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int first) {
     __shared__ double smem[32];
     if (sc->status != CG_RUNNING)
         return;
-    double a0 = 0.0, a1 = 0.0;
-    for (int i = threadIdx.x; i < n; i += FCG_FINISH) {
+    // two independent sums per value and thread over a fixed assignment
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+    int i = threadIdx.x;
+    for (; i + FCG_FINISH < n; i += 2 * FCG_FINISH) {
         a0 += partial[i];
-        a1 += partial[n + i];
+        a1 += partial[i + FCG_FINISH];
+        b0 += partial[n + i];
+        b1 += partial[n + i + FCG_FINISH];
     }
-    const double zr = block_sum<FCG_FINISH>(a0, smem);
-    const double zap = block_sum<FCG_FINISH>(a1, smem);
+    if (i < n) {
+        a0 += partial[i];
+        b0 += partial[n + i];
+    }
+    const double zr = block_sum<FCG_FINISH>(a0 + a1, smem);
+    const double zap = block_sum<FCG_FINISH>(b0 + b1, smem);
     if (threadIdx.x == 0) {
         double beta = 0.0;
         if (!first)

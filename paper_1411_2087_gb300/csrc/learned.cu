@@ -662,9 +662,23 @@ static int fcg_run(stag_net n, int prec, bool use_net, double mass, double tol2b
     return lat->sc_host->status;
 }
 
+static int learned_impl(stag_net n, stag_field x, const stag_field b, double mass, double rel_tol, int max_iter,
+                        stag_solve_info *info);
+
 extern "C" int stag_cg_solve_learned(stag_net n, stag_field x, const stag_field b, double mass, double rel_tol,
                                      int max_iter, stag_solve_info *info) {
     STAG_NVTX("stag_cg_solve_learned");
+    if (!n || !x || !b || x == b || check_net_field(n, b, "stag_cg_solve_learned") != STAG_OK)
+        return learned_impl(n, x, b, mass, rel_tol, max_iter, info);  // reports the error
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const int st = learned_impl(n, x, rs.scaled ? rs.scaled : b, mass, rel_tol, max_iter, info);
+    STAG_TRY(rhs_scale_end(&rs, &x, 1));
+    return st;
+}
+
+static int learned_impl(stag_net n, stag_field x, const stag_field b, double mass, double rel_tol, int max_iter,
+                        stag_solve_info *info) {
     if (info)
         memset(info, 0, sizeof *info);
     if (!n || !x || !b)
@@ -737,4 +751,68 @@ extern "C" int stag_cg_solve_learned(stag_net n, stag_field x, const stag_field 
         return fail(local.status, "stag_cg_solve_learned: true |r|/|b| = %.3e after %d iterations",
                     local.true_rel_resid, iters);
     return STAG_OK;
+}
+
+// ---- mixed-precision flexible CG with the net ---------------------------
+static cudaError_t learned_precond_enqueue(void *ctx, int lo, const void *rs, void *z, const void *Ap, int first,
+                                           cudaStream_t s) {
+    stag_net n = (stag_net)ctx;
+    stag_lattice lat = n->lat;
+    const int S = lat->geom.stride;
+    cudaError_t e = net_apply_path(n, lo, rs, S, z, S, true, true, Ap, status_flag(lat), s);
+    if (e != cudaSuccess)
+        return e;
+    return launch_fcg_finish(lat->partial, net_grid(lat->geom), lat->sc, first, s);
+}
+
+extern "C" int stag_cg_solve_learned_mixed(stag_net n, stag_field x, const stag_field b, double mass,
+                                           double rel_tol, int max_iter, int inner_prec, double delta,
+                                           stag_solve_info *info) {
+    STAG_NVTX("stag_cg_solve_learned_mixed");
+    if (info)
+        memset(info, 0, sizeof *info);
+    if (!n || !x || !b)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_learned_mixed: NULL argument");
+    STAG_TRY(check_net_field(n, x, "stag_cg_solve_learned_mixed"));
+    STAG_TRY(check_net_field(n, b, "stag_cg_solve_learned_mixed"));
+    if (x->prec != b->prec || x == b || (x->prec != STAG_F64 && x->prec != STAG_DF64))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_learned_mixed: x and b must be distinct F64 or DF64 fields");
+    if (inner_prec != STAG_F32 && inner_prec != STAG_F16)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_learned_mixed: inner precision must be F32 or F16");
+    if (!(mass > 0) || !std::isfinite(mass) || !(rel_tol >= 0) || !std::isfinite(rel_tol) || max_iter < 0)
+        return fail(STAG_ERR_ARG, "stag_cg_solve_learned_mixed: need mass > 0, rel_tol >= 0, max_iter >= 0");
+    if (!(delta > 0 && delta < 1))
+        return fail(STAG_ERR_ARG, "stag_cg_solve_learned_mixed: delta must be in (0, 1)");
+    stag_lattice lat = n->lat;
+    const int hi = x->prec, lo = inner_prec;
+    if (!lat->has_gauge || !lat->links[hi] || !lat->links[lo])
+        return fail(STAG_ERR_STATE, "stag_cg_solve_learned_mixed: needs %s and %s gauge copies", prec_name(hi),
+                    prec_name(lo));
+    DEVICE_SCOPE(lat->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    STAG_TRY(alloc_vec(lat, lo, &n->z[lo]));
+    // the deployed preconditioner: binary16 weights, 16-bit links
+    CUDA_TRY(net_coefficients(n, 1, lat->stream));
+    MixedPrecond pc;
+    pc.enqueue = learned_precond_enqueue;
+    pc.ctx = n;
+    pc.z = n->z[lo];
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const stag_field bs = rs.scaled ? rs.scaled : b;
+    stag_solve_info first;
+    int st = mixed_solve_raw(lat, hi, lo, x->data, bs->data, bs->bytes, mass, rel_tol, max_iter, delta, &first, &pc);
+    if (st == STAG_ERR_BREAKDOWN || st == STAG_ERR_NOT_CONVERGED) {
+        // the plain mixed solver from x = 0
+        stag_solve_info second;
+        st = mixed_solve_raw(lat, hi, lo, x->data, bs->data, bs->bytes, mass, rel_tol, max_iter, delta, &second);
+        second.iters += first.iters;
+        second.restarts += first.restarts;
+        first = second;
+    }
+    STAG_TRY(rhs_scale_end(&rs, &x, 1));
+    first.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info)
+        *info = first;
+    return st;
 }

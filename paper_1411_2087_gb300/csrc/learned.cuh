@@ -26,13 +26,15 @@ cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int 
                                  cudaStream_t s);
 cudaError_t launch_net_path_chain(int C, const float *w32, const int off[3], const double2 *G, double2 *grad,
                                   cudaStream_t s);
-// chi [8][3][stride] (odd sites) from the even input r (precision prec, stride rs)
+// chi (odd sites; FP32 [8][3][stride] with FP32 links, 16-bit [8][3][stride]
+// plus float norms [8][stride] with 16-bit links) from the even input r
+// (precision prec, stride rs)
 cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const NetPath *path, const void *r,
-                           int rs, float2 *chi, const int *gate, cudaStream_t s);
+                           int rs, void *chi, const int *gate, cudaStream_t s);
 // z = c0 r + sum_a T_a chi_a (even); dots adds the per-block partials of
 // Re<z, r> and Re<z, Ap> (0 without Ap): 2 * net_grid doubles
 cudaError_t launch_net_out(int prec_in, int prec_out, const Geom &g, const NetLinkSet &nl, const NetPath *path,
-                           const float2 *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
+                           const void *chi, const void *r, int rs, void *z, int zs, bool dots, const void *Ap,
                            double *partial, const int *gate, cudaStream_t s);
 int net_grid(const Geom &g);
 int net_grad_blocks(const Geom &g);

@@ -38,7 +38,8 @@ static cudaError_t enqueue_reliable_update(stag_lattice lat, int hi, int lo, cud
 // conditional IF node whose handle (*rel_cond, created on the loop-body
 // graph) mixed_update sets, captured on the second stream `side`.
 static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool host_mode, cudaStream_t side = nullptr,
-                                      cudaGraphConditionalHandle *rel_cond = nullptr) {
+                                      cudaGraphConditionalHandle *rel_cond = nullptr,
+                                      const MixedPrecond *pc = nullptr) {
     CgWork &L = lat->cg[lo];
     cudaStream_t s = lat->stream;
     const Geom &g = lat->geom;
@@ -85,18 +86,34 @@ static cudaError_t enqueue_mixed_body(stag_lattice lat, int hi, int lo, bool hos
         if (e != cudaSuccess)
             return e;
     }
+    if (pc) {
+        // flexible: z = N(r_s), beta, p = z + beta p
+        if ((e = pc->enqueue(pc->ctx, lo, L.r, pc->z, L.Ap, 0, s)) != cudaSuccess)
+            return e;
+        return launch_cg_p_update(lo, g, pc->z, L.p, lat->sc, s);
+    }
     return launch_cg_p_update(lo, g, L.r, L.p, lat->sc, s);
 }
 
-static cudaError_t enqueue_mixed_init(stag_lattice lat, int hi, int lo) {
+static cudaError_t enqueue_mixed_init(stag_lattice lat, int hi, int lo, const MixedPrecond *pc = nullptr) {
     CgWork &H = lat->cg[hi];
     CgWork &L = lat->cg[lo];
-    return launch_mixed_init(hi, lo, lat->geom, H.xw, H.r, H.bw, lat->xs, L.r, L.p, lat->partial,
-                             lat->sc, lat->stream);
+    cudaError_t e = launch_mixed_init(hi, lo, lat->geom, H.xw, H.r, H.bw, lat->xs, L.r, L.p, lat->partial,
+                                      lat->sc, lat->stream);
+    if (e != cudaSuccess || !pc)
+        return e;
+    // flexible: p = z = N(b), rr = <b, z>
+    if ((e = pc->enqueue(pc->ctx, lo, L.r, pc->z, nullptr, 1, lat->stream)) != cudaSuccess)
+        return e;
+    return cudaMemcpyAsync(L.p, pc->z, field_bytes(lat, lo), cudaMemcpyDeviceToDevice, lat->stream);
 }
 
-static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
-    auto &mg = lat->mixed[hi][lo];
+// the mixed solver's graph: init, then WHILE(body) with the reliable update
+// in an IF node.  Without a preconditioner it is kept per (hi, lo) on the
+// lattice (mg); with one the caller runs and destroys it.
+static int build_mixed_graph(stag_lattice lat, int hi, int lo, const MixedPrecond *pc = nullptr,
+                             stag_lattice_s::MixedGraph *out = nullptr) {
+    auto &mg = out ? *out : lat->mixed[hi][lo];
     cudaStream_t s = lat->stream;
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -119,7 +136,7 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
     if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return bail("begin capture", e);
-    if ((e = enqueue_mixed_init(lat, hi, lo)) != cudaSuccess)
+    if ((e = enqueue_mixed_init(lat, hi, lo, pc)) != cudaSuccess)
         return bail("init", e);
     cudaStreamCaptureStatus st;
     const cudaGraphNode_t *deps = nullptr;
@@ -149,7 +166,7 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
         return bail("begin body capture", e);
     }
     cudaGraphConditionalHandle rel_cond = 0;
-    e = enqueue_mixed_body(lat, hi, lo, false, side, &rel_cond);
+    e = enqueue_mixed_body(lat, hi, lo, false, side, &rel_cond, pc);
     cudaStreamDestroy(side);
     if (e != cudaSuccess)
         return bail("body", e);
@@ -170,7 +187,7 @@ static int build_mixed_graph(stag_lattice lat, int hi, int lo) {
 // arguments already checked
 int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *b_data,
                            size_t bytes, double mass, double rel_tol, int max_iter, double delta,
-                           stag_solve_info *info) {
+                           stag_solve_info *info, const MixedPrecond *pc) {
     STAG_TRY(ensure_cg_work(lat, hi));
     STAG_TRY(ensure_cg_work(lat, lo));
     if (!lat->xs) {
@@ -182,18 +199,37 @@ int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *
     CgWork &H = lat->cg[hi];
     cudaStream_t s = lat->stream;
     CUDA_TRY(cudaMemcpyAsync(H.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
+    // flexible mode flag, after the scalars are uploaded (pageable source:
+    // read when cudaMemcpyAsync returns)
+    const int fcg_flag = pc ? 1 : 0;
+    auto set_fcg = [&]() {
+        return cudaMemcpyAsync((char *)lat->sc + offsetof(CgScalars, fcg), &fcg_flag, sizeof fcg_flag,
+                               cudaMemcpyHostToDevice, s);
+    };
     if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
-        auto &mg = lat->mixed[hi][lo];
+        stag_lattice_s::MixedGraph once;
+        auto &mg = pc ? once : lat->mixed[hi][lo];
         if (!mg.exec)
-            STAG_TRY(build_mixed_graph(lat, hi, lo));
+            STAG_TRY(build_mixed_graph(lat, hi, lo, pc, &mg));
         STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, true, mg.cond, delta, true, mg.rel_cond));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(cudaGraphLaunch(mg.exec, s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
+        cudaError_t e = set_fcg();
+        if (e == cudaSuccess)
+            e = cudaEventRecord(lat->ev0, s);
+        if (e == cudaSuccess)
+            e = cudaGraphLaunch(mg.exec, s);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(lat->ev1, s);
+        if (pc) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(once.exec);
+            cudaGraphDestroy(once.graph);
+        }
+        CUDA_TRY(e);
     } else {
         STAG_TRY(upload_scalars(lat, mass, rel_tol, max_iter, false, 0, delta));
+        CUDA_TRY(set_fcg());
         CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        CUDA_TRY(enqueue_mixed_init(lat, hi, lo));
+        CUDA_TRY(enqueue_mixed_init(lat, hi, lo, pc));
         const int chunk = lat->cg_chunk;
         const long long max_chunks = (long long)max_iter / chunk + 2;
         for (long long k = 0; k < max_chunks; k++) {
@@ -203,7 +239,7 @@ int mixed_solve_raw(stag_lattice lat, int hi, int lo, void *x_data, const void *
             if (lat->sc_host->status != CG_RUNNING)
                 break;
             for (int j = 0; j < chunk; j++)
-                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true));
+                CUDA_TRY(enqueue_mixed_body(lat, hi, lo, true, nullptr, nullptr, pc));
         }
         CUDA_TRY(cudaEventRecord(lat->ev1, s));
     }
@@ -273,7 +309,12 @@ extern "C" int stag_cg_solve_mixed(stag_lattice lat, stag_field x, const stag_fi
         return fail(STAG_ERR_STATE, "stag_cg_solve_mixed: needs %s and %s gauge copies", prec_name(hi),
                     prec_name(lo));
     DEVICE_SCOPE(lat->device);
-    return mixed_solve_raw(lat, hi, lo, x->data, b->data, b->bytes, mass, rel_tol, max_iter, delta, info);
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const stag_field bs = rs.scaled ? rs.scaled : b;
+    const int st = mixed_solve_raw(lat, hi, lo, x->data, bs->data, bs->bytes, mass, rel_tol, max_iter, delta, info);
+    STAG_TRY(rhs_scale_end(&rs, &x, 1));
+    return st;
 }
 
 
@@ -515,8 +556,12 @@ extern "C" int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double
     for (int k = 0; k < n; k++)
         xd[k] = xs[k]->data;
     stag_solve_info local[MS_MAX];
-    const int st = ms_solve_raw(lat, prec, xd, shifts, n, b->data, b->bytes, mass, rel_tol, max_iter,
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const stag_field bs = rs.scaled ? rs.scaled : b;
+    const int st = ms_solve_raw(lat, prec, xd, shifts, n, bs->data, bs->bytes, mass, rel_tol, max_iter,
                                 local, nullptr);
+    STAG_TRY(rhs_scale_end(&rs, xs, n));
     if (infos)
         memcpy(infos, local, sizeof(stag_solve_info) * n);
     if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED && st != STAG_ERR_BREAKDOWN)
@@ -545,11 +590,26 @@ int shifted_residual(stag_lattice lat, int hi, const void *x, const void *b, dou
     return STAG_OK;
 }
 
+static int multishift_mixed_impl(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                                 const stag_field b, double mass, double rel_tol, int max_iter,
+                                 int inner_prec, double delta, stag_solve_info *infos);
+
 extern "C" int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,
                                         const stag_field b, double mass, double rel_tol, int max_iter,
                                         int inner_prec, double delta, stag_solve_info *infos) {
     STAG_NVTX("stag_cg_multishift_mixed");
     STAG_TRY(check_ms_args(lat, xs, shifts, n, b, mass, rel_tol, max_iter, "stag_cg_multishift_mixed"));
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    const int st = multishift_mixed_impl(lat, xs, shifts, n, rs.scaled ? rs.scaled : b, mass, rel_tol, max_iter,
+                                         inner_prec, delta, infos);
+    STAG_TRY(rhs_scale_end(&rs, xs, n));
+    return st;
+}
+
+static int multishift_mixed_impl(stag_lattice lat, stag_field *xs, const double *shifts, int n,
+                                 const stag_field b, double mass, double rel_tol, int max_iter,
+                                 int inner_prec, double delta, stag_solve_info *infos) {
     const int hi = b->prec;
     if (hi != STAG_F64 && hi != STAG_DF64)
         return fail(STAG_ERR_STATE, "stag_cg_multishift_mixed: fields must be F64 or DF64");
@@ -927,11 +987,56 @@ static int batch_solve_raw(int n, stag_lattice *lats, void *const *x, const void
     return worst;
 }
 
+// per-system source normalisation around a batched solve
+struct BatchRhsScale {
+    std::vector<RhsScale> rs;
+    std::vector<stag_field> b;
+    int begin(int n, const stag_field *bs) {
+        rs.assign(n, RhsScale());
+        b.assign(bs, bs + n);
+        for (int i = 0; i < n; i++) {
+            const int st = rhs_scale_begin(bs[i], &rs[i]);
+            if (st != STAG_OK) {
+                end(i, nullptr);
+                return st;
+            }
+            if (rs[i].scaled)
+                b[i] = rs[i].scaled;
+        }
+        return STAG_OK;
+    }
+    // xs NULL: only free the copies of the first n systems
+    int end(int n, stag_field *xs) {
+        int worst = STAG_OK;
+        for (int i = 0; i < n; i++) {
+            const int st = xs ? rhs_scale_end(&rs[i], &xs[i], 1) : rhs_scale_end(&rs[i], nullptr, 0);
+            if (st != STAG_OK && worst == STAG_OK)
+                worst = st;
+        }
+        return worst;
+    }
+};
+
+static int batched_impl(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs, const double *masses,
+                        double rel_tol, int max_iter, stag_solve_info *infos);
+static int batched_mixed_impl(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                              const double *masses, double rel_tol, int max_iter, int inner_prec, double delta,
+                              stag_solve_info *infos);
+
 extern "C" int stag_cg_solve_batched(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
                                      const double *masses, double rel_tol, int max_iter,
                                      stag_solve_info *infos) {
     STAG_NVTX("stag_cg_solve_batched");
     STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched"));
+    BatchRhsScale sc;
+    STAG_TRY(sc.begin(n, bs));
+    const int st = batched_impl(n, lats, xs, sc.b.data(), masses, rel_tol, max_iter, infos);
+    STAG_TRY(sc.end(n, xs));
+    return st;
+}
+
+static int batched_impl(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs, const double *masses,
+                        double rel_tol, int max_iter, stag_solve_info *infos) {
     const int prec = bs[0]->prec;
     if (prec != STAG_F64 && prec != STAG_DF64 && prec != STAG_F32)
         return fail(STAG_ERR_STATE, "stag_cg_solve_batched: fields must be F64, DF64 or F32");
@@ -959,6 +1064,17 @@ extern "C" int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field
                                            double delta, stag_solve_info *infos) {
     STAG_NVTX("stag_cg_solve_batched_mixed");
     STAG_TRY(check_batch(n, lats, xs, bs, masses, rel_tol, max_iter, "stag_cg_solve_batched_mixed"));
+    BatchRhsScale sc;
+    STAG_TRY(sc.begin(n, bs));
+    const int st = batched_mixed_impl(n, lats, xs, sc.b.data(), masses, rel_tol, max_iter, inner_prec, delta,
+                                      infos);
+    STAG_TRY(sc.end(n, xs));
+    return st;
+}
+
+static int batched_mixed_impl(int n, stag_lattice *lats, stag_field *xs, const stag_field *bs,
+                              const double *masses, double rel_tol, int max_iter, int inner_prec, double delta,
+                              stag_solve_info *infos) {
     const int hi = bs[0]->prec;
     if (hi != STAG_F64 && hi != STAG_DF64)
         return fail(STAG_ERR_STATE, "stag_cg_solve_batched_mixed: fields must be F64 or DF64");

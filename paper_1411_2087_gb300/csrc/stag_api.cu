@@ -548,6 +548,21 @@ static int field_io(stag_field f, const double *src, double *dst, int ptr_kind) 
         if (e == cudaSuccess && src)
             e = cudaMemcpyAsync(canon, src, bytes, cudaMemcpyHostToDevice, lat->stream);
     }
+    if (e == cudaSuccess && src && f->prec != STAG_F64) {
+        // the float-based formats hold entries up to the FP32 range only
+        if (!lat->absmax)
+            e = cudaMalloc(&lat->absmax, 2 * sizeof(unsigned));
+        unsigned flag = 0;
+        if (e == cudaSuccess)
+            e = launch_finite_overflow(canon, (long long)lat->Vh * 6, lat->absmax, lat->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&flag, lat->absmax, sizeof flag, cudaMemcpyDeviceToHost, lat->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(lat->stream);
+        if (e == cudaSuccess && flag)
+            return fail(STAG_ERR_ARG, "field import: a finite entry lies beyond the FP32 range of a %s field "
+                        "(the field is unchanged)", prec_name(f->prec));
+    }
     if (e == cudaSuccess)
         e = src ? launch_import(f->prec, lat->geom, canon, f->data, lat->stream)
                 : launch_export(f->prec, lat->geom, f->data, canon, lat->stream);
@@ -796,6 +811,71 @@ static void fill_info(stag_lattice lat, int prec, const CgScalars &h, float ms,
     }
 }
 
+// --------------------------------------------------------------------------
+// source normalisation of the solvers
+// --------------------------------------------------------------------------
+// Double-float and FP32 keep the float exponent range, so a source whose
+// entries are far from 1 would push the residual's squares out of it as the
+// solve proceeds.  When the exponent of b's largest entry lies outside
+// [-kRhsWindow, kRhsWindow], the solve runs on a copy b 2^-k and the solution
+// is multiplied by 2^k afterwards; powers of two scale every intermediate
+// exactly, so the arithmetic is that of the unscaled solve wherever the
+// latter stays in range.  FP64 fields are left alone.
+constexpr int kRhsWindow = 16;
+
+int rhs_scale_begin(const stag_field b, RhsScale *rs) {
+    rs->k = 0;
+    rs->scaled = nullptr;
+    if (b->prec == STAG_F64)
+        return STAG_OK;
+    stag_lattice lat = b->lat;
+    DEVICE_SCOPE(lat->device);
+    if (!lat->absmax)
+        CUDA_TRY(cudaMalloc(&lat->absmax, 2 * sizeof(unsigned)));
+    unsigned bits = 0;
+    CUDA_TRY(launch_field_absmax(b->prec, lat->geom, b->data, lat->absmax, lat->stream));
+    CUDA_TRY(cudaMemcpyAsync(&bits, lat->absmax, sizeof bits, cudaMemcpyDeviceToHost, lat->stream));
+    CUDA_TRY(cudaStreamSynchronize(lat->stream));
+    float m;
+    memcpy(&m, &bits, sizeof m);
+    if (!(m > 0.f) || !(m < INFINITY))
+        return STAG_OK;
+    int k = 0;
+    std::frexp(m, &k);
+    k -= 1;  // m in [2^k, 2^(k+1))
+    if (k >= -kRhsWindow && k <= kRhsWindow)
+        return STAG_OK;
+    stag_field f = nullptr;
+    STAG_TRY(stag_field_create(lat, STAG_EVEN, b->prec, &f));
+    cudaError_t e = cudaMemcpyAsync(f->data, b->data, b->bytes, cudaMemcpyDeviceToDevice, lat->stream);
+    if (e == cudaSuccess)
+        e = launch_field_ldexp(b->prec, lat->geom, f->data, -k, lat->stream);
+    if (e != cudaSuccess) {
+        stag_field_destroy(f);
+        return fail(STAG_ERR_CUDA, "source normalisation: %s", cudaGetErrorString(e));
+    }
+    rs->k = k;
+    rs->scaled = f;
+    return STAG_OK;
+}
+
+int rhs_scale_end(RhsScale *rs, stag_field const *xs, int n) {
+    if (!rs->scaled)
+        return STAG_OK;
+    stag_lattice lat = rs->scaled->lat;
+    DEVICE_SCOPE(lat->device);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; i++)
+        e = launch_field_ldexp(xs[i]->prec, xs[i]->lat->geom, xs[i]->data, rs->k, xs[i]->lat->stream);
+    for (int i = 0; i < n && e == cudaSuccess; i++)
+        e = cudaStreamSynchronize(xs[i]->lat->stream);
+    stag_field_destroy(rs->scaled);
+    rs->scaled = nullptr;
+    if (e != cudaSuccess)
+        return fail(STAG_ERR_CUDA, "source normalisation: %s", cudaGetErrorString(e));
+    return STAG_OK;
+}
+
 // trace (may be NULL): (alpha_k, beta_k, |r_{k+1}|^2) of the first trace_len
 // iterations; tracing runs those iterations host-driven, one at a time
 static int cg_solve_impl(stag_lattice lat, stag_field x, const stag_field b, double mass,
@@ -886,10 +966,30 @@ static int cg_solve_impl(stag_lattice lat, stag_field x, const stag_field b, dou
     return STAG_OK;
 }
 
+// cg_solve_impl on b, or on b 2^-k with the solution scaled back
+static int cg_solve_scaled(stag_lattice lat, stag_field x, const stag_field b, double mass, double rel_tol,
+                           int max_iter, stag_solve_info *info, double *trace, int trace_len) {
+    if (!lat || !x || !b || x == b || x->prec != b->prec || b->lat != lat || b->parity != STAG_EVEN)
+        return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, trace, trace_len);  // reports the error
+    RhsScale rs;
+    STAG_TRY(rhs_scale_begin(b, &rs));
+    stag_solve_info local;
+    const int st = cg_solve_impl(lat, x, rs.scaled ? rs.scaled : b, mass, rel_tol, max_iter, &local, trace,
+                                 trace_len);
+    if (info)
+        *info = local;
+    // |r_{k+1}|^2 of the entries written, back in the units of b
+    if (trace && rs.k)
+        for (int k = 0; k < trace_len && k < local.iters; k++)
+            trace[3 * k + 2] = std::ldexp(trace[3 * k + 2], 2 * rs.k);
+    STAG_TRY(rhs_scale_end(&rs, &x, 1));
+    return st;
+}
+
 extern "C" int stag_cg_solve(stag_lattice lat, stag_field x, const stag_field b, double mass,
                              double rel_tol, int max_iter, stag_solve_info *info) {
     STAG_NVTX("stag_cg_solve");
-    return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, nullptr, 0);
+    return cg_solve_scaled(lat, x, b, mass, rel_tol, max_iter, info, nullptr, 0);
 }
 
 extern "C" int stag_cg_solve_traced(stag_lattice lat, stag_field x, const stag_field b, double mass,
@@ -900,7 +1000,7 @@ extern "C" int stag_cg_solve_traced(stag_lattice lat, stag_field x, const stag_f
         memset(info, 0, sizeof *info);
     if (!trace || trace_len < 0)
         return fail(STAG_ERR_ARG, "stag_cg_solve_traced: need a trace buffer and trace_len >= 0");
-    return cg_solve_impl(lat, x, b, mass, rel_tol, max_iter, info, trace, trace_len);
+    return cg_solve_scaled(lat, x, b, mass, rel_tol, max_iter, info, trace, trace_len);
 }
 
 

@@ -56,7 +56,7 @@ EXPORTED = [
     "stag_net_create", "stag_net_destroy", "stag_net_num_weights", "stag_net_set_weights",
     "stag_net_get_weights", "stag_net_apply", "stag_net_collect_pairs", "stag_net_num_pairs",
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
-    "stag_net_set_loss",
+    "stag_net_set_loss", "stag_cg_solve_learned_mixed",
     "stag_apply_M_noalloc",
     "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced", "stag_cb_neighbor",
     "stag_field_bytes", "stag_field_wrap",
@@ -135,6 +135,7 @@ def lib():
             "stag_net_train": ([P, I, I, D, ctypes.c_uint, P], I),
             "stag_net_set_loss": ([P, I], I),
             "stag_cg_solve_learned": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_cg_solve_learned_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_mixed": ([P, P, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift": ([P, P, P, I, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_multishift_mixed": ([P, P, P, I, P, D, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
@@ -594,6 +595,19 @@ class Net:
         info = SolveInfo()
         st = lib().stag_cg_solve_learned(self.handle, x.handle, b.handle, float(mass), float(tol),
                                          int(max_iter), ctypes.byref(info))
+        if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def cg_mixed(self, x: Field, b: Field, mass: float, tol: float = 1e-10, max_iter: int = 20000,
+                 inner="f16", delta: float = 0.1, raise_on_failure: bool = False) -> dict:
+        """Mixed-precision flexible CG with the net (stag_cg_solve_learned_mixed)."""
+        info = SolveInfo()
+        ip = PREC[inner] if isinstance(inner, str) else int(inner)
+        st = lib().stag_cg_solve_learned_mixed(self.handle, x.handle, b.handle, float(mass), float(tol),
+                                               int(max_iter), ip, float(delta), ctypes.byref(info))
         if raise_on_failure or st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
             _check(st)
         d = info.as_dict()

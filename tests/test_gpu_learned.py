@@ -158,7 +158,7 @@ def test_training_lowers_loss_and_net_cuts_iterations():
     N = oracle.long_links(dims, U)
     Vh = int(np.prod(dims)) // 2
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, N, precisions=("df64", "f32"))
+        lat.upload_gauge(U, N, precisions=("df64", "f32", "f16"))
         net = stag.Net(lat, U, channels=8, seed=1)
         for s in range(4):
             fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1200 + s).numpy())
@@ -173,6 +173,13 @@ def test_training_lowers_loss_and_net_cuts_iterations():
         plain = lat.cg(fx, fb, mass, 1e-10, 20000)
         learned = net.cg(fx, fb, mass, 1e-10, 20000)
         x = fx.export()
+        # the same net inside the mixed-precision flexible CG (FP32 and 16-bit
+        # iteration, double-float reliable updates) against the mixed CG
+        mixed = {}
+        for inner in ("f32", "f16"):
+            plain_m = lat.cg_mixed(fx, fb, mass, 1e-10, 20000, inner)
+            learned_m = net.cg_mixed(fx, fb, mass, 1e-10, 20000, inner)
+            mixed[inner] = (plain_m, learned_m, fx.export())
         net.close()
     res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
     assert learned["return"] == stag.OK, learned
@@ -181,6 +188,12 @@ def test_training_lowers_loss_and_net_cuts_iterations():
     # halve the condition number: about 1.4x fewer iterations
     assert learned["iters"] <= 0.8 * plain["iters"], (learned, plain)
     assert learned["restarts"] == 0
+    for inner, (plain_m, learned_m, xm) in mixed.items():
+        res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, xm)) / np.linalg.norm(b)
+        assert learned_m["return"] == stag.OK, (inner, learned_m)
+        assert res <= 1.05e-10, (inner, res)
+        # no fallback (a fallback adds a whole plain solve to the count)
+        assert learned_m["iters"] <= 0.8 * plain_m["iters"], (inner, learned_m, plain_m)
 
 
 def test_error_loss_training_runs():
