@@ -342,6 +342,8 @@ def run_native(args):
     batched = None
     if not args.no_batched and world == 1:
         batched = batched_comparison(local, rank)
+    # one lattice split over the ranks (strong scaling), on every N
+    ddr = dd_section(local, rank, world, pg, args.steps)
     fp64 = None
     precision = None
     if not args.no_precision and world == 1:
@@ -399,8 +401,64 @@ def run_native(args):
         "learned_vs_fp64": learned,
         "fp64_ieee": fp64,
         "precision_error": precision,
+        "domain_decomposition": ddr,
     }
     return line
+
+
+def dd_section(local, rank, world, pg, steps):
+    """The main workload (32^3x64, m = 0.02, to 1e-10, double float) as one
+    lattice cut in t over the N ranks (stag_ddr_*), NCCL as the communicator:
+    strong scaling.  Seconds per solve are the largest over the ranks; GB/s
+    counts the whole lattice's CG bytes (iterations x 5280 B x Vh)."""
+    import torch
+    from paper_1411_2087_gb300 import stag
+    if DIMS[3] // world < 3:
+        return {"skipped": f"{world} ranks leave slabs thinner than 3 of {DIMS[3]} slices"}
+    dev = torch.device("cuda", local)
+    try:
+        uid = stag.nccl_unique_id() if rank == 0 else None
+    except stag.StagError as e:
+        return {"skipped": str(e)}
+    if pg is not None:
+        box = [uid]
+        pg.broadcast_object_list(box, src=0)
+        uid = box[0]
+    U, b_host = make_inputs(DIMS, dev, 0)
+    torch.cuda.synchronize()
+    Vh = int(np.prod(DIMS)) // 2
+    stream = torch.cuda.Stream(dev)
+    comm = stag.NcclComm(rank, world, uid, local)
+    try:
+        with stag.Lattice(DIMS, device=local, stream=stream.cuda_stream) as lat:
+            lat.upload_gauge(U, None, precisions=("df64",))
+            del U
+            torch.cuda.empty_cache()
+            lat.autotune("df64")
+            d = stag.DDRank(lat, comm)
+            fb = lat.field(stag.EVEN, "df64", b_host)
+            fx = lat.field(stag.EVEN, "df64")
+            info = d.cg(fx, fb, MASS, TOL, 20000)
+            n = max(1, min(int(steps), 5))
+            if pg is not None:
+                pg.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(n):
+                info = d.cg(fx, fb, MASS, TOL, 20000)
+            torch.cuda.synchronize()
+            secs = (time.perf_counter() - t0) / n
+            d.close()
+    finally:
+        comm.close()
+    secs, _ = aggregate_ranks(pg, [secs], [0.0])
+    return {"workload": f"{'x'.join(map(str, DIMS))}, m={MASS}, tol={TOL}, double float, one lattice over "
+                        f"{world} rank(s) split in t",
+            "ranks": world, "scaling": "strong", "comm": "nccl",
+            "seconds_per_solve": round(secs, 4), "iters": info["iters"],
+            "gbs": round(info["iters"] * cg_bytes_per_iter_site("df64") * Vh / secs / 1e9, 1),
+            "true_rel_resid": info["true_rel_resid"], "ok": info["return"] == stag.OK,
+            "slab": stag.ddr_layout(DIMS, world, rank)}
 
 
 # nominal GB300 FP64 rate (FLOP/s); the stencil needs 576 FP64 multiply-adds

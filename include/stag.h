@@ -493,6 +493,86 @@ int stag_dd_dslash(stag_lattice lat, int ndomains, stag_field out, const stag_fi
 int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x_even, const stag_field b_even,
                      double mass, double rel_tol, int max_iter, stag_solve_info *info);
 
+/* ---- domain decomposition over ranks ----------------------------------------
+ * The paper's multi-node MILC runs (Sec. 2 and 3) split the lattice over MPI
+ * ranks that exchange the boundary sites of the vector Dslash acts on and sum
+ * the CG's inner products globally.  Here the t direction is cut into `size`
+ * slabs, one per rank, as for stag_dd_* (rank r owns slices [t0, t0 + nt),
+ * nt = Lt / size, the first Lt % size ranks one more; every nt must be >= 3).
+ * Each rank holds a full-size lattice on its own GPU with the whole gauge
+ * field uploaded: a rank reads the links of its slab and of the three slices
+ * below it, and the upload is their exchange.  Fields on a rank carry values
+ * on its slab; the library overwrites the three slices on either side (the
+ * halo) of every vector it applies Dslash to, and leaves the rest alone.
+ * Before each Dslash a rank sends the three lowest slices of the input to
+ * rank - 1 and the three highest to rank + 1 (periodically) and receives its
+ * halo from them; the CG's global sums (|b|^2, <p, Mp>, |r|^2) are the slab
+ * sums added by the communicator's allreduce.
+ *
+ * The communicator is the caller's (MPI, a torch.distributed group, NCCL
+ * through stag_comm_nccl_create, ...).  A message is the three slices of one
+ * parity in the field's internal layout: component plane by component plane
+ * (16-bit fields: then the per-site norms), each 3 * Lx*Ly*Lz/2 entries. */
+typedef struct {
+    void *ctx;           /* passed back to the callbacks                          */
+    int rank, size;      /* 0 <= rank < size                                      */
+    int device_buffers;  /* 0: exchange gets host memory and completes before it
+                            returns; 1: device memory of the rank's device, and it
+                            may enqueue the transfer on `stream` (the lattice's)   */
+    /* send `bytes` of to_prev to rank - 1 and of to_next to rank + 1 (mod size);
+     * receive from rank - 1 into from_prev and from rank + 1 into from_next.
+     * With size 1 both neighbours are the rank itself.  Returns 0 on success. */
+    int (*exchange)(void *ctx, const void *to_prev, const void *to_next, void *from_prev, void *from_next,
+                    unsigned long long bytes, void *stream);
+    /* sum n doubles (host memory) over all ranks, in place; the same result on
+     * every rank.  Returns 0 on success. */
+    int (*allreduce)(void *ctx, double *vals, int n);
+} stag_comm;
+
+typedef struct stag_ddr_s *stag_ddr;
+
+/* The slab of rank `rank` of `size` on a lattice `dims`: t0 and nt.  Host
+ * only; STAG_ERR_ARG for bad dims or a slab thinner than 3 slices. */
+int stag_ddr_layout(const int dims[4], int size, int rank, int *t0, int *nt);
+
+/* The halo exchange of one parity field held in host memory in the
+ * canonical layout (complex128 [Vh][3], full size): the halo slices of
+ * `field` are filled from the neighbours' boundary slices through `comm`
+ * (whose device_buffers must be 0), with the messages the device path sends
+ * (converted to complex128).  Host only: it lets a test on machines without
+ * a GPU drive the protocol.  Errors: STAG_ERR_ARG, or STAG_ERR_STATE when a
+ * callback fails. */
+int stag_ddr_exchange_host(const int dims[4], int parity, const stag_comm *comm, double *field);
+
+/* A rank's view of a decomposed lattice: `lat` is the rank's full-size
+ * lattice (gauge uploaded in the precisions used), `comm` is copied. */
+int stag_ddr_create(stag_lattice lat, const stag_comm *comm, stag_ddr *out);
+int stag_ddr_destroy(stag_ddr d);
+
+/* out = D in on the rank's slab (out's parity selects D_eo or D_oe), after
+ * exchanging in's halo; fields of opposite parity and one precision with a
+ * gauge copy of it.  Synchronous. */
+int stag_ddr_dslash(stag_ddr d, stag_field out, stag_field in);
+
+/* CG for M x = b over all ranks (every rank calls it with its slab of b);
+ * the rank's slab of x receives its part of the solution.  F64 or DF64
+ * fields.  The iteration is host-driven: two halo exchanges and two
+ * allreduces per iteration.  info->true_rel_resid is |b - M x| / |b| over the
+ * whole lattice (one more exchange and allreduce).  Same return values as
+ * stag_cg_solve, the same on every rank. */
+int stag_ddr_cg_solve(stag_ddr d, stag_field x, const stag_field b, double mass, double rel_tol, int max_iter,
+                      stag_solve_info *info);
+
+/* NCCL as the communicator: device-buffer exchange (grouped ncclSend/ncclRecv
+ * on the lattice stream) and allreduce (ncclAllReduce of the doubles through a
+ * device buffer).  stag_comm_nccl_id writes a new 128-byte unique id on one
+ * rank, which the caller distributes; every rank then calls
+ * stag_comm_nccl_create with it, its rank and the device it uses (a
+ * collective call).  STAG_ERR_STATE if the library was built without NCCL. */
+int stag_comm_nccl_id(unsigned char id[128]);
+int stag_comm_nccl_create(int rank, int size, const unsigned char id[128], int device, stag_comm *out);
+int stag_comm_nccl_destroy(stag_comm *c);
+
 /* ---- diagnostics ----------------------------------------------------------
  * The neighbour arithmetic of the Dslash kernels, run on the host: the
  * checkerboard index of the site reached from site `cb` of parity `parity`

@@ -60,6 +60,8 @@ EXPORTED = [
     "stag_apply_M_noalloc",
     "stag_dd_dslash", "stag_dd_cg_solve", "stag_cg_solve_traced", "stag_cb_neighbor",
     "stag_field_bytes", "stag_field_wrap",
+    "stag_ddr_layout", "stag_ddr_exchange_host", "stag_ddr_create", "stag_ddr_destroy", "stag_ddr_dslash",
+    "stag_ddr_cg_solve", "stag_comm_nccl_id", "stag_comm_nccl_create", "stag_comm_nccl_destroy",
     "stag_strerror", "stag_last_error_message", "stag_version",
 ]
 
@@ -72,6 +74,17 @@ class StagError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} (status {status})")
         self.status = status
+
+
+# communicator callbacks of the rank decomposition (stag_comm in stag.h)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class CommStruct(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("rank", ctypes.c_int), ("size", ctypes.c_int),
+                ("device_buffers", ctypes.c_int), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -146,6 +159,15 @@ def lib():
             "stag_cb_neighbor": ([P, I, ctypes.c_longlong, I, I, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(I)], I),
             "stag_dd_cg_solve": ([P, I, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_ddr_layout": ([P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)], I),
+            "stag_ddr_exchange_host": ([P, I, ctypes.POINTER(CommStruct), P], I),
+            "stag_ddr_create": ([P, ctypes.POINTER(CommStruct), PP], I),
+            "stag_ddr_destroy": ([P], I),
+            "stag_ddr_dslash": ([P, P, P], I),
+            "stag_ddr_cg_solve": ([P, P, P, D, D, I, ctypes.POINTER(SolveInfo)], I),
+            "stag_comm_nccl_id": ([P], I),
+            "stag_comm_nccl_create": ([I, I, P, I, ctypes.POINTER(CommStruct)], I),
+            "stag_comm_nccl_destroy": ([ctypes.POINTER(CommStruct)], I),
             "stag_strerror": ([I], ctypes.c_char_p),
             "stag_last_error_message": ([], ctypes.c_char_p),
             "stag_version": ([], ctypes.c_char_p),
@@ -473,6 +495,123 @@ def apply_M_noalloc(dims, fat, lng, mass, in_even, out_even, bc=BC_DEFAULT, c1=C
                                       ctypes.c_void_p(in_even.data_ptr()),
                                       ctypes.c_void_p(out_even.data_ptr()),
                                       ctypes.c_void_p(stream) if stream else None))
+
+
+# --------------------------------------------------------------------------
+# domain decomposition over ranks
+# --------------------------------------------------------------------------
+
+def ddr_layout(dims, size: int, rank: int):
+    """(t0, nt): the slab of `rank` of `size` (stag_ddr_layout)."""
+    t0, nt = ctypes.c_int(), ctypes.c_int()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(lib().stag_ddr_layout(d, int(size), int(rank), ctypes.byref(t0), ctypes.byref(nt)))
+    return t0.value, nt.value
+
+
+class HostComm:
+    """A communicator over host memory from two Python callables:
+    exchange(to_prev: bytes, to_next: bytes) -> (from_prev, from_next) and
+    allreduce(values: list[float]) -> list[float] (sums over the ranks).
+    Exceptions in the callables become a failed call (status 1)."""
+
+    def __init__(self, rank: int, size: int, exchange, allreduce):
+        self.rank, self.size = int(rank), int(size)
+        self._exchange, self._allreduce = exchange, allreduce
+        self.error = None
+
+        def ex(ctx, to_prev, to_next, from_prev, from_next, nbytes, stream):
+            try:
+                fp, fn = self._exchange(ctypes.string_at(to_prev, nbytes), ctypes.string_at(to_next, nbytes))
+                if len(fp) != nbytes or len(fn) != nbytes:
+                    raise ValueError("exchange returned messages of the wrong size")
+                ctypes.memmove(from_prev, fp, nbytes)
+                ctypes.memmove(from_next, fn, nbytes)
+                return 0
+            except BaseException as e:  # noqa: BLE001 - reported through the status
+                self.error = e
+                return 1
+
+        def ar(ctx, vals, n):
+            try:
+                out = self._allreduce([vals[k] for k in range(n)])
+                for k in range(n):
+                    vals[k] = float(out[k])
+                return 0
+            except BaseException as e:  # noqa: BLE001
+                self.error = e
+                return 1
+
+        self._cb = (EXCHANGE_FN(ex), ALLREDUCE_FN(ar))
+        self.struct = CommStruct(None, self.rank, self.size, 0, self._cb[0], self._cb[1])
+
+
+class NcclComm:
+    """NCCL as the communicator (stag_comm_nccl_create); `uid` is the
+    128-byte id from nccl_unique_id() on one rank, shared by the caller."""
+
+    def __init__(self, rank: int, size: int, uid: bytes, device: int):
+        if len(uid) != 128:
+            raise ValueError("an NCCL unique id has 128 bytes")
+        self.struct = CommStruct()
+        buf = (ctypes.c_ubyte * 128).from_buffer_copy(uid)
+        _check(lib().stag_comm_nccl_create(int(rank), int(size), buf, int(device), ctypes.byref(self.struct)))
+        self.rank, self.size = int(rank), int(size)
+
+    def close(self):
+        if self.struct.ctx:
+            _check(lib().stag_comm_nccl_destroy(ctypes.byref(self.struct)))
+
+
+def nccl_unique_id() -> bytes:
+    buf = (ctypes.c_ubyte * 128)()
+    _check(lib().stag_comm_nccl_id(buf))
+    return bytes(buf)
+
+
+def ddr_exchange_host(dims, parity: int, comm, field):
+    """stag_ddr_exchange_host on a canonical complex128 [Vh][3] numpy array
+    (modified in place: its halo slices)."""
+    Vh = int(np.prod(dims)) // 2
+    p, kind, keep = _as_buffer(field, (Vh, 3), writable=True)
+    if kind != PTR_HOST:
+        raise ValueError("stag_ddr_exchange_host works on host memory")
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(lib().stag_ddr_exchange_host(d, int(parity), ctypes.byref(comm.struct), p))
+
+
+class DDRank:
+    """One rank's view of a lattice split in t over the ranks of `comm`
+    (stag_ddr_*): `lattice` is this rank's full-size lattice."""
+
+    def __init__(self, lattice: "Lattice", comm):
+        self.lattice, self.comm = lattice, comm
+        h = ctypes.c_void_p()
+        _check(lib().stag_ddr_create(lattice.handle, ctypes.byref(comm.struct), ctypes.byref(h)))
+        self.handle = h
+        self.t0, self.nt = ddr_layout(lattice.dims, comm.size, comm.rank)
+        if not hasattr(lattice, "_nets"):
+            lattice._nets = set()
+        lattice._nets.add(self)
+
+    def dslash(self, out: Field, inp: Field):
+        _check(lib().stag_ddr_dslash(self.handle, out.handle, inp.handle))
+
+    def cg(self, x: Field, b: Field, mass: float, tol: float = 1e-10, max_iter: int = 20000) -> dict:
+        info = SolveInfo()
+        st = lib().stag_ddr_cg_solve(self.handle, x.handle, b.handle, float(mass), float(tol), int(max_iter),
+                                     ctypes.byref(info))
+        if st not in (OK, ERR_NOT_CONVERGED, ERR_BREAKDOWN):
+            _check(st)
+        d = info.as_dict()
+        d["return"] = st
+        return d
+
+    def close(self):
+        if self.handle:
+            _check(lib().stag_ddr_destroy(self.handle))
+            self.handle = None
+            getattr(self.lattice, "_nets", set()).discard(self)
 
 
 def cg_batched(systems, tol: float = 1e-10, max_iter: int = 20000, mixed: Optional[str] = None,
