@@ -306,16 +306,50 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
                                 const double *masses, double rel_tol, int max_iter, int inner_prec,
                                 double delta, stag_solve_info *infos);
 
-/* Autotuner: time the candidate block sizes (128, 256 threads) of the Dslash
- * kernel, of the solvers' M Dslash (m^2 p - D t with one <p, Mp> partial per
- * block) and of the batched multi-right-hand-side Dslash in precision `prec`
- * on this lattice (10 launches each after 2 warm-ups, CUDA events on the
- * lattice stream) and keep the fastest of each for every later call on this
- * lattice.  dslash_us[2] and batch_us[2] (may be NULL) receive the measured
- * microseconds per launch for 128 and 256 of the Dslash and the batched
- * Dslash (the batched entries are 0 for STAG_F16, which has no batched
- * kernels).  Needs a gauge copy of `prec`; overwrites the lattice's internal
- * work vectors. */
+/* Autotuner.  Candidates, in precision `prec` on this lattice (10 launches
+ * each after 2 warm-ups, CUDA events on the lattice stream):
+ *   STAG_TUNE_DSLASH  the Dslash: block 64, 128, 256 or 512 threads, in two
+ *                     register variants (regs 1: the compiler's choice,
+ *                     2: at most 64 registers, 1024 resident threads per SM)
+ *   STAG_TUNE_M       the solvers' M Dslash (m^2 p - D t with one <p, Mp>
+ *                     partial per block): the same candidates
+ *   STAG_TUNE_BATCH   the batched multi-right-hand-side Dslash: block 128 or
+ *                     256, and the right-hand sides sharing one link load
+ *                     (group: FP32 4 or 8, F64/DF64 2 or 4; decided by the
+ *                     time per right-hand side); none in 16-bit storage
+ * The fastest of each kind is kept for every later call on the lattice and
+ * cached for the process per (dims, precision, link layout, device); when
+ * the environment variable STAG_TUNE_CACHE names a file, the cache is read
+ * from it at the first call and every new choice appended to it.  Every
+ * candidate computes the same numbers (the block size only changes the order
+ * of the solvers' partial sums).  Needs a gauge copy of `prec`; overwrites
+ * the lattice's internal work vectors. */
+typedef struct {
+    int kernel;    /* STAG_TUNE_DSLASH, STAG_TUNE_M or STAG_TUNE_BATCH          */
+    int block;     /* threads per block                                        */
+    int regs;      /* Dslash kinds: 1 compiler's choice, 2 capped; batched 0   */
+    int group;     /* batched: right-hand sides per group; others 0            */
+    double us;     /* microseconds per launch; 0 for a choice from the cache    */
+    int chosen;    /* 1 for the configuration kept                             */
+} stag_tune_result;
+enum { STAG_TUNE_DSLASH = 0, STAG_TUNE_M = 1, STAG_TUNE_BATCH = 2 };
+enum { STAG_TUNE_FORCE = 1 };  /* time again even if the cache holds a choice */
+
+/* Tune (or take the cached choice, *cached = 1: then only the chosen
+ * configurations are reported, untimed).  out: up to cap results; *n the
+ * number written.  flags: 0 or STAG_TUNE_FORCE.  n, cached may be NULL. */
+int stag_lattice_autotune_all(stag_lattice lat, int prec, unsigned flags, stag_tune_result *out, int cap,
+                              int *n, int *cached);
+
+/* Set one kind's configuration by hand (regs 0 = the library's default
+ * variant; group 0 = the largest).  Bad values: STAG_ERR_ARG. */
+int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, int block, int regs, int group);
+
+/* The autotuner, timed again (STAG_TUNE_FORCE): dslash_us[2] and batch_us[2]
+ * (may be NULL) receive, for blocks of 128 and 256 threads, the fastest
+ * Dslash candidate's microseconds per launch and the batched Dslash's time
+ * for one launch over the largest group at its fastest group size (0 for
+ * STAG_F16). */
 int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us);
 
 /* ---- learned preconditioner ------------------------------------------------

@@ -155,8 +155,11 @@ struct stag_lattice_s {
     void *bxlo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 solutions of the sloppy batched phase
     void *bblo[BATCH_MAX_G * BATCH_KMAX] = {};  // FP32 right-hand sides of that phase
     int batch_block[4] = {128, 128, 128, 128};  // block size of the batched kernels (autotuned)
+    int batch_k[4] = {0, 0, 0, 0};              // right-hand sides per batched group (0 = the largest)
     int dslash_block[4] = {0, 0, 0, 0};         // block size of the Dslash kernels (0 = default)
+    int dslash_regs[4] = {0, 0, 0, 0};          // its register variant (REGS_*)
     int mdslash_block[4] = {0, 0, 0, 0};        // block size of the M Dslash with <p, Mp> partials (0 = as above)
+    int mdslash_regs[4] = {0, 0, 0, 0};         // its register variant
     int cg_launch = STAG_CG_LAUNCH_GRAPH;  // how stag_cg_solve drives its iterations
     int cg_chunk = 32;                     // iterations between status polls (host mode)
 };
@@ -231,6 +234,7 @@ static inline DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, co
     a.out = out;
     a.partial = lat->partial;
     a.sc = lat->sc;
+    a.regs = lat->dslash_regs[prec];
     if (prec == STAG_F16) {
         a.link_scale[0] = lat->link_scale[0];
         a.link_scale[1] = lat->link_scale[1];
@@ -318,6 +322,7 @@ static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *
     DslashArgs a = dslash_args(lat, prec, STAG_EVEN, t, Ap);
     a.p = p;
     a.skip_if_done = skip_if_done;
+    a.regs = lat->mdslash_block[prec] > 0 ? lat->mdslash_regs[prec] : lat->dslash_regs[prec];
     const int block = m_block(lat, prec);
     cudaError_t e = launch_dslash(prec, EPI_M_PART, a, block, s);
     if (e != cudaSuccess)

@@ -44,6 +44,7 @@ struct BatchCtl {
 
 struct BatchArgs {
     int G;
+    int kmax;     // the largest group: selects the kernels' K
     int nblocks;  // total blocks of the grouped launch
     int dnblocks; // total blocks of a lane-mapped Dslash launch
     BatchGroup grp[BATCH_MAX_G];

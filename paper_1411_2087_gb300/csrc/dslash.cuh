@@ -46,7 +46,12 @@ struct DslashArgs {
     int c0, cn;             // output sites c0 .. c0+cn-1 (cn = 0: all Vh)
     float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
     int bc_neg[4];          // boundary sign of direction mu is -1
+    int regs;               // EPI_NONE, EPI_M_PART: REGS_DEFAULT, REGS_FREE or REGS_CAPPED (autotuned)
 };
+
+// register variant of the stencil (DslashArgs::regs): the launcher's
+// measured default, the compiler's free choice, or at most 64 registers
+enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2 };
 
 // rebuild row 2 of L = s U (U in SU(3)) from rows 0 and 1: conj(r0 x r1) / s
 template <class R>

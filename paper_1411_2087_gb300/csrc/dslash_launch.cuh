@@ -18,12 +18,23 @@ namespace stag {
 template <int P, int EPI, bool COMP>
 constexpr bool kCapped = (P == P_F16 && (COMP || EPI != EPI_NONE)) || (P == P_F32 && !COMP);
 
+// The plain stencil and the M stencil with <p, Mp> partials (the solvers'
+// two kernels per iteration) are instantiated in both register variants, so
+// that the autotuner can time them; the other epilogues use the default.
 template <int P, int EPI, int BLOCK, bool COMP>
 static void launch_one(int grid, const DslashArgs &a, cudaStream_t s) {
-    if constexpr (kCapped<P, EPI, COMP>)
+    constexpr bool tunable = EPI == EPI_NONE || EPI == EPI_M_PART;
+    const bool capped = tunable && a.regs != REGS_DEFAULT ? a.regs == REGS_CAPPED : kCapped<P, EPI, COMP>;
+    if constexpr (tunable) {
+        if (capped)
+            dslash_kernel_capped<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+        else
+            dslash_kernel<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+    } else if constexpr (kCapped<P, EPI, COMP>) {
         dslash_kernel_capped<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
-    else
+    } else {
         dslash_kernel<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+    }
 }
 
 template <int P, int BLOCK, bool COMP>
@@ -59,8 +70,10 @@ static cudaError_t launch_p_b(int epi, const DslashArgs &a, cudaStream_t s) {
 
 template <int P> cudaError_t launch_dslash_p(int epi, const DslashArgs &a, int block, cudaStream_t s) {
     switch (block) {
+    case 64: return launch_p_b<P, 64>(epi, a, s);
     case 128: return launch_p_b<P, 128>(epi, a, s);
     case 256: return launch_p_b<P, 256>(epi, a, s);
+    case 512: return launch_p_b<P, 512>(epi, a, s);
     default: return cudaErrorInvalidValue;
     }
 }

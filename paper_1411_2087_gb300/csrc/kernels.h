@@ -89,6 +89,7 @@ cudaError_t launch_convert(int prec_out, int prec_in, const Geom &g, const void 
 struct BatchArgs;
 cudaError_t launch_batch(int prec, int what, const BatchArgs &a, int block, cudaStream_t s);
 int batch_max_k(int prec);
+int batch_min_k(int prec);
 
 // record the calling thread's last error message (read back by
 // stag_last_error_message) and return `code`

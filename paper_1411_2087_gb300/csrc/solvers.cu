@@ -4,6 +4,9 @@
 #include "api_internal.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
 
 // --------------------------------------------------------------------------
 // mixed-precision CG with reliable updates (kernels_mixed.cu has the method)
@@ -712,7 +715,8 @@ struct BatchPlan {
 // allocate work vectors and reduction buffers; x/b are raw buffers
 static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, const void *const *b,
                       int prec) {
-    const int K = batch_max_k(prec);
+    // systems per group: the lattice's tuned group size, else the largest
+    auto group_k = [&](stag_lattice L) { return L->batch_k[prec] > 0 ? L->batch_k[prec] : batch_max_k(prec); };
     memset(&P.a, 0, sizeof P.a);
     P.nsys = n;
     P.prec = prec;
@@ -728,6 +732,7 @@ static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, c
             if (lats[j] == lats[i])
                 slot++;
         slot_of_lat[i] = slot;
+        const int K = group_k(lats[i]);
         const bool new_group = G == 0 || lats[i] != lats[i - 1] || P.a.grp[G - 1].K == K;
         if (new_group) {
             if (G == BATCH_MAX_G)
@@ -760,6 +765,9 @@ static int plan_batch(BatchPlan &P, int n, stag_lattice *lats, void *const *x, c
     }
     P.a.G = G;
     P.a.nblocks = blocks;
+    P.a.kmax = 0;
+    for (int gi = 0; gi < G; gi++)
+        P.a.kmax = std::max(P.a.kmax, P.a.grp[gi].K);
     // lane-mapped Dslash (double-float, FP64): one thread per (site, system)
     int dblocks = 0;
     for (int gi = 0; gi < G; gi++) {
@@ -1156,108 +1164,281 @@ static int batched_mixed_impl(int n, stag_lattice *lats, stag_field *xs, const s
 // autotuner: time the candidate block sizes, keep the fastest per lattice
 // and precision
 // --------------------------------------------------------------------------
-extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us) {
-    STAG_NVTX("stag_lattice_autotune");
-    if (!lat)
-        return fail(STAG_ERR_ARG, "stag_lattice_autotune: lattice is NULL");
-    if (!prec_valid(prec))
-        return fail(STAG_ERR_ARG, "stag_lattice_autotune: bad precision %d", prec);
-    if (!lat->has_gauge || !lat->links[prec])
-        return fail(STAG_ERR_STATE, "stag_lattice_autotune: no %s gauge copy uploaded", prec_name(prec));
-    DEVICE_SCOPE(lat->device);
-    STAG_TRY(ensure_cg_work(lat, prec));
+// --------------------------------------------------------------------------
+// autotuner
+// --------------------------------------------------------------------------
+// The choices of one (lattice shape, precision, link layout, device): block
+// size and register variant of the Dslash and of the M Dslash with partials,
+// block size and group size of the batched Dslash.
+struct TuneChoice {
+    int dblock = 0, dregs = 0, mblock = 0, mregs = 0, bblock = 0, bk = 0;
+};
+
+static std::mutex g_tune_mutex;
+static std::map<std::string, TuneChoice> g_tune_cache;
+static bool g_tune_file_read = false;
+
+static std::string tune_key(const stag_lattice lat, int prec) {
+    cudaDeviceProp prop;
+    std::string dev = "unknown";
+    if (cudaGetDeviceProperties(&prop, lat->device) == cudaSuccess) {
+        dev = prop.name;
+        for (char &c : dev)
+            if (c == ' ')
+                c = '_';
+    }
+    char buf[256];
+    snprintf(buf, sizeof buf, "%d %d %d %d %d %d %s", lat->dims[0], lat->dims[1], lat->dims[2], lat->dims[3], prec,
+             lat->links_c12[prec] ? 1 : 0, dev.c_str());
+    return buf;
+}
+
+// the optional file cache: one line per key, "stag-tune <key> <six ints>"
+static const char *tune_file() { return getenv("STAG_TUNE_CACHE"); }
+
+static void tune_file_read_locked() {
+    if (g_tune_file_read)
+        return;
+    g_tune_file_read = true;
+    const char *path = tune_file();
+    if (!path)
+        return;
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        int d[4], prec, comp;
+        char dev[200];
+        TuneChoice c;
+        if (sscanf(line, "stag-tune %d %d %d %d %d %d %199s %d %d %d %d %d %d", &d[0], &d[1], &d[2], &d[3], &prec,
+                   &comp, dev, &c.dblock, &c.dregs, &c.mblock, &c.mregs, &c.bblock, &c.bk) == 13) {
+            char key[256];
+            snprintf(key, sizeof key, "%d %d %d %d %d %d %s", d[0], d[1], d[2], d[3], prec, comp, dev);
+            g_tune_cache[key] = c;
+        }
+    }
+    fclose(f);
+}
+
+static void tune_file_append(const std::string &key, const TuneChoice &c) {
+    const char *path = tune_file();
+    if (!path)
+        return;
+    FILE *f = fopen(path, "a");
+    if (!f)
+        return;
+    fprintf(f, "stag-tune %s %d %d %d %d %d %d\n", key.c_str(), c.dblock, c.dregs, c.mblock, c.mregs, c.bblock, c.bk);
+    fclose(f);
+}
+
+static void apply_choice(stag_lattice lat, int prec, const TuneChoice &c) {
+    lat->dslash_block[prec] = c.dblock;
+    lat->dslash_regs[prec] = c.dregs;
+    lat->mdslash_block[prec] = c.mblock;
+    lat->mdslash_regs[prec] = c.mregs;
+    if (c.bblock > 0) {
+        lat->batch_block[prec] = c.bblock;
+        lat->batch_k[prec] = c.bk;
+    }
+}
+
+// microseconds per launch of `launch` (2 warm-ups, `reps` timed launches,
+// CUDA events on the lattice stream)
+template <class F>
+static int time_launch(stag_lattice lat, F launch, int reps, double *us) {
     cudaStream_t s = lat->stream;
+    for (int i = 0; i < 2; i++)
+        CUDA_TRY(launch());
+    CUDA_TRY(cudaEventRecord(lat->ev0, s));
+    for (int i = 0; i < reps; i++)
+        CUDA_TRY(launch());
+    CUDA_TRY(cudaEventRecord(lat->ev1, s));
+    CUDA_TRY(cudaEventSynchronize(lat->ev1));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
+    *us = 1e3 * ms / reps;
+    return STAG_OK;
+}
+
+static const int kTuneBlocks[4] = {64, 128, 256, 512};
+
+static int tune_all(stag_lattice lat, int prec, std::vector<stag_tune_result> &res, TuneChoice &c) {
+    STAG_TRY(ensure_cg_work(lat, prec));
     CgWork &w = lat->cg[prec];
-    const int cand[2] = {128, 256};
+    cudaStream_t s = lat->stream;
     const int reps = 10;
-    double best = 1e300;
-    int best_b = 128;
-    for (int k = 0; k < 2; k++) {
-        DslashArgs a = dslash_args(lat, prec, STAG_ODD, w.p, w.t);
-        for (int i = 0; i < 2; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        for (int i = 0; i < reps; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_NONE, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
-        CUDA_TRY(cudaEventSynchronize(lat->ev1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
-        const double us = 1e3 * ms / reps;
-        if (dslash_us)
-            dslash_us[k] = us;
-        if (us < best) {
-            best = us;
-            best_b = cand[k];
-        }
+    // the Dslash and the M Dslash with partials: block x register variant
+    for (int kind = 0; kind < 2; kind++) {
+        double best = 1e300;
+        for (int bi = 0; bi < 4; bi++)
+            for (int regs = REGS_FREE; regs <= REGS_CAPPED; regs++) {
+                const int block = kTuneBlocks[bi];
+                DslashArgs a = kind == 0 ? dslash_args(lat, prec, STAG_ODD, w.p, w.t)
+                                         : dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
+                a.p = w.p;
+                a.regs = regs;
+                const int epi = kind == 0 ? EPI_NONE : EPI_M_PART;
+                double us = 0;
+                STAG_TRY(time_launch(lat, [&]() { return launch_dslash(prec, epi, a, block, s); }, reps, &us));
+                stag_tune_result r = {kind == 0 ? STAG_TUNE_DSLASH : STAG_TUNE_M, block, regs, 0, us, 0};
+                res.push_back(r);
+                if (us < best) {
+                    best = us;
+                    (kind == 0 ? c.dblock : c.mblock) = block;
+                    (kind == 0 ? c.dregs : c.mregs) = regs;
+                }
+            }
     }
-    lat->dslash_block[prec] = best_b;
-    // the M Dslash with <p, Mp> partials of the solvers' iterations
-    best = 1e300;
-    best_b = 128;
-    for (int k = 0; k < 2; k++) {
-        DslashArgs a = dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
-        a.p = w.p;
-        for (int i = 0; i < 2; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_M_PART, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev0, s));
-        for (int i = 0; i < reps; i++)
-            CUDA_TRY(launch_dslash(prec, EPI_M_PART, a, cand[k], s));
-        CUDA_TRY(cudaEventRecord(lat->ev1, s));
-        CUDA_TRY(cudaEventSynchronize(lat->ev1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, lat->ev0, lat->ev1));
-        const double us = 1e3 * ms / reps;
-        if (us < best) {
-            best = us;
-            best_b = cand[k];
-        }
-    }
-    lat->mdslash_block[prec] = best_b;
     if (prec == STAG_F16)
         return STAG_OK;  // no batched kernels in 16-bit storage
-    // batched kernels: one group with the largest K on this lattice
-    const int K = batch_max_k(prec);
-    std::vector<stag_lattice> lats(K, lat);
-    std::vector<void *> x(K);
-    std::vector<const void *> b(K);
-    for (int i = 0; i < K; i++) {
+    // the batched Dslash: block x systems per group, one group of K systems;
+    // the time per right-hand side decides
+    const int kmax = batch_max_k(prec);
+    for (int i = 0; i < kmax; i++)
         STAG_TRY(alloc_vec(lat, prec, &lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0]));
-        x[i] = lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0];
-        b[i] = w.p;
-    }
-    best = 1e300;
-    best_b = 128;
-    for (int k = 0; k < 2; k++) {
-        lat->batch_block[prec] = cand[k];
-        BatchPlan P;
-        STAG_TRY(plan_batch(P, K, lats.data(), x.data(), b.data(), prec));
-        cudaError_t e = cudaSuccess;
-        for (int i = 0; i < 2 && e == cudaSuccess; i++)
-            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(lat->ev0, s);
-        for (int i = 0; i < reps && e == cudaSuccess; i++)
-            e = launch_batch(prec, BATCH_DSLASH_X, P.a, cand[k], s);
-        if (e == cudaSuccess)
-            e = cudaEventRecord(lat->ev1, s);
-        if (e == cudaSuccess)
-            e = cudaEventSynchronize(lat->ev1);
-        float ms = 0.f;
-        if (e == cudaSuccess)
-            e = cudaEventElapsedTime(&ms, lat->ev0, lat->ev1);
-        P.release();
-        if (e != cudaSuccess)
-            return fail(STAG_ERR_CUDA, "stag_lattice_autotune: %s", cudaGetErrorString(e));
-        const double us = 1e3 * ms / reps;
-        if (batch_us)
-            batch_us[k] = us;
-        if (us < best) {
-            best = us;
-            best_b = cand[k];
+    double best = 1e300;
+    const int saved_block = lat->batch_block[prec], saved_k = lat->batch_k[prec];
+    for (int K = batch_min_k(prec); K <= kmax; K *= 2)
+        for (int block = 128; block <= 256; block *= 2) {
+            std::vector<stag_lattice> lats(K, lat);
+            std::vector<void *> x(K);
+            std::vector<const void *> b(K);
+            for (int i = 0; i < K; i++) {
+                x[i] = lat->bwork[prec][BATCH_MAX_G * BATCH_KMAX - 1 - i][0];
+                b[i] = w.p;
+            }
+            lat->batch_block[prec] = block;
+            lat->batch_k[prec] = K;
+            BatchPlan P;
+            int st = plan_batch(P, K, lats.data(), x.data(), b.data(), prec);
+            double us = 0;
+            if (st == STAG_OK)
+                st = time_launch(lat, [&]() { return launch_batch(prec, BATCH_DSLASH_X, P.a, block, s); }, reps, &us);
+            P.release();
+            if (st != STAG_OK) {
+                lat->batch_block[prec] = saved_block;
+                lat->batch_k[prec] = saved_k;
+                return st;
+            }
+            stag_tune_result r = {STAG_TUNE_BATCH, block, 0, K, us, 0};
+            res.push_back(r);
+            if (us / K < best) {
+                best = us / K;
+                c.bblock = block;
+                c.bk = K;
+            }
+        }
+    return STAG_OK;
+}
+
+static int check_tune_args(stag_lattice lat, int prec, const char *who) {
+    if (!lat)
+        return fail(STAG_ERR_ARG, "%s: lattice is NULL", who);
+    if (!prec_valid(prec))
+        return fail(STAG_ERR_ARG, "%s: bad precision %d", who, prec);
+    if (!lat->has_gauge || !lat->links[prec])
+        return fail(STAG_ERR_STATE, "%s: no %s gauge copy uploaded", who, prec_name(prec));
+    return STAG_OK;
+}
+
+extern "C" int stag_lattice_autotune_all(stag_lattice lat, int prec, unsigned flags, stag_tune_result *out,
+                                         int cap, int *n, int *cached) {
+    STAG_NVTX("stag_lattice_autotune_all");
+    if (n)
+        *n = 0;
+    if (cached)
+        *cached = 0;
+    STAG_TRY(check_tune_args(lat, prec, "stag_lattice_autotune_all"));
+    if (cap < 0 || (cap > 0 && !out) || (flags & ~STAG_TUNE_FORCE))
+        return fail(STAG_ERR_ARG, "stag_lattice_autotune_all: bad output buffer or flags");
+    DEVICE_SCOPE(lat->device);
+    const std::string key = tune_key(lat, prec);
+    TuneChoice c;
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        tune_file_read_locked();
+        auto it = g_tune_cache.find(key);
+        if (!(flags & STAG_TUNE_FORCE) && it != g_tune_cache.end()) {
+            c = it->second;
+            hit = true;
         }
     }
-    lat->batch_block[prec] = best_b;
+    std::vector<stag_tune_result> res;
+    if (hit) {
+        // the cached choices, untimed
+        res.push_back({STAG_TUNE_DSLASH, c.dblock, c.dregs, 0, 0.0, 1});
+        res.push_back({STAG_TUNE_M, c.mblock, c.mregs, 0, 0.0, 1});
+        if (c.bblock > 0)
+            res.push_back({STAG_TUNE_BATCH, c.bblock, 0, c.bk, 0.0, 1});
+    } else {
+        STAG_TRY(tune_all(lat, prec, res, c));
+        for (auto &r : res)
+            r.chosen = (r.kernel == STAG_TUNE_DSLASH && r.block == c.dblock && r.regs == c.dregs) ||
+                       (r.kernel == STAG_TUNE_M && r.block == c.mblock && r.regs == c.mregs) ||
+                       (r.kernel == STAG_TUNE_BATCH && r.block == c.bblock && r.group == c.bk);
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = c;
+        tune_file_append(key, c);
+    }
+    apply_choice(lat, prec, c);
+    const int m = (int)res.size() < cap ? (int)res.size() : cap;
+    for (int k = 0; k < m; k++)
+        out[k] = res[k];
+    if (n)
+        *n = m;
+    if (cached)
+        *cached = hit ? 1 : 0;
+    return STAG_OK;
+}
+
+extern "C" int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, int block, int regs, int group) {
+    STAG_TRY(check_tune_args(lat, prec, "stag_lattice_set_tuning"));
+    switch (kernel) {
+    case STAG_TUNE_DSLASH:
+    case STAG_TUNE_M:
+        if ((block != 64 && block != 128 && block != 256 && block != 512) || regs < REGS_DEFAULT || regs > REGS_CAPPED)
+            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: block 64/128/256/512, regs 0..2");
+        (kernel == STAG_TUNE_DSLASH ? lat->dslash_block : lat->mdslash_block)[prec] = block;
+        (kernel == STAG_TUNE_DSLASH ? lat->dslash_regs : lat->mdslash_regs)[prec] = regs;
+        return STAG_OK;
+    case STAG_TUNE_BATCH:
+        if (prec == STAG_F16 || (block != 128 && block != 256) ||
+            (group != 0 && (group < batch_min_k(prec) || group > batch_max_k(prec) || (group & (group - 1)))))
+            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: batched block 128/256, group 0 or a power of two "
+                        "in [%d, %d] (no batched kernels in 16-bit storage)", batch_min_k(prec), batch_max_k(prec));
+        lat->batch_block[prec] = block;
+        lat->batch_k[prec] = group;
+        return STAG_OK;
+    default:
+        return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: unknown kernel %d", kernel);
+    }
+}
+
+extern "C" int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double *batch_us) {
+    STAG_NVTX("stag_lattice_autotune");
+    STAG_TRY(check_tune_args(lat, prec, "stag_lattice_autotune"));
+    stag_tune_result r[64];
+    int n = 0;
+    STAG_TRY(stag_lattice_autotune_all(lat, prec, STAG_TUNE_FORCE, r, 64, &n, nullptr));
+    // per block size of 128 and 256: the fastest register variant / group size
+    for (int q = 0; q < 2; q++) {
+        const int block = q ? 256 : 128;
+        double bd = 0, per_rhs = 0;
+        for (int k = 0; k < n; k++) {
+            if (r[k].block != block)
+                continue;
+            if (r[k].kernel == STAG_TUNE_DSLASH && (bd == 0 || r[k].us < bd))
+                bd = r[k].us;
+            if (r[k].kernel == STAG_TUNE_BATCH && (per_rhs == 0 || r[k].us / r[k].group < per_rhs))
+                per_rhs = r[k].us / r[k].group;
+        }
+        if (dslash_us)
+            dslash_us[q] = bd;
+        if (batch_us)  // one launch over the largest group
+            batch_us[q] = per_rhs * (prec == STAG_F16 ? 0 : batch_max_k(prec));
+    }
     return STAG_OK;
 }
 

@@ -53,6 +53,7 @@ EXPORTED = [
     "stag_dslash_eo", "stag_dslash_oe", "stag_apply_M",
     "stag_cg_solve", "stag_cg_solve_mixed", "stag_cg_multishift", "stag_cg_multishift_mixed",
     "stag_cg_solve_batched", "stag_cg_solve_batched_mixed", "stag_lattice_autotune",
+    "stag_lattice_autotune_all", "stag_lattice_set_tuning",
     "stag_net_create", "stag_net_destroy", "stag_net_num_weights", "stag_net_set_weights",
     "stag_net_get_weights", "stag_net_apply", "stag_net_collect_pairs", "stag_net_num_pairs",
     "stag_net_get_pair", "stag_net_loss_grad", "stag_net_train", "stag_cg_solve_learned",
@@ -85,6 +86,14 @@ ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ct
 class CommStruct(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("rank", ctypes.c_int), ("size", ctypes.c_int),
                 ("device_buffers", ctypes.c_int), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("block", ctypes.c_int), ("regs", ctypes.c_int),
+                ("group", ctypes.c_int), ("us", ctypes.c_double), ("chosen", ctypes.c_int)]
+
+
+TUNE_KINDS = {0: "dslash", 1: "M", 2: "batch"}
 
 
 class SolveInfo(ctypes.Structure):
@@ -135,6 +144,9 @@ def lib():
             "stag_cg_solve_batched": ([I, P, P, P, P, D, I, ctypes.POINTER(SolveInfo)], I),
             "stag_cg_solve_batched_mixed": ([I, P, P, P, P, D, I, I, D, ctypes.POINTER(SolveInfo)], I),
             "stag_lattice_autotune": ([P, I, P, P], I),
+            "stag_lattice_autotune_all": ([P, I, ctypes.c_uint, ctypes.POINTER(TuneResult), I,
+                                           ctypes.POINTER(I), ctypes.POINTER(I)], I),
+            "stag_lattice_set_tuning": ([P, I, I, I, I, I], I),
             "stag_net_create": ([P, P, I, I, ctypes.c_uint, PP], I),
             "stag_net_destroy": ([P], I),
             "stag_net_num_weights": ([P, ctypes.POINTER(I)], I),
@@ -441,6 +453,21 @@ class Lattice:
         b = (ctypes.c_double * 2)()
         _check(lib().stag_lattice_autotune(self.handle, PREC[prec], d, b))
         return {"dslash_us": {128: d[0], 256: d[1]}, "batch_us": {128: b[0], 256: b[1]}}
+
+    def autotune_all(self, prec="df64", force: bool = False):
+        """(results, cached): every candidate timed (or the cached choice);
+        results are dicts with kernel, block, regs, group, us, chosen."""
+        buf = (TuneResult * 64)()
+        n, cached = ctypes.c_int(), ctypes.c_int()
+        _check(lib().stag_lattice_autotune_all(self.handle, PREC[prec], 1 if force else 0, buf, 64,
+                                               ctypes.byref(n), ctypes.byref(cached)))
+        res = [{"kernel": TUNE_KINDS[r.kernel], "block": r.block, "regs": r.regs, "group": r.group,
+                "us": r.us, "chosen": bool(r.chosen)} for r in buf[:n.value]]
+        return res, bool(cached.value)
+
+    def set_tuning(self, prec, kernel: str, block: int, regs: int = 0, group: int = 0):
+        k = {v: key for key, v in TUNE_KINDS.items()}[kernel]
+        _check(lib().stag_lattice_set_tuning(self.handle, PREC[prec], k, int(block), int(regs), int(group)))
 
     def close(self):
         for n in list(getattr(self, "_nets", [])):
