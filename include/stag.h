@@ -264,12 +264,17 @@ int stag_cg_multishift(stag_lattice lat, stag_field *xs, const double *shifts, i
                        const stag_field b, double mass, double rel_tol, int max_iter,
                        stag_solve_info *infos);
 
-/* Multi-shift CG in FP32 to max(rel_tol, 1e-5), then every shift refined to
- * rel_tol by stag_cg_solve_mixed-style reliable-update CG (inner_prec F32 or
- * F16, delta) on its own residual, the correction added in the precision of
- * xs and b (F64 or DF64).  Needs gauge copies of that precision, F32 and
- * inner_prec.  infos[s]: iters = multi-shift iterations, restarts =
- * refinement iterations, iter_rel_resid = residual after the FP32 phase,
+/* Mixed-precision multi-shift CG.  Phase 1: the multi-shift iteration with
+ * every vector (x_s, p_s, r) in the precision of xs and b (F64 or DF64) and
+ * the Dslash pair in FP32, with reliable updates (delta, as in
+ * stag_cg_solve_mixed) that recompute the base system's residual in the high
+ * precision; convergence is declared on such a residual.  The shifted
+ * residuals cannot be recomputed inside the shared Krylov space, so phase 2
+ * refines every shift whose recomputed residual misses rel_tol with
+ * reliable-update CG (inner_prec F32 or F16, delta) on its own residual, the
+ * correction added in the high precision.  Needs gauge copies of that
+ * precision, F32 and inner_prec.  infos[s]: iters = multi-shift iterations,
+ * restarts = refinement iterations, iter_rel_resid = residual after phase 1,
  * true_rel_resid = final recomputed residual, seconds = wall time of the
  * whole call. */
 int stag_cg_multishift_mixed(stag_lattice lat, stag_field *xs, const double *shifts, int n,

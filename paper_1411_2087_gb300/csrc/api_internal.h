@@ -142,6 +142,7 @@ struct stag_lattice_s {
     } mixed[4][4];
     // multi-shift CG
     ShiftState *ms_state = nullptr;        // device, MS_MAX entries
+    cudaGraphConditionalHandle ms_rel_cond = 0;  // mixed multi-shift graph: the reliable-update branch
     ShiftState *ms_state_host = nullptr;   // pinned mirror
     double *ms_true = nullptr;             // device, |b - (M + sigma_s) x_s|^2 per shift
     double *ms_true_host = nullptr;        // pinned mirror
@@ -318,16 +319,17 @@ static inline int m_block(const stag_lattice lat, int prec) {
 // Ap = m^2 p - D_eo t with <p, Ap> summed by pap_finish: alpha and the
 // breakdown test in sc (skip_if_done: both return at once after the solve)
 static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *t, void *Ap, const void *p,
-                                        bool skip_if_done, cudaStream_t s) {
+                                        bool skip_if_done, cudaStream_t s, const int *gate = nullptr) {
     DslashArgs a = dslash_args(lat, prec, STAG_EVEN, t, Ap);
     a.p = p;
     a.skip_if_done = skip_if_done;
+    a.gate = gate;
     a.regs = lat->mdslash_block[prec] > 0 ? lat->mdslash_regs[prec] : lat->dslash_regs[prec];
     const int block = m_block(lat, prec);
     cudaError_t e = launch_dslash(prec, EPI_M_PART, a, block, s);
     if (e != cudaSuccess)
         return e;
-    return launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s);
+    return launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s, gate);
 }
 
 // Source normalisation (stag_api.cu): when the exponent k of b's largest

@@ -64,6 +64,9 @@ struct CgScalars {
     // mixed precision with a flexible preconditioner: rr holds <r_s, z> and
     // beta comes from the preconditioner step, not from |r_s|^2
     int fcg;
+    // mixed multi-shift: this iteration's Dslash pair in the high precision
+    // (hi_op) or the low one (lo_op = !hi_op), the gates of the two paths
+    int ms_hi_op, ms_lo_op;
 };
 
 // multi-shift CG
@@ -85,6 +88,9 @@ struct MsArgs {
     void *p[MS_MAX];               // search directions
     const void *b;                 // right-hand side
     void *r;                       // residual of the base system
+    void *p_lo;                    // mixed precision: low-precision copy of the base direction
+    const void *Ap_hi;             // mixed precision: M p from the high-precision path
+    double theta2;                 // the high-precision path runs while |r|^2 > theta2 |b|^2
 };
 
 }  // namespace stag

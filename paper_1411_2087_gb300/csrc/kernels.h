@@ -26,7 +26,9 @@ cudaError_t launch_cg_p_update(int prec, const Geom &g, const void *r, void *p,
 // block order; then alpha = |r|^2 / <p, M p> and the breakdown test (as the
 // EPI_M_PAP epilogue).  Returns at once when skip_if_done and the solve has
 // stopped.
-cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s);
+// gate (may be NULL): return at once while *gate == 0
+cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s,
+                              const int *gate = nullptr);
 
 // canonical complex128 [Vh][3] (device) <-> internal field layout
 cudaError_t launch_import(int prec, const Geom &g, const double *canon, void *field, cudaStream_t s);
@@ -75,12 +77,15 @@ cudaError_t launch_mixed_restart(int hi, int lo, const Geom &g, const void *r, v
                                  cudaStream_t s);
 
 // multi-shift CG (kernels_multishift.cu) and vector helpers
+// lo >= 0: mixed precision (vectors in prec, the Dslash pair in lo = FP32)
 cudaError_t launch_ms_init(int prec, const Geom &g, const MsArgs &a, double *partial, CgScalars *sc,
-                           ShiftState *st, cudaStream_t s);
+                           ShiftState *st, cudaStream_t s, int lo = -1);
 cudaError_t launch_ms_update(int prec, const Geom &g, const MsArgs &a, const void *Ap, double *partial,
-                             CgScalars *sc, ShiftState *st, cudaStream_t s);
+                             CgScalars *sc, ShiftState *st, cudaStream_t s, int lo = -1);
 cudaError_t launch_ms_p(int prec, const Geom &g, const MsArgs &a, const CgScalars *sc,
-                        const ShiftState *st, cudaStream_t s);
+                        const ShiftState *st, cudaStream_t s, int lo = -1);
+// after a reliable update of the base residual (gated on sc->reliable)
+cudaError_t launch_ms_restart(const MsArgs &a, CgScalars *sc, ShiftState *st, cudaStream_t s);
 cudaError_t launch_axpy1(int prec, const Geom &g, const void *x, void *y, cudaStream_t s);
 cudaError_t launch_convert(int prec_out, int prec_in, const Geom &g, const void *in, void *out,
                            cudaStream_t s);

@@ -143,9 +143,11 @@ cg_p_kernel(Geom g, const typename Fmt<P>::Elem *r, typename Fmt<P>::Elem *p, co
 constexpr int FINISH_BLOCK = 1024;
 
 __global__ void __launch_bounds__(FINISH_BLOCK)
-pap_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int skip_if_done) {
+pap_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int skip_if_done, const int *gate) {
     __shared__ double smem[32];
     if (skip_if_done && sc->status != CG_RUNNING)
+        return;
+    if (gate && *gate == 0)
         return;
     // four independent sums per thread over a fixed assignment, then the block tree
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -167,8 +169,9 @@ pap_finish_kernel(const double *__restrict__ partial, int n, CgScalars *sc, int 
     }
 }
 
-cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s) {
-    pap_finish_kernel<<<1, FINISH_BLOCK, 0, s>>>(partial, n, sc, skip_if_done ? 1 : 0);
+cudaError_t launch_pap_finish(const double *partial, int n, CgScalars *sc, bool skip_if_done, cudaStream_t s,
+                              const int *gate) {
+    pap_finish_kernel<<<1, FINISH_BLOCK, 0, s>>>(partial, n, sc, skip_if_done ? 1 : 0, gate);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,19 @@
 // recurrence keeps zeta = 1, so every system, the base included, is updated
 // by the same code.  A shift stops (its x_s and p_s freeze) once
 // zeta_{k+1}^2 |r|^2 <= tol^2 |b|^2.
+//
+// Mixed precision (MsArgs::p_lo set): the vectors stay in the high precision
+// P and only the Dslash pair runs in the low precision PL, on a copy p_lo of
+// the base direction that ms_p_kernel writes; M p arrives in PL.  Whenever
+// |r| has dropped below delta times its largest value since the last update,
+// or every shift claims convergence, the base residual is recomputed in P,
+// r = b - (M + sigma_0) x_0 (reliable update; the shifted residuals stay
+// zeta_s r), and convergence is only declared on such a residual.  The
+// Dslash pair of an iteration runs in P instead while |r| > theta |b|: a
+// rounding error of the operator enters every shifted solution in proportion
+// to |r| at the time, and the shifted solutions cannot be corrected inside
+// the shared space later, so the early iterations, where |r| is large, use
+// the exact operator (sc->ms_hi_op / ms_lo_op gate the two paths).
 #include "dslash.cuh"
 #include "kernels.h"
 
@@ -35,7 +48,7 @@ STAG_D void ms_set_condition(CgScalars *sc) {
 }
 
 // x_s = 0, p_s = b for all shifts; r = b; |b|^2; shift state reset
-template <int P>
+template <int P, int PL>
 __global__ void __launch_bounds__(MSB)
 ms_init_kernel(Geom g, MsArgs a, double *partial, CgScalars *sc, ShiftState *st) {
     using F = Fmt<P>;
@@ -55,6 +68,14 @@ ms_init_kernel(Geom g, MsArgs a, double *partial, CgScalars *sc, ShiftState *st)
             store_vec<P>((E *)a.x[s], g.stride, c, z);
             store_vec<P>((E *)a.p[s], g.stride, c, bv);
         }
+        if constexpr (PL >= 0) {
+            using RL = typename Fmt<PL>::R;
+            cplx<RL> lv[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                lv[k] = cconv<RL, R>(bv[k]);
+            store_vec<PL>((typename Fmt<PL>::Elem *)a.p_lo, g.stride, c, lv);
+        }
         dot = re_dot3<R>(bv, bv);
     }
     double total;
@@ -68,6 +89,11 @@ ms_init_kernel(Geom g, MsArgs a, double *partial, CgScalars *sc, ShiftState *st)
         sc->alpha_prev = 1.0;
         sc->beta_prev = 0.0;
         sc->ms_xdone = 0;
+        sc->rmax = sqrt(total);
+        sc->reliable = 0;
+        sc->restarts = 0;
+        sc->ms_hi_op = total > a.theta2 * total ? 1 : 0;
+        sc->ms_lo_op = 1 - sc->ms_hi_op;
         const bool done = total <= sc->rr_stop;
         for (int s = 0; s < a.n; s++) {
             st[s].zeta_prev = 1.0;
@@ -107,12 +133,13 @@ STAG_D void ms_shift_scalars(const MsArgs &a, const CgScalars *sc, const ShiftSt
 
 // r -= alpha Ap, |r|^2; the shift scalars of this iteration (the solution
 // updates x_s += alpha^s p_s run in ms_p_kernel, which reads p_s anyway)
-template <int P>
+template <int P, int PA>
 __global__ void __launch_bounds__(MSB)
 ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *sc, ShiftState *st) {
     using F = Fmt<P>;
     using R = typename F::R;
     using E = typename F::Elem;
+    using RA = typename Fmt<PA>::R;
     __shared__ double smem[32];
     __shared__ double zeta_next[MS_MAX], alpha_s[MS_MAX];
     __shared__ int active[MS_MAX];
@@ -122,6 +149,9 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
     if (blockIdx.x == 0 && threadIdx.x == 0)
         sc->ms_xdone = sc->iter;
     const bool run = sc->status == CG_RUNNING;
+    // which path computed M p this iteration (read before any block's ticket,
+    // so before the last block below sets it for the next iteration)
+    const bool hi_path = PA == P || sc->ms_hi_op;
     if (run)
         ms_shift_scalars(a, sc, st, zeta_next, alpha_s);
     if (threadIdx.x < MS_MAX)
@@ -133,7 +163,15 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
         const R alpha = scalar_as<R>(sc->alpha);
         cplx<R> rv[3], av[3];
         load_vec<P>((const E *)a.r, g.stride, c, rv);
-        load_vec<P>((const E *)Ap, g.stride, c, av);
+        if (hi_path) {
+            load_vec<P>((const E *)(PA == P ? Ap : a.Ap_hi), g.stride, c, av);
+        } else {
+            cplx<RA> al[3];
+            load_vec<PA>((const typename Fmt<PA>::Elem *)Ap, g.stride, c, al);
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                av[k] = cconv<R, RA>(al[k]);
+        }
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             mac(rv[k].re, -alpha, av[k].re);
@@ -173,20 +211,58 @@ ms_update_kernel(Geom g, MsArgs a, const void *Ap, double *partial, CgScalars *s
             sc->alpha_prev = sc->alpha.d;
             sc->beta_prev = beta;
             sc->rr = total;
-            if (!(total < INFINITY))
+            const double rn = sqrt(total);
+            sc->reliable = 0;
+            if (!(total < INFINITY)) {
                 sc->status = CG_BREAKDOWN;
-            else if (!any)
+            } else if (sc->delta > 0.0 && ((!hi_path && rn < sc->delta * sc->rmax) || !any ||
+                                           sc->iter >= sc->max_iter)) {
+                // mixed precision: the base residual is recomputed first, and
+                // the stop is decided on it (ms_restart_kernel); iterations on
+                // the exact operator need no update on the way
+                sc->reliable = 1;
+            } else if (!any) {
                 sc->status = CG_CONVERGED;
-            else if (sc->iter >= sc->max_iter)
+            } else if (sc->iter >= sc->max_iter) {
                 sc->status = CG_MAXITER;
+            }
+            sc->rmax = fmax(sc->rmax, rn);
+            sc->ms_hi_op = total > a.theta2 * sc->bb ? 1 : 0;
+            sc->ms_lo_op = 1 - sc->ms_hi_op;
         }
+        if (sc->has_rel_cond)
+            cudaGraphSetConditional(sc->rel_cond, sc->reliable ? 1u : 0u);
         ms_set_condition(sc);
     }
 }
 
+// after a reliable update (r = b - (M + sigma_0) x_0 recomputed, |r|^2 in
+// true_rr): the base CG continues from the true residual; the stop decided
+// on it (one block, one thread)
+__global__ void ms_restart_kernel(const MsArgs a, CgScalars *sc, ShiftState *st) {
+    if (sc->reliable == 0 || threadIdx.x != 0)
+        return;
+    const double rt = sc->true_rr;
+    sc->restarts += 1;
+    sc->rr = rt;
+    sc->rmax = sqrt(rt);
+    sc->ms_hi_op = rt > a.theta2 * sc->bb ? 1 : 0;
+    sc->ms_lo_op = 1 - sc->ms_hi_op;
+    bool any = false;
+    for (int s = 0; s < a.n; s++)
+        any |= st[s].active != 0;
+    if (!(rt < INFINITY))
+        sc->status = CG_BREAKDOWN;
+    else if (!any)
+        sc->status = CG_CONVERGED;
+    else if (sc->iter >= sc->max_iter)
+        sc->status = CG_MAXITER;
+    ms_set_condition(sc);
+}
+
 // x_s += alpha^s p_s for the shifts active in this iteration, then
 // p_s = zeta_{k+1} r + beta^s p_s for those still active
-template <int P>
+template <int P, int PL>
 __global__ void __launch_bounds__(MSB)
 ms_p_kernel(Geom g, MsArgs a, const CgScalars *sc, const ShiftState *st) {
     using F = Fmt<P>;
@@ -243,6 +319,17 @@ ms_p_kernel(Geom g, MsArgs a, const CgScalars *sc, const ShiftState *st) {
             o[k].im = rnorm<R>(o[k].im);
         }
         store_vec<P>((E *)a.p[s], g.stride, c, o);
+        if constexpr (PL >= 0) {
+            if (s == a.base) {
+                // the low-precision copy of the base direction for the Dslash
+                using RL = typename Fmt<PL>::R;
+                cplx<RL> lv[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    lv[k] = cconv<RL, R>(o[k]);
+                store_vec<PL>((typename Fmt<PL>::Elem *)a.p_lo, g.stride, c, lv);
+            }
+        }
     }
 }
 
@@ -291,21 +378,55 @@ convert_kernel(Geom g, const typename Fmt<PI>::Elem *in, typename Fmt<PO>::Elem 
     default: return cudaErrorInvalidValue;                                \
     }
 
+// lo: the precision of the Dslash pair (-1: the vectors' own precision);
+// mixed precision exists for F64 and DF64 vectors with an FP32 operator
 cudaError_t launch_ms_init(int prec, const Geom &g, const MsArgs &a, double *partial, CgScalars *sc,
-                           ShiftState *st, cudaStream_t s) {
-    MS_PREC_SWITCH(prec, ms_init_kernel<P><<<grid_of(g), MSB, 0, s>>>(g, a, partial, sc, st));
+                           ShiftState *st, cudaStream_t s, int lo) {
+    if (lo == P_F32 && (prec == P_F64 || prec == P_DF64)) {
+        if (prec == P_F64)
+            ms_init_kernel<P_F64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, partial, sc, st);
+        else
+            ms_init_kernel<P_DF64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, partial, sc, st);
+        return cudaGetLastError();
+    }
+    if (lo >= 0)
+        return cudaErrorInvalidValue;
+    MS_PREC_SWITCH(prec, ms_init_kernel<P, -1><<<grid_of(g), MSB, 0, s>>>(g, a, partial, sc, st));
     return cudaGetLastError();
 }
 
 cudaError_t launch_ms_update(int prec, const Geom &g, const MsArgs &a, const void *Ap, double *partial,
-                             CgScalars *sc, ShiftState *st, cudaStream_t s) {
-    MS_PREC_SWITCH(prec, ms_update_kernel<P><<<grid_of(g), MSB, 0, s>>>(g, a, Ap, partial, sc, st));
+                             CgScalars *sc, ShiftState *st, cudaStream_t s, int lo) {
+    if (lo == P_F32 && (prec == P_F64 || prec == P_DF64)) {
+        if (prec == P_F64)
+            ms_update_kernel<P_F64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, Ap, partial, sc, st);
+        else
+            ms_update_kernel<P_DF64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, Ap, partial, sc, st);
+        return cudaGetLastError();
+    }
+    if (lo >= 0)
+        return cudaErrorInvalidValue;
+    MS_PREC_SWITCH(prec, ms_update_kernel<P, P><<<grid_of(g), MSB, 0, s>>>(g, a, Ap, partial, sc, st));
     return cudaGetLastError();
 }
 
 cudaError_t launch_ms_p(int prec, const Geom &g, const MsArgs &a, const CgScalars *sc,
-                        const ShiftState *st, cudaStream_t s) {
-    MS_PREC_SWITCH(prec, ms_p_kernel<P><<<grid_of(g), MSB, 0, s>>>(g, a, sc, st));
+                        const ShiftState *st, cudaStream_t s, int lo) {
+    if (lo == P_F32 && (prec == P_F64 || prec == P_DF64)) {
+        if (prec == P_F64)
+            ms_p_kernel<P_F64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, sc, st);
+        else
+            ms_p_kernel<P_DF64, P_F32><<<grid_of(g), MSB, 0, s>>>(g, a, sc, st);
+        return cudaGetLastError();
+    }
+    if (lo >= 0)
+        return cudaErrorInvalidValue;
+    MS_PREC_SWITCH(prec, ms_p_kernel<P, -1><<<grid_of(g), MSB, 0, s>>>(g, a, sc, st));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ms_restart(const MsArgs &a, CgScalars *sc, ShiftState *st, cudaStream_t s) {
+    ms_restart_kernel<<<1, 32, 0, s>>>(a, sc, st);
     return cudaGetLastError();
 }
 

@@ -338,26 +338,102 @@ static int ensure_ms_state(stag_lattice lat) {
     return STAG_OK;
 }
 
-static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, bool host_mode) {
+// the base residual recomputed in the vectors' precision (mixed multi-shift:
+// gated on sc->reliable), then the restart of the base scalars
+static cudaError_t enqueue_ms_reliable(stag_lattice lat, int prec, const MsArgs &a, cudaStream_t s) {
     CgWork &w = lat->cg[prec];
+    cudaError_t e;
+    DslashArgs a3 = dslash_args(lat, prec, STAG_ODD, a.x[a.base], w.t);
+    a3.gate = reliable_flag(lat);
+    if ((e = launch_dslash(prec, EPI_NONE, a3, lat->dslash_block[prec], s)) != cudaSuccess)
+        return e;
+    DslashArgs a4 = dslash_args(lat, prec, STAG_EVEN, w.t, a.r);
+    a4.p = a.x[a.base];
+    a4.b = a.b;
+    a4.gate = reliable_flag(lat);
+    if ((e = launch_dslash(prec, EPI_RESID_STORE, a4, lat->dslash_block[prec], s)) != cudaSuccess)
+        return e;
+    return launch_ms_restart(a, lat->sc, lat->ms_state, s);
+}
+
+// one iteration; lo >= 0: the Dslash pair in FP32 on a.p_lo (mixed), with
+// the reliable update in an IF node when captured (side != nullptr, as in
+// the mixed solver) or gated kernels otherwise
+static const int *scalar_flag(stag_lattice lat, size_t off) { return (const int *)((const char *)lat->sc + off); }
+
+// the Dslash pair M p_base of one iteration in precision op, with the
+// <p, M p> partials and alpha; gate: run only while *gate != 0
+static cudaError_t enqueue_ms_op(stag_lattice lat, int op, const void *pb, bool host_mode, const int *gate,
+                                 cudaStream_t s) {
+    CgWork &w = lat->cg[op];
+    DslashArgs a1 = dslash_args(lat, op, STAG_ODD, pb, w.t);
+    a1.skip_if_done = host_mode;
+    a1.gate = gate;
+    cudaError_t e = launch_dslash(op, EPI_NONE, a1, lat->dslash_block[op], s);
+    if (e != cudaSuccess)
+        return e;
+    return enqueue_m_pap(lat, op, w.t, w.Ap, pb, host_mode, s, gate);
+}
+
+static cudaError_t enqueue_ms_body(stag_lattice lat, int prec, const MsArgs &a, bool host_mode, int lo = -1,
+                                   cudaStream_t side = nullptr) {
     cudaStream_t s = lat->stream;
     cudaError_t e;
-    DslashArgs a1 = dslash_args(lat, prec, STAG_ODD, a.p[a.base], w.t);
-    a1.skip_if_done = host_mode;
-    if ((e = launch_dslash(prec, EPI_NONE, a1, lat->dslash_block[prec], s)) != cudaSuccess)
-        return e;
-    if ((e = enqueue_m_pap(lat, prec, w.t, w.Ap, a.p[a.base], host_mode, s)) != cudaSuccess)
-        return e;
-    if ((e = launch_ms_update(prec, lat->geom, a, w.Ap, lat->partial, lat->sc, lat->ms_state, s)) !=
+    if (lo < 0) {
+        if ((e = enqueue_ms_op(lat, prec, a.p[a.base], host_mode, nullptr, s)) != cudaSuccess)
+            return e;
+    } else {
+        // the exact operator while |r| is large, the FP32 one afterwards
+        if ((e = enqueue_ms_op(lat, prec, a.p[a.base], host_mode, scalar_flag(lat, offsetof(CgScalars, ms_hi_op)),
+                               s)) != cudaSuccess ||
+            (e = enqueue_ms_op(lat, lo, a.p_lo, host_mode, scalar_flag(lat, offsetof(CgScalars, ms_lo_op)), s)) !=
+                cudaSuccess)
+            return e;
+    }
+    const void *Ap = lat->cg[lo >= 0 ? lo : prec].Ap;
+    if ((e = launch_ms_update(prec, lat->geom, a, Ap, lat->partial, lat->sc, lat->ms_state, s, lo)) !=
         cudaSuccess)
         return e;
-    return launch_ms_p(prec, lat->geom, a, lat->sc, lat->ms_state, s);
+    if ((e = launch_ms_p(prec, lat->geom, a, lat->sc, lat->ms_state, s, lo)) != cudaSuccess)
+        return e;
+    if (lo < 0)
+        return cudaSuccess;
+    if (!side)
+        return enqueue_ms_reliable(lat, prec, a, s);
+    cudaStreamCaptureStatus st;
+    cudaGraph_t body = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, &body, &deps, nullptr, &ndeps)) != cudaSuccess)
+        return e;
+    cudaGraphConditionalHandle rel_cond;
+    if ((e = cudaGraphConditionalHandleCreate(&rel_cond, body, 0, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return e;
+    // the kernels set the IF condition through the handle in the scalars
+    lat->ms_rel_cond = rel_cond;
+    cudaGraphNodeParams ip = {cudaGraphNodeTypeConditional};
+    ip.conditional.handle = rel_cond;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t branch;
+    if ((e = cudaGraphAddNode(&branch, body, deps, nullptr, ndeps, &ip)) != cudaSuccess)
+        return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(s, &branch, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaStreamBeginCaptureToGraph(side, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return e;
+    cudaError_t e2 = enqueue_ms_reliable(lat, prec, a, side);
+    cudaGraph_t branch_out = nullptr;
+    e = cudaStreamEndCapture(side, &branch_out);
+    return e2 != cudaSuccess ? e2 : e;
 }
 
 // one graph: init, WHILE(body); built per call (the solution buffers are
 // the caller's) and destroyed after it
 static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass_base, double tol,
-                        int max_iter) {
+                        int max_iter, int lo, double delta) {
     cudaStream_t s = lat->stream;
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -381,7 +457,7 @@ static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass
     if ((e = cudaStreamBeginCaptureToGraph(s, graph, nullptr, nullptr, 0,
                                            cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return bail("begin capture", e);
-    if ((e = launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s)) != cudaSuccess)
+    if ((e = launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s, lo)) != cudaSuccess)
         return bail("init", e);
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t *deps = nullptr;
@@ -402,17 +478,27 @@ static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass
     if ((e = cudaStreamEndCapture(s, &captured)) != cudaSuccess)
         return bail("end capture", e);
     cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t side = nullptr;
+    if (lo >= 0 && (e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail("side stream", e);
     if ((e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0,
-                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        if (side)
+            cudaStreamDestroy(side);
         return bail("begin body capture", e);
-    if ((e = enqueue_ms_body(lat, prec, a, false)) != cudaSuccess)
+    }
+    e = enqueue_ms_body(lat, prec, a, false, lo, side);
+    if (side)
+        cudaStreamDestroy(side);
+    if (e != cudaSuccess)
         return bail("body", e);
     cudaGraph_t body_out = nullptr;
     if ((e = cudaStreamEndCapture(s, &body_out)) != cudaSuccess)
         return bail("end body capture", e);
     if ((e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
         return bail("instantiate", e);
-    STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, true, cond));
+    STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, true, cond, lo >= 0 ? delta : 0.0, lo >= 0,
+                            lo >= 0 ? lat->ms_rel_cond : 0));
     if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess)
         return bail("launch", e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -423,10 +509,14 @@ static int run_ms_graph(stag_lattice lat, int prec, const MsArgs &a, double mass
 }
 
 // multi-shift CG on raw buffers of precision prec; infos[s] per shift
+// lo >= 0: the Dslash pair in FP32 with reliable updates of the base
+// residual at delta (vectors in prec: F64 or DF64)
 static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const double *shifts, int n,
                         const void *b_data, size_t bytes, double mass, double tol, int max_iter,
-                        stag_solve_info *infos, double *seconds) {
+                        stag_solve_info *infos, double *seconds, int lo = -1, double delta = 0.0) {
     STAG_TRY(ensure_cg_work(lat, prec));
+    if (lo >= 0)
+        STAG_TRY(ensure_cg_work(lat, lo));
     STAG_TRY(ensure_ms_state(lat));
     for (int k = 0; k < n; k++)
         STAG_TRY(alloc_vec(lat, prec, &lat->ms_p[prec][k]));
@@ -446,14 +536,21 @@ static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const d
     }
     a.b = w.bw;
     a.r = w.r;
+    a.p_lo = lo >= 0 ? lat->cg[lo].p : nullptr;
+    a.Ap_hi = w.Ap;
+    // FP32 operator: its rounding (about 6e-8 relative) enters the shifted
+    // solutions in proportion to |r|, so it takes over once |r| < theta |b|,
+    // theta = tol / (16 * 6e-8)
+    const double theta = lo >= 0 ? std::min(1.0, tol / (16 * 6e-8)) : 0.0;
+    a.theta2 = theta * theta;
     const double mass_base = std::sqrt(mass * mass + shifts[a.base]);
     CUDA_TRY(cudaMemcpyAsync(w.bw, b_data, bytes, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaEventRecord(lat->ev0, s));
     if (lat->cg_launch == STAG_CG_LAUNCH_GRAPH) {
-        STAG_TRY(run_ms_graph(lat, prec, a, mass_base, tol, max_iter));
+        STAG_TRY(run_ms_graph(lat, prec, a, mass_base, tol, max_iter, lo, delta));
     } else {
-        STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, false, 0));
-        CUDA_TRY(launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s));
+        STAG_TRY(upload_scalars(lat, mass_base, tol, max_iter, false, 0, lo >= 0 ? delta : 0.0));
+        CUDA_TRY(launch_ms_init(prec, lat->geom, a, lat->partial, lat->sc, lat->ms_state, s, lo));
         const int chunk = lat->cg_chunk;
         const long long max_chunks = (long long)max_iter / chunk + 2;
         for (long long k = 0; k < max_chunks; k++) {
@@ -463,7 +560,7 @@ static int ms_solve_raw(stag_lattice lat, int prec, void *const *x_data, const d
             if (lat->sc_host->status != CG_RUNNING)
                 break;
             for (int j = 0; j < chunk; j++)
-                CUDA_TRY(enqueue_ms_body(lat, prec, a, true));
+                CUDA_TRY(enqueue_ms_body(lat, prec, a, true, lo));
         }
     }
     CUDA_TRY(cudaEventRecord(lat->ev1, s));
@@ -628,29 +725,29 @@ static int multishift_mixed_impl(stag_lattice lat, stag_field *xs, const double 
     cudaStream_t s = lat->stream;
     const Geom &g = lat->geom;
     STAG_TRY(ensure_cg_work(lat, hi));
-    STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_blo));
-    for (int k = 0; k < n; k++)
-        STAG_TRY(alloc_vec(lat, STAG_F32, &lat->ms_xlo[k]));
     STAG_TRY(alloc_vec(lat, hi, &lat->ms_rhi[hi]));
     STAG_TRY(alloc_vec(lat, hi, &lat->ms_ehi[hi]));
     // |b|^2 in the high precision: the residual of x = 0
     CUDA_TRY(cudaMemsetAsync(lat->ms_ehi[hi], 0, field_bytes(lat, hi), s));
     double bb = 0;
     STAG_TRY(shifted_residual(lat, hi, lat->ms_ehi[hi], b->data, mass, nullptr, &bb));
-    // phase 1: all shifts at once in FP32, to max(rel_tol, 1e-5)
-    CUDA_TRY(launch_convert(STAG_F32, hi, g, b->data, lat->ms_blo, s));
-    const double sloppy_tol = rel_tol > 1e-5 ? rel_tol : 1e-5;
+    // phase 1: all shifts in one Krylov space, vectors in the high precision,
+    // the Dslash pair in FP32, reliable updates of the base residual
+    void *xd[MS_MAX];
+    for (int k = 0; k < n; k++)
+        xd[k] = xs[k]->data;
     stag_solve_info lo_info[MS_MAX];
-    int st = ms_solve_raw(lat, STAG_F32, lat->ms_xlo, shifts, n, lat->ms_blo, field_bytes(lat, STAG_F32),
-                          mass, sloppy_tol, max_iter, lo_info, nullptr);
+    int st = ms_solve_raw(lat, hi, xd, shifts, n, b->data, b->bytes, mass, rel_tol, max_iter, lo_info, nullptr,
+                          STAG_F32, delta);
     if (st != STAG_OK && st != STAG_ERR_NOT_CONVERGED)
         return st;
-    // phase 2: per shift, x_k = x_lo, then the mixed solver on its residual
+    // phase 2: a shift whose recomputed residual misses the tolerance (the
+    // shifted systems cannot take reliable updates inside the shared space)
+    // is refined by the mixed solver on its own residual
     int worst = STAG_OK;
     stag_solve_info out[MS_MAX];
     for (int k = 0; k < n; k++) {
         memset(&out[k], 0, sizeof out[k]);
-        CUDA_TRY(launch_convert(hi, STAG_F32, g, lat->ms_xlo[k], xs[k]->data, s));
         const double mk = std::sqrt(mass * mass + shifts[k]);
         double rr0 = 0;
         STAG_TRY(shifted_residual(lat, hi, xs[k]->data, b->data, mk, lat->ms_rhi[hi], &rr0));
@@ -1323,8 +1420,12 @@ static int tune_all(stag_lattice lat, int prec, std::vector<stag_tune_result> &r
             }
             stag_tune_result r = {STAG_TUNE_BATCH, block, 0, K, us, 0};
             res.push_back(r);
-            if (us / K < best) {
-                best = us / K;
+            // a smaller group must win clearly: systems that do not fill
+            // whole groups leave partly empty ones, which a single-group
+            // timing does not see
+            const double per_rhs = us / K * (K < kmax ? 1.15 : 1.0);
+            if (per_rhs < best) {
+                best = per_rhs;
                 c.bblock = block;
                 c.bk = K;
             }
