@@ -71,6 +71,8 @@ def parse():
                     help="time the Dslash kernels of every precision on --dims (autotuner launches) and exit")
     ap.add_argument("--compress12", action="store_true",
                     help="with --kernels-only: 12-real links for the FP32 and 16-bit copies")
+    ap.add_argument("--net-only", action="store_true",
+                    help="time one application of the learned preconditioner (solver form) and exit")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
                     help="host: the same CG kernels launched one by one (per-kernel profiling)")
     return ap.parse_args()
@@ -969,6 +971,39 @@ def run_kernels_only(args):
     return out
 
 
+def run_net_only(args):
+    """The learned preconditioner's application in the solver's form
+    (binary16 weights, 16-bit links, DF64 in and out) on 32^3x64, CUDA
+    events over 20 applications after 3 warm-ups; the net's weights do not
+    change its cost, so it is not trained here."""
+    import torch
+    from paper_1411_2087_gb300 import stag, synth
+    dims = tuple(int(v) for v in args.dims.split(",")) if args.dims else LEARNED_DIMS
+    dev = torch.device("cuda", 0)
+    U = synth.su3_field(dims, 0.3, 1010, device=dev)
+    torch.cuda.synchronize()
+    Vh = int(np.prod(dims)) // 2
+    stream = torch.cuda.Stream(dev)
+    with stag.Lattice(dims, stream=stream.cuda_stream) as lat:
+        net = stag.Net(lat, U, channels=8, seed=1)
+        del U
+        fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1400))
+        fz = lat.field(stag.EVEN, "df64")
+        for _ in range(3):
+            net.apply(fz, fb, fp16_weights=True, links16=True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(20):
+            net.apply(fz, fb, fp16_weights=True, links16=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / 20
+        net.close()
+    return {"net_only": True, "lattice": list(dims), "apply_ms": round(ms, 4),
+            "form": "binary16 weights, 16-bit links, DF64 fields"}
+
+
 def main():
     args = parse()
     world = dist_env()[1]
@@ -977,6 +1012,9 @@ def main():
                  f"--nproc-per-node {args.gpus}); this launch has WORLD_SIZE={world}")
     if args.kernels_only:
         print(json.dumps(run_kernels_only(args)), flush=True)
+        return
+    if args.net_only:
+        print(json.dumps(run_net_only(args)), flush=True)
         return
     if args.impl == "reference":
         line = run_reference(args)
