@@ -71,6 +71,8 @@ def parse():
                     help="time the Dslash kernels of every precision on --dims (autotuner launches) and exit")
     ap.add_argument("--compress12", action="store_true",
                     help="with --kernels-only: 12-real links for the FP32 and 16-bit copies")
+    ap.add_argument("--kernels-prec", default="f64,df64,f32,f16",
+                    help="with --kernels-only: the precisions to time (comma-separated)")
     ap.add_argument("--net-only", action="store_true",
                     help="time one application of the learned preconditioner (solver form) and exit")
     ap.add_argument("--cg-launch", default="graph", choices=["graph", "host"],
@@ -954,9 +956,12 @@ def run_kernels_only(args):
     torch.cuda.synchronize()
     out = {"kernels_only": True, "lattice": list(dims), "compress12": bool(args.compress12)}
     link_reals = 12 if args.compress12 else 18
+    want = [p for p in args.kernels_prec.split(",") if p]
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, None, precisions=("f64", "df64", "f32", "f16"), compress12=args.compress12)
+        lat.upload_gauge(U, None, precisions=tuple(want), compress12=args.compress12)
         for prec, rb in (("f64", 8), ("df64", 8), ("f32", 4), ("f16", 2)):
+            if prec not in want:
+                continue
             t = lat.autotune(prec)
             best = min(t["dslash_us"].values())
             if prec == "f16":

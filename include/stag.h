@@ -316,6 +316,10 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
  *   STAG_TUNE_DSLASH  the Dslash: block 64, 128, 256 or 512 threads, in two
  *                     register variants (regs 1: the compiler's choice,
  *                     2: at most 64 registers, 1024 resident threads per SM)
+ *                     and, for STAG_F16 on 12-real links with Lt a multiple
+ *                     of 4 and at least 8, regs 3: two sites (x, y, z, t)
+ *                     and (x, y, z, t + Lt/2) per thread in packed FP32x2
+ *                     arithmetic (the same bits as the one-site forms)
  *   STAG_TUNE_M       the solvers' M Dslash (m^2 p - D t with one <p, Mp>
  *                     partial per block): the same candidates
  *   STAG_TUNE_BATCH   the batched multi-right-hand-side Dslash: block 128 or
@@ -332,7 +336,7 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
 typedef struct {
     int kernel;    /* STAG_TUNE_DSLASH, STAG_TUNE_M or STAG_TUNE_BATCH          */
     int block;     /* threads per block                                        */
-    int regs;      /* Dslash kinds: 1 compiler's choice, 2 capped; batched 0   */
+    int regs;      /* Dslash kinds: 1 free, 2 capped, 3 site pairs; batched 0 */
     int group;     /* batched: right-hand sides per group; others 0            */
     double us;     /* microseconds per launch; 0 for a choice from the cache    */
     int chosen;    /* 1 for the configuration kept                             */
@@ -347,7 +351,8 @@ int stag_lattice_autotune_all(stag_lattice lat, int prec, unsigned flags, stag_t
                               int *n, int *cached);
 
 /* Set one kind's configuration by hand (regs 0 = the library's default
- * variant; group 0 = the largest).  Bad values: STAG_ERR_ARG. */
+ * variant, 1..3 as above, 3 falling back to the default where the pair form
+ * does not apply; group 0 = the largest).  Bad values: STAG_ERR_ARG. */
 int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, int block, int regs, int group);
 
 /* The autotuner, timed again (STAG_TUNE_FORCE): dslash_us[2] and batch_us[2]

@@ -329,7 +329,8 @@ static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *
     cudaError_t e = launch_dslash(prec, EPI_M_PART, a, block, s);
     if (e != cudaSuccess)
         return e;
-    return launch_pap_finish(lat->partial, dslash_grid(lat->geom, block), lat->sc, skip_if_done, s, gate);
+    const int n = pair16_used(prec, EPI_M_PART, a) ? dslash_pair16_grid(lat->geom, block) : dslash_grid(lat->geom, block);
+    return launch_pap_finish(lat->partial, n, lat->sc, skip_if_done, s, gate);
 }
 
 // Source normalisation (stag_api.cu): when the exponent k of b's largest

@@ -46,12 +46,14 @@ struct DslashArgs {
     int c0, cn;             // output sites c0 .. c0+cn-1 (cn = 0: all Vh)
     float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
     int bc_neg[4];          // boundary sign of direction mu is -1
-    int regs;               // EPI_NONE, EPI_M_PART: REGS_DEFAULT, REGS_FREE or REGS_CAPPED (autotuned)
+    int regs;               // EPI_NONE, EPI_M_PART: REGS_* (autotuned)
 };
 
 // register variant of the stencil (DslashArgs::regs): the launcher's
-// measured default, the compiler's free choice, or at most 64 registers
-enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2 };
+// measured default, the compiler's free choice, at most 64 registers, or
+// (compressed 16-bit stencil, EPI_NONE and EPI_M_PART) two sites per thread
+// in packed FP32x2 arithmetic where pair16_applies, else the default
+enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2, REGS_PAIR = 3 };
 
 // rebuild row 2 of L = s U (U in SU(3)) from rows 0 and 1: conj(r0 x r1) / s
 template <class R>
@@ -94,110 +96,11 @@ STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float i
     }
 }
 
-// --------------------------------------------------------------------------
-// 16-bit storage in raw units.  A link entry is ls q (ls = the field's
-// scale), a vector component (n / 32767) q (n = the site's norm), q the
-// stored integers.  The products run on the integers (exact in float) and one
-// coefficient per hop, ls n / 32767, carries the scales; row 2 of a 12-real
-// link, conj(row0 x row1) in raw units, carries the extra factor ls / s of
-// the rebuild.  This saves the 24 scale multiplies of every hop.
-// --------------------------------------------------------------------------
-STAG_D float load_vec_raw16(const short2 *__restrict__ v, int S, int j, cplx<float> w[3]) {
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        const short2 q = ld_keep(v + b * S + j);
-        w[b] = cplx<float>{(float)q.x, (float)q.y};
-    }
-    return ld_keep((const float *)(v + 3 * S) + j);
-}
+}  // namespace stag
 
-// the nine raw entries of one 16-bit link; for the 12-real layout row 2 is
-// conj(row0 x row1) without the 1/s factor
-template <bool COMP>
-STAG_D void load_link_raw16(const void *G, int kind, int S, int idx, cplx<float> L[9]) {
-    if constexpr (COMP) {
-        const char *kb = (const char *)G + (size_t)kind * C12<P_F16>::kind_bytes((size_t)S);
-        C12<P_F16>::load(kb, S, idx, 1.f, L);
-        reconstruct_row2(L, 1.f);
-    } else {
-        const short2 *Lp = (const short2 *)G + kind * 9 * S + idx;
-#pragma unroll
-        for (int e = 0; e < 9; e++) {
-            const short2 q = ld_stream(Lp + e * S);
-            L[e] = cplx<float>{(float)q.x, (float)q.y};
-        }
-    }
-}
+#include "stencil16.cuh"
 
-template <bool COMP>
-STAG_D void dslash_site_f16(const Geom &g, int par, int c, const void *__restrict__ Gout,
-                            const void *__restrict__ Gin, const short2 *__restrict__ in, const DslashArgs &a,
-                            cplx<float> acc[3]) {
-    const int S = g.stride;
-    int x[4];
-    cb_coords(g, c, par, x);
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        int esum = 0;
-#pragma unroll
-        for (int nu = 0; nu < mu; nu++)
-            esum += x[nu];
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int s = h ? 3 : 1;
-            const int kind = 4 * h + mu;
-            const float ls = a.link_scale[h];
-            const float lsq = ls * (1.f / kQ16);
-            // forward: + L(x) psi(x + s mu)
-            {
-                const int j = cb_hop(g, c, x, mu, +s);
-                cplx<float> v[3];
-                const float cf = load_vec_raw16(in, S, j, v) * lsq;
-                float cf2 = cf;
-                if (COMP) {
-                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
-                    cf2 = cf * ls * (flip ? -a.inv_c[h] : a.inv_c[h]);
-                }
-                cplx<float> L[9];
-                load_link_raw16<COMP>(Gout, kind, S, c, L);
-#pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    cplx<float> t = czero<float>();
-#pragma unroll
-                    for (int b = 0; b < 3; b++)
-                        cmac(t, L[3 * r + b], v[b]);
-                    const float k = r == 2 ? cf2 : cf;
-                    acc[r].re = fmaf(k, t.re, acc[r].re);
-                    acc[r].im = fmaf(k, t.im, acc[r].im);
-                }
-            }
-            // backward: - L(x - s mu)^+ psi(x - s mu)
-            {
-                const int j = cb_hop(g, c, x, mu, -s);
-                cplx<float> v[3];
-                const float cf = -load_vec_raw16(in, S, j, v) * lsq;
-                if (COMP) {
-                    // row 2 of L meets component 2 of psi in L^+ psi
-                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
-                    const float k2 = ls * (flip ? -a.inv_c[h] : a.inv_c[h]);
-                    v[2].re *= k2;
-                    v[2].im *= k2;
-                }
-                cplx<float> L[9];
-                load_link_raw16<COMP>(Gin, kind, S, j, L);
-#pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    cplx<float> t = czero<float>();
-#pragma unroll
-                    for (int b = 0; b < 3; b++)
-                        cmac_conj(t, L[3 * b + r], v[b]);
-                    acc[r].re = fmaf(cf, t.re, acc[r].re);
-                    acc[r].im = fmaf(cf, t.im, acc[r].im);
-                }
-            }
-        }
-    }
-}
+namespace stag {
 
 // acc += D psi at checkerboard site c of parity par
 template <int P, bool COMP = false>
@@ -206,9 +109,10 @@ STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ 
                         const DslashArgs &a, cplx<typename Fmt<P>::R> acc[3]) {
     using R = typename Fmt<P>::R;
     if constexpr (P == P_F16 && COMP) {
-        // the 18-real 16-bit stencil keeps its scaled form: in raw units the
-        // compiler hoists its loads into 255 registers and it runs no faster
-        dslash_site_f16<COMP>(g, par, c, Gout, Gin, in, a, acc);
+        // raw integer units (stencil16.cuh); the 18-real 16-bit stencil keeps
+        // its scaled form: in raw units the compiler hoists its loads into
+        // 255 registers and it runs no faster
+        stencil16_site(g, par, c, Gout, Gin, in, a, acc);
         return;
     }
     const int S = g.stride;
@@ -285,60 +189,59 @@ template <class R> STAG_D red_t<R> re_dot3(const cplx<R> a[3], const cplx<R> b[3
     return to_red(s);
 }
 
-template <int P, int EPI, int BLOCK, bool COMP>
-STAG_D void dslash_body(const DslashArgs &a) {
+// the epilogue of output site c: store D psi (EPI_NONE) or o = m^2 p - D psi
+// (and for the residual forms b - o); returns the site's share of the sum
+// the epilogue reduces (<p, o> or |b - o|^2)
+template <int P, int EPI>
+STAG_D red_t<typename Fmt<P>::R> dslash_epilogue(const DslashArgs &a, int c, cplx<typename Fmt<P>::R> acc[3]) {
     using F = Fmt<P>;
     using R = typename F::R;
     using E = typename F::Elem;
-    __shared__ double smem[32];
-    // the status is uniform over the grid: either every block returns here or none
-    if (a.skip_if_done && a.sc->status != CG_RUNNING)
-        return;
-    if (a.gate && *a.gate == 0)
-        return;
-    const int c = a.c0 + blockIdx.x * BLOCK + threadIdx.x;
     const int S = a.g.stride;
     red_t<R> dot = red_zero<red_t<R>>();
-    if (c < a.c0 + (a.cn ? a.cn : a.g.Vh)) {
-        cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
-        dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
-        if (EPI == EPI_NONE) {
+    if (EPI == EPI_NONE) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            acc[k].re = rnorm<R>(acc[k].re);
+            acc[k].im = rnorm<R>(acc[k].im);
+        }
+        store_vec<P>((E *)a.out, S, c, acc);
+    } else {
+        const R m2 = scalar_as<R>(a.m2_in_args ? a.m2 : a.sc->m2);
+        cplx<R> p[3], o[3];
+        load_vec<P>((const E *)a.p, S, c, p);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            o[k] = cneg(acc[k]);
+            mac(o[k].re, m2, p[k].re);
+            mac(o[k].im, m2, p[k].im);
+            o[k].re = rnorm<R>(o[k].re);
+            o[k].im = rnorm<R>(o[k].im);
+        }
+        if (EPI == EPI_RESID || EPI == EPI_RESID_STORE) {
+            cplx<R> bb[3];
+            load_vec<P>((const E *)a.b, S, c, bb);
 #pragma unroll
             for (int k = 0; k < 3; k++) {
-                acc[k].re = rnorm<R>(acc[k].re);
-                acc[k].im = rnorm<R>(acc[k].im);
+                o[k].re = rsub(bb[k].re, o[k].re);
+                o[k].im = rsub(bb[k].im, o[k].im);
             }
-            store_vec<P>((E *)a.out, S, c, acc);
-        } else {
-            const R m2 = scalar_as<R>(a.m2_in_args ? a.m2 : a.sc->m2);
-            cplx<R> p[3], o[3];
-            load_vec<P>((const E *)a.p, S, c, p);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                o[k] = cneg(acc[k]);
-                mac(o[k].re, m2, p[k].re);
-                mac(o[k].im, m2, p[k].im);
-                o[k].re = rnorm<R>(o[k].re);
-                o[k].im = rnorm<R>(o[k].im);
-            }
-            if (EPI == EPI_RESID || EPI == EPI_RESID_STORE) {
-                cplx<R> bb[3];
-                load_vec<P>((const E *)a.b, S, c, bb);
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    o[k].re = rsub(bb[k].re, o[k].re);
-                    o[k].im = rsub(bb[k].im, o[k].im);
-                }
-                dot = re_dot3<R>(o, o);
-                if (EPI == EPI_RESID_STORE)
-                    store_vec<P>((E *)a.out, S, c, o);
-            } else {
+            dot = re_dot3<R>(o, o);
+            if (EPI == EPI_RESID_STORE)
                 store_vec<P>((E *)a.out, S, c, o);
-                if (EPI == EPI_M_PAP || EPI == EPI_M_PART)
-                    dot = re_dot3<R>(p, o);
-            }
+        } else {
+            store_vec<P>((E *)a.out, S, c, o);
+            if (EPI == EPI_M_PAP || EPI == EPI_M_PART)
+                dot = re_dot3<R>(p, o);
         }
     }
+    return dot;
+}
+
+// the block's (EPI_M_PART) or the grid's (EPI_M_PAP, EPI_RESID*) sum of the
+// sites' shares, and what the epilogue makes of it
+template <int EPI, int BLOCK, class T>
+STAG_D void dslash_reduce(const DslashArgs &a, T dot, double *smem) {
     if (EPI == EPI_M_PART) {
         // no ticket: the block's partial is all this kernel contributes
         const double s = block_sum<BLOCK>(dot, smem);
@@ -361,6 +264,58 @@ STAG_D void dslash_body(const DslashArgs &a) {
     }
 }
 
+template <int P, int EPI, int BLOCK, bool COMP>
+STAG_D void dslash_body(const DslashArgs &a) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    using E = typename F::Elem;
+    __shared__ double smem[32];
+    // the status is uniform over the grid: either every block returns here or none
+    if (a.skip_if_done && a.sc->status != CG_RUNNING)
+        return;
+    if (a.gate && *a.gate == 0)
+        return;
+    const int c = a.c0 + blockIdx.x * BLOCK + threadIdx.x;
+    red_t<R> dot = red_zero<red_t<R>>();
+    if (c < a.c0 + (a.cn ? a.cn : a.g.Vh)) {
+        cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
+        dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
+        dot = dslash_epilogue<P, EPI>(a, c, acc);
+    }
+    dslash_reduce<EPI, BLOCK>(a, dot, smem);
+}
+
+// The compressed 16-bit stencil on the pair (c, c + Vh/2) per thread
+// (stencil16_pair: all Vh sites, Lt a multiple of 4 and at least 8); block
+// partials of EPI_M_PART cover both sites of each thread.
+template <int EPI, int BLOCK>
+STAG_D void pair16_body(const DslashArgs &a) {
+    __shared__ double smem[32];
+    if (a.skip_if_done && a.sc->status != CG_RUNNING)
+        return;
+    if (a.gate && *a.gate == 0)
+        return;
+    const int H = a.g.Vh >> 1;
+    const int c = blockIdx.x * BLOCK + threadIdx.x;
+    df dot = df_zero();
+    if (c < H) {
+        cplx<float2> acc[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+            acc[k] = cplx<float2>{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        stencil16_pair(a.g, a.out_par, c, a.links_out, a.links_in, (const short2 *)a.in, a, acc);
+        cplx<float> lo[3], hi[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            lo[k] = cplx<float>{acc[k].re.x, acc[k].im.x};
+            hi[k] = cplx<float>{acc[k].re.y, acc[k].im.y};
+        }
+        dot = dslash_epilogue<P_F16, EPI>(a, c, lo);
+        dot = red_add(dot, dslash_epilogue<P_F16, EPI>(a, c + H, hi));
+    }
+    dslash_reduce<EPI, BLOCK>(a, dot, smem);
+}
+
 // One launch of the stencil.  The capped form asks for at least 1024 resident
 // threads per SM (at most 64 registers).  Left free, the compiler hoists the
 // compressed 16-bit stencil's loads into 255 registers at a low occupancy,
@@ -375,6 +330,20 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
 template <int P, int EPI, int BLOCK, bool COMP>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(DslashArgs a) {
     dslash_body<P, EPI, BLOCK, COMP>(a);
+}
+
+// whether a launch of precision prec and epilogue epi runs the pair form
+STAG_HD bool pair16_used(int prec, int epi, const DslashArgs &a) {
+    return prec == P_F16 && a.compressed && a.regs == REGS_PAIR && (epi == EPI_NONE || epi == EPI_M_PART) &&
+           a.c0 == 0 && (a.cn == 0 || a.cn == a.g.Vh) && pair16_applies(a.g);
+}
+STAG_HD int dslash_pair16_grid(const Geom &g, int block) { return ((g.Vh >> 1) + block - 1) / block; }
+
+// the pair form (REGS_PAIR): the compiler's choice, which keeps both sites'
+// loads of a hop in flight
+template <int EPI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) dslash_pair16_kernel(DslashArgs a) {
+    pair16_body<EPI, BLOCK>(a);
 }
 
 }  // namespace stag

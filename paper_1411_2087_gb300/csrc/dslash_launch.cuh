@@ -39,6 +39,16 @@ static void launch_one(int grid, const DslashArgs &a, cudaStream_t s) {
 
 template <int P, int BLOCK, bool COMP>
 static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
+    if constexpr (P == P_F16 && COMP) {
+        if (pair16_used(P, epi, a)) {
+            const int grid = dslash_pair16_grid(a.g, BLOCK);
+            if (epi == EPI_NONE)
+                dslash_pair16_kernel<EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a);
+            else
+                dslash_pair16_kernel<EPI_M_PART, BLOCK><<<grid, BLOCK, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const int n = a.cn ? a.cn : a.g.Vh;
     const int grid = (n + BLOCK - 1) / BLOCK;
     if (grid == 0)

@@ -826,8 +826,8 @@ constexpr int kRhsWindow = 16;
 int rhs_scale_begin(const stag_field b, RhsScale *rs) {
     rs->k = 0;
     rs->scaled = nullptr;
-    if (b->prec == STAG_F64)
-        return STAG_OK;
+    if (b->prec != STAG_DF64 && b->prec != STAG_F32)
+        return STAG_OK;  // FP64 has the range; 16-bit fields carry a norm per site
     stag_lattice lat = b->lat;
     DEVICE_SCOPE(lat->device);
     if (!lat->absmax)

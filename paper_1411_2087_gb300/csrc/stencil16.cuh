@@ -1,0 +1,282 @@
+// The compressed 16-bit stencil (12-real links, 16-bit colour vectors), in
+// raw integer units, written once over a lane type V:
+//
+//   V = float    one output site per thread
+//   V = float2   two output sites per thread, the pair (x, y, z, t) and
+//                (x, y, z, t + Lt/2), in Blackwell's packed FP32x2
+//                arithmetic (one FFMA2 does the same multiply-add on both)
+//
+// Both forms run the same IEEE operations in the same order on every lane,
+// so they give the same bits.  In the pair form the two sites share their
+// coordinates, every x/y/z hop offset and every Kogut-Susskind and boundary
+// sign; only the t hops differ (one site of the pair can wrap forward, the
+// other backward).  This halves the floating-point instructions per site
+// and removes half of the index arithmetic, the two costs that keep the
+// one-site form below the memory roof.
+//
+// Units: a link entry is ls q (ls the field's scale), a vector component
+// (n / 32767) q (n the site's norm), q the stored integers.  Rows 0 and 1 of
+// a link are stored; with X = row0 x row1 (raw), row 2 of the link is
+// conj(X) ls / s (s = c eta b of that link), which the hop's coefficients
+// carry.
+#pragma once
+#include "fields.cuh"
+
+namespace stag {
+
+STAG_D float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+STAG_D float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+STAG_D float vmul(float a, float b) { return __fmul_rn(a, b); }
+STAG_D float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+STAG_D float vneg(float a) { return -a; }
+STAG_D float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+template <class V> STAG_D V vsplat(float s);
+template <> STAG_D float vsplat<float>(float s) { return s; }
+template <> STAG_D float2 vsplat<float2>(float s) { return make_float2(s, s); }
+
+// integer halves of a 32-bit word as floats (exact)
+STAG_D float q_lo(int w) { return (float)(short)(w & 0xffff); }
+STAG_D float q_hi(int w) { return (float)(w >> 16); }
+
+// X = row0 x row1 of the raw link (L[0..2] row 0, L[3..5] row 1)
+template <class V>
+STAG_D void cross01(const cplx<V> L[6], cplx<V> X[3]) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        const cplx<V> &ak = L[k], &al = L[l], &bk = L[3 + k], &bl = L[3 + l];
+        // ak bl - al bk
+        V re = vmul(ak.re, bl.re);
+        re = vfma(vneg(ak.im), bl.im, re);
+        re = vfma(vneg(al.re), bk.re, re);
+        re = vfma(al.im, bk.im, re);
+        V im = vmul(ak.re, bl.im);
+        im = vfma(ak.im, bl.re, im);
+        im = vfma(vneg(al.re), bk.im, im);
+        im = vfma(vneg(al.im), bk.re, im);
+        X[j] = cplx<V>{re, im};
+    }
+}
+
+// forward hop: acc_r += cf (L v)_r for rows 0, 1 and acc_2 += cf2 (conj(X) . v)
+template <class V>
+STAG_D void hop_fwd16(cplx<V> acc[3], const cplx<V> L[6], const cplx<V> v[3], V cf, V cf2) {
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        V tr = vmul(L[3 * r].re, v[0].re);
+        tr = vfma(vneg(L[3 * r].im), v[0].im, tr);
+        V ti = vmul(L[3 * r].re, v[0].im);
+        ti = vfma(L[3 * r].im, v[0].re, ti);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            tr = vfma(L[3 * r + b].re, v[b].re, tr);
+            tr = vfma(vneg(L[3 * r + b].im), v[b].im, tr);
+            ti = vfma(L[3 * r + b].re, v[b].im, ti);
+            ti = vfma(L[3 * r + b].im, v[b].re, ti);
+        }
+        acc[r].re = vfma(cf, tr, acc[r].re);
+        acc[r].im = vfma(cf, ti, acc[r].im);
+    }
+    cplx<V> X[3];
+    cross01(L, X);
+    V tr = vmul(X[0].re, v[0].re);
+    tr = vfma(X[0].im, v[0].im, tr);
+    V ti = vmul(X[0].re, v[0].im);
+    ti = vfma(vneg(X[0].im), v[0].re, ti);
+#pragma unroll
+    for (int b = 1; b < 3; b++) {
+        tr = vfma(X[b].re, v[b].re, tr);
+        tr = vfma(X[b].im, v[b].im, tr);
+        ti = vfma(X[b].re, v[b].im, ti);
+        ti = vfma(vneg(X[b].im), v[b].re, ti);
+    }
+    acc[2].re = vfma(cf2, tr, acc[2].re);
+    acc[2].im = vfma(cf2, ti, acc[2].im);
+}
+
+// backward hop: acc_r += cf (L^+ v)_r, with L^+ v = sum_b conj(L_br) v_b and
+// conj(L_2r) = X_r k2 (k2 = ls / s of the link)
+template <class V>
+STAG_D void hop_bwd16(cplx<V> acc[3], const cplx<V> L[6], const cplx<V> v[3], V cf, V k2) {
+    cplx<V> X[3];
+    cross01(L, X);
+    const cplx<V> w = {vmul(v[2].re, k2), vmul(v[2].im, k2)};
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        V tr = vmul(L[r].re, v[0].re);
+        tr = vfma(L[r].im, v[0].im, tr);
+        tr = vfma(L[3 + r].re, v[1].re, tr);
+        tr = vfma(L[3 + r].im, v[1].im, tr);
+        tr = vfma(X[r].re, w.re, tr);
+        tr = vfma(vneg(X[r].im), w.im, tr);
+        V ti = vmul(L[r].re, v[0].im);
+        ti = vfma(vneg(L[r].im), v[0].re, ti);
+        ti = vfma(L[3 + r].re, v[1].im, ti);
+        ti = vfma(vneg(L[3 + r].im), v[1].re, ti);
+        ti = vfma(X[r].re, w.im, ti);
+        ti = vfma(X[r].im, w.re, ti);
+        acc[r].re = vfma(cf, tr, acc[r].re);
+        acc[r].im = vfma(cf, ti, acc[r].im);
+    }
+}
+
+// ---- loads: one site (V = float) ----------------------------------------
+
+// raw vector of site j; returns its norm
+STAG_D float ld_vec16(const short2 *__restrict__ v, int S, int j, cplx<float> w[3]) {
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const short2 q = ld_keep(v + b * S + j);
+        w[b] = cplx<float>{(float)q.x, (float)q.y};
+    }
+    return ld_keep((const float *)(v + 3 * S) + j);
+}
+
+// rows 0, 1 of link idx of one kind (12-real 16-bit layout)
+STAG_D void ld_link16(const char *kb, int S, int idx, cplx<float> L[6]) {
+    const int4 a = ld_stream((const int4 *)kb + idx);
+    const int2 b = ld_stream((const int2 *)(kb + (size_t)16 * S) + idx);
+    L[0] = cplx<float>{q_lo(a.x), q_hi(a.x)};
+    L[1] = cplx<float>{q_lo(a.y), q_hi(a.y)};
+    L[2] = cplx<float>{q_lo(a.z), q_hi(a.z)};
+    L[3] = cplx<float>{q_lo(a.w), q_hi(a.w)};
+    L[4] = cplx<float>{q_lo(b.x), q_hi(b.x)};
+    L[5] = cplx<float>{q_lo(b.y), q_hi(b.y)};
+}
+
+// ---- loads: a pair of sites (V = float2, lanes ja, jb) -------------------
+
+STAG_D float2 ld_vec16(const short2 *__restrict__ v, int S, int ja, int jb, cplx<float2> w[3]) {
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+        const short2 qa = ld_keep(v + b * S + ja), qb = ld_keep(v + b * S + jb);
+        w[b] = cplx<float2>{make_float2((float)qa.x, (float)qb.x), make_float2((float)qa.y, (float)qb.y)};
+    }
+    const float *n = (const float *)(v + 3 * S);
+    return make_float2(ld_keep(n + ja), ld_keep(n + jb));
+}
+
+STAG_D void ld_link16(const char *kb, int S, int ia, int ib, cplx<float2> L[6]) {
+    const int4 a = ld_stream((const int4 *)kb + ia), c = ld_stream((const int4 *)kb + ib);
+    const int2 b = ld_stream((const int2 *)(kb + (size_t)16 * S) + ia);
+    const int2 d = ld_stream((const int2 *)(kb + (size_t)16 * S) + ib);
+    const int wa[6] = {a.x, a.y, a.z, a.w, b.x, b.y}, wb[6] = {c.x, c.y, c.z, c.w, d.x, d.y};
+#pragma unroll
+    for (int e = 0; e < 6; e++)
+        L[e] = cplx<float2>{make_float2(q_lo(wa[e]), q_lo(wb[e])), make_float2(q_hi(wa[e]), q_hi(wb[e]))};
+}
+
+// ---- the site loops -------------------------------------------------------
+
+// acc += D psi at checkerboard site c of parity par (one site)
+template <class A>
+STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict__ Gout,
+                           const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
+                           cplx<float> acc[3]) {
+    const int S = g.stride;
+    int x[4];
+    cb_coords(g, c, par, x);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int esum = 0;
+#pragma unroll
+        for (int nu = 0; nu < mu; nu++)
+            esum += x[nu];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int s = h ? 3 : 1;
+            const char *ko = (const char *)Gout + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+            const char *ki = (const char *)Gin + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+            const float ls = a.link_scale[h], lsq = ls * (1.f / kQ16);
+            {
+                const int j = cb_hop(g, c, x, mu, +s);
+                const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
+                cplx<float> v[3], L[6];
+                const float cf = vmul(ld_vec16(in, S, j, v), lsq);
+                ld_link16(ko, S, c, L);
+                hop_fwd16(acc, L, v, cf, vmul(cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h])));
+            }
+            {
+                const int j = cb_hop(g, c, x, mu, -s);
+                const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
+                cplx<float> v[3], L[6];
+                const float cf = vmul(ld_vec16(in, S, j, v), -lsq);
+                ld_link16(ki, S, j, L);
+                hop_bwd16(acc, L, v, cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h]));
+            }
+        }
+    }
+}
+
+// The pair form applies when Lt is a multiple of 4 and at least 8: then
+// (x, y, z, t) and (x, y, z, t + Lt/2), t < Lt/2, have the same x (the
+// checkerboard offset depends on t through t's parity only), sit H = Vh/2
+// apart in the checkerboard index, and a hop of at most 3 along t wraps at
+// most one of them (the lower one backward, the upper one forward).
+STAG_HD bool pair16_applies(const Geom &g) { return g.L[3] % 4 == 0 && g.L[3] >= 8; }
+
+// acc += D psi at sites c and c + H (c < H = Vh/2) of parity par
+template <class A>
+STAG_D void stencil16_pair(const Geom &g, int par, int c, const void *__restrict__ Gout,
+                           const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
+                           cplx<float2> acc[3]) {
+    const int S = g.stride, H = g.Vh >> 1;
+    int x[4];
+    cb_coords(g, c, par, x);
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int esum = 0;
+#pragma unroll
+        for (int nu = 0; nu < mu; nu++)
+            esum += x[nu];
+        const int eta = esum & 1;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int s = h ? 3 : 1;
+            const char *ko = (const char *)Gout + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+            const char *ki = (const char *)Gin + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+            const float ls = a.link_scale[h], lsq = ls * (1.f / kQ16);
+            const float kp = ls * a.inv_c[h];  // ls / s for eta b = +1
+            int jf_a, jf_b, jb_a, jb_b;
+            float2 kf, kb;
+            if (mu < 3) {
+                // the same hop and signs for both sites
+                jf_a = cb_hop(g, c, x, mu, +s);
+                jb_a = cb_hop(g, c, x, mu, -s);
+                jf_b = jf_a + H;
+                jb_b = jb_a + H;
+                const int ff = (eta + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
+                const int fb = (eta + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
+                kf = vsplat<float2>(ff ? -kp : kp);
+                kb = vsplat<float2>(fb ? -kp : kp);
+            } else {
+                // t hops: the lower site (t < Lt/2) wraps only backward, the
+                // upper one only forward
+                const int t = x[3], Lh = g.L[3] >> 1, P = g.plane[3];
+                const int wf = t + s >= Lh;  // upper site's forward hop wraps
+                const int wb = t < s;        // lower site's backward hop wraps
+                jf_a = c + s * P;
+                jf_b = c + H + s * P - (wf ? g.Vh : 0);
+                jb_a = c - s * P + (wb ? g.Vh : 0);
+                jb_b = c + H - s * P;
+                const int bn = a.bc_neg[3];
+                kf = make_float2(eta ? -kp : kp, (eta ^ (bn & wf)) ? -kp : kp);
+                kb = make_float2((eta ^ (bn & wb)) ? -kp : kp, eta ? -kp : kp);
+            }
+            {
+                cplx<float2> v[3], L[6];
+                const float2 cf = vmul(ld_vec16(in, S, jf_a, jf_b, v), vsplat<float2>(lsq));
+                ld_link16(ko, S, c, c + H, L);
+                hop_fwd16(acc, L, v, cf, vmul(cf, kf));
+            }
+            {
+                cplx<float2> v[3], L[6];
+                const float2 cf = vmul(ld_vec16(in, S, jb_a, jb_b, v), vsplat<float2>(-lsq));
+                ld_link16(ki, S, jb_a, jb_b, L);
+                hop_bwd16(acc, L, v, cf, kb);
+            }
+        }
+    }
+}
+
+}  // namespace stag

@@ -125,3 +125,17 @@ def test_import_beyond_fp32_range_refused(problem):
         nan = b.copy()
         nan[0, 0] = np.nan
         lat.field(stag.EVEN, "df64", nan)
+
+
+def test_reduced_precision_solve_refused_before_scaling(problem):
+    """CG needs F64 or DF64 fields: an FP32 or 16-bit solve is refused with
+    STAG_ERR_STATE (the source normalisation does not run first)."""
+    U, N, b = problem
+    with stag.Lattice(DIMS) as lat:
+        lat.upload_gauge(U, N, precisions=("f32", "f16"))
+        for prec in ("f32", "f16"):
+            fb = lat.field(stag.EVEN, prec, b * 1e-25)
+            fx = lat.field(stag.EVEN, prec)
+            with pytest.raises(stag.StagError) as ei:
+                lat.cg(fx, fb, MASS, 1e-6, 100)
+            assert ei.value.status == stag.ERR_STATE, (prec, ei.value)
