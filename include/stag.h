@@ -81,7 +81,8 @@ enum {
  * STAG_F32   float storage and arithmetic.
  * STAG_F16   16-bit storage ("half" in the lattice-QCD sense): signed
  *            fixed point, links with one scale per field (the largest folded
- *            entry), colour vectors with one float norm per site; float
+ *            entry), colour vectors with one float norm per site (a site's
+ *            three components and its norm share one 16-byte cell); float
  *            arithmetic.  1/32767 of the scale per entry.
  */
 enum { STAG_F64 = 0, STAG_F32 = 1, STAG_F16 = 2, STAG_DF64 = 3 };
@@ -317,9 +318,13 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
  *                     register variants (regs 1: the compiler's choice,
  *                     2: at most 64 registers, 1024 resident threads per SM)
  *                     and, for STAG_F16 on 12-real links with Lt a multiple
- *                     of 4 and at least 8, regs 3: two sites (x, y, z, t)
- *                     and (x, y, z, t + Lt/2) per thread in packed FP32x2
- *                     arithmetic (the same bits as the one-site forms)
+ *                     of 4 and at least 8, two sites (x, y, z, t) and
+ *                     (x, y, z, t + Lt/2) per thread in packed FP32x2
+ *                     arithmetic (the same bits as the one-site forms), with
+ *                     at least 768 resident threads per SM (regs 3), the
+ *                     compiler's choice (regs 4), or the loads of the next
+ *                     hops in flight through a shared-memory ring of
+ *                     cp.async copies (regs 5)
  *   STAG_TUNE_M       the solvers' M Dslash (m^2 p - D t with one <p, Mp>
  *                     partial per block): the same candidates
  *   STAG_TUNE_BATCH   the batched multi-right-hand-side Dslash: block 128 or
@@ -336,7 +341,7 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
 typedef struct {
     int kernel;    /* STAG_TUNE_DSLASH, STAG_TUNE_M or STAG_TUNE_BATCH          */
     int block;     /* threads per block                                        */
-    int regs;      /* Dslash kinds: 1 free, 2 capped, 3 site pairs; batched 0 */
+    int regs;      /* Dslash: 1 free, 2 capped, 3-5 site pairs; batched 0    */
     int group;     /* batched: right-hand sides per group; others 0            */
     double us;     /* microseconds per launch; 0 for a choice from the cache    */
     int chosen;    /* 1 for the configuration kept                             */
@@ -351,8 +356,9 @@ int stag_lattice_autotune_all(stag_lattice lat, int prec, unsigned flags, stag_t
                               int *n, int *cached);
 
 /* Set one kind's configuration by hand (regs 0 = the library's default
- * variant, 1..3 as above, 3 falling back to the default where the pair form
- * does not apply; group 0 = the largest).  Bad values: STAG_ERR_ARG. */
+ * variant, 1..5 as above, 3 to 5 falling back to the default where the
+ * pair form does not apply; group 0 = the largest).  Bad values:
+ * STAG_ERR_ARG. */
 int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, int block, int regs, int group);
 
 /* The autotuner, timed again (STAG_TUNE_FORCE): dslash_us[2] and batch_us[2]
@@ -555,8 +561,9 @@ int stag_dd_cg_solve(stag_lattice lat, int ndomains, stag_field x_even, const st
  *
  * The communicator is the caller's (MPI, a torch.distributed group, NCCL
  * through stag_comm_nccl_create, ...).  A message is the three slices of one
- * parity in the field's internal layout: component plane by component plane
- * (16-bit fields: then the per-site norms), each 3 * Lx*Ly*Lz/2 entries. */
+ * parity in the field's internal layout: component plane by component plane,
+ * each 3 * Lx*Ly*Lz/2 entries (16-bit fields: one plane of 16-byte cells,
+ * the site's three components and its norm). */
 typedef struct {
     void *ctx;           /* passed back to the callbacks                          */
     int rank, size;      /* 0 <= rank < size                                      */

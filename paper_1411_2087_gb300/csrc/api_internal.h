@@ -186,6 +186,7 @@ static inline Geom geom_of(const int dims[4], long long stride) {
     g.plane[1] = dims[0] / 2;
     g.plane[2] = dims[0] * dims[1] / 2;
     g.plane[3] = dims[0] * dims[1] * dims[2] / 2;
+    geom_set_div(g);
     return g;
 }
 

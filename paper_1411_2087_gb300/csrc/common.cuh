@@ -121,22 +121,50 @@ template <class R> STAG_D void cmac_conj(cplx<R> &acc, const cplx<R> &u, const c
 // --------------------------------------------------------------------------
 // geometry
 // --------------------------------------------------------------------------
+// Division by a fixed divisor d as a multiply (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, n / d equals
+// (mulhi(m, n) + n) >> l for every 0 <= n < 2^31.
+struct FastDiv {
+    unsigned m;
+    int l;
+};
+inline FastDiv fastdiv_make(int d) {
+    int l = 0;
+    while ((1LL << l) < d)
+        l++;
+    const unsigned long long m = ((1ULL << 32) * ((1ULL << l) - (unsigned long long)d)) / (unsigned long long)d + 1;
+    return FastDiv{(unsigned)m, l};
+}
+STAG_HD int fastdiv(int n, FastDiv f) {
+    const unsigned t = (unsigned)(((unsigned long long)f.m * (unsigned)n) >> 32);
+    return (int)((t + (unsigned)n) >> f.l);
+}
+
 struct Geom {
     int L[4];     // Lx, Ly, Lz, Lt
     int Lxh;      // Lx / 2
     int Vh;       // sites per parity
     int stride;   // elements between colour/component planes (>= Vh, padded)
     int plane[4]; // cb-index step of one hop: 1/2 (x, handled apart), Lx/2, Lx*Ly/2, Lx*Ly*Lz/2
+    FastDiv div[3]; // division by Lxh, Ly, Lz (geom_set_div)
 };
+
+// the divisors of cb_coords; every Geom is finished with this
+inline void geom_set_div(Geom &g) {
+    g.div[0] = fastdiv_make(g.Lxh);
+    g.div[1] = fastdiv_make(g.L[1]);
+    g.div[2] = fastdiv_make(g.L[2]);
+}
 
 // coordinates of checkerboard site c of parity par
 STAG_HD void cb_coords(const Geom &g, int c, int par, int x[4]) {
-    int xh = c % g.Lxh;
-    int r = c / g.Lxh;
-    x[1] = r % g.L[1];
-    r /= g.L[1];
-    x[2] = r % g.L[2];
-    x[3] = r / g.L[2];
+    const int r1 = fastdiv(c, g.div[0]);
+    const int xh = c - r1 * g.Lxh;
+    const int r2 = fastdiv(r1, g.div[1]);
+    x[1] = r1 - r2 * g.L[1];
+    x[3] = fastdiv(r2, g.div[2]);
+    x[2] = r2 - x[3] * g.L[2];
     x[0] = 2 * xh + ((par + x[1] + x[2] + x[3]) & 1);
 }
 

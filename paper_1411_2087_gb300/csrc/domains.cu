@@ -143,17 +143,13 @@ int copy_slices(const Domains &D, const void *src, void *dst, int t, int n) {
     const int Lt = g.L[3];
     const size_t per = (size_t)g.plane[3];  // checkerboard sites of one time slice
     const size_t S = (size_t)g.stride;
-    const size_t eb = prec_link_elem_bytes(D.prec);
+    const size_t eb = vec_site_bytes(D.prec);
+    const int planes = D.prec == STAG_F16 ? 1 : 3;  // 16-bit: one cell per site holds all
     for (int k = 0; k < n; k++) {
         const size_t tt = (size_t)(((t + k) % Lt + Lt) % Lt);
-        for (int a = 0; a < 3; a++) {
+        for (int a = 0; a < planes; a++) {
             const size_t off = (a * S + tt * per) * eb;
             CUDA_TRY(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, per * eb,
-                                     cudaMemcpyDeviceToDevice, lat->stream));
-        }
-        if (D.prec == STAG_F16) {  // per-site norms after the three component planes
-            const size_t off = 3 * S * eb + tt * per * sizeof(float);
-            CUDA_TRY(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, per * sizeof(float),
                                      cudaMemcpyDeviceToDevice, lat->stream));
         }
     }
@@ -196,7 +192,7 @@ Geom slab_geom(const Domains &D, int i) {
     return g;
 }
 void *slab(const Domains &D, int i, void *v) {
-    return (char *)v + (size_t)D.d[i].t0 * D.lat->geom.plane[3] * prec_link_elem_bytes(D.prec);
+    return (char *)v + (size_t)D.d[i].t0 * D.lat->geom.plane[3] * vec_site_bytes(D.prec);
 }
 
 // scalars of domain i before a reducing kernel: running, no stopping test

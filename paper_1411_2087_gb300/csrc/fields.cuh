@@ -3,7 +3,9 @@
 //
 // Layout (structure of arrays, one checkerboard):
 //   colour vector   Elem v[3][stride]           component a of site c at a*stride + c
-//                   (16-bit: followed by float norm[stride], one per site)
+//                   16-bit: one 16-byte cell per site instead, the three
+//                   components (int16 pairs) and the site's float norm, so
+//                   that a gather of one neighbour is one 16-byte load
 //   links           Elem G[2][8][9][stride]     [site parity][kind][row*3+col][cb site]
 //                   kind 0..3 = folded one-link U~_mu, 4..7 = folded three-link N~_mu
 // One Elem holds one complex number: a warp loading component j of 32
@@ -57,8 +59,8 @@ template <> struct Fmt<P_F32> {
 // 16-bit storage: signed fixed point q = round(v / scale * 32767), float
 // arithmetic.  Links use one scale per field (the largest |entry| of the
 // folded one-link or three-link field); colour vectors one per site (the
-// largest |component| at that site), stored in a float plane after the three
-// component planes.
+// largest |component| at that site), stored in the site's cell after its
+// three components.
 constexpr float kQ16 = 32767.f;
 
 STAG_D short q16(float v) { return (short)__float2int_rn(fminf(fmaxf(v, -kQ16), kQ16)); }
@@ -136,10 +138,13 @@ inline size_t prec_vec_bytes(int p, size_t stride) {
     case P_F64: return 3 * stride * sizeof(double2);
     case P_DF64: return 3 * stride * sizeof(float4);
     case P_F32: return 3 * stride * sizeof(float2);
-    case P_F16: return 3 * stride * sizeof(short2) + stride * sizeof(float);
+    case P_F16: return stride * sizeof(int4);  // one 16-byte cell per site
     default: return 0;
     }
 }
+// bytes from one site's entry of a colour vector to the next site's (within
+// a component plane; a 16-bit field's cell holds all components)
+inline size_t vec_site_bytes(int p) { return p == P_F16 ? 16 : prec_vec_bytes(p, 1) / 3; }
 inline size_t prec_link_elem_bytes(int p) {
     switch (p) {
     case P_F64: return sizeof(double2);
@@ -161,15 +166,19 @@ STAG_D void load_vec(const typename Fmt<P>::Elem *__restrict__ v, int stride, in
         w[a] = Fmt<P>::unpack(ld_keep(v + a * stride + c));
 }
 
+// the 16-bit cell of site c: components 0..2 as int16 pairs (re low, im
+// high) in x, y, z, the norm's bits in w
+STAG_D int4 ld_cell16(const short2 *__restrict__ v, int c) { return ld_keep((const int4 *)v + c); }
+
 template <>
 STAG_D void load_vec<P_F16>(const short2 *__restrict__ v, int stride, int c, cplx<float> w[3]) {
-    const float *norm = (const float *)(v + 3 * stride);
-    const float s = ld_keep(norm + c) * (1.f / kQ16);
+    (void)stride;
+    const int4 q = ld_cell16(v, c);
+    const float s = __int_as_float(q.w) * (1.f / kQ16);
+    const int qa[3] = {q.x, q.y, q.z};
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const short2 q = ld_keep(v + a * stride + c);
-        w[a] = cplx<float>{(float)q.x * s, (float)q.y * s};
-    }
+    for (int a = 0; a < 3; a++)
+        w[a] = cplx<float>{(float)(short)(qa[a] & 0xffff) * s, (float)(qa[a] >> 16) * s};
 }
 
 template <int P>
@@ -182,15 +191,18 @@ STAG_D void store_vec(typename Fmt<P>::Elem *__restrict__ v, int stride, int c,
 
 template <>
 STAG_D void store_vec<P_F16>(short2 *__restrict__ v, int stride, int c, const cplx<float> w[3]) {
+    (void)stride;
     float m = 0.f;
 #pragma unroll
     for (int a = 0; a < 3; a++)
         m = fmaxf(m, fmaxf(fabsf(w[a].re), fabsf(w[a].im)));
     const float inv = m > 0.f ? kQ16 / m : 0.f;
+    int q[3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        __stcs(v + a * stride + c, make_short2(q16(w[a].re * inv), q16(w[a].im * inv)));
-    __stcs((float *)(v + 3 * stride) + c, m);
+        q[a] = (int)((unsigned)(unsigned short)q16(w[a].re * inv) |
+                     ((unsigned)(unsigned short)q16(w[a].im * inv) << 16));
+    __stcs((int4 *)v + c, make_int4(q[0], q[1], q[2], __float_as_int(m)));
 }
 
 // to/from canonical complex128 for export and the double-valued epilogues

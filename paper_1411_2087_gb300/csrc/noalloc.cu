@@ -209,6 +209,7 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double bc[4], doubl
     a.g.plane[1] = dims[0] / 2;
     a.g.plane[2] = dims[0] * dims[1] / 2;
     a.g.plane[3] = dims[0] * dims[1] * dims[2] / 2;
+    geom_set_div(a.g);
     a.c1 = c1;
     a.c3 = c3;
     a.fat = (const double2 *)fat;

@@ -55,18 +55,18 @@ HaloRanges halo_ranges(int Lt, const Slab &s) {
     return h;
 }
 
-// one message: for each component plane (and the norm plane of a 16-bit
-// field) the kHaloSlices * per entries starting at slice t
+// one message: for each component plane the kHaloSlices * per entries
+// starting at slice t (a 16-bit field has one plane of 16-byte cells)
 struct PlaneSet {
-    size_t elem;   // bytes of one entry of the component planes
-    bool norms;    // 16-bit: a float norm plane follows
+    size_t elem;   // bytes of one site's entry in a plane
+    int count;     // planes
 };
 
-PlaneSet planes_of(int prec) { return PlaneSet{prec_link_elem_bytes(prec), prec == STAG_F16}; }
+PlaneSet planes_of(int prec) { return PlaneSet{vec_site_bytes(prec), prec == STAG_F16 ? 1 : 3}; }
 
 size_t message_bytes(const Geom &g, int prec) {
     const PlaneSet p = planes_of(prec);
-    return (size_t)kHaloSlices * g.plane[3] * (3 * p.elem + (p.norms ? sizeof(float) : 0));
+    return (size_t)kHaloSlices * g.plane[3] * p.elem * p.count;
 }
 
 // field (device, internal layout) slices [t, t + kHaloSlices) <-> message (device)
@@ -75,15 +75,8 @@ cudaError_t copy_message(const Geom &g, int prec, void *field, int t, void *msg,
     const size_t per = (size_t)g.plane[3], S = (size_t)g.stride;
     const size_t width = kHaloSlices * per * p.elem;
     char *f = (char *)field + (size_t)t * per * p.elem;
-    cudaError_t e = pack ? cudaMemcpy2DAsync(msg, width, f, S * p.elem, width, 3, cudaMemcpyDeviceToDevice, s)
-                         : cudaMemcpy2DAsync(f, S * p.elem, msg, width, width, 3, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess || !p.norms)
-        return e;
-    char *fn = (char *)field + 3 * S * p.elem + (size_t)t * per * sizeof(float);
-    char *mn = (char *)msg + 3 * width;
-    const size_t nb = kHaloSlices * per * sizeof(float);
-    return pack ? cudaMemcpyAsync(mn, fn, nb, cudaMemcpyDeviceToDevice, s)
-                : cudaMemcpyAsync(fn, mn, nb, cudaMemcpyDeviceToDevice, s);
+    return pack ? cudaMemcpy2DAsync(msg, width, f, S * p.elem, width, p.count, cudaMemcpyDeviceToDevice, s)
+                : cudaMemcpy2DAsync(f, S * p.elem, msg, width, width, p.count, cudaMemcpyDeviceToDevice, s);
 }
 
 bool comm_valid(const stag_comm *c) {
@@ -267,7 +260,7 @@ static Geom slab_geom(const stag_ddr d) {
     return g;
 }
 static void *slab_ptr(const stag_ddr d, int prec, void *v) {
-    return (char *)v + (size_t)d->slab.t0 * d->lat->geom.plane[3] * prec_link_elem_bytes(prec);
+    return (char *)v + (size_t)d->slab.t0 * d->lat->geom.plane[3] * vec_site_bytes(prec);
 }
 
 // scalars before a reducing kernel: running, no stopping test

@@ -1369,13 +1369,13 @@ static int tune_all(stag_lattice lat, int prec, std::vector<stag_tune_result> &r
     for (int kind = 0; kind < 2; kind++) {
         double best = 1e300;
         for (int bi = 0; bi < 4; bi++)
-            for (int regs = REGS_FREE; regs <= REGS_PAIR; regs++) {
+            for (int regs = REGS_FREE; regs <= REGS_PAIR_ASYNC; regs++) {
                 const int block = kTuneBlocks[bi];
                 DslashArgs a = kind == 0 ? dslash_args(lat, prec, STAG_ODD, w.p, w.t)
                                          : dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
                 a.p = w.p;
                 a.regs = regs;
-                if (regs == REGS_PAIR && !pair16_used(prec, EPI_NONE, a))
+                if (regs >= REGS_PAIR && !pair16_used(prec, EPI_NONE, a))
                     continue;  // the pair form exists for the compressed 16-bit stencil only
                 const int epi = kind == 0 ? EPI_NONE : EPI_M_PART;
                 double us = 0;
@@ -1501,8 +1501,8 @@ extern "C" int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, i
     switch (kernel) {
     case STAG_TUNE_DSLASH:
     case STAG_TUNE_M:
-        if ((block != 64 && block != 128 && block != 256 && block != 512) || regs < REGS_DEFAULT || regs > REGS_PAIR)
-            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: block 64/128/256/512, regs 0..3");
+        if ((block != 64 && block != 128 && block != 256 && block != 512) || regs < REGS_DEFAULT || regs > REGS_PAIR_ASYNC)
+            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: block 64/128/256/512, regs 0..5");
         (kernel == STAG_TUNE_DSLASH ? lat->dslash_block : lat->mdslash_block)[prec] = block;
         (kernel == STAG_TUNE_DSLASH ? lat->dslash_regs : lat->mdslash_regs)[prec] = regs;
         return STAG_OK;

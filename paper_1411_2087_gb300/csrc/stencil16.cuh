@@ -122,14 +122,13 @@ STAG_D void hop_bwd16(cplx<V> acc[3], const cplx<V> L[6], const cplx<V> v[3], V 
 
 // ---- loads: one site (V = float) ----------------------------------------
 
-// raw vector of site j; returns its norm
-STAG_D float ld_vec16(const short2 *__restrict__ v, int S, int j, cplx<float> w[3]) {
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        const short2 q = ld_keep(v + b * S + j);
-        w[b] = cplx<float>{(float)q.x, (float)q.y};
-    }
-    return ld_keep((const float *)(v + 3 * S) + j);
+// raw vector of site j (its 16-byte cell); returns its norm
+STAG_D float ld_vec16(const short2 *__restrict__ v, int j, cplx<float> w[3]) {
+    const int4 q = ld_cell16(v, j);
+    w[0] = cplx<float>{q_lo(q.x), q_hi(q.x)};
+    w[1] = cplx<float>{q_lo(q.y), q_hi(q.y)};
+    w[2] = cplx<float>{q_lo(q.z), q_hi(q.z)};
+    return __int_as_float(q.w);
 }
 
 // rows 0, 1 of link idx of one kind (12-real 16-bit layout)
@@ -146,14 +145,16 @@ STAG_D void ld_link16(const char *kb, int S, int idx, cplx<float> L[6]) {
 
 // ---- loads: a pair of sites (V = float2, lanes ja, jb) -------------------
 
-STAG_D float2 ld_vec16(const short2 *__restrict__ v, int S, int ja, int jb, cplx<float2> w[3]) {
-#pragma unroll
-    for (int b = 0; b < 3; b++) {
-        const short2 qa = ld_keep(v + b * S + ja), qb = ld_keep(v + b * S + jb);
-        w[b] = cplx<float2>{make_float2((float)qa.x, (float)qb.x), make_float2((float)qa.y, (float)qb.y)};
-    }
-    const float *n = (const float *)(v + 3 * S);
-    return make_float2(ld_keep(n + ja), ld_keep(n + jb));
+STAG_D cplx<float2> q2(int wa, int wb) {
+    return cplx<float2>{make_float2(q_lo(wa), q_lo(wb)), make_float2(q_hi(wa), q_hi(wb))};
+}
+
+STAG_D float2 ld_vec16(const short2 *__restrict__ v, int ja, int jb, cplx<float2> w[3]) {
+    const int4 qa = ld_cell16(v, ja), qb = ld_cell16(v, jb);
+    w[0] = q2(qa.x, qb.x);
+    w[1] = q2(qa.y, qb.y);
+    w[2] = q2(qa.z, qb.z);
+    return make_float2(__int_as_float(qa.w), __int_as_float(qb.w));
 }
 
 STAG_D void ld_link16(const char *kb, int S, int ia, int ib, cplx<float2> L[6]) {
@@ -192,7 +193,7 @@ STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict
                 const int j = cb_hop(g, c, x, mu, +s);
                 const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
                 cplx<float> v[3], L[6];
-                const float cf = vmul(ld_vec16(in, S, j, v), lsq);
+                const float cf = vmul(ld_vec16(in, j, v), lsq);
                 ld_link16(ko, S, c, L);
                 hop_fwd16(acc, L, v, cf, vmul(cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h])));
             }
@@ -200,7 +201,7 @@ STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict
                 const int j = cb_hop(g, c, x, mu, -s);
                 const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
                 cplx<float> v[3], L[6];
-                const float cf = vmul(ld_vec16(in, S, j, v), -lsq);
+                const float cf = vmul(ld_vec16(in, j, v), -lsq);
                 ld_link16(ki, S, j, L);
                 hop_bwd16(acc, L, v, cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h]));
             }
@@ -265,17 +266,152 @@ STAG_D void stencil16_pair(const Geom &g, int par, int c, const void *__restrict
             }
             {
                 cplx<float2> v[3], L[6];
-                const float2 cf = vmul(ld_vec16(in, S, jf_a, jf_b, v), vsplat<float2>(lsq));
+                const float2 cf = vmul(ld_vec16(in, jf_a, jf_b, v), vsplat<float2>(lsq));
                 ld_link16(ko, S, c, c + H, L);
                 hop_fwd16(acc, L, v, cf, vmul(cf, kf));
             }
             {
                 cplx<float2> v[3], L[6];
-                const float2 cf = vmul(ld_vec16(in, S, jb_a, jb_b, v), vsplat<float2>(-lsq));
+                const float2 cf = vmul(ld_vec16(in, jb_a, jb_b, v), vsplat<float2>(-lsq));
                 ld_link16(ki, S, jb_a, jb_b, L);
                 hop_bwd16(acc, L, v, cf, kb);
             }
         }
+    }
+}
+
+}  // namespace stag
+
+// ---- the pair form with an asynchronous ring ------------------------------
+//
+// Each thread copies the links and neighbour vectors of hop k + RING into
+// shared memory with cp.async while it computes hop k, so that RING hops of
+// both sites' loads are in flight without holding registers.  A slot holds,
+// per thread, five 16-byte cells: link rows 0-1 (entries e0..e3) of site A
+// and of site B, the two sites' vectors (three int16 pairs and the norm),
+// and both sites' link entries e4, e5.  Every thread reads only its own
+// cells, so no barrier is needed.
+namespace stag {
+
+STAG_D void cp_async16(unsigned dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+STAG_D void cp_async8(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+STAG_D void cp_async16ca(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+STAG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> STAG_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// ring depth for a block size: 40 KB of shared memory per block at most
+template <int BLOCK> __host__ __device__ constexpr int pair16_ring() { return BLOCK <= 128 ? 4 : 40960 / (80 * BLOCK); }
+
+// the indices of hop k = 4 mu + 2 h + dir (dir 1: backward) of the pair
+// (c, c + H): neighbour vectors at ja, jb, links at ia, ib of kind 4h + mu
+// in the output parity's (dir 0) or the input parity's field (dir 1)
+STAG_D void pair16_hop_index(const Geom &g, int c, const int x[4], int k, int &ja, int &jb, int &ia, int &ib) {
+    const int mu = k >> 2, s = ((k >> 1) & 1) ? 3 : 1, dir = k & 1, H = g.Vh >> 1;
+    if (mu < 3) {
+        ja = cb_hop(g, c, x, mu, dir ? -s : s);
+        jb = ja + H;
+    } else {
+        const int t = x[3], Lh = g.L[3] >> 1, P = g.plane[3];
+        if (dir == 0) {
+            ja = c + s * P;
+            jb = c + H + s * P - (t + s >= Lh ? g.Vh : 0);
+        } else {
+            ja = c - s * P + (t < s ? g.Vh : 0);
+            jb = c + H - s * P;
+        }
+    }
+    ia = dir ? ja : c;
+    ib = dir ? jb : c + H;
+}
+
+// the row-2 factors ls / s of hop k for the two sites (eta b folded)
+template <class A>
+STAG_D float2 pair16_hop_k2(const Geom &g, const int x[4], int k, const A &a) {
+    const int mu = k >> 2, h = (k >> 1) & 1, s = h ? 3 : 1, dir = k & 1;
+    int esum = 0;
+#pragma unroll
+    for (int nu = 0; nu < mu; nu++)
+        esum += x[nu];
+    const int eta = esum & 1;
+    const float kp = a.link_scale[h] * a.inv_c[h];
+    if (mu < 3) {
+        const int f = (eta + (a.bc_neg[mu] ? hop_wraps(x[mu], dir ? -s : s, g.L[mu]) : 0)) & 1;
+        return vsplat<float2>(f ? -kp : kp);
+    }
+    const int t = x[3], Lh = g.L[3] >> 1, bn = a.bc_neg[3];
+    if (dir == 0)
+        return make_float2(eta ? -kp : kp, (eta ^ (bn & (t + s >= Lh))) ? -kp : kp);
+    return make_float2((eta ^ (bn & (t < s))) ? -kp : kp, eta ? -kp : kp);
+}
+
+template <int BLOCK>
+STAG_D void pair16_issue(unsigned cell, const Geom &g, int c, const int x[4], int k, const void *Gout,
+                         const void *Gin, const short2 *in) {
+    const int S = g.stride;
+    int ja, jb, ia, ib;
+    pair16_hop_index(g, c, x, k, ja, jb, ia, ib);
+    const int mu = k >> 2, h = (k >> 1) & 1, dir = k & 1;
+    const char *kb = (const char *)(dir ? Gin : Gout) + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+    constexpr unsigned R = 16 * BLOCK;  // bytes between a slot's cells
+    cp_async16(cell, kb + (size_t)ia * 16);
+    cp_async16(cell + R, kb + (size_t)ib * 16);
+    const char *k2 = kb + (size_t)16 * S;
+    cp_async8(cell + 4 * R, k2 + (size_t)ia * 8);
+    cp_async8(cell + 4 * R + 8, k2 + (size_t)ib * 8);
+    cp_async16ca(cell + 2 * R, (const int4 *)in + ja);
+    cp_async16ca(cell + 3 * R, (const int4 *)in + jb);
+}
+
+// acc += D psi at sites c and c + H (c < H = Vh/2), loads through the ring
+// (ring: this block's RING * 5 * BLOCK cells of 16 bytes)
+template <int BLOCK, class A>
+STAG_D void stencil16_pair_async(const Geom &g, int par, int c, const void *__restrict__ Gout,
+                                 const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
+                                 int4 *ring, cplx<float2> acc[3]) {
+    constexpr int RING = pair16_ring<BLOCK>();
+    int x[4];
+    cb_coords(g, c, par, x);
+    const unsigned cell0 = (unsigned)__cvta_generic_to_shared(ring + threadIdx.x);
+#pragma unroll
+    for (int k = 0; k < RING; k++) {
+        pair16_issue<BLOCK>(cell0 + (unsigned)(k * 5 * BLOCK * 16), g, c, x, k, Gout, Gin, in);
+        cp_async_commit();
+    }
+#pragma unroll
+    for (int k = 0; k < 16; k++) {
+        cp_async_wait<RING - 1>();
+        const int slot = k % RING, h = (k >> 1) & 1, dir = k & 1;
+        const int4 *cell = ring + slot * 5 * BLOCK + threadIdx.x;
+        const int4 la = cell[0], lb = cell[BLOCK], va = cell[2 * BLOCK], vb = cell[3 * BLOCK], l2 = cell[4 * BLOCK];
+        cplx<float2> L[6], v[3];
+        L[0] = q2(la.x, lb.x);
+        L[1] = q2(la.y, lb.y);
+        L[2] = q2(la.z, lb.z);
+        L[3] = q2(la.w, lb.w);
+        L[4] = q2(l2.x, l2.z);
+        L[5] = q2(l2.y, l2.w);
+        v[0] = q2(va.x, vb.x);
+        v[1] = q2(va.y, vb.y);
+        v[2] = q2(va.z, vb.z);
+        const float lsq = a.link_scale[h] * (1.f / kQ16);
+        const float2 nrm = make_float2(__int_as_float(va.w), __int_as_float(vb.w));
+        const float2 k2 = pair16_hop_k2(g, x, k, a);
+        if (dir == 0) {
+            const float2 cf = vmul(nrm, vsplat<float2>(lsq));
+            hop_fwd16(acc, L, v, cf, vmul(cf, k2));
+        } else {
+            hop_bwd16(acc, L, v, vmul(nrm, vsplat<float2>(-lsq)), k2);
+        }
+        // the slot's cells are in registers now; refill it with hop k + RING
+        if (k + RING < 16)
+            pair16_issue<BLOCK>(cell0 + (unsigned)(slot * 5 * BLOCK * 16), g, c, x, k + RING, Gout, Gin, in);
+        cp_async_commit();
     }
 }
 
