@@ -318,13 +318,11 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
  *                     register variants (regs 1: the compiler's choice,
  *                     2: at most 64 registers, 1024 resident threads per SM)
  *                     and, for STAG_F16 on 12-real links with Lt a multiple
- *                     of 4 and at least 8, two sites (x, y, z, t) and
- *                     (x, y, z, t + Lt/2) per thread in packed FP32x2
- *                     arithmetic (the same bits as the one-site forms), with
- *                     at least 768 resident threads per SM (regs 3), the
- *                     compiler's choice (regs 4), or the loads of the next
- *                     hops in flight through a shared-memory ring of
- *                     cp.async copies (regs 5)
+ *                     of 4 and at least 8, regs 3: two sites (x, y, z, t)
+ *                     and (x, y, z, t + Lt/2) per thread in packed FP32x2
+ *                     arithmetic (the same bits as the one-site forms), the
+ *                     next hop's loads in flight through a shared-memory
+ *                     ring of cp.async copies
  *   STAG_TUNE_M       the solvers' M Dslash (m^2 p - D t with one <p, Mp>
  *                     partial per block): the same candidates
  *   STAG_TUNE_BATCH   the batched multi-right-hand-side Dslash: block 128 or
@@ -341,7 +339,7 @@ int stag_cg_solve_batched_mixed(int n, stag_lattice *lats, stag_field *xs, const
 typedef struct {
     int kernel;    /* STAG_TUNE_DSLASH, STAG_TUNE_M or STAG_TUNE_BATCH          */
     int block;     /* threads per block                                        */
-    int regs;      /* Dslash: 1 free, 2 capped, 3-5 site pairs; batched 0    */
+    int regs;      /* Dslash: 1 free, 2 capped, 3 site pairs; batched 0      */
     int group;     /* batched: right-hand sides per group; others 0            */
     double us;     /* microseconds per launch; 0 for a choice from the cache    */
     int chosen;    /* 1 for the configuration kept                             */
@@ -356,9 +354,8 @@ int stag_lattice_autotune_all(stag_lattice lat, int prec, unsigned flags, stag_t
                               int *n, int *cached);
 
 /* Set one kind's configuration by hand (regs 0 = the library's default
- * variant, 1..5 as above, 3 to 5 falling back to the default where the
- * pair form does not apply; group 0 = the largest).  Bad values:
- * STAG_ERR_ARG. */
+ * variant, 1..3 as above, 3 falling back to the default where the pair
+ * form does not apply; group 0 = the largest).  Bad values: STAG_ERR_ARG. */
 int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, int block, int regs, int group);
 
 /* The autotuner, timed again (STAG_TUNE_FORCE): dslash_us[2] and batch_us[2]

@@ -52,10 +52,9 @@ struct DslashArgs {
 // register variant of the stencil (DslashArgs::regs): the launcher's
 // measured default, the compiler's free choice, at most 64 registers, or
 // (compressed 16-bit stencil, EPI_NONE and EPI_M_PART) two sites per thread
-// in packed FP32x2 arithmetic where pair16_applies, else the default, with
-// at least 768 resident threads per SM, with the compiler's choice, or with
-// the loads through a shared-memory ring of cp.async copies
-enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2, REGS_PAIR = 3, REGS_PAIR_FREE = 4, REGS_PAIR_ASYNC = 5 };
+// in packed FP32x2 arithmetic with the loads through a shared-memory ring
+// (stencil16_pair_async) where pair16_applies, else the default
+enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2, REGS_PAIR = 3 };
 
 // rebuild row 2 of L = s U (U in SU(3)) from rows 0 and 1: conj(r0 x r1) / s
 template <class R>
@@ -288,12 +287,12 @@ STAG_D void dslash_body(const DslashArgs &a) {
 }
 
 // The compressed 16-bit stencil on the pair (c, c + Vh/2) per thread
-// (stencil16_pair: all Vh sites, Lt a multiple of 4 and at least 8); block
-// partials of EPI_M_PART cover both sites of each thread.
-template <int EPI, int BLOCK, bool ASYNC>
+// (stencil16_pair_async: all Vh sites, Lt a multiple of 4 and at least 8);
+// block partials of EPI_M_PART cover both sites of each thread.
+template <int EPI, int BLOCK>
 STAG_D void pair16_body(const DslashArgs &a) {
     __shared__ double smem[32];
-    __shared__ int4 ring[ASYNC ? pair16_ring<BLOCK>() * 5 * BLOCK : 1];
+    __shared__ int4 ring[pair16_ring<BLOCK>() * 5 * BLOCK];
     if (a.skip_if_done && a.sc->status != CG_RUNNING)
         return;
     if (a.gate && *a.gate == 0)
@@ -306,11 +305,8 @@ STAG_D void pair16_body(const DslashArgs &a) {
 #pragma unroll
         for (int k = 0; k < 3; k++)
             acc[k] = cplx<float2>{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if constexpr (ASYNC)
-            stencil16_pair_async<BLOCK>(a.g, a.out_par, c, a.links_out, a.links_in, (const short2 *)a.in, a,
-                                        ring, acc);
-        else
-            stencil16_pair(a.g, a.out_par, c, a.links_out, a.links_in, (const short2 *)a.in, a, acc);
+        stencil16_pair_async<BLOCK, pair16_ring<BLOCK>()>(a.g, a.out_par, c, a.links_out, a.links_in,
+                                                          (const short2 *)a.in, a, ring, acc);
         cplx<float> lo[3], hi[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -341,27 +337,19 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(Dsla
 
 // whether a launch of precision prec and epilogue epi runs the pair form
 STAG_HD bool pair16_used(int prec, int epi, const DslashArgs &a) {
-    return prec == P_F16 && a.compressed && a.regs >= REGS_PAIR && a.regs <= REGS_PAIR_ASYNC &&
+    return prec == P_F16 && a.compressed && a.regs == REGS_PAIR &&
            (epi == EPI_NONE || epi == EPI_M_PART) &&
            a.c0 == 0 && (a.cn == 0 || a.cn == a.g.Vh) && pair16_applies(a.g);
 }
 STAG_HD int dslash_pair16_grid(const Geom &g, int block) { return ((g.Vh >> 1) + block - 1) / block; }
 
-// the pair form: the compiler's choice (REGS_PAIR_FREE, about 114
-// registers, 16 resident warps per SM) or at least 768 resident threads per
-// SM (REGS_PAIR, at most 85 registers)
+// the pair form (REGS_PAIR): at least 768 resident threads per SM, at most
+// 85 registers (80 used).  At 48^3x96 this measured 351 us against 381-417
+// us with 640 threads and 96 registers (rings of 2 or 4 hops) and 386 us
+// with 512 threads and 124 registers.
 template <int EPI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) dslash_pair16_kernel(DslashArgs a) {
-    pair16_body<EPI, BLOCK, false>(a);
-}
-template <int EPI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (768 / BLOCK > 0 ? 768 / BLOCK : 1)) dslash_pair16_kernel_capped(DslashArgs a) {
-    pair16_body<EPI, BLOCK, false>(a);
-}
-// the pair form with its loads through a shared-memory ring (REGS_PAIR_ASYNC)
-template <int EPI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (640 / BLOCK > 0 ? 640 / BLOCK : 1)) dslash_pair16_kernel_async(DslashArgs a) {
-    pair16_body<EPI, BLOCK, true>(a);
+__global__ void __launch_bounds__(BLOCK, (768 / BLOCK > 0 ? 768 / BLOCK : 1)) dslash_pair16_kernel(DslashArgs a) {
+    pair16_body<EPI, BLOCK>(a);
 }
 
 }  // namespace stag

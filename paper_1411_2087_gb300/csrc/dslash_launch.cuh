@@ -37,25 +37,15 @@ static void launch_one(int grid, const DslashArgs &a, cudaStream_t s) {
     }
 }
 
-template <int EPI, int BLOCK>
-static void launch_pair16(int grid, const DslashArgs &a, cudaStream_t s) {
-    if (a.regs == REGS_PAIR)
-        dslash_pair16_kernel_capped<EPI, BLOCK><<<grid, BLOCK, 0, s>>>(a);
-    else if (a.regs == REGS_PAIR_FREE)
-        dslash_pair16_kernel<EPI, BLOCK><<<grid, BLOCK, 0, s>>>(a);
-    else
-        dslash_pair16_kernel_async<EPI, BLOCK><<<grid, BLOCK, 0, s>>>(a);
-}
-
 template <int P, int BLOCK, bool COMP>
 static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
     if constexpr (P == P_F16 && COMP) {
         if (pair16_used(P, epi, a)) {
             const int grid = dslash_pair16_grid(a.g, BLOCK);
             if (epi == EPI_NONE)
-                launch_pair16<EPI_NONE, BLOCK>(grid, a, s);
+                dslash_pair16_kernel<EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a);
             else
-                launch_pair16<EPI_M_PART, BLOCK>(grid, a, s);
+                dslash_pair16_kernel<EPI_M_PART, BLOCK><<<grid, BLOCK, 0, s>>>(a);
             return cudaGetLastError();
         }
     }

@@ -1290,7 +1290,8 @@ static std::string tune_key(const stag_lattice lat, int prec) {
     return buf;
 }
 
-// the optional file cache: one line per key, "stag-tune <key> <six ints>"
+// the optional file cache: one line per key, "stag-tune2 <key> <six ints>"
+// (lines of other formats, such as those of earlier candidate sets, are ignored)
 static const char *tune_file() { return getenv("STAG_TUNE_CACHE"); }
 
 static void tune_file_read_locked() {
@@ -1308,7 +1309,7 @@ static void tune_file_read_locked() {
         int d[4], prec, comp;
         char dev[200];
         TuneChoice c;
-        if (sscanf(line, "stag-tune %d %d %d %d %d %d %199s %d %d %d %d %d %d", &d[0], &d[1], &d[2], &d[3], &prec,
+        if (sscanf(line, "stag-tune2 %d %d %d %d %d %d %199s %d %d %d %d %d %d", &d[0], &d[1], &d[2], &d[3], &prec,
                    &comp, dev, &c.dblock, &c.dregs, &c.mblock, &c.mregs, &c.bblock, &c.bk) == 13) {
             char key[256];
             snprintf(key, sizeof key, "%d %d %d %d %d %d %s", d[0], d[1], d[2], d[3], prec, comp, dev);
@@ -1325,7 +1326,7 @@ static void tune_file_append(const std::string &key, const TuneChoice &c) {
     FILE *f = fopen(path, "a");
     if (!f)
         return;
-    fprintf(f, "stag-tune %s %d %d %d %d %d %d\n", key.c_str(), c.dblock, c.dregs, c.mblock, c.mregs, c.bblock, c.bk);
+    fprintf(f, "stag-tune2 %s %d %d %d %d %d %d\n", key.c_str(), c.dblock, c.dregs, c.mblock, c.mregs, c.bblock, c.bk);
     fclose(f);
 }
 
@@ -1369,13 +1370,13 @@ static int tune_all(stag_lattice lat, int prec, std::vector<stag_tune_result> &r
     for (int kind = 0; kind < 2; kind++) {
         double best = 1e300;
         for (int bi = 0; bi < 4; bi++)
-            for (int regs = REGS_FREE; regs <= REGS_PAIR_ASYNC; regs++) {
+            for (int regs = REGS_FREE; regs <= REGS_PAIR; regs++) {
                 const int block = kTuneBlocks[bi];
                 DslashArgs a = kind == 0 ? dslash_args(lat, prec, STAG_ODD, w.p, w.t)
                                          : dslash_args(lat, prec, STAG_EVEN, w.t, w.Ap);
                 a.p = w.p;
                 a.regs = regs;
-                if (regs >= REGS_PAIR && !pair16_used(prec, EPI_NONE, a))
+                if (regs == REGS_PAIR && !pair16_used(prec, EPI_NONE, a))
                     continue;  // the pair form exists for the compressed 16-bit stencil only
                 const int epi = kind == 0 ? EPI_NONE : EPI_M_PART;
                 double us = 0;
@@ -1501,8 +1502,8 @@ extern "C" int stag_lattice_set_tuning(stag_lattice lat, int prec, int kernel, i
     switch (kernel) {
     case STAG_TUNE_DSLASH:
     case STAG_TUNE_M:
-        if ((block != 64 && block != 128 && block != 256 && block != 512) || regs < REGS_DEFAULT || regs > REGS_PAIR_ASYNC)
-            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: block 64/128/256/512, regs 0..5");
+        if ((block != 64 && block != 128 && block != 256 && block != 512) || regs < REGS_DEFAULT || regs > REGS_PAIR)
+            return fail(STAG_ERR_ARG, "stag_lattice_set_tuning: block 64/128/256/512, regs 0..3");
         (kernel == STAG_TUNE_DSLASH ? lat->dslash_block : lat->mdslash_block)[prec] = block;
         (kernel == STAG_TUNE_DSLASH ? lat->dslash_regs : lat->mdslash_regs)[prec] = regs;
         return STAG_OK;

@@ -216,70 +216,6 @@ STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict
 // most one of them (the lower one backward, the upper one forward).
 STAG_HD bool pair16_applies(const Geom &g) { return g.L[3] % 4 == 0 && g.L[3] >= 8; }
 
-// acc += D psi at sites c and c + H (c < H = Vh/2) of parity par
-template <class A>
-STAG_D void stencil16_pair(const Geom &g, int par, int c, const void *__restrict__ Gout,
-                           const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
-                           cplx<float2> acc[3]) {
-    const int S = g.stride, H = g.Vh >> 1;
-    int x[4];
-    cb_coords(g, c, par, x);
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        int esum = 0;
-#pragma unroll
-        for (int nu = 0; nu < mu; nu++)
-            esum += x[nu];
-        const int eta = esum & 1;
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int s = h ? 3 : 1;
-            const char *ko = (const char *)Gout + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
-            const char *ki = (const char *)Gin + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
-            const float ls = a.link_scale[h], lsq = ls * (1.f / kQ16);
-            const float kp = ls * a.inv_c[h];  // ls / s for eta b = +1
-            int jf_a, jf_b, jb_a, jb_b;
-            float2 kf, kb;
-            if (mu < 3) {
-                // the same hop and signs for both sites
-                jf_a = cb_hop(g, c, x, mu, +s);
-                jb_a = cb_hop(g, c, x, mu, -s);
-                jf_b = jf_a + H;
-                jb_b = jb_a + H;
-                const int ff = (eta + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
-                const int fb = (eta + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
-                kf = vsplat<float2>(ff ? -kp : kp);
-                kb = vsplat<float2>(fb ? -kp : kp);
-            } else {
-                // t hops: the lower site (t < Lt/2) wraps only backward, the
-                // upper one only forward
-                const int t = x[3], Lh = g.L[3] >> 1, P = g.plane[3];
-                const int wf = t + s >= Lh;  // upper site's forward hop wraps
-                const int wb = t < s;        // lower site's backward hop wraps
-                jf_a = c + s * P;
-                jf_b = c + H + s * P - (wf ? g.Vh : 0);
-                jb_a = c - s * P + (wb ? g.Vh : 0);
-                jb_b = c + H - s * P;
-                const int bn = a.bc_neg[3];
-                kf = make_float2(eta ? -kp : kp, (eta ^ (bn & wf)) ? -kp : kp);
-                kb = make_float2((eta ^ (bn & wb)) ? -kp : kp, eta ? -kp : kp);
-            }
-            {
-                cplx<float2> v[3], L[6];
-                const float2 cf = vmul(ld_vec16(in, jf_a, jf_b, v), vsplat<float2>(lsq));
-                ld_link16(ko, S, c, c + H, L);
-                hop_fwd16(acc, L, v, cf, vmul(cf, kf));
-            }
-            {
-                cplx<float2> v[3], L[6];
-                const float2 cf = vmul(ld_vec16(in, jb_a, jb_b, v), vsplat<float2>(-lsq));
-                ld_link16(ki, S, jb_a, jb_b, L);
-                hop_bwd16(acc, L, v, cf, kb);
-            }
-        }
-    }
-}
-
 }  // namespace stag
 
 // ---- the pair form with an asynchronous ring ------------------------------
@@ -305,8 +241,10 @@ STAG_D void cp_async16ca(unsigned dst, const void *src) {
 STAG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> STAG_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// ring depth for a block size: 40 KB of shared memory per block at most
-template <int BLOCK> __host__ __device__ constexpr int pair16_ring() { return BLOCK <= 128 ? 4 : 40960 / (80 * BLOCK); }
+// ring depth: two hops in flight per thread (deeper rings measured slower
+// at 768 resident threads per SM, and need more shared memory than 48 KB
+// per block of 256); blocks of 512 keep one
+template <int BLOCK> __host__ __device__ constexpr int pair16_ring() { return BLOCK <= 256 ? 2 : 1; }
 
 // the indices of hop k = 4 mu + 2 h + dir (dir 1: backward) of the pair
 // (c, c + H): neighbour vectors at ja, jb, links at ia, ib of kind 4h + mu
@@ -370,11 +308,10 @@ STAG_D void pair16_issue(unsigned cell, const Geom &g, int c, const int x[4], in
 
 // acc += D psi at sites c and c + H (c < H = Vh/2), loads through the ring
 // (ring: this block's RING * 5 * BLOCK cells of 16 bytes)
-template <int BLOCK, class A>
+template <int BLOCK, int RING, class A>
 STAG_D void stencil16_pair_async(const Geom &g, int par, int c, const void *__restrict__ Gout,
                                  const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
                                  int4 *ring, cplx<float2> acc[3]) {
-    constexpr int RING = pair16_ring<BLOCK>();
     int x[4];
     cb_coords(g, c, par, x);
     const unsigned cell0 = (unsigned)__cvta_generic_to_shared(ring + threadIdx.x);

@@ -1,7 +1,9 @@
 """The autotuner (stag_lattice_autotune_all, stag_lattice_set_tuning).
 
 * Every Dslash candidate (block 64..512, both register variants) gives the
-  same output bit for bit, in every precision and link layout; so does M.
+  same output bit for bit, in every precision and link layout; so does M
+  (the two-site 16-bit form, a third candidate where it applies, is checked
+  bit for bit in tests/test_gpu_pair16.py).
 * The solvers meet the r11 criteria with every M-Dslash and batched
   candidate (block sizes reorder the partial sums, so not bit for bit).
 * The first call times every candidate and keeps one per kind; later calls
@@ -143,4 +145,19 @@ def test_cache_file_across_processes(tmp_path):
     strip = [[(r["kernel"], r["block"], r["regs"], r["group"]) for r in o["chosen"]] for o in outs]
     assert strip[0] == strip[1]
     lines = path.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("stag-tune 6 6 4 8 1 0 ")
+    assert len(lines) == 1 and lines[0].startswith("stag-tune2 6 6 4 8 1 0 ")
+
+
+@pytest.mark.parametrize("dims,pairs", [((4, 4, 4, 8), True), ((6, 4, 6, 10), False)])
+def test_pair_candidate_only_where_it_applies(dims, pairs):
+    """The two-site 16-bit form (regs 3) is a candidate on 12-real links with
+    Lt a multiple of 4 (and at least 8) only."""
+    U, N = fields(dims)
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, N, precisions=("f16",), compress12=True)
+        res, _ = lat.autotune_all("f16", force=True)
+        for kind in ("dslash", "M"):
+            regs = [r["regs"] for r in res if r["kernel"] == kind]
+            assert len(regs) == (12 if pairs else 8)
+            assert (3 in regs) == pairs
+        assert not any(r["kernel"] == "batch" for r in res)

@@ -1,7 +1,6 @@
-"""The pair form of the compressed 16-bit stencil (regs 3, 4, 5): two output
-sites (x, y, z, t) and (x, y, z, t + Lt/2) per thread in packed FP32x2
-arithmetic, with registers capped, left to the compiler, or with the loads
-through a shared-memory ring of cp.async copies.
+"""The pair form of the compressed 16-bit stencil (regs 3): two output sites
+(x, y, z, t) and (x, y, z, t + Lt/2) per thread in packed FP32x2 arithmetic,
+their loads through a shared-memory ring of cp.async copies.
 
 * D and M equal the one-site forms bit for bit, for every block size, on
   lattices whose Lt is a multiple of 4 (8, 12, 16), with every boundary sign
@@ -58,7 +57,7 @@ def test_pair_matches_one_site_and_oracle(dims, bc):
         assert rel_err(ref[0], want_o) <= 3e-4 and rel_err(ref[1], want_e) <= 3e-4
         assert rel_err(ref[2], want_m) <= 8e-4
         for block in BLOCKS:
-            for regs in (3, 4, 5):
+            for regs in (3,):
                 lat.set_tuning("f16", "dslash", block, regs)
                 got = run()
                 for g, w in zip(got, ref):
@@ -81,7 +80,7 @@ def test_solvers_with_the_pair_form(dims):
         fb = lat.field(stag.EVEN, "df64", b)
         iters = {}
         for block in (64, 256):
-            for regs in (1, 3, 4, 5):
+            for regs in (1, 3):
                 lat.set_tuning("f16", "dslash", block, regs)
                 lat.set_tuning("f16", "M", block, regs)
                 # mixed CG: the 16-bit iteration's alpha comes from the M
