@@ -61,6 +61,8 @@ def parse():
                     help="skip the mixed-precision comparison on the 48^3x96 workload")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-preconditioner comparison on the 32^3x64, m=0.005 workload")
+    ap.add_argument("--no-dd", action="store_true",
+                    help="skip the one-lattice-over-the-ranks (domain decomposition) section")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the IEEE FP64 and reduced-precision-error sections")
     ap.add_argument("--learned-pairs", type=int, default=4096)
@@ -348,7 +350,7 @@ def run_native(args):
     if not args.no_batched and world == 1:
         batched = batched_comparison(local, rank)
     # one lattice split over the ranks (strong scaling), on every N
-    ddr = dd_section(local, rank, world, pg, args.steps)
+    ddr = None if args.no_dd else dd_section(local, rank, world, pg, args.steps)
     fp64 = None
     precision = None
     if not args.no_precision and world == 1:
