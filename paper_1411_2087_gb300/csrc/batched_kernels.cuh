@@ -154,73 +154,59 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_kernel(BatchArgs a, int ou
     }
 }
 
-// Lane-mapped multi-RHS Dslash (double-float and FP64): thread t of the
-// group's range handles site t / GK for system t % GK (GK = systems in the
-// group), with the single-site stencil; epilogues as batch_dslash_kernel.
-template <int P, int EPI, int BLOCK, int K>
-__global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, int out_par, int src_x) {
+// the epilogue of system k at site c of a lane-mapped Dslash: store D psi
+// (EPI_NONE), or m_k^2 p_k - D psi and its share of <p_k, Ap_k> (EPI_M_PAP),
+// or the share of |b_k - M x_k|^2 (EPI_RESID)
+template <int P, int EPI>
+STAG_D red_t<typename Fmt<P>::R> batch_lane_epilogue(const BatchArgs &a, const BatchGroup &G, int k, int c,
+                                                      cplx<typename Fmt<P>::R> acc[3]) {
     using F = Fmt<P>;
     using R = typename F::R;
     using E = typename F::Elem;
-    __shared__ double smem[32];
-    __shared__ int act[K];
-    const int gi = group_of_lanes(a, blockIdx.x);
-    const BatchGroup &G = a.grp[gi];
-    load_active<K>(a, G, act, EPI != EPI_RESID && !src_x);
-    const int lblk = blockIdx.x - G.dblock0;
-    const int t = lblk * BLOCK + threadIdx.x;
-    const int k = t % G.K;
-    const int c = t / G.K;
-    const Geom &g = G.g;
-    const int S = g.stride;
+    const int S = G.g.stride;
     red_t<R> dk = red_zero<red_t<R>>();
-    if (c < g.Vh && act[k]) {
-        DslashArgs da = {};
-        da.link_scale[0] = G.link_scale[0];
-        da.link_scale[1] = G.link_scale[1];
-        cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
-        // EPI_NONE: D_oe of p (or of x for the true residual); otherwise D_eo of the odd t
-        const E *vin = (const E *)(EPI == EPI_NONE ? (src_x ? G.x[k] : G.p[k]) : G.t[k]);
-        dslash_site<P, false>(g, out_par, c, G.links[out_par], G.links[1 - out_par], vin, da, acc);
-        if (EPI == EPI_NONE) {
+    if (EPI == EPI_NONE) {
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            acc[r].re = rnorm<R>(acc[r].re);
+            acc[r].im = rnorm<R>(acc[r].im);
+        }
+        store_vec<P>((E *)G.t[k], S, c, acc);
+    } else {
+        const R m2 = scalar_as<R>(a.sys[G.sys0 + k].m2);
+        cplx<R> pv[3], o[3];
+        load_vec<P>((const E *)(EPI == EPI_RESID ? G.x[k] : G.p[k]), S, c, pv);
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            o[r] = cneg(acc[r]);
+            mac(o[r].re, m2, pv[r].re);
+            mac(o[r].im, m2, pv[r].im);
+            o[r].re = rnorm<R>(o[r].re);
+            o[r].im = rnorm<R>(o[r].im);
+        }
+        if (EPI == EPI_RESID) {
+            cplx<R> bv[3];
+            load_vec<P>((const E *)G.b[k], S, c, bv);
 #pragma unroll
             for (int r = 0; r < 3; r++) {
-                acc[r].re = rnorm<R>(acc[r].re);
-                acc[r].im = rnorm<R>(acc[r].im);
+                o[r].re = rsub(bv[r].re, o[r].re);
+                o[r].im = rsub(bv[r].im, o[r].im);
             }
-            store_vec<P>((E *)G.t[k], S, c, acc);
+            dk = re_dot3<R>(o, o);
         } else {
-            const R m2 = scalar_as<R>(a.sys[G.sys0 + k].m2);
-            cplx<R> pv[3], o[3];
-            load_vec<P>((const E *)(EPI == EPI_RESID ? G.x[k] : G.p[k]), S, c, pv);
-#pragma unroll
-            for (int r = 0; r < 3; r++) {
-                o[r] = cneg(acc[r]);
-                mac(o[r].re, m2, pv[r].re);
-                mac(o[r].im, m2, pv[r].im);
-                o[r].re = rnorm<R>(o[r].re);
-                o[r].im = rnorm<R>(o[r].im);
-            }
-            if (EPI == EPI_RESID) {
-                cplx<R> bv[3];
-                load_vec<P>((const E *)G.b[k], S, c, bv);
-#pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    o[r].re = rsub(bv[r].re, o[r].re);
-                    o[r].im = rsub(bv[r].im, o[r].im);
-                }
-                dk = re_dot3<R>(o, o);
-            } else {
-                store_vec<P>((E *)G.Ap[k], S, c, o);
-                dk = re_dot3<R>(pv, o);
-            }
+            store_vec<P>((E *)G.Ap[k], S, c, o);
+            dk = re_dot3<R>(pv, o);
         }
     }
+    return dk;
+}
+
+// the group's sums of a lane-mapped Dslash and what its last block makes of
+// them: alpha_k (EPI_M_PAP) or the true residual (EPI_RESID)
+template <int EPI, int BLOCK, int K, class T>
+STAG_D void batch_lane_reduce(const BatchArgs &a, int gi, const BatchGroup &G, const int *act, int lblk,
+                              const T (&dot)[K], double *smem) {
     if (EPI == EPI_M_PAP || EPI == EPI_RESID) {
-        red_t<R> dot[K];
-#pragma unroll
-        for (int kk = 0; kk < K; kk++)
-            dot[kk] = kk == k ? dk : red_zero<red_t<R>>();
         double tot[K];
         if (group_sum<BLOCK, K>(dot, G.K, G.partial, lblk, G.dnblocks, &a.tickets[gi], smem, tot) &&
             threadIdx.x == 0) {
@@ -239,6 +225,51 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, 
             }
         }
     }
+}
+
+// the vector a lane-mapped Dslash reads for system k: D_oe of p (or of x
+// for the true residual), or D_eo of the odd t
+template <int EPI>
+STAG_D const void *batch_lane_input(const BatchGroup &G, int k, int src_x) {
+    return EPI == EPI_NONE ? (src_x ? G.x[k] : G.p[k]) : G.t[k];
+}
+
+// Lane-mapped multi-RHS Dslash (double-float and FP64): thread t of the
+// group's range handles site t / GK for system t % GK (GK = systems in the
+// group), with the single-site stencil; epilogues as batch_dslash_kernel.
+template <int P, int EPI, int BLOCK, int K>
+__global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, int out_par, int src_x) {
+    using F = Fmt<P>;
+    using R = typename F::R;
+    using E = typename F::Elem;
+    __shared__ double smem[32];
+    __shared__ int act[K];
+    const int gi = group_of_lanes(a, blockIdx.x);
+    const BatchGroup &G = a.grp[gi];
+    load_active<K>(a, G, act, EPI != EPI_RESID && !src_x);
+    const int lblk = blockIdx.x - G.dblock0;
+    const int t = lblk * BLOCK + threadIdx.x;
+    const int k = t % G.K;
+    const int c = t / G.K;
+    const Geom &g = G.g;
+    red_t<R> dot[K];
+#pragma unroll
+    for (int kk = 0; kk < K; kk++)
+        dot[kk] = red_zero<red_t<R>>();
+    if (c < g.Vh && act[k]) {
+        DslashArgs da = {};
+        da.link_scale[0] = G.link_scale[0];
+        da.link_scale[1] = G.link_scale[1];
+        cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
+        dslash_site<P, false>(g, out_par, c, G.links[out_par], G.links[1 - out_par],
+                              (const E *)batch_lane_input<EPI>(G, k, src_x), da, acc);
+        const red_t<R> dk = batch_lane_epilogue<P, EPI>(a, G, k, c, acc);
+#pragma unroll
+        for (int kk = 0; kk < K; kk++)
+            if (kk == k)
+                dot[kk] = dk;
+    }
+    batch_lane_reduce<EPI, BLOCK, K>(a, gi, G, act, lblk, dot, smem);
 }
 
 // x = 0, r = b, p = b, |b|^2 per system

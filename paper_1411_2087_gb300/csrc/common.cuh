@@ -16,6 +16,9 @@ namespace stag {
 // error-free transformation, sums Knuth's TwoSum, so that one multiply-add
 // keeps about 48 significant bits.  Accumulators may carry an unnormalised
 // lo (the sum of all captured rounding errors); df_norm() renormalises.
+// The operations use explicitly rounded intrinsics, so that the compiler
+// fuses no multiply into a later add (which would break TwoSum's premise
+// s = fl(a + b)).
 // --------------------------------------------------------------------------
 struct df {
     float hi, lo;
@@ -35,9 +38,9 @@ STAG_HD double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
 // TwoSum: s + e == a + b exactly
 STAG_D void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 STAG_D df df_norm(df a) {
@@ -48,29 +51,29 @@ STAG_D df df_norm(df a) {
 
 // acc += a * b  (acc lo left unnormalised)
 STAG_D void df_mac(df &acc, df a, df b) {
-    float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
     float s, t;
     two_sum(acc.hi, p, s, t);
     acc.hi = s;
-    acc.lo = acc.lo + (t + e);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
 }
 
 STAG_D df df_add(df a, df b) {
     float s, e;
     two_sum(a.hi, b.hi, s, e);
-    e += a.lo + b.lo;
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
     return df_norm(df_make(s, e));
 }
 STAG_D df df_sub(df a, df b) { return df_add(a, -b); }
 
 STAG_D df df_mul(df a, df b) {
-    float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
     return df_norm(df_make(p, e));
 }
 
