@@ -575,6 +575,11 @@ typedef struct {
     /* sum n doubles (host memory) over all ranks, in place; the same result on
      * every rank.  Returns 0 on success. */
     int (*allreduce)(void *ctx, double *vals, int n);
+    /* optional (NULL if absent; needs device_buffers = 1): the same sum of n
+     * doubles in device memory, enqueued on `stream` without waiting.  With
+     * it the CG's sums stay on the device and the host waits once every
+     * eight iterations instead of twice per iteration. */
+    int (*allreduce_dev)(void *ctx, double *dev_vals, int n, void *stream);
 } stag_comm;
 
 typedef struct stag_ddr_s *stag_ddr;
@@ -604,16 +609,23 @@ int stag_ddr_dslash(stag_ddr d, stag_field out, stag_field in);
 
 /* CG for M x = b over all ranks (every rank calls it with its slab of b);
  * the rank's slab of x receives its part of the solution.  F64 or DF64
- * fields.  The iteration is host-driven: two halo exchanges and two
- * allreduces per iteration.  info->true_rel_resid is |b - M x| / |b| over the
- * whole lattice (one more exchange and allreduce).  Same return values as
- * stag_cg_solve, the same on every rank. */
+ * fields.  Per iteration: two halo exchanges, each overlapped with the
+ * stencil on the slab's interior (slices more than three from a face; slabs
+ * of at least 7 slices), and two allreduces of one value each.  alpha, beta
+ * and the stopping test are computed on the device from the global sums, so
+ * every rank takes the same decisions; with comm->allreduce_dev the iteration
+ * is enqueued in chunks of eight with one host wait per chunk (iterations
+ * after the stop do nothing but the exchanges), else the host waits for each
+ * allreduce.  info->true_rel_resid is |b - M x| / |b| over the whole lattice
+ * (one more exchange and allreduce).  Same return values as stag_cg_solve,
+ * the same on every rank. */
 int stag_ddr_cg_solve(stag_ddr d, stag_field x, const stag_field b, double mass, double rel_tol, int max_iter,
                       stag_solve_info *info);
 
 /* NCCL as the communicator: device-buffer exchange (grouped ncclSend/ncclRecv
- * on the lattice stream) and allreduce (ncclAllReduce of the doubles through a
- * device buffer).  stag_comm_nccl_id writes a new 128-byte unique id on one
+ * on the stream it is given), allreduce (ncclAllReduce of the doubles through
+ * a device buffer) and the device allreduce (ncclAllReduce in place on the
+ * stream).  stag_comm_nccl_id writes a new 128-byte unique id on one
  * rank, which the caller distributes; every rank then calls
  * stag_comm_nccl_create with it, its rank and the device it uses (a
  * collective call).  STAG_ERR_STATE if the library was built without NCCL. */

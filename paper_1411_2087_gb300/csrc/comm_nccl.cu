@@ -1,11 +1,12 @@
 // NCCL as the communicator of the rank decomposition (stag_comm_nccl_*;
 // documentation in include/stag.h).  The exchange is one NCCL group of two
-// sends and two receives on the lattice stream, ordered so that each pair of
+// sends and two receives on the stream it is given, ordered so that each pair of
 // ranks matches them the same way for any number of ranks (including one,
 // where a rank sends to itself, and two, where both neighbours are the same
 // rank): every rank sends towards rank + 1 first and receives from rank - 1
-// first.  The allreduce sums the doubles through a device buffer on the
-// communicator's own stream.  Compiled against nccl.h when the build finds
+// first.  The host allreduce sums the doubles through a device buffer on the
+// communicator's own stream; the device allreduce sums in place on the
+// caller's stream.  Compiled against nccl.h when the build finds
 // it; otherwise the entry points report that NCCL is missing.
 #include "api_internal.h"
 
@@ -59,6 +60,14 @@ int nccl_allreduce(void *ctx, double *vals, int n) {
     return rc;
 }
 
+int nccl_allreduce_dev(void *ctx, double *dev_vals, int n, void *stream) {
+    NcclCtx *c = (NcclCtx *)ctx;
+    if (n < 0)
+        return 1;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return ncclAllReduce(dev_vals, dev_vals, n, ncclDouble, ncclSum, c->comm, s) == ncclSuccess ? 0 : 2;
+}
+
 }  // namespace
 
 extern "C" int stag_comm_nccl_id(unsigned char id[128]) {
@@ -110,6 +119,7 @@ extern "C" int stag_comm_nccl_create(int rank, int size, const unsigned char id[
     out->device_buffers = 1;
     out->exchange = nccl_exchange;
     out->allreduce = nccl_allreduce;
+    out->allreduce_dev = nccl_allreduce_dev;
     return STAG_OK;
 }
 

@@ -7,9 +7,15 @@
 // input (one parity, every component plane) into two messages, hands them to
 // the caller's communicator with its halo buffers, unpacks what arrives into
 // the three slices on either side of its slab, and runs the stencil on its
-// slab's output sites only.  The CG's global sums are slab sums that the
-// communicator adds.  The vector kernels see the slab as a field of its own:
-// the same layout with the base moved to the slab's first site.
+// slab's output sites only.  The exchange runs on a second stream while the
+// stencil covers the slab's interior (the slices more than three away from
+// either face), and the two three-slice boundary ranges follow once the halo
+// has landed.  The CG's global sums are slab sums that the communicator adds;
+// the CG's scalar recurrence (alpha, beta, the stopping test) runs on the
+// device from those sums, so that with a communicator that sums device
+// values on the stream (NCCL) the host waits only every few iterations.  The
+// vector kernels see the slab as a field of its own: the same layout with
+// the base moved to the slab's first site.
 #include "api_internal.h"
 
 #include <climits>
@@ -81,7 +87,72 @@ cudaError_t copy_message(const Geom &g, int prec, void *field, int t, void *msg,
 
 bool comm_valid(const stag_comm *c) {
     return c && c->exchange && c->allreduce && c->size >= 1 && c->rank >= 0 && c->rank < c->size &&
-           (c->device_buffers == 0 || c->device_buffers == 1);
+           (c->device_buffers == 0 || c->device_buffers == 1) && (!c->allreduce_dev || c->device_buffers == 1);
+}
+
+// The global scalars of the rank CG, on the device next to the slab's
+// CgScalars: the slab's partial sums are copied here, summed over the ranks
+// in place, and turned into alpha, beta and the status by the kernels below.
+struct DdScal {
+    double pap;      // <p, M p>: the slab's, then the global sum
+    double rr;       // |r|^2 of this iteration: the slab's, then the global sum
+    double rr_prev;  // the global |r|^2 of the previous iteration
+    double rr_stop;  // tol^2 |b|^2
+    int max_iter;
+    int iter_seen;   // sc->iter when dd_rr_kernel last ran
+    int ran;         // the update kernel ran in this iteration
+    int pad;
+};
+
+// one block: the slab's <p, Mp> from the n block partials, in block order
+__global__ void dd_pap_kernel(const double *__restrict__ partial, int n, DdScal *dd) {
+    __shared__ double smem[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256)
+        acc += partial[i];
+    acc = block_sum<256>(acc, smem);
+    if (threadIdx.x == 0)
+        dd->pap = acc;
+}
+
+// alpha = |r|^2 / <p, Mp> from the global sums; breakdown on every rank alike
+__global__ void dd_alpha_kernel(CgScalars *sc, DdScal *dd) {
+    if (sc->status != CG_RUNNING)
+        return;
+    const double pap = dd->pap;
+    sc->pAp = pap;
+    if (!(pap > 0.0 && pap < INFINITY)) {
+        sc->status = CG_BREAKDOWN;
+        sc->alpha = make_dpair(0.0);
+    } else {
+        sc->alpha = make_dpair(dd->rr_prev / pap);
+    }
+}
+
+// the slab's |r|^2 if the update kernel ran in this iteration, else 0
+__global__ void dd_rr_kernel(const CgScalars *sc, DdScal *dd) {
+    dd->ran = sc->iter != dd->iter_seen;
+    dd->iter_seen = sc->iter;
+    dd->rr = dd->ran ? sc->rr : 0.0;
+}
+
+// beta and the stopping test from the global |r|^2 (the status the update
+// kernel may have set from the slab's sum is replaced by the global one)
+__global__ void dd_beta_kernel(CgScalars *sc, DdScal *dd) {
+    if (!dd->ran)
+        return;
+    const double rr = dd->rr;
+    sc->beta = make_dpair(rr / dd->rr_prev);
+    sc->rr = rr;
+    dd->rr_prev = rr;
+    if (!(rr < INFINITY))
+        sc->status = CG_BREAKDOWN;
+    else if (rr <= dd->rr_stop)
+        sc->status = CG_CONVERGED;
+    else if (sc->iter >= dd->max_iter)
+        sc->status = CG_MAXITER;
+    else
+        sc->status = CG_RUNNING;
 }
 
 }  // namespace
@@ -94,6 +165,12 @@ struct stag_ddr_s {
     void *dsend[2] = {}, *drecv[2] = {};  // device messages: [0] prev side, [1] next side
     void *hsend[2] = {}, *hrecv[2] = {};  // pinned host copies (host-memory communicators)
     CgScalars *sc = nullptr;         // the slab's partial sums
+    DdScal *dd = nullptr;            // the global scalars of the CG (device)
+    double *partial = nullptr;       // block partials of the split M Dslash
+    double *hval = nullptr;          // pinned: one value through a host allreduce
+    CgScalars *hsc = nullptr;        // pinned: the status read every few iterations
+    cudaStream_t side = nullptr;     // the halo exchange, beside the interior stencil
+    cudaEvent_t ev_in = nullptr, ev_halo = nullptr;
 };
 
 static void ddr_free(stag_ddr d) {
@@ -109,6 +186,20 @@ static void ddr_free(stag_ddr d) {
     }
     if (d->sc)
         cudaFree(d->sc);
+    if (d->dd)
+        cudaFree(d->dd);
+    if (d->partial)
+        cudaFree(d->partial);
+    if (d->hval)
+        cudaFreeHost(d->hval);
+    if (d->hsc)
+        cudaFreeHost(d->hsc);
+    if (d->ev_in)
+        cudaEventDestroy(d->ev_in);
+    if (d->ev_halo)
+        cudaEventDestroy(d->ev_halo);
+    if (d->side)
+        cudaStreamDestroy(d->side);
 }
 
 extern "C" int stag_ddr_layout(const int dims[4], int size, int rank, int *t0, int *nt) {
@@ -189,6 +280,20 @@ extern "C" int stag_ddr_create(stag_lattice lat, const stag_comm *comm, stag_ddr
     }
     if (e == cudaSuccess)
         e = cudaMalloc(&d->sc, sizeof(CgScalars));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d->dd, sizeof(DdScal));
+    if (e == cudaSuccess)  // the split M Dslash: up to three launches of blocks of 64 or more
+        e = cudaMalloc(&d->partial, sizeof(double) * ((size_t)lat->Vh / 64 + 4));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&d->hval, sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMallocHost(&d->hsc, sizeof(CgScalars));
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&d->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&d->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&d->ev_halo, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         ddr_free(d);
         delete d;
@@ -210,11 +315,11 @@ extern "C" int stag_ddr_destroy(stag_ddr d) {
     return STAG_OK;
 }
 
-// fill the halo of a field (device, precision prec) from the neighbours
-static int exchange_halo(stag_ddr d, int prec, void *field) {
+// fill the halo of a field (device, precision prec) from the neighbours,
+// in order on stream s
+static int exchange_halo(stag_ddr d, int prec, void *field, cudaStream_t s) {
     stag_lattice lat = d->lat;
     const Geom &g = lat->geom;
-    cudaStream_t s = lat->stream;
     const HaloRanges h = halo_ranges(g.L[3], d->slab);
     const size_t bytes = message_bytes(g, prec);
     CUDA_TRY(copy_message(g, prec, field, h.send_prev, d->dsend[0], true, s));
@@ -237,19 +342,71 @@ static int exchange_halo(stag_ddr d, int prec, void *field) {
     return STAG_OK;
 }
 
-// the stencil on the slab's output sites (halo of `in` already filled)
-static int slab_dslash(stag_ddr d, int prec, int out_par, int epi, const void *in, void *out, const void *p,
-                       const void *b, double m2) {
+// the stencil on slices [t, t + n) of the slab (halo of `in` filled where
+// they need it); EPI_M_PART writes its block partials from d->partial + *np
+// on and advances *np
+static int slab_range(stag_ddr d, int prec, int out_par, int epi, const void *in, void *out, const void *p,
+                      const void *b, double m2, int t, int n, int *np) {
     stag_lattice lat = d->lat;
+    if (n <= 0)
+        return STAG_OK;
     DslashArgs a = dslash_args(lat, prec, out_par, in, out);
-    a.c0 = d->slab.t0 * lat->geom.plane[3];
-    a.cn = d->slab.nt * lat->geom.plane[3];
+    a.c0 = t * lat->geom.plane[3];
+    a.cn = n * lat->geom.plane[3];
     a.p = p;
     a.b = b;
     a.sc = d->sc;
+    a.skip_if_done = epi == EPI_NONE || epi == EPI_M_PART;  // the CG's no-op iterations after it stops
+    a.partial = d->partial + (np ? *np : 0);
     a.m2 = make_dpair(m2);
     a.m2_in_args = 1;
-    CUDA_TRY(launch_dslash(prec, epi, a, lat->dslash_block[prec], lat->stream));
+    const int block = lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
+    CUDA_TRY(launch_dslash(prec, epi, a, block, lat->stream));
+    if (np)
+        *np += (a.cn + block - 1) / block;
+    return STAG_OK;
+}
+
+// exchange the halo of `in`, then the stencil on the whole slab: the
+// interior (slices more than kHaloSlices from a face) runs while the
+// exchange is in flight on the side stream, the two boundary ranges after
+// it (EPI_NONE or EPI_M_PART; *np receives the number of block partials)
+static int slab_dslash(stag_ddr d, int prec, int out_par, int epi, const void *in, void *out, const void *p,
+                       double m2, int *np) {
+    stag_lattice lat = d->lat;
+    cudaStream_t s = lat->stream;
+    const int t0 = d->slab.t0, nt = d->slab.nt, h = kHaloSlices;
+    if (np)
+        *np = 0;
+    if (nt <= 2 * h) {
+        STAG_TRY(exchange_halo(d, prec, (void *)in, s));
+        return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, nt, np);
+    }
+    CUDA_TRY(cudaEventRecord(d->ev_in, s));
+    CUDA_TRY(cudaStreamWaitEvent(d->side, d->ev_in, 0));
+    STAG_TRY(slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0 + h, nt - 2 * h, np));
+    STAG_TRY(exchange_halo(d, prec, (void *)in, d->side));
+    CUDA_TRY(cudaEventRecord(d->ev_halo, d->side));
+    CUDA_TRY(cudaStreamWaitEvent(s, d->ev_halo, 0));
+    STAG_TRY(slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, h, np));
+    return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0 + nt - h, h, np);
+}
+
+// sum one device double over the ranks, in place, in order on the lattice
+// stream: through the communicator's device allreduce, or through host
+// memory (then the host waits)
+static int allreduce_value(stag_ddr d, double *dev) {
+    cudaStream_t s = d->lat->stream;
+    if (d->comm.allreduce_dev) {
+        if (d->comm.allreduce_dev(d->comm.ctx, dev, 1, s) != 0)
+            return fail(STAG_ERR_STATE, "domain decomposition: the communicator's device allreduce failed");
+        return STAG_OK;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d->hval, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (d->comm.allreduce(d->comm.ctx, d->hval, 1) != 0)
+        return fail(STAG_ERR_STATE, "domain decomposition: the communicator's allreduce failed");
+    CUDA_TRY(cudaMemcpyAsync(dev, d->hval, sizeof(double), cudaMemcpyHostToDevice, s));
     return STAG_OK;
 }
 
@@ -301,8 +458,8 @@ extern "C" int stag_ddr_dslash(stag_ddr d, stag_field out, stag_field in) {
     if (!lat->has_gauge || !lat->links[prec])
         return fail(STAG_ERR_STATE, "stag_ddr_dslash: no %s gauge copy uploaded", prec_name(prec));
     DEVICE_SCOPE(lat->device);
-    STAG_TRY(exchange_halo(d, prec, in->data));
-    STAG_TRY(slab_dslash(d, prec, out->parity, EPI_NONE, in->data, out->data, nullptr, nullptr, 0.0));
+    STAG_TRY(put_scalars(d, 0.0, 0.0, 0.0));  // running: the stencil's gate
+    STAG_TRY(slab_dslash(d, prec, out->parity, EPI_NONE, in->data, out->data, nullptr, 0.0, nullptr));
     CUDA_TRY(cudaStreamSynchronize(lat->stream));
     return STAG_OK;
 }
@@ -335,58 +492,69 @@ extern "C" int stag_ddr_cg_solve(stag_ddr d, stag_field x, const stag_field b, d
     const double m2 = mass * mass;
     auto sl = [&](void *v) { return slab_ptr(d, prec, v); };
 
-    // x = 0, r = b, p = b on the slab, and |b|^2
+    // x = 0, r = b, p = b on the slab, and |b|^2 over the ranks
     STAG_TRY(put_scalars(d, 0.0, 0.0, 0.0));
     CUDA_TRY(launch_cg_init(prec, sg, sl(w.xw), sl(w.r), sl(w.p), sl(b->data), lat->partial, d->sc, s));
     double bb = 0.0;
     STAG_TRY(global_sum(d, offsetof(CgScalars, bb), &bb));
     const double stop = rel_tol * rel_tol * bb;
-    double rr = bb;
-    int it = 0;
-    int status = !(bb < INFINITY) ? CG_BREAKDOWN : rr <= stop ? CG_CONVERGED : CG_RUNNING;
-    while (status == CG_RUNNING && it < max_iter) {
-        // t = D_oe p (halo of p), then Ap = m^2 p - D_eo t and <p, Ap> (halo of t)
-        STAG_TRY(exchange_halo(d, prec, w.p));
-        STAG_TRY(slab_dslash(d, prec, STAG_ODD, EPI_NONE, w.p, w.t, nullptr, nullptr, m2));
-        STAG_TRY(put_scalars(d, rr, 0.0, 0.0));
-        STAG_TRY(exchange_halo(d, prec, w.t));
-        STAG_TRY(slab_dslash(d, prec, STAG_EVEN, EPI_M_PAP, w.t, w.Ap, w.p, nullptr, m2));
-        double pAp = 0.0;
-        STAG_TRY(global_sum(d, offsetof(CgScalars, pAp), &pAp));
-        if (!(pAp > 0.0 && pAp < INFINITY)) {
-            status = CG_BREAKDOWN;
-            break;
-        }
-        const double alpha = rr / pAp;
-        // x += alpha p, r -= alpha Ap, |r|^2
-        STAG_TRY(put_scalars(d, rr, alpha, 0.0));
-        CUDA_TRY(launch_cg_update(prec, sg, sl(w.xw), sl(w.r), sl(w.p), sl(w.Ap), lat->partial, d->sc, s));
-        double rr_new = 0.0;
-        STAG_TRY(global_sum(d, offsetof(CgScalars, rr), &rr_new));
-        it++;
-        const double beta = rr_new / rr;
-        rr = rr_new;
-        if (!(rr < INFINITY)) {
-            status = CG_BREAKDOWN;
-            break;
-        }
-        if (rr <= stop) {
-            status = CG_CONVERGED;
-            break;
-        }
-        // p = r + beta p
-        STAG_TRY(put_scalars(d, rr, alpha, beta));
-        CUDA_TRY(launch_cg_p_update(prec, sg, sl(w.r), sl(w.p), d->sc, s));
+    {
+        // the device scalars: running (the slab's kernels test nothing
+        // themselves), |r|^2 = |b|^2; the global test lives in DdScal
+        int st0 = !(bb < INFINITY) ? CG_BREAKDOWN : bb <= stop ? CG_CONVERGED : max_iter <= 0 ? CG_MAXITER
+                                                                                             : CG_RUNNING;
+        STAG_TRY(put_scalars(d, bb, 0.0, 0.0));
+        CUDA_TRY(cudaMemcpyAsync(&d->sc->status, &st0, sizeof st0, cudaMemcpyHostToDevice, s));
+        DdScal h;
+        memset(&h, 0, sizeof h);
+        h.rr_prev = bb;
+        h.rr_stop = stop;
+        h.max_iter = max_iter;
+        CUDA_TRY(cudaMemcpyAsync(d->dd, &h, sizeof h, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));  // pageable sources
     }
-    if (status == CG_RUNNING)
-        status = CG_MAXITER;
+    // the iteration, enqueued in chunks: with a device allreduce the host
+    // reads the status once per chunk, and iterations after the stop are
+    // no-ops on every rank alike (the status derives from global sums only)
+    const int chunk = d->comm.allreduce_dev ? 8 : 1;
+    int enqueued = 0;
+    for (;;) {
+        CUDA_TRY(cudaMemcpyAsync(d->hsc, d->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (d->hsc->status != CG_RUNNING || enqueued >= max_iter)
+            break;
+        for (int k = 0; k < chunk && enqueued < max_iter; k++, enqueued++) {
+            // t = D_oe p, then Ap = m^2 p - D_eo t with the slab's <p, Ap> partials
+            int np = 0;
+            STAG_TRY(slab_dslash(d, prec, STAG_ODD, EPI_NONE, w.p, w.t, nullptr, m2, nullptr));
+            STAG_TRY(slab_dslash(d, prec, STAG_EVEN, EPI_M_PART, w.t, w.Ap, w.p, m2, &np));
+            dd_pap_kernel<<<1, 256, 0, s>>>(d->partial, np, d->dd);
+            CUDA_TRY(cudaGetLastError());
+            STAG_TRY(allreduce_value(d, &d->dd->pap));
+            dd_alpha_kernel<<<1, 1, 0, s>>>(d->sc, d->dd);
+            CUDA_TRY(cudaGetLastError());
+            // x += alpha p, r -= alpha Ap and the slab's |r|^2; then the global
+            // |r|^2, beta and the stopping test; p = r + beta p
+            CUDA_TRY(launch_cg_update(prec, sg, sl(w.xw), sl(w.r), sl(w.p), sl(w.Ap), lat->partial, d->sc, s));
+            dd_rr_kernel<<<1, 1, 0, s>>>(d->sc, d->dd);
+            CUDA_TRY(cudaGetLastError());
+            STAG_TRY(allreduce_value(d, &d->dd->rr));
+            dd_beta_kernel<<<1, 1, 0, s>>>(d->sc, d->dd);
+            CUDA_TRY(cudaGetLastError());
+            CUDA_TRY(launch_cg_p_update(prec, sg, sl(w.r), sl(w.p), d->sc, s));
+        }
+    }
+    int status = d->hsc->status == CG_RUNNING ? CG_MAXITER : d->hsc->status;
+    const int it = d->hsc->iter;
+    double rr = 0.0;
+    CUDA_TRY(cudaMemcpy(&rr, &d->dd->rr_prev, sizeof rr, cudaMemcpyDeviceToHost));
     // the slab of x, then |b - M x|^2 over all ranks
     CUDA_TRY(cudaMemcpyAsync(x->data, w.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
-    STAG_TRY(exchange_halo(d, prec, x->data));
-    STAG_TRY(slab_dslash(d, prec, STAG_ODD, EPI_NONE, x->data, w.t, nullptr, nullptr, m2));
     STAG_TRY(put_scalars(d, 0.0, 0.0, 0.0));
-    STAG_TRY(exchange_halo(d, prec, w.t));
-    STAG_TRY(slab_dslash(d, prec, STAG_EVEN, EPI_RESID, w.t, nullptr, x->data, b->data, m2));
+    STAG_TRY(slab_dslash(d, prec, STAG_ODD, EPI_NONE, x->data, w.t, nullptr, m2, nullptr));
+    STAG_TRY(exchange_halo(d, prec, w.t, s));
+    STAG_TRY(slab_range(d, prec, STAG_EVEN, EPI_RESID, w.t, nullptr, x->data, b->data, m2, d->slab.t0,
+                        d->slab.nt, nullptr));
     double rr_true = 0.0;
     STAG_TRY(global_sum(d, offsetof(CgScalars, true_rr), &rr_true));
     stag_solve_info local;

@@ -81,11 +81,14 @@ class StagError(RuntimeError):
 EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_void_p)
 ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+ALLREDUCE_DEV_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_void_p)
 
 
 class CommStruct(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("rank", ctypes.c_int), ("size", ctypes.c_int),
-                ("device_buffers", ctypes.c_int), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN)]
+                ("device_buffers", ctypes.c_int), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN),
+                ("allreduce_dev", ALLREDUCE_DEV_FN)]
 
 
 class TuneResult(ctypes.Structure):

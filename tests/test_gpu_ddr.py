@@ -7,12 +7,15 @@ another: the ranks meet only on the host, in the mailbox's exchange and
 allreduce.  Checks:
 
 * each rank's slab of stag_ddr_dslash equals the single-domain Dslash
-  bit for bit (same kernel, same links, the received halo);
+  bit for bit (same kernel, same links, the received halo), also where the
+  slab's interior is computed while the halo is exchanged;
 * the CG over 1, 2 and 3 ranks (F64 and double float) gives a solution whose
   true residual, recomputed by the FP64 oracle on the ranks' slabs put
   together, meets 1e-10, in the oracle's iteration count (within max(3, 1%));
 * NCCL as the communicator, with one rank (NCCL sends to itself), gives the
-  same Dslash and solution as the mailbox.
+  same Dslash and solution as the mailbox: its device allreduce drives the
+  CG with one host wait per eight iterations, the mailbox's host allreduce
+  with one per sum, and the device-side scalar recurrence is the same.
 """
 import threading
 
@@ -25,6 +28,7 @@ from paper_1411_2087_gb300 import stag, synth
 pytestmark = pytest.mark.gpu
 
 DIMS, MASS = (6, 4, 4, 12), 0.1
+DIMS16 = (4, 4, 6, 16)  # slabs of 8 and 16 slices: the interior stencil overlaps the exchange
 
 
 class Mailbox:
@@ -56,14 +60,18 @@ class Mailbox:
         return stag.HostComm(rank, self.size, exchange, allreduce)
 
 
-@pytest.fixture(scope="module")
-def problem():
-    U = synth.su3_field(DIMS, 0.3, 1000).numpy()
-    N = oracle.long_links(DIMS, U)
-    Vh = int(np.prod(DIMS)) // 2
+def make_problem(dims):
+    U = synth.su3_field(dims, 0.3, 1000).numpy()
+    N = oracle.long_links(dims, U)
+    Vh = int(np.prod(dims)) // 2
     b = synth.gaussian_colour_field(Vh, 1100).numpy()
     psi_o = synth.gaussian_colour_field(Vh, 1101).numpy()
     return U, N, b, psi_o
+
+
+@pytest.fixture(scope="module")
+def problem():
+    return make_problem(DIMS)
 
 
 def run_ranks(size, fn):
@@ -88,9 +96,9 @@ def run_ranks(size, fn):
     return out
 
 
-def rank_job(U, N, b, psi_o, prec):
+def rank_job(U, N, b, psi_o, prec, dims=DIMS):
     def job(rank, comm):
-        with stag.Lattice(DIMS) as lat:
+        with stag.Lattice(dims) as lat:
             lat.upload_gauge(U, N, precisions=(prec,))
             d = stag.DDRank(lat, comm)
             fo = lat.field(stag.ODD, prec, psi_o)
@@ -108,18 +116,18 @@ def rank_job(U, N, b, psi_o, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "df64"])
-@pytest.mark.parametrize("size", [1, 2, 3])
-def test_ranks_dslash_and_cg(problem, size, prec):
-    U, N, b, psi_o = problem
+@pytest.mark.parametrize("dims,size", [(DIMS, 1), (DIMS, 2), (DIMS, 3), (DIMS16, 2)])
+def test_ranks_dslash_and_cg(dims, size, prec):
+    U, N, b, psi_o = make_problem(dims)
     Vh = len(b)
-    per = DIMS[0] * DIMS[1] * DIMS[2] // 2
-    with stag.Lattice(DIMS) as lat:
+    per = dims[0] * dims[1] * dims[2] // 2
+    with stag.Lattice(dims) as lat:
         lat.upload_gauge(U, N, precisions=(prec,))
         fo = lat.field(stag.ODD, prec, psi_o)
         fe = lat.field(stag.EVEN, prec)
         lat.dslash(fe, fo)
         want_d = fe.export()
-    res = run_ranks(size, rank_job(U, N, b, psi_o, prec))
+    res = run_ranks(size, rank_job(U, N, b, psi_o, prec, dims))
     x = np.zeros_like(b)
     covered = np.zeros(Vh, bool)
     for t0, nt, de, xr, info in res:
@@ -132,10 +140,10 @@ def test_ranks_dslash_and_cg(problem, size, prec):
     # every rank took the same decisions
     assert len({r[4]["iters"] for r in res}) == 1
     assert len({r[4]["true_rel_resid"] for r in res}) == 1
-    rel = np.linalg.norm(b - oracle.apply_M(DIMS, U, N, MASS, x)) / np.linalg.norm(b)
+    rel = np.linalg.norm(b - oracle.apply_M(dims, U, N, MASS, x)) / np.linalg.norm(b)
     assert rel <= 1.05e-10, rel
     assert abs(rel - res[0][4]["true_rel_resid"]) <= 1e-3 * rel
-    _, info_o = oracle.cg(DIMS, U, N, MASS, b, tol=1e-10)
+    _, info_o = oracle.cg(dims, U, N, MASS, b, tol=1e-10)
     it = res[0][4]["iters"]
     assert abs(it - info_o["iters"]) <= max(3, 0.01 * info_o["iters"]), (it, info_o["iters"])
 
@@ -156,6 +164,44 @@ def test_nccl_single_rank_matches_mailbox(problem):
     assert np.array_equal(de, dem)
     assert info["return"] == stag.OK and info["iters"] == infom["iters"]
     assert np.array_equal(x, xm)
+
+
+@pytest.mark.parametrize("max_iter", [0, 5, 13])
+def test_nccl_max_iter_stops_exactly(problem, max_iter):
+    """The device-driven CG enqueues chunks of eight iterations; max_iter cuts
+    it off at the same iteration count as the host-driven path."""
+    U, N, b, psi_o = problem
+    try:
+        uid = stag.nccl_unique_id()
+    except stag.StagError as e:
+        pytest.skip(f"libstag built without NCCL: {e}")
+    comm = stag.NcclComm(0, 1, uid, 0)
+    try:
+        with stag.Lattice(DIMS) as lat:
+            lat.upload_gauge(U, N, precisions=("df64",))
+            d = stag.DDRank(lat, comm)
+            fb = lat.field(stag.EVEN, "df64", b)
+            fx = lat.field(stag.EVEN, "df64")
+            info = d.cg(fx, fb, MASS, 1e-10, max_iter)
+            x = fx.export()
+            d.close()
+    finally:
+        comm.close()
+    assert info["return"] == stag.ERR_NOT_CONVERGED and info["iters"] == max_iter, info
+    hm = run_ranks(1, lambda rank, c: _short_cg(U, N, b, max_iter, c))[0]
+    assert hm[1]["iters"] == max_iter and np.array_equal(x, hm[0])
+
+
+def _short_cg(U, N, b, max_iter, comm):
+    with stag.Lattice(DIMS) as lat:
+        lat.upload_gauge(U, N, precisions=("df64",))
+        d = stag.DDRank(lat, comm)
+        fb = lat.field(stag.EVEN, "df64", b)
+        fx = lat.field(stag.EVEN, "df64")
+        info = d.cg(fx, fb, MASS, 1e-10, max_iter)
+        x = fx.export()
+        d.close()
+    return x, info
 
 
 def test_ranks_refuse_bad_layouts(problem):
