@@ -44,6 +44,7 @@ struct DslashArgs {
     float link_scale[2];    // 16-bit links: value = q * scale (one-link, three-link)
     int compressed;         // links in the 12-real layout (FP32, 16-bit)
     int c0, cn;             // output sites c0 .. c0+cn-1 (cn = 0: all Vh)
+    int c0b, cnb;           // with cn > 0: also sites c0b .. c0b+cnb-1 (cnb = 0: none)
     float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
     int bc_neg[4];          // boundary sign of direction mu is -1
     int regs;               // EPI_NONE, EPI_M_PART: REGS_* (autotuned)
@@ -276,9 +277,13 @@ STAG_D void dslash_body(const DslashArgs &a) {
         return;
     if (a.gate && *a.gate == 0)
         return;
-    const int c = a.c0 + blockIdx.x * BLOCK + threadIdx.x;
+    // site i of the launch: the range c0.., then the second range c0b..
+    const int i = blockIdx.x * BLOCK + threadIdx.x;
+    const int n1 = a.cn ? a.cn : a.g.Vh;
+    const int n2 = a.cn ? a.cnb : 0;
+    const int c = i < n1 ? a.c0 + i : a.c0b + (i - n1);
     red_t<R> dot = red_zero<red_t<R>>();
-    if (c < a.c0 + (a.cn ? a.cn : a.g.Vh)) {
+    if (i < n1 + n2) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
         dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
         dot = dslash_epilogue<P, EPI>(a, c, acc);
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(Dsla
 STAG_HD bool pair16_used(int prec, int epi, const DslashArgs &a) {
     return prec == P_F16 && a.compressed && a.regs == REGS_PAIR &&
            (epi == EPI_NONE || epi == EPI_M_PART) &&
-           a.c0 == 0 && (a.cn == 0 || a.cn == a.g.Vh) && pair16_applies(a.g);
+           a.c0 == 0 && (a.cn == 0 || a.cn == a.g.Vh) && a.cnb == 0 && pair16_applies(a.g);
 }
 STAG_HD int dslash_pair16_grid(const Geom &g, int block) { return ((g.Vh >> 1) + block - 1) / block; }
 

@@ -49,7 +49,7 @@ static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
             return cudaGetLastError();
         }
     }
-    const int n = a.cn ? a.cn : a.g.Vh;
+    const int n = (a.cn ? a.cn : a.g.Vh) + (a.cn ? a.cnb : 0);
     const int grid = (n + BLOCK - 1) / BLOCK;
     if (grid == 0)
         return cudaSuccess;

@@ -342,17 +342,20 @@ static int exchange_halo(stag_ddr d, int prec, void *field, cudaStream_t s) {
     return STAG_OK;
 }
 
-// the stencil on slices [t, t + n) of the slab (halo of `in` filled where
-// they need it); EPI_M_PART writes its block partials from d->partial + *np
-// on and advances *np
+// the stencil on slices [t, t + n) (and [t2, t2 + n2) in the same launch)
+// of the slab, with the halo of `in` filled where they need it; EPI_M_PART
+// writes its block partials from d->partial + *np on and advances *np
 static int slab_range(stag_ddr d, int prec, int out_par, int epi, const void *in, void *out, const void *p,
-                      const void *b, double m2, int t, int n, int *np) {
+                      const void *b, double m2, int t, int n, int t2, int n2, int *np) {
     stag_lattice lat = d->lat;
     if (n <= 0)
         return STAG_OK;
+    const int P = lat->geom.plane[3];
     DslashArgs a = dslash_args(lat, prec, out_par, in, out);
-    a.c0 = t * lat->geom.plane[3];
-    a.cn = n * lat->geom.plane[3];
+    a.c0 = t * P;
+    a.cn = n * P;
+    a.c0b = t2 * P;
+    a.cnb = n2 > 0 ? n2 * P : 0;
     a.p = p;
     a.b = b;
     a.sc = d->sc;
@@ -360,17 +363,23 @@ static int slab_range(stag_ddr d, int prec, int out_par, int epi, const void *in
     a.partial = d->partial + (np ? *np : 0);
     a.m2 = make_dpair(m2);
     a.m2_in_args = 1;
-    const int block = lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
+    int block = lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
+    if (epi != EPI_NONE) {  // the M Dslash's own tuning, as in the single-lattice solvers
+        block = m_block(lat, prec);
+        a.regs = lat->mdslash_block[prec] > 0 ? lat->mdslash_regs[prec] : lat->dslash_regs[prec];
+    }
     CUDA_TRY(launch_dslash(prec, epi, a, block, lat->stream));
     if (np)
-        *np += (a.cn + block - 1) / block;
+        *np += (a.cn + a.cnb + block - 1) / block;
     return STAG_OK;
 }
 
-// exchange the halo of `in`, then the stencil on the whole slab: the
-// interior (slices more than kHaloSlices from a face) runs while the
-// exchange is in flight on the side stream, the two boundary ranges after
-// it (EPI_NONE or EPI_M_PART; *np receives the number of block partials)
+// exchange the halo of `in`, then the stencil on the whole slab (EPI_NONE
+// or EPI_M_PART; *np receives the number of block partials).  The interior
+// (slices more than kHaloSlices from a face) runs while the exchange is in
+// flight on the side stream, the two boundary ranges in one launch after it.
+// One rank owns the whole lattice: its halo is its own slices, so there is
+// nothing to exchange.
 static int slab_dslash(stag_ddr d, int prec, int out_par, int epi, const void *in, void *out, const void *p,
                        double m2, int *np) {
     stag_lattice lat = d->lat;
@@ -378,18 +387,19 @@ static int slab_dslash(stag_ddr d, int prec, int out_par, int epi, const void *i
     const int t0 = d->slab.t0, nt = d->slab.nt, h = kHaloSlices;
     if (np)
         *np = 0;
+    if (d->comm.size == 1)
+        return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, nt, 0, 0, np);
     if (nt <= 2 * h) {
         STAG_TRY(exchange_halo(d, prec, (void *)in, s));
-        return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, nt, np);
+        return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, nt, 0, 0, np);
     }
     CUDA_TRY(cudaEventRecord(d->ev_in, s));
     CUDA_TRY(cudaStreamWaitEvent(d->side, d->ev_in, 0));
-    STAG_TRY(slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0 + h, nt - 2 * h, np));
+    STAG_TRY(slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0 + h, nt - 2 * h, 0, 0, np));
     STAG_TRY(exchange_halo(d, prec, (void *)in, d->side));
     CUDA_TRY(cudaEventRecord(d->ev_halo, d->side));
     CUDA_TRY(cudaStreamWaitEvent(s, d->ev_halo, 0));
-    STAG_TRY(slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, h, np));
-    return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0 + nt - h, h, np);
+    return slab_range(d, prec, out_par, epi, in, out, p, nullptr, m2, t0, h, t0 + nt - h, h, np);
 }
 
 // sum one device double over the ranks, in place, in order on the lattice
@@ -552,9 +562,10 @@ extern "C" int stag_ddr_cg_solve(stag_ddr d, stag_field x, const stag_field b, d
     CUDA_TRY(cudaMemcpyAsync(x->data, w.xw, x->bytes, cudaMemcpyDeviceToDevice, s));
     STAG_TRY(put_scalars(d, 0.0, 0.0, 0.0));
     STAG_TRY(slab_dslash(d, prec, STAG_ODD, EPI_NONE, x->data, w.t, nullptr, m2, nullptr));
-    STAG_TRY(exchange_halo(d, prec, w.t, s));
+    if (d->comm.size > 1)
+        STAG_TRY(exchange_halo(d, prec, w.t, s));
     STAG_TRY(slab_range(d, prec, STAG_EVEN, EPI_RESID, w.t, nullptr, x->data, b->data, m2, d->slab.t0,
-                        d->slab.nt, nullptr));
+                        d->slab.nt, 0, 0, nullptr));
     double rr_true = 0.0;
     STAG_TRY(global_sum(d, offsetof(CgScalars, true_rr), &rr_true));
     stag_solve_info local;

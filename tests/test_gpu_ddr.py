@@ -12,11 +12,13 @@ allreduce.  Checks:
 * the CG over 1, 2 and 3 ranks (F64 and double float) gives a solution whose
   true residual, recomputed by the FP64 oracle on the ranks' slabs put
   together, meets 1e-10, in the oracle's iteration count (within max(3, 1%));
-* NCCL as the communicator, with one rank (NCCL sends to itself), gives the
-  same Dslash and solution as the mailbox: its device allreduce drives the
-  CG with one host wait per eight iterations, the mailbox's host allreduce
-  with one per sum, and the device-side scalar recurrence is the same.
+* NCCL as the communicator, with one rank, gives the same Dslash and solution
+  as the mailbox: its device allreduce drives the CG with one host wait per
+  eight iterations, the mailbox's host allreduce with one per sum, and the
+  device-side scalar recurrence is the same; its exchange (a rank sending to
+  itself) and allreduces are checked on device buffers directly.
 """
+import ctypes
 import threading
 
 import numpy as np
@@ -164,6 +166,42 @@ def test_nccl_single_rank_matches_mailbox(problem):
     assert np.array_equal(de, dem)
     assert info["return"] == stag.OK and info["iters"] == infom["iters"]
     assert np.array_equal(x, xm)
+
+
+def test_nccl_callbacks_single_rank():
+    """The NCCL communicator's callbacks on device buffers, one rank (a rank
+    that owns the whole lattice exchanges nothing, so the solver tests do not
+    reach them): the exchange delivers what the rank sent to its next
+    neighbour into from_prev and what it sent to its previous one into
+    from_next; both allreduces return the values unchanged."""
+    import torch
+    try:
+        uid = stag.nccl_unique_id()
+    except stag.StagError as e:
+        pytest.skip(f"libstag built without NCCL: {e}")
+    comm = stag.NcclComm(0, 1, uid, 0)
+    try:
+        c = comm.struct
+        n = 3 * 4096
+        to_prev = torch.arange(n, dtype=torch.uint8, device="cuda")
+        to_next = torch.flip(to_prev, [0]).contiguous()
+        from_prev = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        from_next = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        rc = c.exchange(c.ctx, to_prev.data_ptr(), to_next.data_ptr(), from_prev.data_ptr(), from_next.data_ptr(),
+                        n, stream)
+        torch.cuda.synchronize()
+        assert rc == 0
+        assert torch.equal(from_prev, to_next) and torch.equal(from_next, to_prev)
+        vals = torch.tensor([1.5, -2.25, 3e-300], dtype=torch.float64, device="cuda")
+        want = vals.clone()
+        assert c.allreduce_dev(c.ctx, vals.data_ptr(), 3, stream) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(vals, want)
+        host = (ctypes.c_double * 2)(0.5, 7.0)
+        assert c.allreduce(c.ctx, host, 2) == 0 and list(host) == [0.5, 7.0]
+    finally:
+        comm.close()
 
 
 @pytest.mark.parametrize("max_iter", [0, 5, 13])
