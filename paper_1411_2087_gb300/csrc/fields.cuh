@@ -65,6 +65,14 @@ constexpr float kQ16 = 32767.f;
 
 STAG_D short q16(float v) { return (short)__float2int_rn(fminf(fmaxf(v, -kQ16), kQ16)); }
 
+// the two int16 halves of a 32-bit word (a short2: x low, y high) as floats
+// (exact), and the word from two stored values
+STAG_D float q_lo(int w) { return (float)(short)(w & 0xffff); }
+STAG_D float q_hi(int w) { return (float)(w >> 16); }
+STAG_D int q16_pair(float re, float im) {
+    return (int)((unsigned)(unsigned short)q16(re) | ((unsigned)(unsigned short)q16(im) << 16));
+}
+
 template <> struct Fmt<P_F16> {
     using Elem = short2;
     using R = float;
@@ -200,8 +208,7 @@ STAG_D void store_vec<P_F16>(short2 *__restrict__ v, int stride, int c, const cp
     int q[3];
 #pragma unroll
     for (int a = 0; a < 3; a++)
-        q[a] = (int)((unsigned)(unsigned short)q16(w[a].re * inv) |
-                     ((unsigned)(unsigned short)q16(w[a].im * inv) << 16));
+        q[a] = q16_pair(w[a].re * inv, w[a].im * inv);
     __stcs((int4 *)v + c, make_int4(q[0], q[1], q[2], __float_as_int(m)));
 }
 

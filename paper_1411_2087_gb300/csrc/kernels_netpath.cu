@@ -30,19 +30,52 @@
 namespace stag {
 
 // ---- links -----------------------------------------------------------------
-// Net links per parity in structure-of-arrays form: element e (row*3+col) of
-// U_mu at checkerboard site c of parity par at ((par*4 + mu)*9 + e)*S + c,
-// the boundary sign of a wrapping forward hop folded into the last-slice link.
-// FP32 (float2) or 16-bit (short2, value = q * scale).
+// Net links per parity, the boundary sign of a wrapping forward hop folded
+// into the last-slice link.  FP32 (float2): structure of arrays, element e
+// (row*3+col) of U_mu at checkerboard site c of parity par at
+// ((par*4 + mu)*9 + e)*S + c.  16-bit (short2, value = q * scale): per
+// (par, mu) 36 S bytes, an int4 plane with e0..e3, an int4 plane with
+// e4..e7 and an int plane with e8, so that a link is three loads.
 STAG_D cplx<float> nl_get(float2 v) { return cplx<float>{v.x, v.y}; }
-STAG_D cplx<float> nl_get(short2 v) { return cplx<float>{(float)v.x, (float)v.y}; }
 
 template <class LT>
-STAG_D void nl_load(const LT *__restrict__ NL, int S, int par, int mu, int c, cplx<float> U[9]) {
-    const LT *p = NL + (size_t)((par * 4 + mu) * 9) * S + c;
+STAG_D void nl_load(const LT *__restrict__ NL, int S, int par, int mu, int c, cplx<float> U[9]);
+
+template <>
+STAG_D void nl_load<float2>(const float2 *__restrict__ NL, int S, int par, int mu, int c, cplx<float> U[9]) {
+    const float2 *p = NL + (size_t)((par * 4 + mu) * 9) * S + c;
 #pragma unroll
     for (int e = 0; e < 9; e++)
         U[e] = nl_get(ld_stream(p + (size_t)e * S));
+}
+
+STAG_D const char *nl16_base(const void *NL, int S, int par, int mu) {
+    return (const char *)NL + (size_t)(par * 4 + mu) * 36 * S;
+}
+
+template <>
+STAG_D void nl_load<short2>(const short2 *__restrict__ NL, int S, int par, int mu, int c, cplx<float> U[9]) {
+    const char *base = nl16_base(NL, S, par, mu);
+    const int4 a = ld_stream((const int4 *)base + c);
+    const int4 b = ld_stream((const int4 *)(base + (size_t)16 * S) + c);
+    const int e8 = ld_stream((const int *)(base + (size_t)32 * S) + c);
+    const int w[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, e8};
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        U[e] = cplx<float>{q_lo(w[e]), q_hi(w[e])};
+}
+
+// the address of element e of U_mu at (par, c) in either layout
+STAG_D float2 *nl_slot(float2 *NL, int S, int par, int mu, int c, int e) {
+    return NL + (size_t)((par * 4 + mu) * 9 + e) * S + c;
+}
+STAG_D short2 *nl_slot(short2 *NL, int S, int par, int mu, int c, int e) {
+    char *base = (char *)nl16_base(NL, S, par, mu);
+    if (e < 4)
+        return (short2 *)base + (size_t)c * 4 + e;
+    if (e < 8)
+        return (short2 *)(base + (size_t)16 * S) + (size_t)c * 4 + (e - 4);
+    return (short2 *)(base + (size_t)32 * S) + c;
 }
 
 // h = U v (adj = false) or U^+ v
@@ -89,11 +122,10 @@ __global__ void net_links_cb_kernel(Geom g, double bc0, double bc1, double bc2, 
     const double bc[4] = {bc0, bc1, bc2, bc3};
     const double sgn = (x[mu] == g.L[mu] - 1 && bc[mu] < 0) ? -1.0 : 1.0;
     const int S = g.stride;
-    LT *dst = NL + (size_t)((par * 4 + mu) * 9) * S + (i >> 1);
 #pragma unroll 1
     for (int e = 0; e < 9; e++) {
         const double2 u = fat[((size_t)mu * V + i) * 9 + e];
-        dst[(size_t)e * S] = nl_pack<LT>(sgn * u.x, sgn * u.y, inv_scale);
+        *nl_slot(NL, S, par, mu, i >> 1, e) = nl_pack<LT>(sgn * u.x, sgn * u.y, inv_scale);
     }
 }
 
@@ -257,9 +289,9 @@ constexpr int NET_BLOCK = 128;
 template <class R> STAG_D cplx<float> to_f(const cplx<R> &v) { return cconv<float, R>(v); }
 
 // The odd-site intermediate chi: FP32 (float2 [8][3][S]) with FP32 links,
-// and 16-bit with 16-bit links: short2 [8][3][S] followed by one float norm
-// per site and channel, float [8][S] (value = q * norm / 32767; the norm is
-// the channel's largest |component| at that site).
+// and 16-bit with 16-bit links: one 16-byte cell per channel and site,
+// int4 [8][S], the three components as int16 pairs and the norm (value =
+// q * norm / 32767; the norm is the channel's largest |component| there).
 template <class LT> struct Chi;
 template <> struct Chi<float2> {
     STAG_D static void store(void *chi, int S, int a, int c, const cplx<float> v[3]) {
@@ -281,25 +313,21 @@ template <> struct Chi<float2> {
 };
 template <> struct Chi<short2> {
     STAG_D static void store(void *chi, int S, int a, int c, const cplx<float> v[3]) {
-        short2 *p = (short2 *)chi;
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; k++)
             m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
         const float inv = m > 0.f ? kQ16 / m : 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; k++)
-            __stcs(p + (size_t)(a * 3 + k) * S + c, make_short2(q16(v[k].re * inv), q16(v[k].im * inv)));
-        __stcs((float *)(p + (size_t)24 * S) + (size_t)a * S + c, m);
+        __stcs((int4 *)chi + (size_t)a * S + c,
+               make_int4(q16_pair(v[0].re * inv, v[0].im * inv), q16_pair(v[1].re * inv, v[1].im * inv),
+                         q16_pair(v[2].re * inv, v[2].im * inv), __float_as_int(m)));
     }
     STAG_D static float load(const void *chi, int S, int a, int j, cplx<float> v[3]) {
-        const short2 *p = (const short2 *)chi;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const short2 t = __ldcs(p + (size_t)(a * 3 + k) * S + j);
-            v[k] = cplx<float>{(float)t.x, (float)t.y};
-        }
-        return __ldcs((const float *)(p + (size_t)24 * S) + (size_t)a * S + j) * (1.f / kQ16);
+        const int4 t = __ldcs((const int4 *)chi + (size_t)a * S + j);
+        v[0] = cplx<float>{q_lo(t.x), q_hi(t.x)};
+        v[1] = cplx<float>{q_lo(t.y), q_hi(t.y)};
+        v[2] = cplx<float>{q_lo(t.z), q_hi(t.z)};
+        return __int_as_float(t.w) * (1.f / kQ16);
     }
 };
 

@@ -34,10 +34,6 @@ template <class V> STAG_D V vsplat(float s);
 template <> STAG_D float vsplat<float>(float s) { return s; }
 template <> STAG_D float2 vsplat<float2>(float s) { return make_float2(s, s); }
 
-// integer halves of a 32-bit word as floats (exact)
-STAG_D float q_lo(int w) { return (float)(short)(w & 0xffff); }
-STAG_D float q_hi(int w) { return (float)(w >> 16); }
-
 // X = row0 x row1 of the raw link (L[0..2] row 0, L[3..5] row 1)
 template <class V>
 STAG_D void cross01(const cplx<V> L[6], cplx<V> X[3]) {
