@@ -23,6 +23,8 @@
 // gradient with respect to C[a][b] is <T_b r, T_a^+ g> summed over the odd
 // sites (g = dL/dz*), and the chain rule through the products above gives
 // the gradient of every layer weight.
+#include <type_traits>
+
 #include "kernels.h"
 #include "learned.cuh"
 #include "reduce.cuh"
@@ -380,25 +382,69 @@ net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
                 sh[2 * mu + bw][k][threadIdx.x] = make_float2(h[k].re, h[k].im);
         }
     }
-    cplx<float> h[8][3];
+    if constexpr (!std::is_same<LT, short2>::value) {
+        // FP32 links (training): the scalar mixing, channel by channel
+        cplx<float> h[8][3];
 #pragma unroll
-    for (int b = 0; b < 8; b++)
+        for (int b = 0; b < 8; b++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            const float2 t = sh[b][k][threadIdx.x];
-            h[b][k] = cplx<float>{t.x, t.y};
+            for (int k = 0; k < 3; k++) {
+                const float2 t = sh[b][k][threadIdx.x];
+                h[b][k] = cplx<float>{t.x, t.y};
+            }
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            cplx<float> acc[3] = {czero<float>(), czero<float>(), czero<float>()};
+#pragma unroll
+            for (int b = 0; b < 8; b++) {
+                const cplx<float> w = sC[a * 8 + b];
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    cmac(acc[k], w, h[b][k]);
+            }
+            Chi<LT>::store(chi, S, a, c, acc);
         }
+        return;
+    }
+    // 16-bit links (the solver's form): the mixing, four output channels at
+    // a time and b outermost:
+    // acc[a][k] = sum_b C[a][b] h_b[k] with each accumulator's (re, im) in
+    // one packed FP32x2 register pair, so that a complex multiply-add is two
+    // packed FMAs, w.re (h.re, h.im) and w.im (-h.im, h.re), in the order of
+    // a scalar complex multiply-add
 #pragma unroll
-    for (int a = 0; a < 8; a++) {
-        cplx<float> acc[3] = {czero<float>(), czero<float>(), czero<float>()};
+    for (int a0 = 0; a0 < 8; a0 += 4) {
+        float2 acc[4][3];
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
-            const cplx<float> w = sC[a * 8 + b];
+        for (int a = 0; a < 4; a++)
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                cmac(acc[k], w, h[b][k]);
+                acc[a][k] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            float2 hb[3], hs[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                hb[k] = sh[b][k][threadIdx.x];
+                hs[k] = make_float2(-hb[k].y, hb[k].x);
+            }
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+                const cplx<float> w = sC[(a0 + a) * 8 + b];
+                const float2 wr = make_float2(w.re, w.re), wi = make_float2(w.im, w.im);
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    acc[a][k] = __ffma2_rn(wr, hb[k], acc[a][k]);
+                    acc[a][k] = __ffma2_rn(wi, hs[k], acc[a][k]);
+                }
+            }
         }
-        Chi<LT>::store(chi, S, a, c, acc);
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const cplx<float> v[3] = {cplx<float>{acc[a][0].x, acc[a][0].y}, cplx<float>{acc[a][1].x, acc[a][1].y},
+                                      cplx<float>{acc[a][2].x, acc[a][2].y}};
+            Chi<LT>::store(chi, S, a0 + a, c, v);
+        }
     }
 }
 
