@@ -317,8 +317,14 @@ static inline int m_block(const stag_lattice lat, int prec) {
     return lat->dslash_block[prec] > 0 ? lat->dslash_block[prec] : dslash_default_block(prec);
 }
 
-// Ap = m^2 p - D_eo t with <p, Ap> summed by pap_finish: alpha and the
-// breakdown test in sc (skip_if_done: both return at once after the solve)
+// lattices up to this many sites per parity sum <p, Ap> in the M Dslash's
+// last block (one launch less per iteration, which is what counts when the
+// launches are short); larger ones write block partials and sum them in a
+// one-block kernel, which lets the Dslash blocks retire without a ticket
+constexpr int kSmallVh = 65536;
+
+// Ap = m^2 p - D_eo t with <p, Ap>, alpha and the breakdown test in sc
+// (skip_if_done: everything returns at once after the solve)
 static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *t, void *Ap, const void *p,
                                         bool skip_if_done, cudaStream_t s, const int *gate = nullptr) {
     DslashArgs a = dslash_args(lat, prec, STAG_EVEN, t, Ap);
@@ -327,6 +333,8 @@ static inline cudaError_t enqueue_m_pap(stag_lattice lat, int prec, const void *
     a.gate = gate;
     a.regs = lat->mdslash_block[prec] > 0 ? lat->mdslash_regs[prec] : lat->dslash_regs[prec];
     const int block = m_block(lat, prec);
+    if (lat->geom.Vh <= kSmallVh)
+        return launch_dslash(prec, EPI_M_PAP, a, block, s);
     cudaError_t e = launch_dslash(prec, EPI_M_PART, a, block, s);
     if (e != cudaSuccess)
         return e;
