@@ -88,6 +88,7 @@ enum {
 enum { STAG_F64 = 0, STAG_F32 = 1, STAG_F16 = 2, STAG_DF64 = 3 };
 #define STAG_PREC_BIT(p) (1u << (p))
 #define STAG_COMPRESS12 (1u << 16)
+#define STAG_COMPRESS12_LONG (1u << 17)
 
 enum { STAG_EVEN = 0, STAG_ODD = 1 };
 enum { STAG_PTR_HOST = 0, STAG_PTR_DEVICE = 1 };
@@ -143,7 +144,10 @@ int stag_lattice_set_cg_launch(stag_lattice lat, int mode, int chunk);
  *            loads.  Only valid for special unitary links (checked: a link
  *            deviating from SU(3) by more than 1e-6 gives STAG_ERR_ARG, e.g.
  *            smeared fat links, which the paper notes are not in SU(3));
- *            the full copies are kept for the batched solver.
+ *            the full copies are kept for the batched solver.  With
+ *            STAG_COMPRESS12_LONG instead only the three-link field is
+ *            compressed and checked (the paper's suggestion for smeared fat
+ *            links, Sec. 4): 5/6 of the link bytes.
  *            A later upload replaces all copies.
  * Links holding a NaN, an infinity or an entry beyond the FP32 range give
  * STAG_ERR_ARG (the lattice then has no gauge field).

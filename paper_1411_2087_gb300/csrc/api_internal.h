@@ -120,7 +120,8 @@ struct stag_lattice_s {
     long long V = 0, Vh = 0;
     Geom geom;
     void *links[4] = {nullptr, nullptr, nullptr, nullptr};  // per precision [2][8][9][stride]
-    void *links_c12[4] = {nullptr, nullptr, nullptr, nullptr};  // 12-real copies (FP32, 16-bit)
+    void *links_c12[4] = {nullptr, nullptr, nullptr, nullptr};  // copies with 12-real kinds (FP32, 16-bit)
+    int c12_mask[4] = {0, 0, 0, 0};  // their compression masks (link_kind_offset): 3 all, 2 three-link only
     bool has_gauge = false;
     double c1 = 0, c3 = 0;
     int live_fields = 0;
@@ -242,11 +243,11 @@ static inline DslashArgs dslash_args(stag_lattice lat, int prec, int out_par, co
         a.link_scale[1] = lat->link_scale[1];
     }
     if (lat->links_c12[prec]) {
-        // the 12-real copy replaces the full one for this precision
-        const size_t half = c12_link_bytes(prec, (size_t)lat->geom.stride) / 2;
+        // the copy with 12-real kinds replaces the full one for this precision
+        const size_t half = link_parity_bytes(prec, lat->c12_mask[prec], (size_t)lat->geom.stride);
         a.links_out = (const char *)lat->links_c12[prec] + (size_t)out_par * half;
         a.links_in = (const char *)lat->links_c12[prec] + (size_t)(1 - out_par) * half;
-        a.compressed = 1;
+        a.compressed = lat->c12_mask[prec];
         a.inv_c[0] = (float)(1.0 / lat->c1);
         a.inv_c[1] = (float)(1.0 / lat->c3);
         for (int k = 0; k < 4; k++)

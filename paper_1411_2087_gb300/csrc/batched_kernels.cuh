@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(BLOCK) batch_dslash_lanes_kernel(BatchArgs a, 
         da.link_scale[0] = G.link_scale[0];
         da.link_scale[1] = G.link_scale[1];
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
-        dslash_site<P, false>(g, out_par, c, G.links[out_par], G.links[1 - out_par],
+        dslash_site<P, 0>(g, out_par, c, G.links[out_par], G.links[1 - out_par],
                               (const E *)batch_lane_input<EPI>(G, k, src_x), da, acc);
         const red_t<R> dk = batch_lane_epilogue<P, EPI>(a, G, k, c, acc);
 #pragma unroll

@@ -46,42 +46,62 @@ struct Domains {
     }
 };
 
-// the active link layout of the domain precision: bytes of one parity
+// the active link layout of the domain precision: its compression mask and
+// the bytes of one parity
+int link_mask(const Domains &D) { return D.lat->links_c12[D.prec] ? D.lat->c12_mask[D.prec] : 0; }
 size_t link_half_bytes(const Domains &D) {
-    stag_lattice lat = D.lat;
-    if (lat->links_c12[D.prec])
-        return c12_link_bytes(D.prec, (size_t)lat->geom.stride) / 2;
-    return link_bytes(lat, D.prec) / 2;
+    return link_parity_bytes(D.prec, link_mask(D), (size_t)D.lat->geom.stride);
 }
 const void *link_base(const Domains &D) {
     return D.lat->links_c12[D.prec] ? D.lat->links_c12[D.prec] : D.lat->links[D.prec];
 }
 
+// the planes of one kind's layout (link_kind_bytes): offset within the
+// kind, bytes per site, bytes between consecutive planes of the same shape,
+// and how many such planes
+struct Planes {
+    size_t base, elem, pitch, count;
+};
+int kind_planes(int prec, bool c12, size_t S, Planes pl[3]) {
+    if (c12) {
+        if (prec == STAG_F32) {
+            pl[0] = {0, 16, 16 * S, 3};  // float4 [3][S]
+            return 1;
+        }
+        pl[0] = {0, 16, 16 * S, 1};      // int4 [S]
+        pl[1] = {16 * S, 8, 8 * S, 1};   // int2 [S]
+        return 2;
+    }
+    if (prec == STAG_F16) {
+        pl[0] = {0, 16, 16 * S, 2};      // int4 [2][S]
+        pl[1] = {32 * S, 4, 4 * S, 1};   // int [S]
+        return 2;
+    }
+    const size_t eb = prec_link_elem_bytes(prec);
+    pl[0] = {0, eb, eb * S, 9};          // Elem [9][S]
+    return 1;
+}
+
 // copy the links of slices [t, t + n) (one contiguous range) of both
-// parities: every component plane of the layout, one 2-D copy per plane kind
+// parities: every plane of every kind, one 2-D copy per group of planes
 int copy_link_range(const Domains &D, void *dst, int t, int n) {
     stag_lattice lat = D.lat;
     const size_t S = (size_t)lat->geom.stride;
     const size_t per = (size_t)lat->geom.plane[3];
     const size_t half = link_half_bytes(D);
+    const int mask = link_mask(D);
     const char *src = (const char *)link_base(D);
-    struct Planes { size_t base, pitch, elem, count; };
-    Planes pl[2];
-    int np = 0;
-    if (!lat->links_c12[D.prec]) {
-        pl[np++] = {0, S * prec_link_elem_bytes(D.prec), prec_link_elem_bytes(D.prec), 72};
-    } else if (D.prec == STAG_F32) {
-        pl[np++] = {0, S * 16, 16, 24};          // float4 [8 kinds][3][S]
-    } else {
-        pl[np++] = {0, S * 24, 16, 8};           // int4 [S] of each kind
-        pl[np++] = {S * 16, S * 24, 8, 8};       // int2 [S] of each kind
-    }
     for (int par = 0; par < 2; par++)
-        for (int q = 0; q < np; q++) {
-            const size_t off = par * half + pl[q].base + (size_t)t * per * pl[q].elem;
-            CUDA_TRY(cudaMemcpy2DAsync((char *)dst + off, pl[q].pitch, src + off, pl[q].pitch,
-                                       (size_t)n * per * pl[q].elem, pl[q].count, cudaMemcpyDeviceToDevice,
-                                       lat->stream));
+        for (int kind = 0; kind < 8; kind++) {
+            Planes pl[3];
+            const int np = kind_planes(D.prec, (mask >> (kind >> 2)) & 1, S, pl);
+            for (int q = 0; q < np; q++) {
+                const size_t off = par * half + link_kind_offset(D.prec, mask, kind, S) + pl[q].base +
+                                   (size_t)t * per * pl[q].elem;
+                CUDA_TRY(cudaMemcpy2DAsync((char *)dst + off, pl[q].pitch, src + off, pl[q].pitch,
+                                           (size_t)n * per * pl[q].elem, pl[q].count, cudaMemcpyDeviceToDevice,
+                                           lat->stream));
+            }
         }
     return STAG_OK;
 }

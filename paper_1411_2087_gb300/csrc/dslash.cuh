@@ -29,7 +29,7 @@ enum Epi {
 struct DslashArgs {
     Geom g;
     int out_par;
-    const void *links_out;  // links on sites of the output parity: [8][9][stride]
+    const void *links_out;  // links on sites of the output parity: 8 kinds (link_kind_offset)
     const void *links_in;   // links on sites of the input parity
     const void *in;         // input vector, other parity
     void *out;              // output vector
@@ -42,7 +42,7 @@ struct DslashArgs {
     int skip_if_done;       // return at once when sc->status is no longer CG_RUNNING
     const int *gate;        // if set, return at once unless *gate != 0 (uniform flag)
     float link_scale[2];    // 16-bit links: value = q * scale (one-link, three-link)
-    int compressed;         // links in the 12-real layout (FP32, 16-bit)
+    int compressed;         // compression mask (link_kind_offset): 12-real one-link (bit 0), three-link (bit 1)
     int c0, cn;             // output sites c0 .. c0+cn-1 (cn = 0: all Vh)
     int c0b, cnb;           // with cn > 0: also sites c0b .. c0b+cnb-1 (cnb = 0: none)
     float inv_c[2];         // 1/c1, 1/c3: the reconstruction divides by s = c eta b
@@ -52,8 +52,8 @@ struct DslashArgs {
 
 // register variant of the stencil (DslashArgs::regs): the launcher's
 // measured default, the compiler's free choice, at most 64 registers, or
-// (compressed 16-bit stencil, EPI_NONE and EPI_M_PART) two sites per thread
-// in packed FP32x2 arithmetic with the loads through a shared-memory ring
+// (16-bit stencil, EPI_NONE and EPI_M_PART) two sites per thread in packed
+// FP32x2 arithmetic with the loads through a shared-memory ring
 // (stencil16_pair_async) where pair16_applies, else the default
 enum { REGS_DEFAULT = 0, REGS_FREE = 1, REGS_CAPPED = 2, REGS_PAIR = 3 };
 
@@ -80,22 +80,25 @@ STAG_HD int hop_wraps(int v, int s, int L) {
     return w;
 }
 
-// the nine entries of one link: either stored whole, or rows 0 and 1 of the
-// 12-real layout with row 2 rebuilt (inv_s = 1/(c eta b) of that link)
-template <int P, bool COMP>
+// the nine entries of one link of kind `kind` (compression mask CM): either
+// stored whole, or rows 0 and 1 of the 12-real layout with row 2 rebuilt
+// (inv_s = 1/(c eta b) of that link)
+template <int P, int CM>
 STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float inv_s,
                       cplx<typename Fmt<P>::R> L[9]) {
     using F = Fmt<P>;
-    if constexpr (COMP) {
-        const char *kb = (const char *)G + (size_t)kind * C12<P>::kind_bytes((size_t)S);
-        C12<P>::load(kb, S, idx, ls, L);
-        reconstruct_row2(L, inv_s);
-    } else {
-        const typename F::Elem *Lp = (const typename F::Elem *)G + kind * 9 * S + idx;
-#pragma unroll
-        for (int e = 0; e < 9; e++)
-            L[e] = F::unpack_link(ld_stream(Lp + e * S), ls);
+    const char *kb = (const char *)G + link_kind_offset(P, CM, kind, (size_t)S);
+    if constexpr (CM != 0) {
+        if ((CM >> (kind >> 2)) & 1) {
+            C12<P>::load(kb, S, idx, ls, L);
+            reconstruct_row2(L, inv_s);
+            return;
+        }
     }
+    const typename F::Elem *Lp = (const typename F::Elem *)kb + idx;
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        L[e] = F::unpack_link(ld_stream(Lp + e * S), ls);
 }
 
 }  // namespace stag
@@ -104,17 +107,16 @@ STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float i
 
 namespace stag {
 
-// acc += D psi at checkerboard site c of parity par
-template <int P, bool COMP = false>
+// acc += D psi at checkerboard site c of parity par (links with compression
+// mask CM)
+template <int P, int CM = 0>
 STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ Gout,
                         const void *__restrict__ Gin, const typename Fmt<P>::Elem *__restrict__ in,
                         const DslashArgs &a, cplx<typename Fmt<P>::R> acc[3]) {
     using R = typename Fmt<P>::R;
-    if constexpr (P == P_F16 && COMP) {
-        // raw integer units (stencil16.cuh); the 18-real 16-bit stencil keeps
-        // its scaled form: in raw units the compiler hoists its loads into
-        // 255 registers and it runs no faster
-        stencil16_site(g, par, c, Gout, Gin, in, a, acc);
+    if constexpr (P == P_F16) {
+        // raw integer units (stencil16.cuh)
+        stencil16_site<CM>(g, par, c, Gout, Gin, in, a, acc);
         return;
     }
     const int S = g.stride;
@@ -138,12 +140,12 @@ STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ 
                 cplx<R> v[3];
                 load_vec<P>(in, S, j, v);
                 float inv_s = 0.f;
-                if (COMP) {
+                if ((CM >> h) & 1) {
                     const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
                     inv_s = flip ? -a.inv_c[h] : a.inv_c[h];
                 }
                 cplx<R> L[9];
-                load_link<P, COMP>(Gout, kind, S, c, ls, inv_s, L);
+                load_link<P, CM>(Gout, kind, S, c, ls, inv_s, L);
 #pragma unroll
                 for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -159,12 +161,12 @@ STAG_D void dslash_site(const Geom &g, int par, int c, const void *__restrict__ 
                 for (int b = 0; b < 3; b++)
                     v[b] = cneg(v[b]);
                 float inv_s = 0.f;
-                if (COMP) {
+                if ((CM >> h) & 1) {
                     const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
                     inv_s = flip ? -a.inv_c[h] : a.inv_c[h];
                 }
                 cplx<R> L[9];
-                load_link<P, COMP>(Gin, kind, S, j, ls, inv_s, L);
+                load_link<P, CM>(Gin, kind, S, j, ls, inv_s, L);
 #pragma unroll
                 for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -266,7 +268,7 @@ STAG_D void dslash_reduce(const DslashArgs &a, T dot, double *smem) {
     }
 }
 
-template <int P, int EPI, int BLOCK, bool COMP>
+template <int P, int EPI, int BLOCK, int CM>
 STAG_D void dslash_body(const DslashArgs &a) {
     using F = Fmt<P>;
     using R = typename F::R;
@@ -285,7 +287,7 @@ STAG_D void dslash_body(const DslashArgs &a) {
     red_t<R> dot = red_zero<red_t<R>>();
     if (i < n1 + n2) {
         cplx<R> acc[3] = {czero<R>(), czero<R>(), czero<R>()};
-        dslash_site<P, COMP>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
+        dslash_site<P, CM>(a.g, a.out_par, c, a.links_out, a.links_in, (const E *)a.in, a, acc);
         dot = dslash_epilogue<P, EPI>(a, c, acc);
     }
     dslash_reduce<EPI, BLOCK>(a, dot, smem);
@@ -294,10 +296,10 @@ STAG_D void dslash_body(const DslashArgs &a) {
 // The compressed 16-bit stencil on the pair (c, c + Vh/2) per thread
 // (stencil16_pair_async: all Vh sites, Lt a multiple of 4 and at least 8);
 // block partials of EPI_M_PART cover both sites of each thread.
-template <int EPI, int BLOCK>
+template <int EPI, int BLOCK, int CM>
 STAG_D void pair16_body(const DslashArgs &a) {
     __shared__ double smem[32];
-    __shared__ int4 ring[pair16_ring<BLOCK>() * 5 * BLOCK];
+    __shared__ int4 ring[pair16_ring<BLOCK, CM>() * pair16_cells<CM>() * BLOCK];
     if (a.skip_if_done && a.sc->status != CG_RUNNING)
         return;
     if (a.gate && *a.gate == 0)
@@ -310,8 +312,8 @@ STAG_D void pair16_body(const DslashArgs &a) {
 #pragma unroll
         for (int k = 0; k < 3; k++)
             acc[k] = cplx<float2>{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        stencil16_pair_async<BLOCK, pair16_ring<BLOCK>()>(a.g, a.out_par, c, a.links_out, a.links_in,
-                                                          (const short2 *)a.in, a, ring, acc);
+        stencil16_pair_async<BLOCK, pair16_ring<BLOCK, CM>(), CM>(a.g, a.out_par, c, a.links_out, a.links_in,
+                                                                  (const short2 *)a.in, a, ring, acc);
         cplx<float> lo[3], hi[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -325,24 +327,23 @@ STAG_D void pair16_body(const DslashArgs &a) {
 }
 
 // One launch of the stencil.  The capped form asks for at least 1024 resident
-// threads per SM (at most 64 registers).  Left free, the compiler hoists the
-// compressed 16-bit stencil's loads into 255 registers at a low occupancy,
-// and gives the uncompressed FP32 and 16-bit epilogue kernels so few
-// registers (32-44) that too few loads are in flight; the launcher picks the
-// capped form for those (kCapped) and the free one for the rest.
-template <int P, int EPI, int BLOCK, bool COMP = false>
+// threads per SM (at most 64 registers).  Left free, the compiler gives the
+// uncompressed FP32 kernels so few registers (32-44) that too few loads are
+// in flight; the launcher picks the capped form for those and for the
+// 16-bit ones (kCapped) and the free one for the rest.
+template <int P, int EPI, int BLOCK, int CM = 0>
 __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs a) {
-    dslash_body<P, EPI, BLOCK, COMP>(a);
+    dslash_body<P, EPI, BLOCK, CM>(a);
 }
 
-template <int P, int EPI, int BLOCK, bool COMP>
+template <int P, int EPI, int BLOCK, int CM>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) dslash_kernel_capped(DslashArgs a) {
-    dslash_body<P, EPI, BLOCK, COMP>(a);
+    dslash_body<P, EPI, BLOCK, CM>(a);
 }
 
 // whether a launch of precision prec and epilogue epi runs the pair form
 STAG_HD bool pair16_used(int prec, int epi, const DslashArgs &a) {
-    return prec == P_F16 && a.compressed && a.regs == REGS_PAIR &&
+    return prec == P_F16 && a.regs == REGS_PAIR &&
            (epi == EPI_NONE || epi == EPI_M_PART) &&
            a.c0 == 0 && (a.cn == 0 || a.cn == a.g.Vh) && a.cnb == 0 && pair16_applies(a.g);
 }
@@ -352,9 +353,9 @@ STAG_HD int dslash_pair16_grid(const Geom &g, int block) { return ((g.Vh >> 1) +
 // 85 registers (80 used).  At 48^3x96 this measured 351 us against 381-417
 // us with 640 threads and 96 registers (rings of 2 or 4 hops) and 386 us
 // with 512 threads and 124 registers.
-template <int EPI, int BLOCK>
+template <int EPI, int BLOCK, int CM>
 __global__ void __launch_bounds__(BLOCK, (768 / BLOCK > 0 ? 768 / BLOCK : 1)) dslash_pair16_kernel(DslashArgs a) {
-    pair16_body<EPI, BLOCK>(a);
+    pair16_body<EPI, BLOCK, CM>(a);
 }
 
 }  // namespace stag

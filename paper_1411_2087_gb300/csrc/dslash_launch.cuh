@@ -6,46 +6,46 @@
 
 namespace stag {
 
-// Which kernels run under the register cap, by measurement (48^3x96, kernel
-// times inside the mixed solves).  Left free, the compiler gives these 32-44
-// registers and keeps too few stencil loads in flight:
-//   16-bit with an epilogue    M with <p, Mp> partials 635 -> 557 us
+// Which kernels run under the register cap by default (before tuning), by
+// measurement (48^3x96, kernel times inside the mixed solves).  Left free,
+// the compiler gives these 32-44 registers and keeps too few stencil loads
+// in flight:
 //   FP32 uncompressed          D_oe 947 -> 901 us, M with partials 954 -> 913 us
-//   16-bit compressed          see dslash_kernel_capped
-// The plain uncompressed 16-bit D_oe stays free (530 us, 540 us capped); FP32
-// compressed (56-62 registers free) and the FP64 and double-float kernels
-// (HBM-bound at their free choice) keep the compiler's choice.
-template <int P, int EPI, bool COMP>
-constexpr bool kCapped = (P == P_F16 && (COMP || EPI != EPI_NONE)) || (P == P_F32 && !COMP);
+//   16-bit, one site           M with <p, Mp> partials 635 -> 557 us (full links)
+// FP32 on 12-real links (56-62 registers free) and the FP64 and double-float
+// kernels (HBM-bound at their free choice) keep the compiler's choice.
+template <int P, int EPI, int CM>
+constexpr bool kCapped = P == P_F16 || (P == P_F32 && CM != 3);
 
 // The plain stencil and the M stencil with <p, Mp> partials (the solvers'
 // two kernels per iteration) are instantiated in both register variants, so
 // that the autotuner can time them; the other epilogues use the default.
-template <int P, int EPI, int BLOCK, bool COMP>
+template <int P, int EPI, int BLOCK, int CM>
 static void launch_one(int grid, const DslashArgs &a, cudaStream_t s) {
     constexpr bool tunable = EPI == EPI_NONE || EPI == EPI_M_PART;
-    const bool capped = tunable && a.regs != REGS_DEFAULT ? a.regs == REGS_CAPPED : kCapped<P, EPI, COMP>;
+    const bool capped = tunable && a.regs != REGS_DEFAULT && a.regs != REGS_PAIR ? a.regs == REGS_CAPPED
+                                                                                 : kCapped<P, EPI, CM>;
     if constexpr (tunable) {
         if (capped)
-            dslash_kernel_capped<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+            dslash_kernel_capped<P, EPI, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
         else
-            dslash_kernel<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
-    } else if constexpr (kCapped<P, EPI, COMP>) {
-        dslash_kernel_capped<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+            dslash_kernel<P, EPI, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
+    } else if constexpr (kCapped<P, EPI, CM>) {
+        dslash_kernel_capped<P, EPI, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
     } else {
-        dslash_kernel<P, EPI, BLOCK, COMP><<<grid, BLOCK, 0, s>>>(a);
+        dslash_kernel<P, EPI, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
     }
 }
 
-template <int P, int BLOCK, bool COMP>
+template <int P, int BLOCK, int CM>
 static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
-    if constexpr (P == P_F16 && COMP) {
+    if constexpr (P == P_F16 && pair16_ring<BLOCK, CM>() > 0) {
         if (pair16_used(P, epi, a)) {
             const int grid = dslash_pair16_grid(a.g, BLOCK);
             if (epi == EPI_NONE)
-                dslash_pair16_kernel<EPI_NONE, BLOCK><<<grid, BLOCK, 0, s>>>(a);
+                dslash_pair16_kernel<EPI_NONE, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
             else
-                dslash_pair16_kernel<EPI_M_PART, BLOCK><<<grid, BLOCK, 0, s>>>(a);
+                dslash_pair16_kernel<EPI_M_PART, BLOCK, CM><<<grid, BLOCK, 0, s>>>(a);
             return cudaGetLastError();
         }
     }
@@ -54,28 +54,33 @@ static cudaError_t launch_p_b_c(int epi, const DslashArgs &a, cudaStream_t s) {
     if (grid == 0)
         return cudaSuccess;
     switch (epi) {
-    case EPI_NONE: launch_one<P, EPI_NONE, BLOCK, COMP>(grid, a, s); break;
-    case EPI_M: launch_one<P, EPI_M, BLOCK, COMP>(grid, a, s); break;
-    case EPI_M_PAP: launch_one<P, EPI_M_PAP, BLOCK, COMP>(grid, a, s); break;
-    case EPI_RESID: launch_one<P, EPI_RESID, BLOCK, COMP>(grid, a, s); break;
-    case EPI_RESID_STORE: launch_one<P, EPI_RESID_STORE, BLOCK, COMP>(grid, a, s); break;
-    case EPI_M_PART: launch_one<P, EPI_M_PART, BLOCK, COMP>(grid, a, s); break;
+    case EPI_NONE: launch_one<P, EPI_NONE, BLOCK, CM>(grid, a, s); break;
+    case EPI_M: launch_one<P, EPI_M, BLOCK, CM>(grid, a, s); break;
+    case EPI_M_PAP: launch_one<P, EPI_M_PAP, BLOCK, CM>(grid, a, s); break;
+    case EPI_RESID: launch_one<P, EPI_RESID, BLOCK, CM>(grid, a, s); break;
+    case EPI_RESID_STORE: launch_one<P, EPI_RESID_STORE, BLOCK, CM>(grid, a, s); break;
+    case EPI_M_PART: launch_one<P, EPI_M_PART, BLOCK, CM>(grid, a, s); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-// the 12-real layout exists for FP32 and 16-bit links only
+// the 12-real layout exists for FP32 and 16-bit links only: every link
+// 12-real (mask 3), or the three-link ones only (mask 2)
 template <int P, int BLOCK>
 static cudaError_t launch_p_b(int epi, const DslashArgs &a, cudaStream_t s) {
     if constexpr (P == P_F32 || P == P_F16) {
-        if (a.compressed)
-            return launch_p_b_c<P, BLOCK, true>(epi, a, s);
+        switch (a.compressed) {
+        case 0: return launch_p_b_c<P, BLOCK, 0>(epi, a, s);
+        case 2: return launch_p_b_c<P, BLOCK, 2>(epi, a, s);
+        case 3: return launch_p_b_c<P, BLOCK, 3>(epi, a, s);
+        default: return cudaErrorInvalidValue;
+        }
     } else {
         if (a.compressed)
             return cudaErrorInvalidValue;
+        return launch_p_b_c<P, BLOCK, 0>(epi, a, s);
     }
-    return launch_p_b_c<P, BLOCK, false>(epi, a, s);
 }
 
 template <int P> cudaError_t launch_dslash_p(int epi, const DslashArgs &a, int block, cudaStream_t s) {

@@ -6,8 +6,10 @@
 //                   16-bit: one 16-byte cell per site instead, the three
 //                   components (int16 pairs) and the site's float norm, so
 //                   that a gather of one neighbour is one 16-byte load
-//   links           Elem G[2][8][9][stride]     [site parity][kind][row*3+col][cb site]
-//                   kind 0..3 = folded one-link U~_mu, 4..7 = folded three-link N~_mu
+//   links           G[2][8][...]                [site parity][kind], kind 0..3 =
+//                   folded one-link U~_mu, 4..7 = folded three-link N~_mu; a
+//                   full kind is Elem [9][stride] ([row*3+col][cb site]), in
+//                   16-bit three planes instead (see link_kind_bytes)
 // One Elem holds one complex number: a warp loading component j of 32
 // consecutive sites touches one contiguous segment.
 #pragma once
@@ -135,9 +137,47 @@ template <> struct C12<P_F16> {
     }
 };
 
-inline size_t c12_link_bytes(int p, size_t stride) {  // both parities, 8 kinds
-    return p == P_F32 ? 2 * 8 * C12<P_F32>::kind_bytes(stride)
-         : p == P_F16 ? 2 * 8 * C12<P_F16>::kind_bytes(stride) : 0;
+// --------------------------------------------------------------------------
+// Link storage by kind.  A full kind is 9 entries per site: Elem [9][stride]
+// planes in FP64, double-float and FP32; in 16-bit three planes, int4
+// [stride] (entries 0..3), int4 [stride] (entries 4..7) and int [stride]
+// (entry 8), each entry an int16 pair, so that a link is three loads.  A
+// 12-real kind is C12's layout.  Per parity the one-link kinds 0..3 come
+// first, then the three-link kinds 4..7; the bits of a compression mask say
+// which group is 12-real (bit 0 one-link, bit 1 three-link).
+// --------------------------------------------------------------------------
+STAG_HD size_t link_kind_bytes(int p, bool c12, size_t S) {
+    if (c12)
+        return p == P_F32 ? 48 * S : 24 * S;
+    return p == P_F32 ? 72 * S : p == P_F16 ? 36 * S : 144 * S;
+}
+STAG_HD size_t link_kind_offset(int p, int mask, int kind, size_t S) {
+    const size_t k1 = link_kind_bytes(p, mask & 1, S), k3 = link_kind_bytes(p, (mask >> 1) & 1, S);
+    return kind < 4 ? (size_t)kind * k1 : 4 * k1 + (size_t)(kind - 4) * k3;
+}
+STAG_HD size_t link_parity_bytes(int p, int mask, size_t S) { return link_kind_offset(p, mask, 8, S); }
+
+// the full 16-bit kind: where entry e of link idx lives, and its nine raw
+// int16 pairs in three loads
+struct L16 {
+    STAG_D static short2 *slot(char *kb, size_t S, size_t idx, int e) {
+        if (e < 4)
+            return (short2 *)kb + idx * 4 + e;
+        if (e < 8)
+            return (short2 *)(kb + 16 * S) + idx * 4 + (e - 4);
+        return (short2 *)(kb + 32 * S) + idx;
+    }
+    STAG_D static void load(const char *kb, size_t S, int idx, int w[9]) {
+        const int4 a = ld_stream((const int4 *)kb + idx);
+        const int4 b = ld_stream((const int4 *)(kb + 16 * S) + idx);
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w;
+        w[4] = b.x, w[5] = b.y, w[6] = b.z, w[7] = b.w;
+        w[8] = ld_stream((const int *)(kb + 32 * S) + idx);
+    }
+};
+
+inline size_t c12_link_bytes(int p, size_t stride, int mask = 3) {  // both parities, 8 kinds
+    return (p == P_F32 || p == P_F16) ? 2 * link_parity_bytes(p, mask, stride) : 0;
 }
 
 // bytes of one colour-vector field / one complex link entry

@@ -45,7 +45,7 @@ cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], doubl
 // fold into the 12-real layout (FP32 or 16-bit; see C12 in fields.cuh)
 cudaError_t launch_fold_links_c12(int prec, const Geom &g, const double bc[4], double c1, double c3,
                                   const double *fat, const double *lng, void *links, const float inv_scale[2],
-                                  cudaStream_t s);
+                                  int mask, cudaStream_t s);
 // largest deviation from SU(3) over nlinks canonical 3x3 complex128
 // matrices, as float bits in *out (device)
 cudaError_t launch_su3_deviation(const double *U, long long nlinks, unsigned *out, cudaStream_t s);

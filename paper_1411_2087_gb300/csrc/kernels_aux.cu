@@ -263,7 +263,8 @@ cudaError_t launch_export(int prec, const Geom &g, const void *field, double *ca
 }
 
 // --------------------------------------------------------------------------
-// link folding: G[par][kind][j][cb] = coef * L[mu][i][j], kind = mu (+4 long)
+// link folding: entry j of kind `kind` = mu (+4 long) at (par, cb) = coef * L[mu][i][j]
+// (the kinds' layouts as link_kind_offset describes)
 //   coef = c * eta_mu(x) * bc_mu^w,  w = floor((x_mu + s) / L_mu), s = 1 or 3
 // so that the stencil applies  + G(x) psi(x+s mu)  and  - G(x-s mu)^+ psi(x-s mu).
 // --------------------------------------------------------------------------
@@ -283,9 +284,18 @@ STAG_D void full_coords(const Geom &g, long long i, int x[4]) {
     x[3] = (int)(i / g.L[2]);
 }
 
+// entry e of the full link at checkerboard site cb of one kind (kind base kb)
+template <int P>
+STAG_D void store_full_link(char *kb, size_t S, size_t cb, int e, double re, double im, float inv_scale) {
+    if constexpr (P == P_F16)
+        *L16::slot(kb, S, cb, e) = Fmt<P>::pack_link(re, im, inv_scale);
+    else
+        ((typename Fmt<P>::Elem *)kb)[(size_t)e * S + cb] = Fmt<P>::pack_link(re, im, inv_scale);
+}
+
 template <int P>
 __global__ void fold_kernel(FoldArgs fa, const double *__restrict__ fat, const double *__restrict__ lng,
-                            typename Fmt<P>::Elem *G) {
+                            char *G) {
     const Geom &g = fa.g;
     const long long V = 2LL * g.Vh;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -310,16 +320,17 @@ __global__ void fold_kernel(FoldArgs fa, const double *__restrict__ fat, const d
     if ((wraps & 1) && fa.bc[mu] < 0)
         coef = -coef;
     const double *src = (three ? lng : fat) + ((size_t)mu * V + i) * 18;
-    typename Fmt<P>::Elem *dst = G + ((size_t)par * 8 + kind) * 9 * g.stride + cb;
+    const size_t S = (size_t)g.stride;
+    char *kb = G + (size_t)par * link_parity_bytes(P, 0, S) + link_kind_offset(P, 0, kind, S);
     for (int j = 0; j < 9; j++)
-        dst[(size_t)j * g.stride] =
-            Fmt<P>::pack_link(coef * src[2 * j], coef * src[2 * j + 1], fa.inv_scale[three ? 1 : 0]);
+        store_full_link<P>(kb, S, cb, j, coef * src[2 * j], coef * src[2 * j + 1], fa.inv_scale[three ? 1 : 0]);
 }
 
-// the same folding into the 12-real layout (rows 0 and 1 only)
+// the same folding into a copy whose kinds of the groups in `mask` (bit 0
+// one-link, bit 1 three-link) take the 12-real layout (rows 0 and 1 only)
 template <int P>
 __global__ void fold_c12_kernel(FoldArgs fa, const double *__restrict__ fat, const double *__restrict__ lng,
-                                char *G) {
+                                char *G, int mask) {
     const Geom &g = fa.g;
     const long long V = 2LL * g.Vh;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -345,14 +356,20 @@ __global__ void fold_c12_kernel(FoldArgs fa, const double *__restrict__ fat, con
         coef = -coef;
     const double *src = (three ? lng : fat) + ((size_t)mu * V + i) * 18;
     const size_t S = (size_t)g.stride;
-    char *kb = G + ((size_t)par * 8 + kind) * C12<P>::kind_bytes(S);
-    for (int e = 0; e < 6; e++)
-        C12<P>::store(kb, S, cb, e, coef * src[2 * e], coef * src[2 * e + 1], fa.inv_scale[three ? 1 : 0]);
+    char *kb = G + (size_t)par * link_parity_bytes(P, mask, S) + link_kind_offset(P, mask, kind, S);
+    const float inv = fa.inv_scale[three ? 1 : 0];
+    if ((mask >> (three ? 1 : 0)) & 1) {
+        for (int e = 0; e < 6; e++)
+            C12<P>::store(kb, S, cb, e, coef * src[2 * e], coef * src[2 * e + 1], inv);
+    } else {
+        for (int e = 0; e < 9; e++)
+            store_full_link<P>(kb, S, cb, e, coef * src[2 * e], coef * src[2 * e + 1], inv);
+    }
 }
 
 cudaError_t launch_fold_links_c12(int prec, const Geom &g, const double bc[4], double c1, double c3,
                                   const double *fat, const double *lng, void *links, const float inv_scale[2],
-                                  cudaStream_t s) {
+                                  int mask, cudaStream_t s) {
     FoldArgs fa;
     fa.g = g;
     for (int k = 0; k < 4; k++)
@@ -363,10 +380,12 @@ cudaError_t launch_fold_links_c12(int prec, const Geom &g, const double bc[4], d
     fa.inv_scale[1] = inv_scale ? inv_scale[1] : 0.f;
     const long long n = 16LL * g.Vh;
     const int grid = (int)((n + 255) / 256);
+    if (mask != 2 && mask != 3)
+        return cudaErrorInvalidValue;
     if (prec == P_F32)
-        fold_c12_kernel<P_F32><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links);
+        fold_c12_kernel<P_F32><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links, mask);
     else if (prec == P_F16)
-        fold_c12_kernel<P_F16><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links);
+        fold_c12_kernel<P_F16><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links, mask);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -434,7 +453,7 @@ cudaError_t launch_fold_links(int prec, const Geom &g, const double bc[4], doubl
     const long long n = 16LL * g.Vh;
     const int grid = (int)((n + 255) / 256);
     STAG_PREC_SWITCH(prec, {
-        fold_kernel<P><<<grid, 256, 0, s>>>(fa, fat, lng, (typename Fmt<P>::Elem *)links);
+        fold_kernel<P><<<grid, 256, 0, s>>>(fa, fat, lng, (char *)links);
     });
     return cudaGetLastError();
 }

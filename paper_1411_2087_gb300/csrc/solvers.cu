@@ -1286,7 +1286,7 @@ static std::string tune_key(const stag_lattice lat, int prec) {
     }
     char buf[256];
     snprintf(buf, sizeof buf, "%d %d %d %d %d %d %s", lat->dims[0], lat->dims[1], lat->dims[2], lat->dims[3], prec,
-             lat->links_c12[prec] ? 1 : 0, dev.c_str());
+             lat->links_c12[prec] ? lat->c12_mask[prec] : 0, dev.c_str());
     return buf;
 }
 

@@ -240,8 +240,12 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         return fail(STAG_ERR_ARG, "stag_gauge_upload: bad ptr_kind %d", ptr_kind);
     if (!std::isfinite(c1) || !std::isfinite(c3))
         return fail(STAG_ERR_ARG, "stag_gauge_upload: coefficients must be finite");
-    const bool compress = (prec_mask & STAG_COMPRESS12) != 0;
-    prec_mask &= ~(unsigned)STAG_COMPRESS12;
+    if ((prec_mask & STAG_COMPRESS12) && (prec_mask & STAG_COMPRESS12_LONG))
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: STAG_COMPRESS12 and STAG_COMPRESS12_LONG exclude each other");
+    // which link groups take the 12-real layout: bit 0 one-link, bit 1 three-link
+    const int cmask = (prec_mask & STAG_COMPRESS12) ? 3 : (prec_mask & STAG_COMPRESS12_LONG) ? 2 : 0;
+    const bool compress = cmask != 0;
+    prec_mask &= ~(unsigned)(STAG_COMPRESS12 | STAG_COMPRESS12_LONG);
     if (prec_mask == 0)
         prec_mask = STAG_PREC_BIT(STAG_F64) | STAG_PREC_BIT(STAG_DF64);
     for (int p = 0; p < 32; p++)
@@ -251,8 +255,9 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
                             prec_name(p));
     if (compress && !(prec_mask & (STAG_PREC_BIT(STAG_F32) | STAG_PREC_BIT(STAG_F16))))
         return fail(STAG_ERR_ARG, "stag_gauge_upload: 12-real compression applies to F32 and F16 copies only");
-    if (compress && (c1 == 0.0 || c3 == 0.0))
-        return fail(STAG_ERR_ARG, "stag_gauge_upload: 12-real compression needs c1 != 0 and c3 != 0");
+    if (compress && (((cmask & 1) && c1 == 0.0) || c3 == 0.0))
+        return fail(STAG_ERR_ARG, "stag_gauge_upload: 12-real compression needs a nonzero coefficient on the "
+                    "compressed links");
     DEVICE_SCOPE(lat->device);
     // device sources may have been written on any stream of the caller
     if (ptr_kind == STAG_PTR_DEVICE)
@@ -298,6 +303,7 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
             cudaFree(lat->links_c12[p]);
             lat->links_c12[p] = nullptr;
         }
+        lat->c12_mask[p] = 0;
     }
     drop_mixed_graphs(lat);
     if (compress) {
@@ -322,10 +328,11 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
         }
         float dev[2];
         memcpy(dev, bits, sizeof dev);
-        if (!(dev[0] <= 1e-6f) || !(dev[1] <= 1e-6f)) {
+        if (((cmask & 1) && !(dev[0] <= 1e-6f)) || !(dev[1] <= 1e-6f)) {
             release();
             return fail(STAG_ERR_ARG, "stag_gauge_upload: links deviate from SU(3) by %.2e (fat) / %.2e (long); "
-                        "12-real compression needs special unitary links", dev[0], dev[1]);
+                        "12-real compression needs special unitary links%s", dev[0], dev[1],
+                        (cmask & 1) ? " (STAG_COMPRESS12_LONG compresses the long links only)" : "");
         }
     }
     lat->has_gauge = false;
@@ -374,13 +381,15 @@ extern "C" int stag_gauge_upload(stag_lattice lat, const double *fat, const doub
             e = launch_fold_links(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links[p], inv_scale,
                                   lat->stream);
         if (e == cudaSuccess && compress && (p == STAG_F32 || p == STAG_F16)) {
-            const size_t cb = c12_link_bytes(p, (size_t)lat->geom.stride);
+            const size_t cb = c12_link_bytes(p, (size_t)lat->geom.stride, cmask);
             e = cudaMalloc(&lat->links_c12[p], cb);
             if (e == cudaSuccess)
                 e = cudaMemsetAsync(lat->links_c12[p], 0, cb, lat->stream);
             if (e == cudaSuccess)
                 e = launch_fold_links_c12(p, lat->geom, lat->bc, c1, c3, fat_d, lng_d, lat->links_c12[p],
-                                          inv_scale, lat->stream);
+                                          inv_scale, cmask, lat->stream);
+            if (e == cudaSuccess)
+                lat->c12_mask[p] = cmask;
         }
         if (e != cudaSuccess) {
             release();

@@ -1,5 +1,5 @@
-// The compressed 16-bit stencil (12-real links, 16-bit colour vectors), in
-// raw integer units, written once over a lane type V:
+// The 16-bit stencil (16-bit links and colour vectors) in raw integer
+// units, written once over a lane type V:
 //
 //   V = float    one output site per thread
 //   V = float2   two output sites per thread, the pair (x, y, z, t) and
@@ -14,11 +14,14 @@
 // and removes half of the index arithmetic, the two costs that keep the
 // one-site form below the memory roof.
 //
+// Each group of links (one-link, three-link) is either full (nine entries)
+// or 12-real, as the compression mask CM says (link_kind_offset).
+//
 // Units: a link entry is ls q (ls the field's scale), a vector component
-// (n / 32767) q (n the site's norm), q the stored integers.  Rows 0 and 1 of
-// a link are stored; with X = row0 x row1 (raw), row 2 of the link is
-// conj(X) ls / s (s = c eta b of that link), which the hop's coefficients
-// carry.
+// (n / 32767) q (n the site's norm), q the stored integers.  Of a 12-real
+// link rows 0 and 1 are stored; with X = row0 x row1 (raw), row 2 of the
+// link is conj(X) ls / s (s = c eta b of that link), which the hop's
+// coefficients carry.
 #pragma once
 #include "fields.cuh"
 
@@ -116,6 +119,48 @@ STAG_D void hop_bwd16(cplx<V> acc[3], const cplx<V> L[6], const cplx<V> v[3], V 
     }
 }
 
+// forward hop, full link: acc_r += cf (L v)_r
+template <class V>
+STAG_D void hop_fwd16_full(cplx<V> acc[3], const cplx<V> L[9], const cplx<V> v[3], V cf) {
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        V tr = vmul(L[3 * r].re, v[0].re);
+        tr = vfma(vneg(L[3 * r].im), v[0].im, tr);
+        V ti = vmul(L[3 * r].re, v[0].im);
+        ti = vfma(L[3 * r].im, v[0].re, ti);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            tr = vfma(L[3 * r + b].re, v[b].re, tr);
+            tr = vfma(vneg(L[3 * r + b].im), v[b].im, tr);
+            ti = vfma(L[3 * r + b].re, v[b].im, ti);
+            ti = vfma(L[3 * r + b].im, v[b].re, ti);
+        }
+        acc[r].re = vfma(cf, tr, acc[r].re);
+        acc[r].im = vfma(cf, ti, acc[r].im);
+    }
+}
+
+// backward hop, full link: acc_r += cf sum_b conj(L_br) v_b
+template <class V>
+STAG_D void hop_bwd16_full(cplx<V> acc[3], const cplx<V> L[9], const cplx<V> v[3], V cf) {
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        V tr = vmul(L[r].re, v[0].re);
+        tr = vfma(L[r].im, v[0].im, tr);
+        V ti = vmul(L[r].re, v[0].im);
+        ti = vfma(vneg(L[r].im), v[0].re, ti);
+#pragma unroll
+        for (int b = 1; b < 3; b++) {
+            tr = vfma(L[3 * b + r].re, v[b].re, tr);
+            tr = vfma(L[3 * b + r].im, v[b].im, tr);
+            ti = vfma(L[3 * b + r].re, v[b].im, ti);
+            ti = vfma(vneg(L[3 * b + r].im), v[b].re, ti);
+        }
+        acc[r].re = vfma(cf, tr, acc[r].re);
+        acc[r].im = vfma(cf, ti, acc[r].im);
+    }
+}
+
 // ---- loads: one site (V = float) ----------------------------------------
 
 // raw vector of site j (its 16-byte cell); returns its norm
@@ -137,6 +182,15 @@ STAG_D void ld_link16(const char *kb, int S, int idx, cplx<float> L[6]) {
     L[3] = cplx<float>{q_lo(a.w), q_hi(a.w)};
     L[4] = cplx<float>{q_lo(b.x), q_hi(b.x)};
     L[5] = cplx<float>{q_lo(b.y), q_hi(b.y)};
+}
+
+// the nine entries of link idx of one full kind
+STAG_D void ld_link16_full(const char *kb, int S, int idx, cplx<float> L[9]) {
+    int w[9];
+    L16::load(kb, (size_t)S, idx, w);
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        L[e] = cplx<float>{q_lo(w[e]), q_hi(w[e])};
 }
 
 // ---- loads: a pair of sites (V = float2, lanes ja, jb) -------------------
@@ -163,10 +217,19 @@ STAG_D void ld_link16(const char *kb, int S, int ia, int ib, cplx<float2> L[6]) 
         L[e] = cplx<float2>{make_float2(q_lo(wa[e]), q_lo(wb[e])), make_float2(q_hi(wa[e]), q_hi(wb[e]))};
 }
 
+STAG_D void ld_link16_full(const char *kb, int S, int ia, int ib, cplx<float2> L[9]) {
+    int wa[9], wb[9];
+    L16::load(kb, (size_t)S, ia, wa);
+    L16::load(kb, (size_t)S, ib, wb);
+#pragma unroll
+    for (int e = 0; e < 9; e++)
+        L[e] = q2(wa[e], wb[e]);
+}
+
 // ---- the site loops -------------------------------------------------------
 
 // acc += D psi at checkerboard site c of parity par (one site)
-template <class A>
+template <int CM, class A>
 STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict__ Gout,
                            const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
                            cplx<float> acc[3]) {
@@ -182,24 +245,40 @@ STAG_D void stencil16_site(const Geom &g, int par, int c, const void *__restrict
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int s = h ? 3 : 1;
-            const char *ko = (const char *)Gout + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
-            const char *ki = (const char *)Gin + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+            const bool c12 = (CM >> h) & 1;
+            const size_t off = link_kind_offset(P_F16, CM, 4 * h + mu, (size_t)S);
+            const char *ko = (const char *)Gout + off;
+            const char *ki = (const char *)Gin + off;
             const float ls = a.link_scale[h], lsq = ls * (1.f / kQ16);
             {
                 const int j = cb_hop(g, c, x, mu, +s);
-                const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
-                cplx<float> v[3], L[6];
+                cplx<float> v[3];
                 const float cf = vmul(ld_vec16(in, j, v), lsq);
-                ld_link16(ko, S, c, L);
-                hop_fwd16(acc, L, v, cf, vmul(cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h])));
+                if (c12) {
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], s, g.L[mu]) : 0)) & 1;
+                    cplx<float> L[6];
+                    ld_link16(ko, S, c, L);
+                    hop_fwd16(acc, L, v, cf, vmul(cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h])));
+                } else {
+                    cplx<float> L[9];
+                    ld_link16_full(ko, S, c, L);
+                    hop_fwd16_full(acc, L, v, cf);
+                }
             }
             {
                 const int j = cb_hop(g, c, x, mu, -s);
-                const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
-                cplx<float> v[3], L[6];
+                cplx<float> v[3];
                 const float cf = vmul(ld_vec16(in, j, v), -lsq);
-                ld_link16(ki, S, j, L);
-                hop_bwd16(acc, L, v, cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h]));
+                if (c12) {
+                    const int flip = (esum + (a.bc_neg[mu] ? hop_wraps(x[mu], -s, g.L[mu]) : 0)) & 1;
+                    cplx<float> L[6];
+                    ld_link16(ki, S, j, L);
+                    hop_bwd16(acc, L, v, cf, ls * (flip ? -a.inv_c[h] : a.inv_c[h]));
+                } else {
+                    cplx<float> L[9];
+                    ld_link16_full(ki, S, j, L);
+                    hop_bwd16_full(acc, L, v, cf);
+                }
             }
         }
     }
@@ -214,15 +293,16 @@ STAG_HD bool pair16_applies(const Geom &g) { return g.L[3] % 4 == 0 && g.L[3] >=
 
 }  // namespace stag
 
-// ---- the pair form with an asynchronous ring ------------------------------
+// ---- the pair form, loads through an asynchronous ring ---------------------
 //
 // Each thread copies the links and neighbour vectors of hop k + RING into
 // shared memory with cp.async while it computes hop k, so that RING hops of
 // both sites' loads are in flight without holding registers.  A slot holds,
-// per thread, five 16-byte cells: link rows 0-1 (entries e0..e3) of site A
-// and of site B, the two sites' vectors (three int16 pairs and the norm),
-// and both sites' link entries e4, e5.  Every thread reads only its own
-// cells, so no barrier is needed.
+// per thread, 16-byte cells: 0, 1 entries e0..e3 of site A's and site B's
+// link; 2, 3 the two sites' vector cells (three int16 pairs and the norm);
+// then, for a 12-real link, 4: both sites' e4, e5; for a full link, 4, 5:
+// e4..e7 of A and B, and 6: e8 of A and of B.  Every thread reads only its
+// own cells, so no barrier is needed.
 namespace stag {
 
 STAG_D void cp_async16(unsigned dst, const void *src) {
@@ -231,16 +311,24 @@ STAG_D void cp_async16(unsigned dst, const void *src) {
 STAG_D void cp_async8(unsigned dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
 }
+STAG_D void cp_async4(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
 STAG_D void cp_async16ca(unsigned dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
 }
 STAG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> STAG_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// cells per slot: 5 when every link is 12-real, 7 when some are full
+template <int CM> __host__ __device__ constexpr int pair16_cells() { return CM == 3 ? 5 : 7; }
+
 // ring depth: two hops in flight per thread (deeper rings measured slower
-// at 768 resident threads per SM, and need more shared memory than 48 KB
-// per block of 256); blocks of 512 keep one
-template <int BLOCK> __host__ __device__ constexpr int pair16_ring() { return BLOCK <= 256 ? 2 : 1; }
+// at 768 resident threads per SM), less where a block's ring would pass 40
+// KB of shared memory; 0: no pair form for this block size
+template <int BLOCK, int CM> __host__ __device__ constexpr int pair16_ring() {
+    return 40960 / (pair16_cells<CM>() * 16 * BLOCK) >= 2 ? 2 : 40960 / (pair16_cells<CM>() * 16 * BLOCK);
+}
 
 // the indices of hop k = 4 mu + 2 h + dir (dir 1: backward) of the pair
 // (c, c + H): neighbour vectors at ja, jb, links at ia, ib of kind 4h + mu
@@ -264,7 +352,8 @@ STAG_D void pair16_hop_index(const Geom &g, int c, const int x[4], int k, int &j
     ib = dir ? jb : c + H;
 }
 
-// the row-2 factors ls / s of hop k for the two sites (eta b folded)
+// the row-2 factors ls / s of hop k (12-real links) for the two sites (eta
+// b folded)
 template <class A>
 STAG_D float2 pair16_hop_k2(const Geom &g, const int x[4], int k, const A &a) {
     const int mu = k >> 2, h = (k >> 1) & 1, s = h ? 3 : 1, dir = k & 1;
@@ -284,66 +373,96 @@ STAG_D float2 pair16_hop_k2(const Geom &g, const int x[4], int k, const A &a) {
     return make_float2((eta ^ (bn & (t < s))) ? -kp : kp, eta ? -kp : kp);
 }
 
-template <int BLOCK>
+template <int BLOCK, int CM>
 STAG_D void pair16_issue(unsigned cell, const Geom &g, int c, const int x[4], int k, const void *Gout,
                          const void *Gin, const short2 *in) {
     const int S = g.stride;
     int ja, jb, ia, ib;
     pair16_hop_index(g, c, x, k, ja, jb, ia, ib);
     const int mu = k >> 2, h = (k >> 1) & 1, dir = k & 1;
-    const char *kb = (const char *)(dir ? Gin : Gout) + (size_t)(4 * h + mu) * C12<P_F16>::kind_bytes((size_t)S);
+    const char *kb = (const char *)(dir ? Gin : Gout) + link_kind_offset(P_F16, CM, 4 * h + mu, (size_t)S);
     constexpr unsigned R = 16 * BLOCK;  // bytes between a slot's cells
     cp_async16(cell, kb + (size_t)ia * 16);
     cp_async16(cell + R, kb + (size_t)ib * 16);
-    const char *k2 = kb + (size_t)16 * S;
-    cp_async8(cell + 4 * R, k2 + (size_t)ia * 8);
-    cp_async8(cell + 4 * R + 8, k2 + (size_t)ib * 8);
+    if ((CM >> h) & 1) {
+        const char *k2 = kb + (size_t)16 * S;
+        cp_async8(cell + 4 * R, k2 + (size_t)ia * 8);
+        cp_async8(cell + 4 * R + 8, k2 + (size_t)ib * 8);
+    } else {
+        const char *k2 = kb + (size_t)16 * S, *k3 = kb + (size_t)32 * S;
+        cp_async16(cell + 4 * R, k2 + (size_t)ia * 16);
+        cp_async16(cell + 5 * R, k2 + (size_t)ib * 16);
+        cp_async4(cell + 6 * R, k3 + (size_t)ia * 4);
+        cp_async4(cell + 6 * R + 4, k3 + (size_t)ib * 4);
+    }
     cp_async16ca(cell + 2 * R, (const int4 *)in + ja);
     cp_async16ca(cell + 3 * R, (const int4 *)in + jb);
 }
 
 // acc += D psi at sites c and c + H (c < H = Vh/2), loads through the ring
-// (ring: this block's RING * 5 * BLOCK cells of 16 bytes)
-template <int BLOCK, int RING, class A>
+// (ring: this block's RING * pair16_cells<CM>() * BLOCK cells of 16 bytes)
+template <int BLOCK, int RING, int CM, class A>
 STAG_D void stencil16_pair_async(const Geom &g, int par, int c, const void *__restrict__ Gout,
                                  const void *__restrict__ Gin, const short2 *__restrict__ in, const A &a,
                                  int4 *ring, cplx<float2> acc[3]) {
+    constexpr int CELLS = pair16_cells<CM>();
     int x[4];
     cb_coords(g, c, par, x);
     const unsigned cell0 = (unsigned)__cvta_generic_to_shared(ring + threadIdx.x);
 #pragma unroll
     for (int k = 0; k < RING; k++) {
-        pair16_issue<BLOCK>(cell0 + (unsigned)(k * 5 * BLOCK * 16), g, c, x, k, Gout, Gin, in);
+        pair16_issue<BLOCK, CM>(cell0 + (unsigned)(k * CELLS * BLOCK * 16), g, c, x, k, Gout, Gin, in);
         cp_async_commit();
     }
 #pragma unroll
     for (int k = 0; k < 16; k++) {
         cp_async_wait<RING - 1>();
         const int slot = k % RING, h = (k >> 1) & 1, dir = k & 1;
-        const int4 *cell = ring + slot * 5 * BLOCK + threadIdx.x;
-        const int4 la = cell[0], lb = cell[BLOCK], va = cell[2 * BLOCK], vb = cell[3 * BLOCK], l2 = cell[4 * BLOCK];
-        cplx<float2> L[6], v[3];
-        L[0] = q2(la.x, lb.x);
-        L[1] = q2(la.y, lb.y);
-        L[2] = q2(la.z, lb.z);
-        L[3] = q2(la.w, lb.w);
-        L[4] = q2(l2.x, l2.z);
-        L[5] = q2(l2.y, l2.w);
+        const int4 *cell = ring + slot * CELLS * BLOCK + threadIdx.x;
+        const int4 la = cell[0], lb = cell[BLOCK], va = cell[2 * BLOCK], vb = cell[3 * BLOCK];
+        cplx<float2> v[3];
         v[0] = q2(va.x, vb.x);
         v[1] = q2(va.y, vb.y);
         v[2] = q2(va.z, vb.z);
         const float lsq = a.link_scale[h] * (1.f / kQ16);
         const float2 nrm = make_float2(__int_as_float(va.w), __int_as_float(vb.w));
-        const float2 k2 = pair16_hop_k2(g, x, k, a);
-        if (dir == 0) {
-            const float2 cf = vmul(nrm, vsplat<float2>(lsq));
-            hop_fwd16(acc, L, v, cf, vmul(cf, k2));
+        if ((CM >> h) & 1) {
+            const int4 l2 = cell[4 * BLOCK];
+            cplx<float2> L[6];
+            L[0] = q2(la.x, lb.x);
+            L[1] = q2(la.y, lb.y);
+            L[2] = q2(la.z, lb.z);
+            L[3] = q2(la.w, lb.w);
+            L[4] = q2(l2.x, l2.z);
+            L[5] = q2(l2.y, l2.w);
+            const float2 k2 = pair16_hop_k2(g, x, k, a);
+            if (dir == 0) {
+                const float2 cf = vmul(nrm, vsplat<float2>(lsq));
+                hop_fwd16(acc, L, v, cf, vmul(cf, k2));
+            } else {
+                hop_bwd16(acc, L, v, vmul(nrm, vsplat<float2>(-lsq)), k2);
+            }
         } else {
-            hop_bwd16(acc, L, v, vmul(nrm, vsplat<float2>(-lsq)), k2);
+            const int4 ma = cell[4 * BLOCK], mb = cell[5 * BLOCK], e8 = cell[6 * BLOCK];
+            cplx<float2> L[9];
+            L[0] = q2(la.x, lb.x);
+            L[1] = q2(la.y, lb.y);
+            L[2] = q2(la.z, lb.z);
+            L[3] = q2(la.w, lb.w);
+            L[4] = q2(ma.x, mb.x);
+            L[5] = q2(ma.y, mb.y);
+            L[6] = q2(ma.z, mb.z);
+            L[7] = q2(ma.w, mb.w);
+            L[8] = q2(e8.x, e8.y);
+            if (dir == 0)
+                hop_fwd16_full(acc, L, v, vmul(nrm, vsplat<float2>(lsq)));
+            else
+                hop_bwd16_full(acc, L, v, vmul(nrm, vsplat<float2>(-lsq)));
         }
         // the slot's cells are in registers now; refill it with hop k + RING
         if (k + RING < 16)
-            pair16_issue<BLOCK>(cell0 + (unsigned)(slot * 5 * BLOCK * 16), g, c, x, k + RING, Gout, Gin, in);
+            pair16_issue<BLOCK, CM>(cell0 + (unsigned)(slot * CELLS * BLOCK * 16), g, c, x, k + RING, Gout, Gin,
+                                    in);
         cp_async_commit();
     }
 }

@@ -34,6 +34,7 @@ ERR_NOMEM = -7
 F64, F32, F16, DF64 = 0, 1, 2, 3
 PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
 COMPRESS12 = 1 << 16
+COMPRESS12_LONG = 1 << 17
 EVEN, ODD = 0, 1
 NET_FP16_WEIGHTS, NET_LINKS16 = 1, 2
 CG_LAUNCH_GRAPH, CG_LAUNCH_HOST = 0, 1
@@ -317,7 +318,9 @@ class Lattice:
 
     # gauge -----------------------------------------------------------------
     def upload_gauge(self, fat, lng=None, c1=C1_NAIK, c3=C3_NAIK, precisions=("f64", "df64"),
-                     compress12: bool = False):
+                     compress12=False):
+        """compress12: False, True (12-real one-link and three-link links in
+        the FP32 and 16-bit copies) or "long" (the three-link links only)."""
         shape = (4, self.V, 3, 3)
         pf, kind, keep_f = _as_buffer(fat, shape)
         if lng is not None:
@@ -326,7 +329,12 @@ class Lattice:
                 raise ValueError("fat and long links must both be on the host or both on the device")
         else:
             pl = None
-        mask = COMPRESS12 if compress12 else 0
+        if compress12 == "long":
+            mask = COMPRESS12_LONG
+        elif compress12 in (True, False):
+            mask = COMPRESS12 if compress12 else 0
+        else:
+            raise ValueError("compress12 must be False, True or 'long'")
         for p in precisions:
             mask |= 1 << (PREC[p] if isinstance(p, str) else int(p))
         _check(lib().stag_gauge_upload(self.handle, pf, pl, float(c1), float(c3), kind, mask))

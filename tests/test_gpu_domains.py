@@ -60,7 +60,8 @@ def test_dd_dslash_matches_single_domain_and_oracle(dims, k, prec):
     assert e1 <= TOL[prec] and e2 <= TOL[prec], (e1, e2)
 
 
-def test_dd_dslash_compressed_links():
+@pytest.mark.parametrize("compress", [True, "long"])
+def test_dd_dslash_compressed_links(compress):
     dims, k = (4, 4, 6, 12), 3
     Vh = int(np.prod(dims)) // 2
     U = synth.su3_field(dims, 0.4, 51).numpy()
@@ -68,7 +69,7 @@ def test_dd_dslash_compressed_links():
     psi_e = synth.gaussian_colour_field(Vh, 52).numpy()
     want = oracle.dslash_parity(dims, U, N, 1, psi_e)
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, N, precisions=("f32", "f16"), compress12=True)
+        lat.upload_gauge(U, N, precisions=("f32", "f16"), compress12=compress)
         for prec in ("f32", "f16"):
             fe = lat.field(stag.EVEN, prec, psi_e)
             ref, dd = lat.field(stag.ODD, prec), lat.field(stag.ODD, prec)

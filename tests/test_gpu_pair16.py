@@ -1,6 +1,7 @@
-"""The pair form of the compressed 16-bit stencil (regs 3): two output sites
+"""The pair form of the 16-bit stencil (regs 3): two output sites
 (x, y, z, t) and (x, y, z, t + Lt/2) per thread in packed FP32x2 arithmetic,
-their loads through a shared-memory ring of cp.async copies.
+their loads through a shared-memory ring of cp.async copies, on full links,
+12-real links and 12-real three-link links with full one-link links.
 
 * D and M equal the one-site forms bit for bit, for every block size, on
   lattices whose Lt is a multiple of 4 (8, 12, 16), with every boundary sign
@@ -29,9 +30,10 @@ def rel_err(got, want):
     return np.abs(got - want).max() / np.abs(want).max()
 
 
+@pytest.mark.parametrize("compress", [True, False, "long"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 2, 12), (4, 6, 4, 16), (6, 4, 6, 10), (4, 4, 4, 4)])
 @pytest.mark.parametrize("bc", [(1.0, 1.0, 1.0, -1.0), (-1.0, 1.0, -1.0, -1.0), (1.0, -1.0, 1.0, 1.0)])
-def test_pair_matches_one_site_and_oracle(dims, bc):
+def test_pair_matches_one_site_and_oracle(dims, bc, compress):
     Vh = int(np.prod(dims)) // 2
     U = synth.su3_field(dims, 0.5, 41).numpy()
     N = oracle.long_links(dims, U)
@@ -41,7 +43,7 @@ def test_pair_matches_one_site_and_oracle(dims, bc):
     want_e = oracle.dslash_parity(dims, U, N, 0, psi_o, bc=bc, c1=C1, c3=C3)
     want_m = oracle.apply_M(dims, U, N, 0.3, psi_e, bc=bc, c1=C1, c3=C3)
     with stag.Lattice(dims, bc=bc) as lat:
-        lat.upload_gauge(U, N, c1=C1, c3=C3, precisions=("f16",), compress12=True)
+        lat.upload_gauge(U, N, c1=C1, c3=C3, precisions=("f16",), compress12=compress)
         fe = lat.field(stag.EVEN, "f16", psi_e)
         fo = lat.field(stag.ODD, "f16", psi_o)
         oo, oe, om = lat.field(stag.ODD, "f16"), lat.field(stag.EVEN, "f16"), lat.field(stag.EVEN, "f16")
@@ -57,15 +59,16 @@ def test_pair_matches_one_site_and_oracle(dims, bc):
         assert rel_err(ref[0], want_o) <= 3e-4 and rel_err(ref[1], want_e) <= 3e-4
         assert rel_err(ref[2], want_m) <= 8e-4
         for block in BLOCKS:
-            for regs in (3,):
+            for regs in (2, 3):
                 lat.set_tuning("f16", "dslash", block, regs)
                 got = run()
                 for g, w in zip(got, ref):
-                    assert np.array_equal(g, w), (block, regs, dims, bc)
+                    assert np.array_equal(g, w), (block, regs, dims, bc, compress)
 
 
+@pytest.mark.parametrize("compress", [True, False, "long"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 6, 4, 12)])
-def test_solvers_with_the_pair_form(dims):
+def test_solvers_with_the_pair_form(dims, compress):
     mass = 0.1
     Vh = int(np.prod(dims)) // 2
     U = synth.su3_field(dims, 0.3, 44).numpy()
@@ -76,7 +79,7 @@ def test_solvers_with_the_pair_form(dims):
         return np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
 
     with stag.Lattice(dims) as lat:
-        lat.upload_gauge(U, N, precisions=("df64", "f16"), compress12=True)
+        lat.upload_gauge(U, N, precisions=("df64", "f16"), compress12=compress)
         fb = lat.field(stag.EVEN, "df64", b)
         iters = {}
         for block in (64, 256):
