@@ -801,9 +801,10 @@ MIXED_DELTA = 0.1
 def mixed_comparison(local, rank, cg_launch):
     """Time to a 1e-10 true residual on the 48^3x96, m = 0.01, eps = 0.35
     workload: double-float CG against mixed precision (FP32 and 16-bit inner
-    iterations with double-float reliable updates, delta = 0.1).  One warm-up
-    and one timed solve each; the true residual of every returned x is
-    recomputed in double-float."""
+    iterations with double-float reliable updates, delta = 0.1) on full
+    links, on 12-real links and (16-bit) on 12-real three-link links only.
+    One warm-up and one timed solve each; the true residual of every
+    returned x is recomputed in double-float."""
     import torch
     from paper_1411_2087_gb300 import stag, synth
     dev = torch.device("cuda", local)
@@ -851,8 +852,16 @@ def mixed_comparison(local, rank, cg_launch):
         for p in ("f32", "f16"):
             lat.autotune(p)
         run_all("_c12", runs[1:])
+        # 12-real three-link links only, full one-link links (the form for
+        # smeared fat links, which are not in SU(3))
+        U = synth.su3_field(MIXED_DIMS, MIXED_EPS, 1002, device=dev)
+        lat.upload_gauge(U, None, precisions=("df64", "f16"), compress12="long")
+        del U
+        torch.cuda.empty_cache()
+        lat.autotune("f16")
+        run_all("_c12long", runs[2:])
         base = out["fp64_df64"]["seconds"]
-        for name in ("mixed_f32", "mixed_f16", "mixed_f32_c12", "mixed_f16_c12"):
+        for name in ("mixed_f32", "mixed_f16", "mixed_f32_c12", "mixed_f16_c12", "mixed_f16_c12long"):
             out[name]["speedup_vs_fp64"] = round(base / out[name]["seconds"], 3)
     return out
 
