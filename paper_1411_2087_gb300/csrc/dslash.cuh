@@ -87,15 +87,23 @@ template <int P, int CM>
 STAG_D void load_link(const void *G, int kind, int S, int idx, float ls, float inv_s,
                       cplx<typename Fmt<P>::R> L[9]) {
     using F = Fmt<P>;
-    const char *kb = (const char *)G + link_kind_offset(P, CM, kind, (size_t)S);
+    using E = typename F::Elem;
+    const E *Lp;
     if constexpr (CM != 0) {
+        const char *kb = (const char *)G + link_kind_offset(P, CM, kind, (size_t)S);
         if ((CM >> (kind >> 2)) & 1) {
             C12<P>::load(kb, S, idx, ls, L);
             reconstruct_row2(L, inv_s);
             return;
         }
+        Lp = (const E *)kb + idx;
+    } else {
+        // all kinds full: a 32-bit element offset (72 planes of one parity
+        // fit, the lattice checks it).  With the 64-bit byte offset the
+        // compiler kept the sixteen links' addresses live and the
+        // double-float stencil grew from 80 to 116 registers.
+        Lp = (const E *)G + (kind * 9 * S + idx);
     }
-    const typename F::Elem *Lp = (const typename F::Elem *)kb + idx;
 #pragma unroll
     for (int e = 0; e < 9; e++)
         L[e] = F::unpack_link(ld_stream(Lp + e * S), ls);
