@@ -1294,6 +1294,22 @@ static std::string tune_key(const stag_lattice lat, int prec) {
 // (lines of other formats, such as those of earlier candidate sets, are ignored)
 static const char *tune_file() { return getenv("STAG_TUNE_CACHE"); }
 
+// a choice read from the file is applied only if stag_lattice_set_tuning
+// would accept each of its parts (a batched group beyond the kernels' size
+// would overrun the per-group arrays)
+static bool tune_choice_valid(int prec, const TuneChoice &c) {
+    auto block_ok = [](int b) { return b == 64 || b == 128 || b == 256 || b == 512; };
+    auto regs_ok = [](int r) { return r >= REGS_DEFAULT && r <= REGS_PAIR; };
+    if (!prec_valid(prec) || !block_ok(c.dblock) || !block_ok(c.mblock) || !regs_ok(c.dregs) ||
+        !regs_ok(c.mregs))
+        return false;
+    if (c.bblock == 0)
+        return c.bk == 0;
+    if (prec == STAG_F16 || (c.bblock != 128 && c.bblock != 256))
+        return false;
+    return c.bk == 0 || (c.bk >= batch_min_k(prec) && c.bk <= batch_max_k(prec) && (c.bk & (c.bk - 1)) == 0);
+}
+
 static void tune_file_read_locked() {
     if (g_tune_file_read)
         return;
@@ -1310,7 +1326,8 @@ static void tune_file_read_locked() {
         char dev[200];
         TuneChoice c;
         if (sscanf(line, "stag-tune2 %d %d %d %d %d %d %199s %d %d %d %d %d %d", &d[0], &d[1], &d[2], &d[3], &prec,
-                   &comp, dev, &c.dblock, &c.dregs, &c.mblock, &c.mregs, &c.bblock, &c.bk) == 13) {
+                   &comp, dev, &c.dblock, &c.dregs, &c.mblock, &c.mregs, &c.bblock, &c.bk) == 13 &&
+            tune_choice_valid(prec, c)) {
             char key[256];
             snprintf(key, sizeof key, "%d %d %d %d %d %d %s", d[0], d[1], d[2], d[3], prec, comp, dev);
             g_tune_cache[key] = c;

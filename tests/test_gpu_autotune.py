@@ -161,3 +161,30 @@ def test_pair_candidate_only_where_it_applies(dims, pairs):
             assert len(regs) == (12 if pairs else 8)
             assert (3 in regs) == pairs
         assert not any(r["kernel"] == "batch" for r in res)
+
+
+def test_cache_file_lines_out_of_range_are_ignored(tmp_path):
+    """A cache line whose choices stag_lattice_set_tuning would refuse (a
+    block size or batched group the kernels do not have) is not applied: the
+    next process times the candidates again."""
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, ROOT=ROOT, STAG_TUNE_CACHE=str(path))
+    p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    first = json.loads(p.stdout.strip().splitlines()[-1])
+    key = " ".join(path.read_text().split()[1:8])
+    bad = [f"stag-tune2 {key} 1000 0 128 0 128 8",   # no 1000-thread Dslash
+           f"stag-tune2 {key} 128 0 128 7 128 8",    # no register variant 7
+           f"stag-tune2 {key} 128 0 128 0 128 64"]   # a group beyond the kernels' arrays
+    path.write_text("\n".join(bad) + "\n")
+    p = subprocess.run([sys.executable, "-c", CHILD], env=env, capture_output=True, text=True, timeout=300)
+    assert p.returncode == 0, p.stderr
+    out = json.loads(p.stdout.strip().splitlines()[-1])
+    assert not out["cached"]
+    for r in out["chosen"]:
+        assert r["block"] in (64, 128, 256, 512) and 0 <= r["regs"] <= 3
+        if r["kernel"] == "batch":
+            assert r["group"] in (4, 8)
+    assert len(first["chosen"]) == len(out["chosen"])
+    lines = path.read_text().splitlines()
+    assert len(lines) == 4 and lines[3].startswith("stag-tune2 6 6 4 8 1 0 ")
