@@ -423,14 +423,20 @@ def dd_section(local, rank, world, pg, steps):
     if DIMS[3] // world < 3:
         return {"skipped": f"{world} ranks leave slabs thinner than 3 of {DIMS[3]} slices"}
     dev = torch.device("cuda", local)
-    try:
-        uid = stag.nccl_unique_id() if rank == 0 else None
-    except stag.StagError as e:
-        return {"skipped": str(e)}
+    # rank 0 makes the NCCL id; every rank learns the id or why there is
+    # none, so that no rank waits in the broadcast for one that gave up
+    uid, err = None, None
+    if rank == 0:
+        try:
+            uid = stag.nccl_unique_id()
+        except stag.StagError as e:
+            err = str(e)
     if pg is not None:
-        box = [uid]
+        box = [(uid, err)]
         pg.broadcast_object_list(box, src=0)
-        uid = box[0]
+        uid, err = box[0]
+    if err is not None:
+        return {"skipped": err}
     U, b_host = make_inputs(DIMS, dev, 0)
     torch.cuda.synchronize()
     Vh = int(np.prod(DIMS)) // 2
