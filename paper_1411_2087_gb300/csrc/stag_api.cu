@@ -44,6 +44,11 @@ extern "C" int stag_lattice_create(stag_lattice *out, const int dims[4], const d
         if (V > (1LL << 31) - 2)
             return fail(STAG_ERR_ARG, "stag_lattice_create: volume too large");
     }
+    // 72 component planes of one parity must be addressable with 32-bit offsets
+    const long long Vh = V / 2;
+    const long long stride = (Vh + 255) / 256 * 256;
+    if (72 * stride >= (1LL << 31))
+        return fail(STAG_ERR_ARG, "stag_lattice_create: volume too large for 32-bit link offsets");
     double bcv[4] = {1.0, 1.0, 1.0, -1.0};
     if (bc) {
         for (int k = 0; k < 4; k++) {
@@ -61,11 +66,6 @@ extern "C" int stag_lattice_create(stag_lattice *out, const int dims[4], const d
     }
     if (device >= ndev)
         return fail(STAG_ERR_ARG, "stag_lattice_create: device %d >= device count %d", device, ndev);
-    // 72 component planes of one parity must be addressable with 32-bit offsets
-    const long long Vh = V / 2;
-    const long long stride = (Vh + 255) / 256 * 256;
-    if (72 * stride >= (1LL << 31))
-        return fail(STAG_ERR_ARG, "stag_lattice_create: volume too large for 32-bit link offsets");
 
     DEVICE_SCOPE(device);
     stag_lattice lat = new (std::nothrow) stag_lattice_s();

@@ -51,6 +51,20 @@ def test_lattice_create_rejects_bad_dims(L, dims):
     assert b"dims" in L.stag_last_error_message()
 
 
+def test_lattice_size_limit_of_32bit_link_offsets(L):
+    """The kernels address the 72 link planes of one parity with 32-bit
+    offsets: 64^3 x 226 (72 x 29,622,272 planes < 2^31) passes the argument
+    checks (and stops at the missing device here), 64^3 x 228 is refused
+    before any CUDA call."""
+    h = ctypes.c_void_p()
+    ok = (ctypes.c_int * 4)(64, 64, 64, 226)
+    assert L.stag_lattice_create(ctypes.byref(h), ok, None, 0, None) == stag.ERR_CUDA
+    big = (ctypes.c_int * 4)(64, 64, 64, 228)
+    assert L.stag_lattice_create(ctypes.byref(h), big, None, 0, None) == stag.ERR_ARG
+    assert b"32-bit link offsets" in L.stag_last_error_message()
+    assert h.value is None
+
+
 def test_lattice_create_rejects_bad_bc_and_null(L):
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(4, 4, 4, 4)

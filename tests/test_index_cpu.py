@@ -56,3 +56,37 @@ def test_arguments_are_checked():
         with pytest.raises(stag.StagError) as e:
             stag.cb_neighbor(*bad)
         assert e.value.status == stag.ERR_ARG
+
+
+def decode(dims, par, cb):
+    """Coordinates of checkerboard site cb of parity par, by integer division."""
+    Lx, Ly, Lz, Lt = dims
+    xh, r = cb % (Lx // 2), cb // (Lx // 2)
+    y, r = r % Ly, r // Ly
+    z, t = r % Lz, r // Lz
+    x = 2 * xh + ((par + y + z + t) & 1)
+    return [x, y, z, t]
+
+
+@pytest.mark.parametrize("dims", [(64, 64, 64, 226), (94, 62, 58, 122), (2, 2, 2, 4096), (4096, 2, 2, 2)])
+def test_large_lattices_sampled(dims):
+    """The decode divides by multiply and shift; at the largest lattice a
+    lattice object accepts (64^3 x 226) and at extents that are not powers
+    of two, sampled sites (and the last ones of each parity) hop where the
+    integer definition says."""
+    Vh = int(np.prod(dims)) // 2
+    rng = np.random.default_rng(11)
+    cbs = list(rng.integers(0, Vh, 400)) + [0, 1, Vh - 2, Vh - 1]
+    for cb in cbs:
+        cb = int(cb)
+        for par in (0, 1):
+            xs = decode(dims, par, cb)
+            for mu in range(4):
+                for s in (1, -1, 3, -3):
+                    y = list(xs)
+                    raw = xs[mu] + s
+                    y[mu] = raw % dims[mu]
+                    wraps = abs(raw // dims[mu]) if raw < 0 else raw // dims[mu]
+                    i = y[0] + dims[0] * (y[1] + dims[1] * (y[2] + dims[2] * y[3]))
+                    got_cb, got_w = stag.cb_neighbor(dims, par, cb, mu, s)
+                    assert (got_cb, got_w) == (i // 2, wraps), (dims, par, cb, xs, mu, s)
