@@ -597,6 +597,7 @@ def learned_comparison(local, rank, n_pairs, epochs):
         del U
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("learned_collect")
         # half the pairs from each of two sources, spread over the solve; a
         # request beyond what two solves hold (one pair per iteration) draws
         # further sources
@@ -612,10 +613,13 @@ def learned_comparison(local, rank, n_pairs, epochs):
             fb.destroy()
             src += 1
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         t1 = time.perf_counter()
         net.set_loss("residual")
+        torch.cuda.nvtx.range_push("learned_train")
         hist = net.train(epochs=epochs, batch=8, lr=1e-2, seed=3)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         t2 = time.perf_counter()
         b = synth.gaussian_colour_field(Vh, 1500 + rank)
         fb = lat.field(stag.EVEN, "df64", b)

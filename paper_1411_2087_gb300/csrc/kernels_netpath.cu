@@ -703,19 +703,28 @@ net_grad_kernel(Geom g, const float2 *__restrict__ NL, const float2 *__restrict_
                                (red[0].y + red[1].y) + (red[2].y + red[3].y));
 }
 
-// G[q] += sum over blocks of partial[blk * 65 + q], in block order
-__global__ void net_grad_finish_kernel(const double2 *__restrict__ partial, int nblk, double2 *G) {
-    const int q = threadIdx.x;
-    if (q >= 65)
-        return;
-    double2 t = make_double2(0.0, 0.0);
-    for (int b = 0; b < nblk; b++) {
+// G[q] += sum over blocks of partial[blk * 65 + q]: block q sums its
+// coefficient, thread t the blocks t, t + 256, ... in order, then the block
+// tree (a fixed order, so the sum is the same on every run).  One thread per
+// coefficient summing all blocks serially took 160 us per call at 32^3x64.
+constexpr int GRAD_FINISH_BLOCK = 256;
+
+__global__ void __launch_bounds__(GRAD_FINISH_BLOCK)
+net_grad_finish_kernel(const double2 *__restrict__ partial, int nblk, double2 *G) {
+    __shared__ double smem[32];
+    const int q = blockIdx.x;
+    double tx = 0.0, ty = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += GRAD_FINISH_BLOCK) {
         const double2 v = partial[(size_t)b * 65 + q];
-        t.x += v.x;
-        t.y += v.y;
+        tx += v.x;
+        ty += v.y;
     }
-    G[q].x += t.x;
-    G[q].y += t.y;
+    tx = block_sum<GRAD_FINISH_BLOCK>(tx, smem);
+    ty = block_sum<GRAD_FINISH_BLOCK>(ty, smem);
+    if (threadIdx.x == 0) {
+        G[q].x += tx;
+        G[q].y += ty;
+    }
 }
 
 int net_grad_blocks(const Geom &g) {
@@ -727,94 +736,106 @@ cudaError_t launch_net_grad(const Geom &g, const float2 *NL32, const float2 *r, 
                             double2 *partial, double2 *G, cudaStream_t s) {
     const int nb = net_grad_blocks(g);
     net_grad_kernel<<<nb, NET_BLOCK, 0, s>>>(g, NL32, r, rs, gv, gs, partial);
-    net_grad_finish_kernel<<<1, 96, 0, s>>>(partial, nb, G);
+    net_grad_finish_kernel<<<65, GRAD_FINISH_BLOCK, 0, s>>>(partial, nb, G);
     return cudaGetLastError();
 }
 
 // ---- losses on the even sites (FP32) -----------------------------------------
 // error loss: g = (z - e) / |e|^2, *loss += |z - e|^2 / |e|^2 (z, g: stride zs;
 // e: stride es)
-__global__ void net_error_loss_kernel(int Vh, const float2 *__restrict__ z, int zs, const float2 *__restrict__ e,
-                                      int es, const double *enorm2, float2 *gv, double *loss) {
+// Loss and dot sums: each site's six products are summed in FP32, the sites
+// of a thread and the block tree in double float (FP32 pipe), one FP64
+// value and one atomic per block.  Accumulated in FP64 per element, with one
+// atomic per warp, these kernels took 66-73 us per call at 32^3x64, bound by
+// the FP64 pipe (1/64 of the FP32 rate).
+constexpr int NET_SUM_BLOCK = 256;
+
+__global__ void __launch_bounds__(NET_SUM_BLOCK)
+net_error_loss_kernel(int Vh, const float2 *__restrict__ z, int zs, const float2 *__restrict__ e, int es,
+                      const double *enorm2, float2 *gv, double *loss) {
+    __shared__ double smem[32];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    double part = 0.0;
+    const double n2 = *enorm2;
+    float part = 0.f;
     if (c < Vh) {
-        const double n2 = *enorm2;
         // a pair with e = 0 carries no information: no loss, no gradient
         const float inv = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const float2 zv = z[(size_t)k * zs + c], ev = e[(size_t)k * es + c];
             const float2 d = make_float2(zv.x - ev.x, zv.y - ev.y);
-            part += (double)d.x * d.x + (double)d.y * d.y;
+            part = fmaf(d.x, d.x, fmaf(d.y, d.y, part));
             gv[(size_t)k * zs + c] = make_float2(d.x * inv, d.y * inv);
         }
-        part *= n2 > 0.0 ? 1.0 / n2 : 0.0;
     }
-    for (int o = 16; o > 0; o >>= 1)
-        part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part != 0.0)
-        atomicAdd(loss, part);
+    const double tot = block_sum<NET_SUM_BLOCK>(df_make(part, 0.f), smem);
+    if (threadIdx.x == 0 && tot != 0.0 && n2 > 0.0)
+        atomicAdd(loss, tot / n2);
 }
 
 // residual loss: q = (Mz - r) / |r|^2 written over mz, *loss += |Mz - r|^2 / |r|^2
-__global__ void net_resid_loss_kernel(int Vh, float2 *mz, int ms, const float2 *__restrict__ r, int rs,
-                                      const double *rnorm2, double *loss) {
+__global__ void __launch_bounds__(NET_SUM_BLOCK)
+net_resid_loss_kernel(int Vh, float2 *mz, int ms, const float2 *__restrict__ r, int rs,
+                      const double *rnorm2, double *loss) {
+    __shared__ double smem[32];
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    double part = 0.0;
+    const double n2 = *rnorm2;
+    float part = 0.f;
     if (c < Vh) {
-        const double n2 = *rnorm2;
         const float inv = n2 > 0.0 ? (float)(1.0 / n2) : 0.f;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const float2 m = mz[(size_t)k * ms + c], rv = r[(size_t)k * rs + c];
             const float2 q = make_float2(m.x - rv.x, m.y - rv.y);
-            part += (double)q.x * q.x + (double)q.y * q.y;
+            part = fmaf(q.x, q.x, fmaf(q.y, q.y, part));
             mz[(size_t)k * ms + c] = make_float2(q.x * inv, q.y * inv);
         }
-        part *= n2 > 0.0 ? 1.0 / n2 : 0.0;
     }
-    for (int o = 16; o > 0; o >>= 1)
-        part += __shfl_down_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0 && part != 0.0)
-        atomicAdd(loss, part);
+    const double tot = block_sum<NET_SUM_BLOCK>(df_make(part, 0.f), smem);
+    if (threadIdx.x == 0 && tot != 0.0 && n2 > 0.0)
+        atomicAdd(loss, tot / n2);
 }
 
 // out[0] += Re<a, b>, out[1] += |a|^2 (even FP32 vectors of strides as, bs)
-__global__ void net_dot2_kernel(int Vh, const float2 *__restrict__ a, int as, const float2 *__restrict__ b, int bs,
-                                double *out) {
-    double p0 = 0.0, p1 = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Vh; c += gridDim.x * blockDim.x)
+__global__ void __launch_bounds__(NET_SUM_BLOCK)
+net_dot2_kernel(int Vh, const float2 *__restrict__ a, int as, const float2 *__restrict__ b, int bs, double *out) {
+    __shared__ double smem[32];
+    df p0 = df_zero(), p1 = df_zero();
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < Vh; c += gridDim.x * blockDim.x) {
+        float s0 = 0.f, s1 = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             const float2 x = a[(size_t)k * as + c], y = b[(size_t)k * bs + c];
-            p0 += (double)x.x * y.x + (double)x.y * y.y;
-            p1 += (double)x.x * x.x + (double)x.y * x.y;
+            s0 = fmaf(x.x, y.x, fmaf(x.y, y.y, s0));
+            s1 = fmaf(x.x, x.x, fmaf(x.y, x.y, s1));
         }
-    for (int o = 16; o > 0; o >>= 1) {
-        p0 += __shfl_down_sync(0xffffffffu, p0, o);
-        p1 += __shfl_down_sync(0xffffffffu, p1, o);
+        p0 = df_add(p0, df_make(s0, 0.f));
+        p1 = df_add(p1, df_make(s1, 0.f));
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(out, p0);
-        atomicAdd(out + 1, p1);
+    const double t0 = block_sum<NET_SUM_BLOCK>(p0, smem);
+    const double t1 = block_sum<NET_SUM_BLOCK>(p1, smem);
+    if (threadIdx.x == 0) {
+        atomicAdd(out, t0);
+        atomicAdd(out + 1, t1);
     }
 }
 
 cudaError_t launch_net_error_loss(int Vh, const float2 *z, int zs, const float2 *e, int es, const double *enorm2,
                                   float2 *gv, double *loss, cudaStream_t s) {
-    net_error_loss_kernel<<<(Vh + 255) / 256, 256, 0, s>>>(Vh, z, zs, e, es, enorm2, gv, loss);
+    net_error_loss_kernel<<<(Vh + NET_SUM_BLOCK - 1) / NET_SUM_BLOCK, NET_SUM_BLOCK, 0, s>>>(Vh, z, zs, e, es,
+                                                                                         enorm2, gv, loss);
     return cudaGetLastError();
 }
 
 cudaError_t launch_net_resid_loss(int Vh, float2 *mz, int ms, const float2 *r, int rs, const double *rnorm2,
                                   double *loss, cudaStream_t s) {
-    net_resid_loss_kernel<<<(Vh + 255) / 256, 256, 0, s>>>(Vh, mz, ms, r, rs, rnorm2, loss);
+    net_resid_loss_kernel<<<(Vh + NET_SUM_BLOCK - 1) / NET_SUM_BLOCK, NET_SUM_BLOCK, 0, s>>>(Vh, mz, ms, r, rs,
+                                                                                         rnorm2, loss);
     return cudaGetLastError();
 }
 
 cudaError_t launch_net_dot2(int Vh, const float2 *a, int as, const float2 *b, int bs, double *out, cudaStream_t s) {
-    net_dot2_kernel<<<256, 256, 0, s>>>(Vh, a, as, b, bs, out);
+    net_dot2_kernel<<<4 * 152, NET_SUM_BLOCK, 0, s>>>(Vh, a, as, b, bs, out);
     return cudaGetLastError();
 }
 
