@@ -378,12 +378,18 @@ int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double 
  * full lattice, no nonlinearity:
  *
  *   y_o(x) = sum_i [ W[0][o][i] psi_i(x)
- *                    + sum_mu ( W[1+2mu][o][i] U_mu(x) psi_i(x+mu)
- *                             + W[2+2mu][o][i] U_mu(x-mu)^+ psi_i(x-mu) ) ]
+ *                    + sum_mu ( W[1+2mu][o][i] V_mu(x) psi_i(x+mu)
+ *                             + W[2+2mu][o][i] V_mu(x-mu)^+ psi_i(x-mu) ) ]
  *
- * with the raw fat links U (no phases or coefficients; the lattice's
- * boundary sign on wrapping hops) and complex colour-blind weights, so the
- * net is gauge covariant.  As a preconditioner it maps an even residual r
+ * with V_mu(x) = eta_mu(x) U_mu(x), the fat links with the Kogut-Susskind
+ * phases eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) and the lattice's boundary
+ * sign on wrapping hops (no coefficients), and complex colour-blind
+ * weights, so the net is gauge covariant.  The phases let the net's
+ * translation-invariant weights form the operator's own two-hop paths
+ * (D^2 = sum over hop pairs with constant coefficients on phased links),
+ * and with them a degree-one polynomial in M; on raw links the paths that
+ * turn from one direction to another carry site-dependent signs, and the
+ * trained net cut CG iterations 1.42x instead of 1.80x (32^3x64, m = 0.005).  As a preconditioner it maps an even residual r
  * (zero on odd sites) to z = N(r) restricted to the even sites.  Weights:
  * (re, im) doubles, layer 1 [9][C][1], layer 2 [9][C][C], layer 3 [9][1][C],
  * concatenated (9 * (2C + C^2) complex numbers).

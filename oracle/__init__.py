@@ -266,6 +266,21 @@ def covconv(dims, U, W, psi, bc=BC_DEFAULT) -> np.ndarray:
     return y
 
 
+def phased_links(dims, U) -> np.ndarray:
+    """eta_mu(x) U_mu(x) with the Kogut-Susskind phases
+    eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) (x fastest): the links the
+    library's net transports with (the boundary sign is applied by covconv)."""
+    d = [int(n) for n in dims]
+    V = volume(d)
+    t, z, y, x = np.meshgrid(*(np.arange(n) for n in d[::-1]), indexing="ij")
+    coords = [c.reshape(-1) for c in (x, y, z, t)]
+    out = np.array(_c(U, (4, V, 3, 3)), copy=True)
+    for mu in range(4):
+        esum = sum(coords[:mu], np.zeros(V, dtype=np.int64))
+        out[mu] *= np.where(esum % 2 == 1, -1.0, 1.0)[:, None, None]
+    return out
+
+
 def net_apply(dims, U, weights, r_even, bc=BC_DEFAULT) -> np.ndarray:
     """The preconditioner: r (even sites) zero-extended to the full lattice,
     the layers applied in order (no nonlinearity), the result restricted to

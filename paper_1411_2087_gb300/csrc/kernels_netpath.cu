@@ -97,7 +97,15 @@ STAG_D void nl_apply(const cplx<float> U[9], bool adj, const cplx<float> v[3], c
 }
 
 // canonical raw fat links complex128 [4][V][3][3] -> net links of both
-// parities; one thread per (mu, site).  inv_scale: 16-bit only.
+// parities, eta_mu(x) b U_mu(x): the Kogut-Susskind phase of the link's site
+// and the boundary sign of a wrapping forward hop folded in, no coefficient;
+// one thread per (mu, site).  inv_scale: 16-bit only.
+//
+// The phases make the net's two-hop paths those of the operator: the
+// product eta_mu(x) eta_nu(x + mu) of a path that turns from mu to nu
+// depends on the site, so with raw links translation-invariant weights
+// could only form the paths that keep their direction; with phased links
+// they can form D^2 itself, and with it a degree-one polynomial in M.
 template <class LT> STAG_D LT nl_pack(double re, double im, float inv_scale);
 template <> STAG_D float2 nl_pack<float2>(double re, double im, float) { return make_float2((float)re, (float)im); }
 template <> STAG_D short2 nl_pack<short2>(double re, double im, float inv) {
@@ -122,7 +130,10 @@ __global__ void net_links_cb_kernel(Geom g, double bc0, double bc1, double bc2, 
     x[3] = rr / g.L[2];
     const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
     const double bc[4] = {bc0, bc1, bc2, bc3};
-    const double sgn = (x[mu] == g.L[mu] - 1 && bc[mu] < 0) ? -1.0 : 1.0;
+    int esum = 0;
+    for (int nu = 0; nu < mu; nu++)
+        esum += x[nu];
+    const double sgn = ((x[mu] == g.L[mu] - 1 && bc[mu] < 0) ? -1.0 : 1.0) * ((esum & 1) ? -1.0 : 1.0);
     const int S = g.stride;
 #pragma unroll 1
     for (int e = 0; e < 9; e++) {

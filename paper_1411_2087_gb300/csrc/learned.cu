@@ -119,7 +119,7 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
             return st;
         }
     }
-    // net links from the raw fat links
+    // net links from the raw fat links (phases and boundary sign folded in)
     double *fat_d = (double *)fat;
     bool owned = false;
     if (ptr_kind == STAG_PTR_HOST) {

@@ -30,7 +30,8 @@ def test_forward_matches_oracle(dims, C):
     Vh = int(np.prod(dims)) // 2
     r = synth.gaussian_colour_field(Vh, 6).numpy()
     Ws = rand_weights(C, 7)
-    want = oracle.net_apply(dims, U, Ws, r)
+    # the net transports with the staggered-phased links
+    want = oracle.net_apply(dims, oracle.phased_links(dims, U), Ws, r)
     with stag.Lattice(dims) as lat:
         net = stag.Net(lat, U, channels=C)
         net.set_weights(Ws)
@@ -93,8 +94,9 @@ def test_gpu_net_is_gauge_covariant():
 
 def resid_loss_oracle(dims, U, N, mass, Ws, rs):
     tot = 0.0
+    Up = oracle.phased_links(dims, U)
     for r in rs:
-        z = oracle.net_apply(dims, U, Ws, r)
+        z = oracle.net_apply(dims, Up, Ws, r)
         q = oracle.apply_M(dims, U, N, mass, z) - r
         tot += float(np.vdot(q, q).real / np.vdot(r, r).real)
     return tot
@@ -123,8 +125,10 @@ def test_gradient_against_oracle_finite_differences(kind):
     rs = [p[0] for p in pairs]
     es = [p[1] for p in pairs]
     if kind == "error":
+        Up = oracle.phased_links(dims, U)
+
         def L(ws):
-            return oracle.net_loss(dims, U, ws, rs, es)
+            return oracle.net_loss(dims, Up, ws, rs, es)
     else:
         def L(ws):
             return resid_loss_oracle(dims, U, N, mass, ws, rs)
