@@ -405,7 +405,11 @@ int stag_lattice_autotune(stag_lattice lat, int prec, double *dslash_us, double 
  * even site) and trains the layer weights through it (the chain rule from
  * dL/dC* to dL/dW*).  FP32 arithmetic; inside the solver the weights are
  * rounded to binary16 and the links read from a 16-bit copy (fixed point,
- * one scale for the field). */
+ * one scale for the field).  When the fat links are special unitary (within
+ * 1e-6, checked at creation) that copy keeps rows 0 and 1 only and the
+ * kernels rebuild row 2 as s conj(row 0 x row 1), s = eta b the link's phase
+ * and boundary sign (the paper's 12-real compression, Sec. 4); otherwise
+ * all nine entries. */
 typedef struct stag_net_s *stag_net;
 
 /* Create a net with C = channels (1, 2, 4 or 8) on `lat` from the raw fat

@@ -67,6 +67,58 @@ STAG_D void nl_load<short2>(const short2 *__restrict__ NL, int S, int par, int m
         U[e] = cplx<float>{q_lo(w[e]), q_hi(w[e])};
 }
 
+// 12-real 16-bit links (special unitary fat links): per (par, mu) an int4
+// plane with entries 0..3 and an int2 plane with entries 4, 5 (rows 0 and
+// 1); row 2 of V = s U (s = eta b = +-1, U in SU(3)) is s conj(r0 x r1), in
+// raw units k2 conj(q0 x q1) with k2 = s * scale
+struct L12 {
+    int4 v;
+};
+
+STAG_D const char *nl12_base(const void *NL, int S, int par, int mu) {
+    return (const char *)NL + (size_t)(par * 4 + mu) * 24 * S;
+}
+
+STAG_D void nl_load12(const L12 *__restrict__ NL, int S, int par, int mu, int c, float k2, cplx<float> U[9]) {
+    const char *base = nl12_base(NL, S, par, mu);
+    const int4 a = ld_stream((const int4 *)base + c);
+    const int2 b = ld_stream((const int2 *)(base + (size_t)16 * S) + c);
+    const int w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+    for (int e = 0; e < 6; e++)
+        U[e] = cplx<float>{q_lo(w[e]), q_hi(w[e])};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        const int k = (j + 1) % 3, l = (j + 2) % 3;
+        // X_j = r0_k r1_l - r0_l r1_k; row 2 entry j = k2 conj(X_j)
+        const float re = U[k].re * U[3 + l].re - U[k].im * U[3 + l].im - (U[l].re * U[3 + k].re - U[l].im * U[3 + k].im);
+        const float im = U[k].re * U[3 + l].im + U[k].im * U[3 + l].re - (U[l].re * U[3 + k].im + U[l].im * U[3 + k].re);
+        U[6 + j] = cplx<float>{k2 * re, -k2 * im};
+    }
+}
+
+// s = eta_mu(x) b of the link a hop of the net takes from site x: its own
+// link (bw = 0; b = -1 when it wraps forward, x_mu = L - 1) or the link of
+// x - mu (bw = 1; that link wraps when x_mu = 0); eta_mu(x - mu) = eta_mu(x)
+STAG_D float nl_link_sign(const Geom &g, const int x[4], int mu, int bw, int bcneg) {
+    int esum = 0;
+#pragma unroll
+    for (int nu = 0; nu < mu; nu++)
+        esum += x[nu];
+    const bool wrap = ((bcneg >> mu) & 1) && (bw ? x[mu] == 0 : x[mu] == g.L[mu] - 1);
+    return ((esum & 1) ^ (wrap ? 1 : 0)) ? -1.f : 1.f;
+}
+
+// link V_mu (or the one the hop bw takes) of any layout, in raw units
+template <class LT>
+STAG_D void net_link(const LT *__restrict__ NL, int S, int par, int mu, int idx, const Geom &g, const int x[4],
+                     int bw, float ls, int bcneg, cplx<float> U[9]) {
+    if constexpr (std::is_same<LT, L12>::value)
+        nl_load12(NL, S, par, mu, idx, nl_link_sign(g, x, mu, bw, bcneg) * ls, U);
+    else
+        nl_load(NL, S, par, mu, idx, U);
+}
+
 // the address of element e of U_mu at (par, c) in either layout
 STAG_D float2 *nl_slot(float2 *NL, int S, int par, int mu, int c, int e) {
     return NL + (size_t)((par * 4 + mu) * 9 + e) * S + c;
@@ -140,6 +192,54 @@ __global__ void net_links_cb_kernel(Geom g, double bc0, double bc1, double bc2, 
         const double2 u = fat[((size_t)mu * V + i) * 9 + e];
         *nl_slot(NL, S, par, mu, i >> 1, e) = nl_pack<LT>(sgn * u.x, sgn * u.y, inv_scale);
     }
+}
+
+// rows 0 and 1 of eta_mu(x) b U_mu(x) into the 12-real 16-bit planes
+__global__ void net_links12_kernel(Geom g, double bc0, double bc1, double bc2, double bc3,
+                                   const double2 *__restrict__ fat, char *NL, float inv_scale) {
+    const long long V = 2LL * g.Vh;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V)
+        return;
+    const int mu = (int)(t / V);
+    const int i = (int)(t % V);
+    int x[4];
+    x[0] = i % g.L[0];
+    int rr = i / g.L[0];
+    x[1] = rr % g.L[1];
+    rr /= g.L[1];
+    x[2] = rr % g.L[2];
+    x[3] = rr / g.L[2];
+    const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const double bc[4] = {bc0, bc1, bc2, bc3};
+    int esum = 0;
+    for (int nu = 0; nu < mu; nu++)
+        esum += x[nu];
+    const double sgn = ((x[mu] == g.L[mu] - 1 && bc[mu] < 0) ? -1.0 : 1.0) * ((esum & 1) ? -1.0 : 1.0);
+    const size_t S = (size_t)g.stride;
+    char *base = NL + (size_t)(par * 4 + mu) * 24 * S;
+    short2 q[6];
+    for (int e = 0; e < 6; e++) {
+        const double2 u = fat[((size_t)mu * V + i) * 9 + e];
+        q[e] = nl_pack<short2>(sgn * u.x, sgn * u.y, inv_scale);
+    }
+    short2 *p4 = (short2 *)base + (size_t)(i >> 1) * 4;
+    for (int e = 0; e < 4; e++)
+        p4[e] = q[e];
+    short2 *p2 = (short2 *)(base + 16 * S) + (size_t)(i >> 1) * 2;
+    p2[0] = q[4];
+    p2[1] = q[5];
+}
+
+size_t net_links12_bytes(const Geom &g) { return (size_t)2 * 4 * 24 * (size_t)g.stride; }
+
+cudaError_t launch_net_links12(const Geom &g, const double bc[4], const double *fat, void *NL12, float inv_scale16,
+                               cudaStream_t s) {
+    const long long n = 8LL * g.Vh;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    net_links12_kernel<<<grid, 256, 0, s>>>(g, bc[0], bc[1], bc[2], bc[3], (const double2 *)fat, (char *)NL12,
+                                            inv_scale16);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double *fat, float2 *NL32, short2 *NL16,
@@ -343,6 +443,7 @@ template <> struct Chi<short2> {
         return __int_as_float(t.w) * (1.f / kQ16);
     }
 };
+template <> struct Chi<L12> : Chi<short2> {};
 
 // chi_a(y) = sum_b C[a][b] (T_b r)(y) on the odd sites; r even (precision P,
 // component stride rs).  Hop index b = 2 mu (+mu) or 2 mu + 1 (-mu).  ls: the
@@ -356,7 +457,7 @@ constexpr int NET_MID_MINB = 6;
 
 template <int P, class LT>
 __global__ void __launch_bounds__(NET_BLOCK, NET_MID_MINB)
-net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
+net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, int bcneg, const NetPath *__restrict__ path,
                const typename Fmt<P>::Elem *__restrict__ r, int rs, void *__restrict__ chi, const int *gate) {
     __shared__ cplx<float> sC[64];
     __shared__ float2 sh[8][3][NET_BLOCK];
@@ -386,14 +487,14 @@ net_mid_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 v[k] = to_f(vr[k]);
-            nl_load(NL, S, bw ? 0 : 1, mu, bw ? j : c, U);
+            net_link(NL, S, bw ? 0 : 1, mu, bw ? j : c, g, x, bw, ls, bcneg, U);
             nl_apply(U, bw, v, h);
 #pragma unroll
             for (int k = 0; k < 3; k++)
                 sh[2 * mu + bw][k][threadIdx.x] = make_float2(h[k].re, h[k].im);
         }
     }
-    if constexpr (!std::is_same<LT, short2>::value) {
+    if constexpr (std::is_same<LT, float2>::value) {
         // FP32 links (training): the scalar mixing, channel by channel
         cplx<float> h[8][3];
 #pragma unroll
@@ -466,7 +567,7 @@ enum { NET_OUT_PLAIN = 0, NET_OUT_DOTS = 1 };
 
 template <int PI, int PO, class LT, int EPI>
 __global__ void __launch_bounds__(NET_BLOCK)
-net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__restrict__ path,
+net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, int bcneg, const NetPath *__restrict__ path,
                const void *__restrict__ chi, const typename Fmt<PI>::Elem *__restrict__ r, int rs,
                typename Fmt<PO>::Elem *__restrict__ z, int zs, const typename Fmt<PO>::Elem *__restrict__ Ap,
                double *partial, const int *gate) {
@@ -489,7 +590,7 @@ net_out_kernel(Geom g, const LT *__restrict__ NL, float ls, const NetPath *__res
                 const int j = cb_hop(g, c, x, mu, bw ? -1 : 1);
                 cplx<float> v[3], U[9], h[3];
                 const float f = Chi<LT>::load(chi, S, 2 * mu + bw, j, v);
-                nl_load(NL, S, bw ? 1 : 0, mu, bw ? j : c, U);
+                net_link(NL, S, bw ? 1 : 0, mu, bw ? j : c, g, x, bw, ls, bcneg, U);
                 nl_apply(U, bw, v, h);
 #pragma unroll
                 for (int k = 0; k < 3; k++) {
@@ -548,12 +649,15 @@ cudaError_t launch_net_mid(int prec, const Geom &g, const NetLinkSet &nl, const 
                            int rs, void *chi, const int *gate, cudaStream_t s) {
     NP_IN_SWITCH(prec, {
         using E = typename Fmt<P>::Elem;
-        if (nl.l16)
-            net_mid_kernel<P, short2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l16, nl.scale16, path,
+        if (nl.l12)
+            net_mid_kernel<P, L12><<<net_grid(g), NET_BLOCK, 0, s>>>(g, (const L12 *)nl.l12, nl.scale16, nl.bcneg,
+                                                                      path, (const E *)r, rs, chi, gate);
+        else if (nl.l16)
+            net_mid_kernel<P, short2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l16, nl.scale16, nl.bcneg, path,
                                                                          (const E *)r, rs, chi, gate);
         else
-            net_mid_kernel<P, float2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l32, 1.f, path, (const E *)r, rs,
-                                                                         chi, gate);
+            net_mid_kernel<P, float2><<<net_grid(g), NET_BLOCK, 0, s>>>(g, nl.l32, 1.f, nl.bcneg, path,
+                                                                         (const E *)r, rs, chi, gate);
     });
     return cudaGetLastError();
 }
@@ -563,12 +667,17 @@ static void net_out_t(const Geom &g, const NetLinkSet &nl, const NetPath *path, 
                       int rs, void *z, int zs, const void *Ap, double *partial, const int *gate, cudaStream_t s) {
     using EI = typename Fmt<PI>::Elem;
     using EO = typename Fmt<PO>::Elem;
-    if (nl.l16)
+    if (nl.l12)
+        net_out_kernel<PI, PO, L12, EPI><<<net_grid(g), NET_BLOCK, 0, s>>>(
+            g, (const L12 *)nl.l12, nl.scale16, nl.bcneg, path, chi, (const EI *)r, rs, (EO *)z, zs,
+            (const EO *)Ap, partial, gate);
+    else if (nl.l16)
         net_out_kernel<PI, PO, short2, EPI><<<net_grid(g), NET_BLOCK, 0, s>>>(
-            g, nl.l16, nl.scale16, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial, gate);
+            g, nl.l16, nl.scale16, nl.bcneg, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial,
+            gate);
     else
         net_out_kernel<PI, PO, float2, EPI><<<net_grid(g), NET_BLOCK, 0, s>>>(
-            g, nl.l32, 1.f, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial, gate);
+            g, nl.l32, 1.f, nl.bcneg, path, chi, (const EI *)r, rs, (EO *)z, zs, (const EO *)Ap, partial, gate);
 }
 
 // input and output of one precision (the solver's), or FP32 pair input with

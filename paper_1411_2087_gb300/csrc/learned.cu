@@ -16,7 +16,9 @@ struct stag_net_s {
     int C = 8;                    // hidden channels: layers 1 -> C -> C -> 1
     float2 *NL32 = nullptr;       // net links, FP32 [2][4][9][stride]
     short2 *NL16 = nullptr;       // the same in 16-bit fixed point
+    void *NL12 = nullptr;         // 16-bit rows 0 and 1 (special unitary fat links only)
     float scale16 = 0.f;          // 16-bit value = q * scale16
+    int bcneg = 0;                // bit mu: boundary sign of direction mu is -1
     int nw = 0;                   // complex weights in all layers
     int off[3] = {0, 0, 0};       // complex offset of each layer's weights
     double *w = nullptr;          // master weights (re, im), device
@@ -43,7 +45,7 @@ struct stag_net_s {
 };
 
 static void net_free(stag_net n) {
-    void *bufs[] = {n->NL32, n->NL16, n->w, n->w32, n->grad, n->m, n->v, n->path, n->chi, n->G, n->gpartial,
+    void *bufs[] = {n->NL32, n->NL16, n->NL12, n->w, n->w32, n->grad, n->m, n->v, n->path, n->chi, n->G, n->gpartial,
                     n->scal, n->enorm2, n->rnorm2, n->fz, n->fmz, n->ft};
     for (void *b : bufs)
         if (b)
@@ -152,8 +154,30 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
         return fail(STAG_ERR_ARG, "stag_net_create: links hold a NaN, an infinity or an entry beyond FP32");
     }
     n->scale16 = amax > 0.f ? amax / kQ16 : 1.f;
+    for (int k = 0; k < 4; k++)
+        n->bcneg |= lat->bc[k] < 0 ? 1 << k : 0;
     if (e == cudaSuccess)
         e = launch_net_links_cb(lat->geom, lat->bc, fat_d, n->NL32, n->NL16, amax > 0.f ? kQ16 / amax : 0.f, s);
+    // special unitary fat links (within 1e-6): the solver's 16-bit net links
+    // keep rows 0 and 1 only and the kernels rebuild row 2 (two thirds of
+    // the link bytes of the net's two stencil passes)
+    if (e == cudaSuccess)
+        e = launch_su3_deviation(fat_d, (long long)(4 * V), amax_d, s);
+    if (e == cudaSuccess) {
+        unsigned bits = 0;
+        e = cudaMemcpyAsync(&bits, amax_d, sizeof bits, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        float dev = 1.f;
+        memcpy(&dev, &bits, sizeof dev);
+        if (e == cudaSuccess && dev <= 1e-6f) {
+            e = cudaMalloc(&n->NL12, net_links12_bytes(lat->geom));
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(n->NL12, 0, net_links12_bytes(lat->geom), s);
+            if (e == cudaSuccess)
+                e = launch_net_links12(lat->geom, lat->bc, fat_d, n->NL12, amax > 0.f ? kQ16 / amax : 0.f, s);
+        }
+    }
     cudaError_t e2 = cudaStreamSynchronize(s);
     if (owned)
         cudaFree(fat_d);
@@ -236,8 +260,10 @@ extern "C" int stag_net_get_weights(const stag_net n, double *w) {
 static NetLinkSet net_links(const stag_net n, bool links16) {
     NetLinkSet s;
     s.l32 = n->NL32;
+    s.bcneg = n->bcneg;
     if (links16) {
         s.l16 = n->NL16;
+        s.l12 = n->NL12;
         s.scale16 = n->scale16;
     }
     return s;

@@ -13,15 +13,23 @@ struct NetPath {
     float2 c0;
 };
 
-// the net's link copies: FP32, and optionally 16-bit (used when l16 is set)
+// the net's link copies: FP32, and optionally 16-bit (used when l16 or l12
+// is set; l12 first)
 struct NetLinkSet {
     const float2 *l32 = nullptr;
     const short2 *l16 = nullptr;
-    float scale16 = 0.f;  // 16-bit value = q * scale16
+    const void *l12 = nullptr;  // 16-bit, rows 0 and 1 only (special unitary links)
+    float scale16 = 0.f;        // 16-bit value = q * scale16
+    int bcneg = 0;              // bit mu: the boundary sign of direction mu is -1
 };
 
 cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double *fat, float2 *NL32, short2 *NL16,
                                 float inv_scale16, cudaStream_t s);
+// rows 0 and 1 of the net links in 16-bit: per (parity, mu) an int4 plane
+// (entries 0..3) and an int2 plane (entries 4, 5), 24 stride bytes
+cudaError_t launch_net_links12(const Geom &g, const double bc[4], const double *fat, void *NL12, float inv_scale16,
+                               cudaStream_t s);
+size_t net_links12_bytes(const Geom &g);
 cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int round_half, NetPath *out,
                                  cudaStream_t s);
 cudaError_t launch_net_path_chain(int C, const float *w32, const int off[3], const double2 *G, double2 *grad,

@@ -64,6 +64,34 @@ def test_forward_matches_oracle(dims, C):
         net.close()
 
 
+@pytest.mark.parametrize("dims,bc,unitary", [((4, 4, 4, 8), (1.0, 1.0, 1.0, -1.0), True),
+                                             ((6, 4, 2, 4), (-1.0, 1.0, -1.0, -1.0), True),
+                                             ((4, 4, 4, 8), (1.0, 1.0, 1.0, -1.0), False)])
+def test_solver_form_links(dims, bc, unitary):
+    """The solver's 16-bit net links: with special unitary fat links the
+    kernels read rows 0 and 1 and rebuild row 2 with the link's phase and
+    boundary sign (every boundary-sign pattern of direction and wrap); with
+    other links they read all nine entries.  Both against the oracle's FP64
+    net on the phased links."""
+    U = synth.su3_field(dims, 0.4, 15).numpy()
+    if not unitary:
+        U = 0.97 * U
+    Vh = int(np.prod(dims)) // 2
+    r = synth.gaussian_colour_field(Vh, 16).numpy()
+    Ws = rand_weights(8, 17)
+    want = oracle.net_apply(dims, oracle.phased_links(dims, U), Ws, r, bc)
+    with stag.Lattice(dims, bc=bc) as lat:
+        net = stag.Net(lat, U, channels=8)
+        net.set_weights(Ws)
+        for prec in ("f32", "df64"):
+            fin = lat.field(stag.EVEN, prec, r)
+            fout = lat.field(stag.EVEN, prec)
+            net.apply(fout, fin, fp16_weights=True, links16=True)
+            err = np.abs(fout.export() - want).max() / np.abs(want).max()
+            assert err < 5e-3, (prec, err)
+        net.close()
+
+
 def test_gpu_net_is_gauge_covariant():
     dims = (4, 4, 4, 6)
     Vh = int(np.prod(dims)) // 2
