@@ -314,20 +314,19 @@ STAG_D void cp_async8(unsigned dst, const void *src) {
 STAG_D void cp_async4(unsigned dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
 }
-STAG_D void cp_async16ca(unsigned dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-}
 STAG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> STAG_D void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // cells per slot: 5 when every link is 12-real, 7 when some are full
 template <int CM> __host__ __device__ constexpr int pair16_cells() { return CM == 3 ? 5 : 7; }
 
-// ring depth: two hops in flight per thread (deeper rings measured slower
-// at 768 resident threads per SM), less where a block's ring would pass 40
-// KB of shared memory; 0: no pair form for this block size
+// ring depth: up to three hops in flight per thread while a block's ring
+// stays within 40 KB of shared memory (128-thread blocks: three hops, 30 KB;
+// 256: two), fewer beyond; 0: no pair form for this block size.  At 48^3x96
+// on 12-real links the 128-thread form took 368 us with three hops against
+// 373.5 us with two (four and more measured slower at 768 threads per SM).
 template <int BLOCK, int CM> __host__ __device__ constexpr int pair16_ring() {
-    return 40960 / (pair16_cells<CM>() * 16 * BLOCK) >= 2 ? 2 : 40960 / (pair16_cells<CM>() * 16 * BLOCK);
+    return 40960 / (pair16_cells<CM>() * 16 * BLOCK) >= 3 ? 3 : 40960 / (pair16_cells<CM>() * 16 * BLOCK);
 }
 
 // the indices of hop k = 4 mu + 2 h + dir (dir 1: backward) of the pair
@@ -395,8 +394,11 @@ STAG_D void pair16_issue(unsigned cell, const Geom &g, int c, const int x[4], in
         cp_async4(cell + 6 * R, k3 + (size_t)ia * 4);
         cp_async4(cell + 6 * R + 4, k3 + (size_t)ib * 4);
     }
-    cp_async16ca(cell + 2 * R, (const int4 *)in + ja);
-    cp_async16ca(cell + 3 * R, (const int4 *)in + jb);
+    // the neighbour cells bypass L1 like the links (at 48^3x96 on 12-real
+    // links 364 against 367 us with L1-allocating copies): their reuse is
+    // across blocks, in L2
+    cp_async16(cell + 2 * R, (const int4 *)in + ja);
+    cp_async16(cell + 3 * R, (const int4 *)in + jb);
 }
 
 // acc += D psi at sites c and c + H (c < H = Vh/2), loads through the ring
