@@ -415,7 +415,10 @@ typedef struct stag_net_s *stag_net;
 /* Create a net with C = channels (1, 2, 4 or 8) on `lat` from the raw fat
  * links (canonical complex128 [4][V][3][3]; a NaN, an infinity or an entry
  * beyond the FP32 range gives STAG_ERR_ARG).  Initial weights: the identity
- * map plus seeded N(0, 1e-2) noise.  Counts as a live object of the
+ * map plus seeded noise; with C = 8 layer 1 puts each hop in a channel of
+ * its own and layer 3 reads the identity path (noise N(0, 1e-3)), so that
+ * layer 3's hop weights set the two-hop paths linearly; with fewer channels
+ * the identity through every channel (noise N(0, 1e-2)).  Counts as a live object of the
  * lattice: destroy nets before their lattice. */
 int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind, int channels, unsigned seed,
                     stag_net *out);
@@ -462,14 +465,20 @@ int stag_net_loss_grad(stag_net n, int first, int count, double *loss, double *g
 /* Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean loss over mini-batches
  * of `batch` pairs for `epochs` passes over the collected pairs, shuffled
  * with `seed`; the step size decays from lr to lr/10 (cosine) over the
- * epochs.  With the residual loss, the first training call first rescales
+ * epochs, and over the net's first 100 Adam steps it ramps up linearly from
+ * lr/100 (so that a short run leaves the net near its start instead of
+ * throwing every weight by about lr per step).  With the residual loss, the
+ * first training call first rescales
  * the last layer by the least-squares optimal factor for the pairs.
  * epoch_loss (may be NULL) receives the mean loss per epoch. */
 int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss);
 
 /* Flexible CG (Notay; Polak-Ribiere beta on real inner products) for
- * M x = b with z = N(r) as the preconditioner (binary16 weights, 16-bit
- * links), from x0 = 0.  A run that
+ * M x = b with z = N_h(r) as the preconditioner, N_h = (N + N^+)/2 the
+ * Hermitian part of the net (binary16 weights, 16-bit links; CG's
+ * recurrences assume a Hermitian preconditioner, and a briefly trained net
+ * is far from Hermitian: at 32^3x64 its Hermitian part needed 229 CG
+ * iterations where the net itself needed 635), from x0 = 0.  A run that
  * claims convergence is checked against the recomputed residual and
  * restarted if they drifted apart; after a breakdown (<r, z> <= 0), or the
  * iteration limit, plain CG (z = r) continues from the current x.

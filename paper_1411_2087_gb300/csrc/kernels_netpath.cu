@@ -295,8 +295,12 @@ STAG_D double2 triple(const NetW &W, int d3, int d2, int d1) {
 // C[a][b] and thread 64 c0
 constexpr int NET_MAX_W = 9 * (2 * 8 + 8 * 8);
 
-__global__ void net_path_coef_kernel(NetW W, NetPath *out) {
+// hermitian: the coefficients of (N + N^+)/2 instead.  T_a^+ = T_abar (abar
+// = a ^ 1, the reversed hop), so N^+ has conj(c0) and the coefficient
+// conj(C[bbar][abar]) on T_a T_b.
+__global__ void net_path_coef_kernel(NetW W, int hermitian, NetPath *out) {
     __shared__ double2 sw[NET_MAX_W];
+    __shared__ double2 sc[65];
     const int nw = 9 * (2 * W.C + W.C * W.C);
     for (int k = threadIdx.x; k < nw; k += blockDim.x)
         sw[k] = W.load(k);
@@ -305,18 +309,29 @@ __global__ void net_path_coef_kernel(NetW W, NetPath *out) {
     const int q = threadIdx.x;
     if (q < 64) {
         const int a = q >> 3, b = q & 7;
-        const double2 v = zadd(zadd(triple(W, 0, a + 1, b + 1), triple(W, a + 1, 0, b + 1)), triple(W, a + 1, b + 1, 0));
+        sc[q] = zadd(zadd(triple(W, 0, a + 1, b + 1), triple(W, a + 1, 0, b + 1)), triple(W, a + 1, b + 1, 0));
+    } else if (q == 64) {
+        sc[64] = triple(W, 0, 0, 0);
+    }
+    __syncthreads();
+    if (q < 64) {
+        double2 v = sc[q];
+        if (hermitian) {
+            const int a = q >> 3, b = q & 7;
+            const double2 t = sc[(b ^ 1) * 8 + (a ^ 1)];
+            v = make_double2(0.5 * (v.x + t.x), 0.5 * (v.y - t.y));
+        }
         out->C[q] = make_float2((float)v.x, (float)v.y);
     } else if (q == 64) {
-        const double2 v = triple(W, 0, 0, 0);
-        out->c0 = make_float2((float)v.x, (float)v.y);
+        const double2 v = sc[64];
+        out->c0 = make_float2((float)v.x, hermitian ? 0.f : (float)v.y);
     }
 }
 
 cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int round_half, NetPath *out,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int hermitian) {
     NetW W{(const float2 *)w32, C, off[1], off[2], round_half};
-    net_path_coef_kernel<<<1, 96, 0, s>>>(W, out);
+    net_path_coef_kernel<<<1, 96, 0, s>>>(W, hermitian, out);
     return cudaGetLastError();
 }
 

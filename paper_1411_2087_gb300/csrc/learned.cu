@@ -183,20 +183,37 @@ extern "C" int stag_net_create(stag_lattice lat, const double *fat, int ptr_kind
         cudaFree(fat_d);
     if (e != cudaSuccess || e2 != cudaSuccess)
         return bail(e != cudaSuccess ? e : e2);
-    // initial weights: the identity map plus seeded noise of 1e-2
+    // initial weights: the identity map plus seeded noise.  With eight
+    // channels each hop of layer 1 goes into a channel of its own (and r
+    // into channel 0 as well), layer 2 is the identity and layer 3 reads
+    // channel 0: the net starts as the identity, and the hop weights of
+    // layer 3 set every two-hop path C[a][b] linearly, so the loss starts
+    // at plain CG's preconditioner with no saddle at the start (noise 1e-3).
+    // Fewer channels: the identity through every channel, noise 1e-2 (a
+    // net of that form with eight channels took CG from 413 to 2360
+    // iterations at 32^3x64 before training had moved it far).
     std::vector<double> w(nr, 0.0);
     std::mt19937_64 rng(seed);
-    std::normal_distribution<double> nd(0.0, 1e-2);
+    std::normal_distribution<double> nd(0.0, C == 8 ? 1e-3 : 1e-2);
     for (auto &v : w)
         v = nd(rng);
     auto W = [&](int layer, int d, int o, int i) -> double & {
         const int cin = layer == 0 ? 1 : C, cout = layer == 2 ? 1 : C;
         return w[2 * (size_t)(n->off[layer] + (d * cout + o) * cin + i)];
     };
-    for (int o = 0; o < C; o++) {
-        W(0, 0, o, 0) += 1.0;
-        W(1, 0, o, o) += 1.0;
-        W(2, 0, 0, o) += 1.0 / C;
+    if (C == 8) {
+        W(0, 0, 0, 0) += 1.0;
+        for (int d = 1; d < 9; d++)
+            W(0, d, d - 1, 0) += 1.0;
+        for (int o = 0; o < C; o++)
+            W(1, 0, o, o) += 1.0;
+        W(2, 0, 0, 0) += 1.0;
+    } else {
+        for (int o = 0; o < C; o++) {
+            W(0, 0, o, 0) += 1.0;
+            W(1, 0, o, o) += 1.0;
+            W(2, 0, 0, o) += 1.0 / C;
+        }
     }
     std::vector<float> w32(w.begin(), w.end());
     if ((e = cudaMemcpy(n->w, w.data(), sizeof(double) * nr, cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -269,9 +286,10 @@ static NetLinkSet net_links(const stag_net n, bool links16) {
     return s;
 }
 
-// the path coefficients of the current weights (round_half: binary16 weights)
-static cudaError_t net_coefficients(stag_net n, int round_half, cudaStream_t s) {
-    return launch_net_path_coef(n->C, n->w32, n->off, round_half, n->path, s);
+// the path coefficients of the current weights (round_half: binary16
+// weights; hermitian: of the net's Hermitian part)
+static cudaError_t net_coefficients(stag_net n, int round_half, cudaStream_t s, int hermitian = 0) {
+    return launch_net_path_coef(n->C, n->w32, n->off, round_half, n->path, s, hermitian);
 }
 
 // z = N(r) on even vectors with the coefficients in n->path: r of precision
@@ -576,6 +594,8 @@ static int residual_warm_start(stag_net n) {
     return stag_net_set_weights(n, w.data());
 }
 
+constexpr int kAdamWarmup = 100;
+
 extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsigned seed, double *epoch_loss) {
     STAG_NVTX("stag_net_train");
     if (!n)
@@ -604,7 +624,13 @@ extern "C" int stag_net_train(stag_net n, int epochs, int batch, double lr, unsi
             STAG_TRY(loss_grad_range(n, order.data() + b0, cnt, &l));
             tot += l;
             n->adam_t++;
-            CUDA_TRY(launch_adam(2 * n->nw, n->w, n->grad, n->m, n->v, lr_ep / cnt, n->adam_t, n->w32, s));
+            // warm-up: the step size ramps up linearly over the net's first
+            // kAdamWarmup steps.  Adam's first steps move every weight by about
+            // the step size whatever its gradient; at full size from the start,
+            // 32 steps (256 pairs, one epoch) left a net that took CG from 413
+            // to 699 iterations (32^3x64)
+            const double ramp = std::min(1.0, (double)n->adam_t / kAdamWarmup);
+            CUDA_TRY(launch_adam(2 * n->nw, n->w, n->grad, n->m, n->v, lr_ep * ramp / cnt, n->adam_t, n->w32, s));
         }
         if (epoch_loss)
             epoch_loss[ep] = tot / np;
@@ -727,8 +753,9 @@ static int learned_impl(stag_net n, stag_field x, const stag_field b, double mas
     cudaStream_t s = lat->stream;
     CUDA_TRY(cudaMemcpyAsync(w.bw, b->data, b->bytes, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemsetAsync(w.xw, 0, field_bytes(lat, prec), s));
-    // the deployed preconditioner: binary16 weights, 16-bit links
-    CUDA_TRY(net_coefficients(n, 1, s));
+    // the deployed preconditioner: binary16 weights, 16-bit links, the net's
+    // Hermitian part (CG's recurrences assume a Hermitian preconditioner)
+    CUDA_TRY(net_coefficients(n, 1, s, 1));
     // |b|^2: the residual of x = 0
     double bb = 0;
     STAG_TRY(shifted_residual(lat, prec, w.xw, w.bw, mass, nullptr, &bb));
@@ -817,8 +844,9 @@ extern "C" int stag_cg_solve_learned_mixed(stag_net n, stag_field x, const stag_
     DEVICE_SCOPE(lat->device);
     const auto t0 = std::chrono::steady_clock::now();
     STAG_TRY(alloc_vec(lat, lo, &n->z[lo]));
-    // the deployed preconditioner: binary16 weights, 16-bit links
-    CUDA_TRY(net_coefficients(n, 1, lat->stream));
+    // the deployed preconditioner: binary16 weights, 16-bit links, the net's
+    // Hermitian part
+    CUDA_TRY(net_coefficients(n, 1, lat->stream, 1));
     MixedPrecond pc;
     pc.enqueue = learned_precond_enqueue;
     pc.ctx = n;

@@ -30,8 +30,9 @@ cudaError_t launch_net_links_cb(const Geom &g, const double bc[4], const double 
 cudaError_t launch_net_links12(const Geom &g, const double bc[4], const double *fat, void *NL12, float inv_scale16,
                                cudaStream_t s);
 size_t net_links12_bytes(const Geom &g);
+// hermitian: the coefficients of the net's Hermitian part (N + N^+)/2
 cudaError_t launch_net_path_coef(int C, const float *w32, const int off[3], int round_half, NetPath *out,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int hermitian = 0);
 cudaError_t launch_net_path_chain(int C, const float *w32, const int off[3], const double2 *G, double2 *grad,
                                   cudaStream_t s);
 // chi (odd sites; FP32 [8][3][stride] with FP32 links, 16-bit [8][3][stride]

@@ -216,9 +216,10 @@ def test_training_lowers_loss_and_net_cuts_iterations():
     res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, x)) / np.linalg.norm(b)
     assert learned["return"] == stag.OK, learned
     assert res <= 1.05e-10, res
-    # a local degree-one (in the hopping term) preconditioner can at best
-    # halve the condition number: about 1.4x fewer iterations
-    assert learned["iters"] <= 0.8 * plain["iters"], (learned, plain)
+    # a degree-one polynomial in M can at best quarter the condition number
+    # (up to 2x fewer iterations); on the phased links the trained net gets
+    # about 1.8x here, beyond the 1.42x of the same net on raw links
+    assert learned["iters"] <= 0.7 * plain["iters"], (learned, plain)
     assert learned["restarts"] == 0
     for inner, (plain_m, learned_m, xm) in mixed.items():
         res = np.linalg.norm(b - oracle.apply_M(dims, U, N, mass, xm)) / np.linalg.norm(b)
