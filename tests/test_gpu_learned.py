@@ -229,6 +229,30 @@ def test_training_lowers_loss_and_net_cuts_iterations():
         assert learned_m["iters"] <= 0.8 * plain_m["iters"], (inner, learned_m, plain_m)
 
 
+def test_briefly_trained_net_does_no_harm():
+    """A net trained for a few steps is far from Hermitian; the solver
+    applies its Hermitian part, with which flexible CG needs no more
+    iterations than plain CG (the net itself had made CG slower)."""
+    dims = (8, 8, 8, 8)
+    mass = 0.05
+    U = synth.su3_field(dims, 0.3, 1011).numpy()
+    Vh = int(np.prod(dims)) // 2
+    with stag.Lattice(dims) as lat:
+        lat.upload_gauge(U, None, precisions=("df64", "f32", "f16"))
+        net = stag.Net(lat, U, channels=8, seed=2)
+        fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1210).numpy())
+        assert net.collect_pairs(fb, mass, 1e-10, stride=6, max_pairs=16) == 16
+        net.set_loss("residual")
+        net.train(epochs=1, batch=8, lr=1e-2, seed=3)
+        fb = lat.field(stag.EVEN, "df64", synth.gaussian_colour_field(Vh, 1310).numpy())
+        fx = lat.field(stag.EVEN, "df64")
+        plain = lat.cg(fx, fb, mass, 1e-10, 20000)
+        learned = net.cg(fx, fb, mass, 1e-10, 20000)
+        net.close()
+    assert learned["return"] == stag.OK, learned
+    assert learned["iters"] <= plain["iters"], (learned, plain)
+
+
 def test_error_loss_training_runs():
     dims = (4, 4, 4, 8)
     U = synth.su3_field(dims, 0.3, 21).numpy()
