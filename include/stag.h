@@ -429,10 +429,11 @@ int stag_net_get_weights(const stag_net n, double *w);
 
 /* out = N(in) on distinct even fields of one precision (F64, DF64 or F32)
  * of the net's lattice.  flags: 0, or an OR of STAG_NET_FP16_WEIGHTS (round
- * the weights to binary16 first) and STAG_NET_LINKS16 (read the 16-bit link
- * copy), which together are the form the learned solver applies; other bits
- * give STAG_ERR_ARG.  Asynchronous. */
-enum { STAG_NET_FP16_WEIGHTS = 1, STAG_NET_LINKS16 = 2 };
+ * the weights to binary16 first), STAG_NET_LINKS16 (read the 16-bit link
+ * copy) and STAG_NET_HERMITIAN (apply the Hermitian part (N + N^+)/2
+ * instead); the three together are the form the learned solvers apply.
+ * Other bits give STAG_ERR_ARG.  Asynchronous. */
+enum { STAG_NET_FP16_WEIGHTS = 1, STAG_NET_LINKS16 = 2, STAG_NET_HERMITIAN = 4 };
 int stag_net_apply(stag_net n, stag_field out_even, const stag_field in_even, int flags);
 
 /* Training pairs from the plain CG: solve M x* = b to rel_tol, then rerun

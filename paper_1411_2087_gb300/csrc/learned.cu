@@ -323,12 +323,12 @@ extern "C" int stag_net_apply(stag_net n, stag_field out_even, const stag_field 
         return fail(STAG_ERR_ARG, "stag_net_apply: precision mismatch");
     if (out_even == in_even)
         return fail(STAG_ERR_ARG, "stag_net_apply: in and out must differ");
-    if (flags & ~(STAG_NET_FP16_WEIGHTS | STAG_NET_LINKS16))
+    if (flags & ~(STAG_NET_FP16_WEIGHTS | STAG_NET_LINKS16 | STAG_NET_HERMITIAN))
         return fail(STAG_ERR_ARG, "stag_net_apply: unknown flags 0x%x", flags);
     DEVICE_SCOPE(n->lat->device);
     cudaStream_t s = n->lat->stream;
     const int S = n->lat->geom.stride;
-    CUDA_TRY(net_coefficients(n, (flags & STAG_NET_FP16_WEIGHTS) ? 1 : 0, s));
+    CUDA_TRY(net_coefficients(n, (flags & STAG_NET_FP16_WEIGHTS) ? 1 : 0, s, (flags & STAG_NET_HERMITIAN) ? 1 : 0));
     CUDA_TRY(net_apply_path(n, in_even->prec, in_even->data, S, out_even->data, S, (flags & STAG_NET_LINKS16) != 0,
                             false, nullptr, nullptr, s));
     return STAG_OK;

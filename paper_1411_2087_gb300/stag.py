@@ -36,7 +36,7 @@ PREC = {"f64": F64, "f32": F32, "f16": F16, "df64": DF64}
 COMPRESS12 = 1 << 16
 COMPRESS12_LONG = 1 << 17
 EVEN, ODD = 0, 1
-NET_FP16_WEIGHTS, NET_LINKS16 = 1, 2
+NET_FP16_WEIGHTS, NET_LINKS16, NET_HERMITIAN = 1, 2, 4
 CG_LAUNCH_GRAPH, CG_LAUNCH_HOST = 0, 1
 PTR_HOST, PTR_DEVICE = 0, 1
 
@@ -722,9 +722,12 @@ class Net:
         """'error' (|N r - e|^2/|e|^2) or 'residual' (|M N r - r|^2/|r|^2)."""
         _check(lib().stag_net_set_loss(self.handle, {"error": 0, "residual": 1}[kind]))
 
-    def apply(self, out: Field, inp: Field, fp16_weights: bool = False, links16: bool = False):
-        """out = N(inp); fp16_weights and links16 together are the solver's form."""
-        flags = (NET_FP16_WEIGHTS if fp16_weights else 0) | (NET_LINKS16 if links16 else 0)
+    def apply(self, out: Field, inp: Field, fp16_weights: bool = False, links16: bool = False,
+              hermitian: bool = False):
+        """out = N(inp), or its Hermitian part (N + N^+)/2; all three flags
+        together are the solvers' form."""
+        flags = ((NET_FP16_WEIGHTS if fp16_weights else 0) | (NET_LINKS16 if links16 else 0)
+                 | (NET_HERMITIAN if hermitian else 0))
         _check(lib().stag_net_apply(self.handle, out.handle, inp.handle, flags))
 
     def collect_pairs(self, b: Field, mass: float, tol: float = 1e-10, stride: int = 10,

@@ -92,6 +92,53 @@ def test_solver_form_links(dims, bc, unitary):
         net.close()
 
 
+def adjoint_net(Ws):
+    """Layers of N^+: reversed order, each W^+[dbar][i][o] = conj(W[d][o][i])
+    with dbar the reversed hop (d = 1 + 2 mu <-> 2 + 2 mu)."""
+    out = []
+    for W in reversed(Ws):
+        A = np.conj(np.transpose(W, (0, 2, 1))).copy()
+        B = A.copy()
+        for mu in range(4):
+            B[1 + 2 * mu] = A[2 + 2 * mu]
+            B[2 + 2 * mu] = A[1 + 2 * mu]
+        out.append(B)
+    return out
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 8), (6, 4, 2, 4)])
+def test_hermitian_part_matches_oracle(dims):
+    """The solvers' preconditioner (N + N^+)/2, formed on the GPU from the
+    path coefficients, against the oracle's net and its adjoint net (layers
+    reversed and adjointed) on the phased links."""
+    U = synth.su3_field(dims, 0.4, 18).numpy()
+    Vh = int(np.prod(dims)) // 2
+    r = synth.gaussian_colour_field(Vh, 19).numpy()
+    Ws = rand_weights(8, 20)
+    Up = oracle.phased_links(dims, U)
+    want = 0.5 * (oracle.net_apply(dims, Up, Ws, r) + oracle.net_apply(dims, Up, adjoint_net(Ws), r))
+    # the adjoint net really is the adjoint: <s, N r> = <N^+ s, r>
+    sv = synth.gaussian_colour_field(Vh, 21).numpy()
+    lhs = np.vdot(sv, oracle.net_apply(dims, Up, Ws, r))
+    rhs = np.vdot(oracle.net_apply(dims, Up, adjoint_net(Ws), sv), r)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    with stag.Lattice(dims) as lat:
+        net = stag.Net(lat, U, channels=8)
+        net.set_weights(Ws)
+        for prec in ("f32", "df64"):
+            fin = lat.field(stag.EVEN, prec, r)
+            fout = lat.field(stag.EVEN, prec)
+            net.apply(fout, fin, hermitian=True)
+            err = np.abs(fout.export() - want).max() / np.abs(want).max()
+            assert err < 1e-5, (prec, err)
+        fin = lat.field(stag.EVEN, "f32", r)
+        fout = lat.field(stag.EVEN, "f32")
+        net.apply(fout, fin, fp16_weights=True, links16=True, hermitian=True)
+        err = np.abs(fout.export() - want).max() / np.abs(want).max()
+        assert err < 5e-3, err
+        net.close()
+
+
 def test_gpu_net_is_gauge_covariant():
     dims = (4, 4, 4, 6)
     Vh = int(np.prod(dims)) // 2
