@@ -258,3 +258,35 @@ def test_phased_links_let_the_net_precondition_further():
         iters[name] = cg(b, lambda r: oracle.net_apply(dims, L, W, r))[0]
     assert 0 < iters["phased"] < iters["raw"] < plain
     assert plain / iters["phased"] >= 1.15 * plain / iters["raw"], (plain, iters)
+
+
+@pytest.mark.parametrize("mistake", ["own_coordinate", "later_coordinates", "t_only", "y_coordinate_missing"])
+def test_phased_link_pin_catches_plausible_mistakes(mistake):
+    """Phase conventions a reader could plausibly write instead: each, used
+    in place of oracle.phased_links, breaks the one-link Dslash equality
+    that pins the helper."""
+    dims, bc = (4, 4, 2, 6), BC
+    V = int(np.prod(dims))
+    U = synth.su3_field(dims, 0.4, 31).numpy()
+    N = oracle.long_links(dims, U)
+    psi = synth.gaussian_colour_field(V, 32).numpy()
+    x = coords(dims)
+    out = U.copy()
+    zero = np.zeros(V, dtype=np.int64)
+    for mu in range(4):
+        if mistake == "own_coordinate":
+            e = sum((x[nu] for nu in range(mu + 1)), zero)
+        elif mistake == "later_coordinates":
+            e = sum((x[nu] for nu in range(mu + 1, 4)), zero)
+        elif mistake == "t_only":
+            e = sum((x[nu] for nu in range(mu)), zero) if mu == 3 else zero
+        else:
+            e = sum((x[nu] for nu in range(mu) if nu != 1), zero)
+        out[mu] = U[mu] * np.where(e % 2 == 1, -1.0, 1.0)[:, None, None]
+    W = np.zeros((9, 1, 1), complex)
+    for mu in range(4):
+        W[1 + 2 * mu] = 1.0
+        W[2 + 2 * mu] = -1.0
+    got = oracle.covconv(dims, out, W, psi[None], bc)[0]
+    want = oracle.dslash_full(dims, U, N, psi, bc, c1=1.0, c3=0.0)
+    assert np.abs(got - want).max() > 1e-3 * np.abs(want).max()
